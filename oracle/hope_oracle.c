@@ -1,0 +1,1115 @@
+/*
+ * hope_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain, slow, obviously-correct FP64 CPU reference ("oracle") of the HOPE
+ * cubed-sphere shallow-water core (arXiv 2411.19185): geometry (section 2),
+ * TPP reconstruction (section 3.1), genuine-2D WENO-Z (section 3.2), ghost-cell
+ * interpolation (section 3.3.1 and the appendix), panel conversion (section
+ * 3.3.2), the LMARS flux (section 3.4), Gauss quadrature (eqs. 3.5-3.6), the
+ * finite-volume tendency (eq. 3.1) and Runge-Kutta stepping (section 3.5).
+ *
+ * Only the tests, the package smoke check and the CPU-baseline leg of the
+ * benchmark may load it.  No code is shared with the CUDA library.
+ *
+ * Small setup solves (1-D cell-average systems, the WENO least-squares normal
+ * equations) run in long double; everything on the data path is double.
+ * Loops over cells carry OpenMP pragmas; every iteration writes only its own
+ * outputs, so results do not depend on the thread count.
+ *
+ * Readings of passages that are garbled or silent in the paper are marked
+ * "reading:" at the point of use.
+ */
+#include "hope_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define PI_L 3.141592653589793238462643383279502884L
+#define QPI (M_PI / 4.0)
+#define MAXK 15
+
+/* ------------------------------------------------------------------------- */
+/* small dense long-double solve with partial pivoting: A (n x n, row major)  */
+/* is overwritten, b receives the solution.                                   */
+/* ------------------------------------------------------------------------- */
+static void solve_ld(int n, long double *A, long double *b) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabsl(A[r * n + c]) > fabsl(A[piv * n + c])) piv = r;
+    if (piv != c) {
+      for (int j = 0; j < n; ++j) {
+        long double t = A[c * n + j];
+        A[c * n + j] = A[piv * n + j];
+        A[piv * n + j] = t;
+      }
+      long double t = b[c];
+      b[c] = b[piv];
+      b[piv] = t;
+    }
+    for (int r = c + 1; r < n; ++r) {
+      long double f = A[r * n + c] / A[c * n + c];
+      if (f == 0.0L) continue;
+      for (int j = c; j < n; ++j) A[r * n + j] -= f * A[c * n + j];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    long double s = b[r];
+    for (int j = r + 1; j < n; ++j) s -= A[r * n + j] * b[j];
+    b[r] = s / A[r * n + r];
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Gauss-Legendre rule on [-1/2, 1/2] (weights sum to 1), used for the edge   */
+/* averages (eq. 3.5) and the cell averages (eq. 3.6).  Newton iteration on   */
+/* the Legendre polynomial P_m from the standard cosine initial guess.        */
+/* ------------------------------------------------------------------------- */
+void orc_gauss(int m, double *x, double *w) {
+  for (int i = 0; i < m; ++i) {
+    long double z = cosl(PI_L * (i + 0.75L) / (m + 0.5L));
+    long double dp = 0.0L;
+    for (int it = 0; it < 100; ++it) {
+      long double p0 = 1.0L, p1 = z;
+      for (int n = 2; n <= m; ++n) {
+        long double p2 = ((2 * n - 1) * z * p1 - (n - 1) * p0) / n;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (m == 1) { p1 = z; p0 = 1.0L; }
+      /* P_m = p1, P_{m-1} = p0 */
+      dp = m * (z * p1 - p0) / (z * z - 1.0L);
+      long double dz = p1 / dp;
+      z -= dz;
+      if (fabsl(dz) < 1e-30L) break;
+    }
+    {
+      long double p0 = 1.0L, p1 = z;
+      for (int n = 2; n <= m; ++n) {
+        long double p2 = ((2 * n - 1) * z * p1 - (n - 1) * p0) / n;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (m == 1) { p1 = z; p0 = 1.0L; }
+      dp = m * (z * p1 - p0) / (z * z - 1.0L);
+    }
+    /* ascending order on [-1/2, 1/2] */
+    x[m - 1 - i] = (double)(0.5L * z);
+    w[m - 1 - i] = (double)(1.0L / ((1.0L - z * z) * dp * dp));
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* 1-D cell-average reconstruction weights (1-D slice of eqs. 3.7-3.15):      */
+/* the stencil is n unit cells centred at offsets o0, o0+1, ..., o0+n-1 from  */
+/* the target cell; the polynomial has monomials xi^a, a = 0..n-1 (reading    */
+/* of eq. 3.7: exponents start at 0, origin at the target-cell centre);       */
+/* out[j] is the weight of cell j in the value at xi:  r = A^{-T} c(xi).      */
+/* Monomials are scaled by s = max|offset|+1/2 for conditioning only.         */
+/* ------------------------------------------------------------------------- */
+static void weights_1d_ld(int n, int o0, long double xi, long double *out) {
+  long double A[MAXK * MAXK], b[MAXK];
+  long double s = 0.5L;
+  for (int j = 0; j < n; ++j) {
+    long double a = fabsl((long double)(o0 + j)) + 0.5L;
+    if (a > s) s = a;
+  }
+  /* M[a][j] = integral over cell j of (x/s)^a dx  (transpose of eq. 3.11's A) */
+  for (int j = 0; j < n; ++j) {
+    long double lo = ((long double)(o0 + j) - 0.5L) / s;
+    long double hi = ((long double)(o0 + j) + 0.5L) / s;
+    long double plo = lo, phi = hi;
+    for (int a = 0; a < n; ++a) {
+      A[a * n + j] = s * (phi - plo) / (long double)(a + 1);
+      plo *= lo;
+      phi *= hi;
+    }
+  }
+  long double c = 1.0L;
+  for (int a = 0; a < n; ++a) {
+    b[a] = c;
+    c *= xi / s;
+  }
+  solve_ld(n, A, b);
+  for (int j = 0; j < n; ++j) out[j] = b[j];
+}
+
+void orc_weights_1d(int n, int o0, double xi, double *out) {
+  long double t[MAXK];
+  weights_1d_ld(n, o0, (long double)xi, t);
+  for (int j = 0; j < n; ++j) out[j] = (double)t[j];
+}
+
+/* TPP weights of a central k x k stencil at (xi, eta): R = r_x (x) r_y, the   */
+/* tensor-product form of R = C A^{-1} (eq. 3.15) for the tensor-product      */
+/* basis of eq. 3.7.  Layout out[b*k + a]: a = x offset + H, b = y offset + H. */
+void orc_tpp_weights_2d(int k, double xi, double eta, double *out) {
+  int H = (k - 1) / 2;
+  long double rx[MAXK], ry[MAXK];
+  weights_1d_ld(k, -H, xi, rx);
+  weights_1d_ld(k, -H, eta, ry);
+  for (int b = 0; b < k; ++b)
+    for (int a = 0; a < k; ++a) out[b * k + a] = (double)(rx[a] * ry[b]);
+}
+
+/* The same weights by the literal 2-D route of eqs. 3.7-3.15: assemble the    */
+/* k^2 x k^2 cell-average matrix A of the monomials x^a y^b and solve          */
+/* A^T r = c(xi, eta).  Only for small k (used to pin the tensor form).       */
+void orc_tpp_weights_2d_literal(int k, double xi, double eta, double *out) {
+  int H = (k - 1) / 2, n = k * k;
+  long double *A = (long double *)malloc(sizeof(long double) * n * n);
+  long double *b = (long double *)malloc(sizeof(long double) * n);
+  long double s = H + 0.5L;
+  for (int cb = 0; cb < k; ++cb)
+    for (int ca = 0; ca < k; ++ca) {
+      int cell = cb * k + ca; /* cell offsets (ca-H, cb-H) */
+      for (int eb = 0; eb < k; ++eb)
+        for (int ea = 0; ea < k; ++ea) {
+          int term = eb * k + ea; /* monomial (x/s)^ea (y/s)^eb */
+          long double xl = (ca - H - 0.5L) / s, xh = (ca - H + 0.5L) / s;
+          long double yl = (cb - H - 0.5L) / s, yh = (cb - H + 0.5L) / s;
+          long double ix = s * (powl(xh, ea + 1) - powl(xl, ea + 1)) / (ea + 1);
+          long double iy = s * (powl(yh, eb + 1) - powl(yl, eb + 1)) / (eb + 1);
+          A[term * n + cell] = ix * iy;
+        }
+    }
+  for (int eb = 0; eb < k; ++eb)
+    for (int ea = 0; ea < k; ++ea)
+      b[eb * k + ea] = powl((long double)xi / s, ea) * powl((long double)eta / s, eb);
+  solve_ld(n, A, b);
+  for (int i = 0; i < n; ++i) out[i] = (double)b[i];
+  free(A);
+  free(b);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Genuine-2D WENO building blocks (section 3.2).                              */
+/* Sub-stencil (sx, sy), sx, sy = 0..l-1, covers the l x l cells with offsets  */
+/* [sx-H, sx-H+l-1] x [sy-H, sy-H+l-1]; it is sub-stencil number sy*l + sx.    */
+/* ------------------------------------------------------------------------- */
+static void sub_weights_2d(int k, int sx, int sy, long double xi, long double eta, long double *out) {
+  int H = (k - 1) / 2, l = (k + 1) / 2;
+  long double rx[MAXK], ry[MAXK];
+  weights_1d_ld(l, sx - H, xi, rx);
+  weights_1d_ld(l, sy - H, eta, ry);
+  for (int b = 0; b < l; ++b)
+    for (int a = 0; a < l; ++a) out[b * l + a] = rx[a] * ry[b];
+}
+
+/* Optimal linear weights gamma at (xi, eta) by the least-squares procedure of */
+/* eqs. 3.16-3.19: R_L gamma = R_H with R_L's columns the sub-stencil weights  */
+/* extended into the k x k stencil (matrix E), solved through the normal       */
+/* equations in long double.  Returns s; resid = max |R_L gamma - R_H|.        */
+int orc_weno_gamma(int k, double xi, double eta, double *gam, double *resid) {
+  int H = (k - 1) / 2, l = (k + 1) / 2, s = l * l, m = k * k;
+  long double *RL = (long double *)calloc((size_t)m * s, sizeof(long double));
+  long double RH[MAXK * MAXK], sub[MAXK * MAXK];
+  long double rx[MAXK], ry[MAXK];
+  weights_1d_ld(k, -H, xi, rx);
+  weights_1d_ld(k, -H, eta, ry);
+  for (int b = 0; b < k; ++b)
+    for (int a = 0; a < k; ++a) RH[b * k + a] = rx[a] * ry[b];
+  for (int sy = 0; sy < l; ++sy)
+    for (int sx = 0; sx < l; ++sx) {
+      int i = sy * l + sx;
+      sub_weights_2d(k, sx, sy, xi, eta, sub);
+      for (int b = 0; b < l; ++b)
+        for (int a = 0; a < l; ++a) /* extension: sub-stencil cell -> big-stencil cell */
+          RL[(size_t)((sy + b) * k + (sx + a)) * s + i] = sub[b * l + a];
+    }
+  long double *NE = (long double *)calloc((size_t)s * s, sizeof(long double));
+  long double rhs[MAXK * MAXK];
+  for (int i = 0; i < s; ++i) {
+    long double t = 0.0L;
+    for (int r = 0; r < m; ++r) t += RL[(size_t)r * s + i] * RH[r];
+    rhs[i] = t;
+    for (int j = 0; j < s; ++j) {
+      long double u = 0.0L;
+      for (int r = 0; r < m; ++r) u += RL[(size_t)r * s + i] * RL[(size_t)r * s + j];
+      NE[i * s + j] = u;
+    }
+  }
+  solve_ld(s, NE, rhs);
+  long double mx = 0.0L;
+  for (int r = 0; r < m; ++r) {
+    long double t = -RH[r];
+    for (int i = 0; i < s; ++i) t += RL[(size_t)r * s + i] * rhs[i];
+    if (fabsl(t) > mx) mx = fabsl(t);
+  }
+  for (int i = 0; i < s; ++i) gam[i] = (double)rhs[i];
+  if (resid) *resid = (double)mx;
+  free(RL);
+  free(NE);
+  return s;
+}
+
+/* Monomial coefficients of a sub-stencil's 1-D polynomial: C[a][j] such that  */
+/* p(xi) = sum_a (sum_j C[a][j] qbar_j) xi^a (no scaling).                     */
+static void coeffs_1d(int l, int o0, long double *C) {
+  long double A[MAXK * MAXK], e[MAXK];
+  for (int j = 0; j < l; ++j) {
+    for (int r = 0; r < l; ++r) {
+      long double lo = (long double)(o0 + r) - 0.5L, hi = (long double)(o0 + r) + 0.5L;
+      for (int a = 0; a < l; ++a) A[r * l + a] = (powl(hi, a + 1) - powl(lo, a + 1)) / (a + 1);
+    }
+    for (int r = 0; r < l; ++r) e[r] = (r == j) ? 1.0L : 0.0L;
+    solve_ld(l, A, e); /* column j of A^{-1} */
+    for (int a = 0; a < l; ++a) C[a * l + j] = e[a];
+  }
+}
+
+/* d^al/dx^al of x^a at x */
+static long double dmono(int a, int al, long double x) {
+  if (al > a) return 0.0L;
+  long double c = 1.0L;
+  for (int t = 0; t < al; ++t) c *= (long double)(a - t);
+  return c * powl(x, a - al);
+}
+
+/* Smoothness indicator of one sub-stencil on the target cell [-1/2,1/2]^2.    */
+/* reading (eq. 3.25 is garbled): beta = sum over (al1, al2) != (0,0),         */
+/* al1, al2 <= l-1, of the integral of the SQUARED mixed derivative            */
+/* d^(al1+al2) p / dx^al1 dy^al2 over the unit target cell (no length weights, */
+/* the cell is a unit square).  The integral is taken with an l x l            */
+/* Gauss-Legendre rule, exact for these degree-2(l-1) integrands.              */
+/* Qsub[b*l + a] holds the sub-stencil cell averages, first cell at offset     */
+/* (o0x, o0y).                                                                 */
+double orc_weno_beta(int l, int o0x, int o0y, const double *Qsub) {
+  long double Cx[MAXK * MAXK], Cy[MAXK * MAXK], c2[MAXK * MAXK];
+  coeffs_1d(l, o0x, Cx);
+  coeffs_1d(l, o0y, Cy);
+  for (int eb = 0; eb < l; ++eb)
+    for (int ea = 0; ea < l; ++ea) {
+      long double t = 0.0L;
+      for (int b = 0; b < l; ++b)
+        for (int a = 0; a < l; ++a) t += Cx[ea * l + a] * Cy[eb * l + b] * Qsub[b * l + a];
+      c2[eb * l + ea] = t;
+    }
+  double gx[MAXK], gw[MAXK];
+  orc_gauss(l, gx, gw);
+  long double beta = 0.0L;
+  for (int a2 = 0; a2 < l; ++a2)
+    for (int a1 = 0; a1 < l; ++a1) {
+      if (a1 == 0 && a2 == 0) continue;
+      for (int qy = 0; qy < l; ++qy)
+        for (int qx = 0; qx < l; ++qx) {
+          long double v = 0.0L;
+          for (int eb = 0; eb < l; ++eb)
+            for (int ea = 0; ea < l; ++ea)
+              v += c2[eb * l + ea] * dmono(ea, a1, gx[qx]) * dmono(eb, a2, gx[qy]);
+          beta += (long double)gw[qx] * gw[qy] * v * v;
+        }
+    }
+  return (double)beta;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Geometry (section 2): gnomonic equiangular cube, unit sphere.               */
+/* Panel p (0-based, paper's panel p+1) maps (X, Y) = (tan x, tan y) to        */
+/* (n_p + X e1_p + Y e2_p)/delta.  Panels 1-4 are centred on the equator at    */
+/* longitude (p-1)*pi/2 with X = tan(lambda - lambda_c) and                    */
+/* Y = tan(theta)/cos(lambda - lambda_c); panel 5 (north) has                  */
+/* X = sin(lambda)/tan(theta), Y = -cos(lambda)/tan(theta); panel 6 (south)    */
+/* X = -sin(lambda)/tan(theta), Y = -cos(lambda)/tan(theta): the forms for     */
+/* which the paper's J (eqs. 2.10-2.11) and sin(theta) (eq. 2.5) hold.         */
+/* ------------------------------------------------------------------------- */
+static const double FR_N[6][3] = {{1, 0, 0}, {0, 1, 0}, {-1, 0, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+static const double FR_E1[6][3] = {{0, 1, 0}, {-1, 0, 0}, {0, -1, 0}, {1, 0, 0}, {0, 1, 0}, {0, 1, 0}};
+static const double FR_E2[6][3] = {{0, 0, 1}, {0, 0, 1}, {0, 0, 1}, {0, 0, 1}, {-1, 0, 0}, {1, 0, 0}};
+
+void orc_xyz(int p, double X, double Y, double *xyz) {
+  double d = sqrt(1.0 + X * X + Y * Y);
+  for (int c = 0; c < 3; ++c) xyz[c] = (FR_N[p][c] + X * FR_E1[p][c] + Y * FR_E2[p][c]) / d;
+}
+
+/* Panel owning a point: largest projection on the panel normal; a tie (point */
+/* on a cube edge, up to 1e-12) goes to the lower panel number (reading c11).  */
+static int owner_panel(const double *xyz, int exclude) {
+  int best = -1;
+  double bv = -2.0;
+  for (int p = 0; p < 6; ++p) {
+    if (p == exclude) continue;
+    double d = xyz[0] * FR_N[p][0] + xyz[1] * FR_N[p][1] + xyz[2] * FR_N[p][2];
+    if (d > bv + 1e-12) { bv = d; best = p; }
+  }
+  return best;
+}
+
+static void to_panel(int p, const double *xyz, double *XY) {
+  double t = xyz[0] * FR_N[p][0] + xyz[1] * FR_N[p][1] + xyz[2] * FR_N[p][2];
+  XY[0] = (xyz[0] * FR_E1[p][0] + xyz[1] * FR_E1[p][1] + xyz[2] * FR_E1[p][2]) / t;
+  XY[1] = (xyz[0] * FR_E2[p][0] + xyz[1] * FR_E2[p][1] + xyz[2] * FR_E2[p][2]) / t;
+}
+
+int orc_locate(const double *xyz, double *XY) {
+  int p = owner_panel(xyz, -1);
+  to_panel(p, xyz, XY);
+  return p;
+}
+
+/* Metric terms (unit sphere), eqs. 2.6-2.8; reading c5: the denominator of    */
+/* eq. 2.6 is (1+X^2)(1+Y^2).  out7 = sqrtG, G^11, G^12, G^22, G_11, G_12, G_22. */
+void orc_metric(double X, double Y, double *o) {
+  double d2 = 1.0 + X * X + Y * Y, d = sqrt(d2);
+  double ax = 1.0 + X * X, ay = 1.0 + Y * Y;
+  o[0] = ax * ay / (d2 * d);
+  double c = d2 / (ax * ay);
+  o[1] = c * ay;
+  o[2] = c * X * Y;
+  o[3] = c * ax;
+  double cl = ax * ay / (d2 * d2);
+  o[4] = cl * ax;
+  o[5] = -cl * X * Y;
+  o[6] = cl * ay;
+}
+
+static void lonlat(const double *xyz, double *lam, double *th) {
+  *lam = atan2(xyz[1], xyz[0]);
+  *th = atan2(xyz[2], sqrt(xyz[0] * xyz[0] + xyz[1] * xyz[1]));
+}
+
+/* J of eq. 2.10 (r = 1), row major: (u_s, v_s) = r J (u, v). */
+void orc_jacobian(int p, double X, double Y, double *J) {
+  double xyz[3], lam, th;
+  orc_xyz(p, X, Y, xyz);
+  lonlat(xyz, &lam, &th);
+  double ct = cos(th), st = sin(th);
+  if (p < 4) {
+    double lp = lam - 0.5 * M_PI * p; /* eq. 2.11 */
+    J[0] = ct;
+    J[1] = 0.0;
+    J[2] = -st * ct * tan(lp);
+    J[3] = cos(lp) * ct * ct + st * st / cos(lp);
+  } else {
+    double tt = tan(th);
+    double g1 = 1.0 + sin(lam) * sin(lam) / (tt * tt);
+    double g2 = 1.0 + cos(lam) * cos(lam) / (tt * tt);
+    double sgn = (p == 4) ? 1.0 : -1.0;
+    J[0] = sgn * cos(lam) * st * g1;
+    J[1] = sin(lam) * st * g2;
+    J[2] = -sgn * sin(lam) * st * st * g1;
+    J[3] = cos(lam) * st * st * g2;
+  }
+}
+
+/* sin(latitude) by eq. 2.5 */
+static double sin_lat(int p, double X, double Y) {
+  double d = sqrt(1.0 + X * X + Y * Y);
+  if (p < 4) return Y / d;
+  return (p == 4) ? 1.0 / d : -1.0 / d;
+}
+
+static void inv2(const double *A, double *B) {
+  double det = A[0] * A[3] - A[1] * A[2];
+  B[0] = A[3] / det;
+  B[1] = -A[1] / det;
+  B[2] = -A[2] / det;
+  B[3] = A[0] / det;
+}
+static void mul2(const double *A, const double *B, double *C) {
+  C[0] = A[0] * B[0] + A[1] * B[2];
+  C[1] = A[0] * B[1] + A[1] * B[3];
+  C[2] = A[2] * B[0] + A[3] * B[2];
+  C[3] = A[2] * B[1] + A[3] * B[3];
+}
+
+/* Conversion of a field value from panel B at (XB, YB) to panel A at         */
+/* (XA, YA), the same point of the sphere: mass ratio sqrtG_A/sqrtG_B          */
+/* (eq. 3.26) and momentum matrix C = (sqrtG_A/sqrtG_B) J_A^{-1} J_B           */
+/* (eqs. 3.27-3.29).                                                            */
+static void conversion(int A, double XA, double YA, int B, double XB, double YB, double *ratio,
+                       double *C) {
+  double mA[7], mB[7], JA[4], JB[4], JAi[4];
+  orc_metric(XA, YA, mA);
+  orc_metric(XB, YB, mB);
+  *ratio = mA[0] / mB[0];
+  orc_jacobian(A, XA, YA, JA);
+  orc_jacobian(B, XB, YB, JB);
+  inv2(JA, JAi);
+  mul2(JAi, JB, C);
+  for (int i = 0; i < 4; ++i) C[i] *= *ratio;
+}
+
+/* ------------------------------------------------------------------------- */
+/* The oracle object                                                           */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int B, ic, jc;  /* source panel and containing cell */
+  double wx[MAXK], wy[MAXK];
+  double ratio, C[4];
+} gqp_t;
+
+typedef struct {
+  int B, sideB, tB, gB;
+  double ratio, C[4]; /* conversion B -> A at the point */
+} nbr_t;
+
+struct orc {
+  int N, k, H, me, npoc, scheme, l, s, ghost_iters, ne;
+  double r, g, omega, eps, dx;
+  double gx[MAXK], gw[MAXK];
+  double *px, *py; /* [npoc] */
+  double *R;       /* [npoc][k*k] */
+  double *Rsub;    /* [npoc][s][l*l] */
+  double *gp, *gm; /* [npoc][s] */
+  double *sigp, *sigm;
+  int nring;       /* ghost cells per panel */
+  int *ring;       /* [nring] jj*ne + ii */
+  gqp_t *gq;       /* [6][nring][me*me] */
+  nbr_t *nb;       /* [6][4][N][me] */
+};
+
+int orc_npoc(const orc *o) { return o->npoc; }
+int orc_halo(const orc *o) { return o->H; }
+
+static double cell_centre(const orc *o, int i) { return -QPI + (i + 0.5) * o->dx; }
+
+/* side s: 0 west (x=-pi/4), 1 east, 2 south (y=-pi/4), 3 north */
+static void edge_point(const orc *o, int side, int t, int gidx, double *x, double *y) {
+  double along = cell_centre(o, t) + o->gx[gidx] * o->dx;
+  switch (side) {
+    case 0: *x = -QPI; *y = along; break;
+    case 1: *x = QPI; *y = along; break;
+    case 2: *x = along; *y = -QPI; break;
+    default: *x = along; *y = QPI; break;
+  }
+}
+
+orc *orc_new(int N, int k, int scheme, double radius, double gravity, double omega, double weno_eps,
+             int ghost_iters) {
+  if (N < 2 || k < 1 || k > MAXK || (k % 2) == 0) return NULL;
+  orc *o = (orc *)calloc(1, sizeof(orc));
+  o->N = N;
+  o->k = k;
+  o->H = (k - 1) / 2;
+  o->me = (k + 1) / 2;
+  o->npoc = 4 * o->me + o->me * o->me;
+  o->scheme = scheme;
+  o->l = (k + 1) / 2;
+  o->s = o->l * o->l;
+  o->ghost_iters = ghost_iters;
+  o->ne = N + 2 * o->H;
+  o->r = radius;
+  o->g = gravity;
+  o->omega = omega;
+  o->eps = weno_eps;
+  o->dx = M_PI / (2.0 * N);
+  if (2 * o->H >= N) { free(o); return NULL; }
+  orc_gauss(o->me, o->gx, o->gw);
+  int me = o->me, np = o->npoc, kk = k * k;
+  o->px = (double *)malloc(sizeof(double) * np);
+  o->py = (double *)malloc(sizeof(double) * np);
+  for (int r = 0; r < me; ++r) {
+    o->px[r] = -0.5; o->py[r] = o->gx[r];
+    o->px[me + r] = 0.5; o->py[me + r] = o->gx[r];
+    o->px[2 * me + r] = o->gx[r]; o->py[2 * me + r] = -0.5;
+    o->px[3 * me + r] = o->gx[r]; o->py[3 * me + r] = 0.5;
+  }
+  for (int h = 0; h < me; ++h)
+    for (int g = 0; g < me; ++g) {
+      o->px[4 * me + h * me + g] = o->gx[g];
+      o->py[4 * me + h * me + g] = o->gx[h];
+    }
+  o->R = (double *)malloc(sizeof(double) * np * kk);
+  for (int pt = 0; pt < np; ++pt) orc_tpp_weights_2d(k, o->px[pt], o->py[pt], o->R + (size_t)pt * kk);
+
+  if (scheme == ORC_WENO) {
+    int l = o->l, s = o->s;
+    o->Rsub = (double *)malloc(sizeof(double) * np * s * l * l);
+    o->gp = (double *)malloc(sizeof(double) * np * s);
+    o->gm = (double *)malloc(sizeof(double) * np * s);
+    o->sigp = (double *)malloc(sizeof(double) * np);
+    o->sigm = (double *)malloc(sizeof(double) * np);
+    long double sub[MAXK * MAXK];
+    for (int pt = 0; pt < np; ++pt) {
+      for (int sy = 0; sy < l; ++sy)
+        for (int sx = 0; sx < l; ++sx) {
+          sub_weights_2d(k, sx, sy, o->px[pt], o->py[pt], sub);
+          for (int c = 0; c < l * l; ++c)
+            o->Rsub[((size_t)pt * s + sy * l + sx) * l * l + c] = (double)sub[c];
+        }
+      double gam[MAXK * MAXK], res;
+      orc_weno_gamma(k, o->px[pt], o->py[pt], gam, &res);
+      /* eq. 3.20 with theta = 3; reading c2: sigma+- = sum gamma+- */
+      double sp = 0.0, sm = 0.0;
+      for (int i = 0; i < s; ++i) {
+        double gpl = 0.5 * (3.0 * fabs(gam[i]) + gam[i]);
+        double gmi = 0.5 * (3.0 * fabs(gam[i]) - gam[i]);
+        o->gp[(size_t)pt * s + i] = gpl;
+        o->gm[(size_t)pt * s + i] = gmi;
+        sp += gpl;
+        sm += gmi;
+      }
+      o->sigp[pt] = sp;
+      o->sigm[pt] = sm;
+    }
+  }
+
+  /* ghost ring cells */
+  int ne = o->ne, H = o->H;
+  o->nring = ne * ne - N * N;
+  o->ring = (int *)malloc(sizeof(int) * o->nring);
+  {
+    int c = 0;
+    for (int jj = 0; jj < ne; ++jj)
+      for (int ii = 0; ii < ne; ++ii) {
+        int i = ii - H, j = jj - H;
+        if (i >= 0 && i < N && j >= 0 && j < N) continue;
+        o->ring[c++] = jj * ne + ii;
+      }
+  }
+  /* ghost quadrature-point tables (section 3.3.1): each ghost cell's me x me  */
+  /* Gauss points, located on the sphere, assigned to the owning panel, and    */
+  /* given that panel's central k x k TPP stencil around the containing cell.  */
+  o->gq = (gqp_t *)malloc(sizeof(gqp_t) * 6 * o->nring * me * me);
+  for (int p = 0; p < 6; ++p)
+    for (int c = 0; c < o->nring; ++c) {
+      int ii = o->ring[c] % ne, jj = o->ring[c] / ne;
+      int i = ii - H, j = jj - H;
+      for (int h = 0; h < me; ++h)
+        for (int g = 0; g < me; ++g) {
+          gqp_t *q = &o->gq[((size_t)p * o->nring + c) * me * me + h * me + g];
+          double x = cell_centre(o, i) + o->gx[g] * o->dx;
+          double y = cell_centre(o, j) + o->gx[h] * o->dx;
+          double X = tan(x), Y = tan(y), xyz[3], XB[2];
+          orc_xyz(p, X, Y, xyz);
+          int B = owner_panel(xyz, -1);
+          to_panel(B, xyz, XB);
+          double xb = atan(XB[0]), yb = atan(XB[1]);
+          int ic = (int)floor((xb + QPI) / o->dx), jc = (int)floor((yb + QPI) / o->dx);
+          if (ic < 0) ic = 0;
+          if (ic > N - 1) ic = N - 1;
+          if (jc < 0) jc = 0;
+          if (jc > N - 1) jc = N - 1;
+          double xi = (xb - cell_centre(o, ic)) / o->dx, eta = (yb - cell_centre(o, jc)) / o->dx;
+          q->B = B;
+          q->ic = ic;
+          q->jc = jc;
+          orc_weights_1d(k, -H, xi, q->wx);
+          orc_weights_1d(k, -H, eta, q->wy);
+          conversion(p, X, Y, B, XB[0], XB[1], &q->ratio, q->C);
+        }
+    }
+  /* panel-edge neighbours of every edge Gauss point (for reading c10) */
+  o->nb = (nbr_t *)malloc(sizeof(nbr_t) * 6 * 4 * N * me);
+  for (int p = 0; p < 6; ++p)
+    for (int side = 0; side < 4; ++side)
+      for (int t = 0; t < N; ++t)
+        for (int g = 0; g < me; ++g) {
+          nbr_t *nb = &o->nb[((p * 4 + side) * N + t) * me + g];
+          double x, y, xyz[3], XB[2];
+          edge_point(o, side, t, g, &x, &y);
+          double X = tan(x), Y = tan(y);
+          orc_xyz(p, X, Y, xyz);
+          int B = owner_panel(xyz, p);
+          to_panel(B, xyz, XB);
+          double xb = atan(XB[0]), yb = atan(XB[1]);
+          int sB;
+          double along;
+          if (fabs(xb) > fabs(yb)) { sB = xb < 0 ? 0 : 1; along = yb; }
+          else { sB = yb < 0 ? 2 : 3; along = xb; }
+          int tB = (int)floor((along + QPI) / o->dx);
+          if (tB < 0) tB = 0;
+          if (tB > N - 1) tB = N - 1;
+          double eta = (along - cell_centre(o, tB)) / o->dx;
+          int gB = 0;
+          for (int q = 1; q < me; ++q)
+            if (fabs(o->gx[q] - eta) < fabs(o->gx[gB] - eta)) gB = q;
+          nb->B = B;
+          nb->sideB = sB;
+          nb->tB = tB;
+          nb->gB = gB;
+          conversion(p, X, Y, B, XB[0], XB[1], &nb->ratio, nb->C);
+        }
+  return o;
+}
+
+void orc_free(orc *o) {
+  if (!o) return;
+  free(o->px); free(o->py); free(o->R); free(o->Rsub); free(o->gp); free(o->gm);
+  free(o->sigp); free(o->sigm); free(o->ring); free(o->gq); free(o->nb);
+  free(o);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Ghost fill (section 3.3.1, appendix eqs. 7.1-7.12): g^(0) = 0, then         */
+/* ghost_iters Jacobi sweeps; each sweep interpolates every ghost Gauss point  */
+/* with the owning panel's TPP stencil (which reads that panel's current       */
+/* ghosts), converts it to the ghost's panel (eqs. 3.26-3.29, per Gauss point) */
+/* and averages with the 2-D Gauss rule (eq. 3.6).                             */
+/* reading c11: a fixed count of sweeps (the paper sets it to 10).             */
+/* ------------------------------------------------------------------------- */
+void orc_fill_ghosts(orc *o, const double *q, double *ext, double *resid) {
+  int N = o->N, H = o->H, ne = o->ne, me = o->me, k = o->k;
+  size_t pe = (size_t)ne * ne, pi = (size_t)N * N;
+  memset(ext, 0, sizeof(double) * 3 * 6 * pe);
+  for (int v = 0; v < 3; ++v)
+    for (int p = 0; p < 6; ++p)
+      for (int j = 0; j < N; ++j)
+        for (int i = 0; i < N; ++i)
+          ext[(v * 6 + p) * pe + (size_t)(j + H) * ne + (i + H)] = q[(v * 6 + p) * pi + (size_t)j * N + i];
+  double *newg = (double *)malloc(sizeof(double) * 3 * 6 * o->nring);
+  double res[3] = {0, 0, 0};
+  for (int it = 0; it < o->ghost_iters; ++it) {
+#pragma omp parallel for schedule(static)
+    for (int pc = 0; pc < 6 * o->nring; ++pc) {
+      int p = pc / o->nring, c = pc % o->nring;
+      double acc[3] = {0, 0, 0};
+      for (int r = 0; r < me * me; ++r) {
+        const gqp_t *g = &o->gq[(size_t)pc * me * me + r];
+        double wq = o->gw[r % me] * o->gw[r / me];
+        double val[3];
+        for (int v = 0; v < 3; ++v) {
+          const double *src = ext + (v * 6 + g->B) * pe;
+          double s = 0.0;
+          for (int b = 0; b < k; ++b)
+            for (int a = 0; a < k; ++a)
+              s += g->wx[a] * g->wy[b] * src[(size_t)(g->jc + b) * ne + (g->ic + a)];
+          val[v] = s;
+        }
+        acc[0] += wq * g->ratio * val[0];
+        acc[1] += wq * (g->C[0] * val[1] + g->C[1] * val[2]);
+        acc[2] += wq * (g->C[2] * val[1] + g->C[3] * val[2]);
+      }
+      for (int v = 0; v < 3; ++v) newg[(v * 6 + p) * o->nring + c] = acc[v];
+    }
+    for (int v = 0; v < 3; ++v) {
+      double s = 0.0;
+      for (int p = 0; p < 6; ++p)
+        for (int c = 0; c < o->nring; ++c) {
+          double *dst = ext + (v * 6 + p) * pe + o->ring[c];
+          double d = newg[(v * 6 + p) * o->nring + c] - *dst;
+          s += d * d;
+          *dst = newg[(v * 6 + p) * o->nring + c];
+        }
+      res[v] = sqrt(s);
+    }
+  }
+  if (resid)
+    for (int v = 0; v < 3; ++v) resid[v] = res[v];
+  free(newg);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Reconstruction at one point of one cell from its k x k stencil.             */
+/* ------------------------------------------------------------------------- */
+static double tpp_point(const orc *o, const double *st, int pt) {
+  const double *w = o->R + (size_t)pt * o->k * o->k;
+  double s = 0.0;
+  for (int c = 0; c < o->k * o->k; ++c) s += w[c] * st[c];
+  return s;
+}
+
+/* tau of eq. 3.24 (reading c4: the double sum as printed, exponent 1) */
+static double weno_tau(int s, const double *beta) {
+  double t = 0.0;
+  for (int e = 0; e < s - 1; ++e)
+    for (int ps = e; ps < s; ++ps) t += fabs(beta[ps] - beta[e]);
+  return 2.0 / ((s + 1.0) * s) * t;
+}
+
+static void weno_betas(const orc *o, const double *st, double *beta) {
+  int k = o->k, l = o->l, H = o->H;
+  double Qs[MAXK * MAXK];
+  for (int sy = 0; sy < l; ++sy)
+    for (int sx = 0; sx < l; ++sx) {
+      for (int b = 0; b < l; ++b)
+        for (int a = 0; a < l; ++a) Qs[b * l + a] = st[(sy + b) * k + (sx + a)];
+      beta[sy * l + sx] = orc_weno_beta(l, sx - H, sy - H, Qs);
+    }
+}
+
+/* WENO-Z value at one point (eqs. 3.21-3.23) given the cell's betas and tau.  */
+/* reading c2: q = sigma+ sum(w+ p) - sigma- sum(w- p), sigma+- = sum gamma+-. */
+static double weno_value(const orc *o, const double *st, int pt, const double *beta, double tau) {
+  int k = o->k, l = o->l, s = o->s;
+  double ap[MAXK * MAXK], am[MAXK * MAXK], pv[MAXK * MAXK], sap = 0.0, sam = 0.0;
+  for (int sy = 0; sy < l; ++sy)
+    for (int sx = 0; sx < l; ++sx) {
+      int i = sy * l + sx;
+      const double *w = o->Rsub + ((size_t)pt * s + i) * l * l;
+      double v = 0.0;
+      for (int b = 0; b < l; ++b)
+        for (int a = 0; a < l; ++a) v += w[b * l + a] * st[(sy + b) * k + (sx + a)];
+      pv[i] = v;
+      double f = 1.0 + tau / (beta[i] + o->eps);
+      ap[i] = o->gp[(size_t)pt * s + i] / o->sigp[pt] * f;
+      am[i] = o->gm[(size_t)pt * s + i] / o->sigm[pt] * f;
+      sap += ap[i];
+      sam += am[i];
+    }
+  double qp = 0.0, qm = 0.0;
+  for (int i = 0; i < s; ++i) {
+    qp += ap[i] / sap * pv[i];
+    qm += am[i] / sam * pv[i];
+  }
+  return o->sigp[pt] * qp - o->sigm[pt] * qm;
+}
+
+double orc_weno_point(const orc *o, const double *st, int pt) {
+  double beta[MAXK * MAXK];
+  weno_betas(o, st, beta);
+  return weno_value(o, st, pt, beta, weno_tau(o->s, beta));
+}
+
+void orc_reconstruct_all(orc *o, const double *ext, double *pts) {
+  int N = o->N, k = o->k, ne = o->ne, np = o->npoc;
+  size_t pe = (size_t)ne * ne;
+#pragma omp parallel for schedule(static)
+  for (int row = 0; row < 3 * 6 * N; ++row) {
+    int v = row / (6 * N), p = (row / N) % 6, j = row % N;
+    double st[MAXK * MAXK], beta[MAXK * MAXK];
+    const double *src = ext + (v * 6 + p) * pe;
+    for (int i = 0; i < N; ++i) {
+      for (int b = 0; b < k; ++b)
+        for (int a = 0; a < k; ++a) st[b * k + a] = src[(size_t)(j + b) * ne + (i + a)];
+      double *out = pts + ((((size_t)v * 6 + p) * N + j) * N + i) * np;
+      if (o->scheme == ORC_WENO) {
+        weno_betas(o, st, beta);
+        double tau = weno_tau(o->s, beta);
+        for (int pt = 0; pt < np; ++pt) out[pt] = weno_value(o, st, pt, beta, tau);
+      } else {
+        for (int pt = 0; pt < np; ++pt) out[pt] = tpp_point(o, st, pt);
+      }
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* LMARS flux (section 3.4, eqs. 3.30-3.38) at an edge point (X, Y) of one     */
+/* panel; dir 0: x-edge (i = 1), 1: y-edge (i = 2).  q in the unit-sphere      */
+/* scaling: q = sqrtG_u (phi, phi u, phi v), true metric G^ij = G_u^ij / r^2.   */
+/* reading c1: |m| (q_R - q_L), i.e. m*sign(m); reading c9: P uses the         */
+/* interface value phi of eq. 3.33.                                            */
+/* ------------------------------------------------------------------------- */
+void orc_lmars(const orc *o, int dir, double X, double Y, const double *qL, const double *qR,
+               double *F) {
+  double m7[7];
+  orc_metric(X, Y, m7);
+  double sG = m7[0], r2 = o->r * o->r;
+  double Gii = (dir == 0 ? m7[1] : m7[3]) / r2; /* true G^ii */
+  double G1i = (dir == 0 ? m7[1] : m7[2]) / r2, G2i = (dir == 0 ? m7[2] : m7[3]) / r2;
+  double phL = qL[0] / sG, phR = qR[0] / sG;
+  double uL = qL[1 + dir] / qL[0], uR = qR[1 + dir] / qR[0];
+  double upL = uL / sqrt(Gii), upR = uR / sqrt(Gii);          /* eq. 3.31 */
+  double c = 0.5 * (sqrt(phL) + sqrt(phR));                     /* eqs. 3.34-3.35 */
+  double ms = 0.5 * (upL + upR - (phR - phL) / c);              /* eq. 3.32 */
+  double ph = 0.5 * (phL + phR - c * (upR - upL));              /* eq. 3.33 */
+  double m = ms * sqrt(Gii);                                    /* eq. 3.36 */
+  double am = fabs(m);
+  for (int v = 0; v < 3; ++v) F[v] = 0.5 * (m * (qL[v] + qR[v]) - am * (qR[v] - qL[v])); /* eq. 3.37 */
+  F[1] += 0.5 * sG * G1i * ph * ph;                             /* eq. 3.38 */
+  F[2] += 0.5 * sG * G2i * ph * ph;
+}
+
+/* Source terms (eqs. 2.2, 2.3; psi_B = 0 without topography) at one point of */
+/* panel p, unit-sphere scaling (both sides of eq. 2.1 divided by r^2).        */
+void orc_sources(const orc *o, int p, double X, double Y, const double *q, double *S) {
+  double m7[7];
+  orc_metric(X, Y, m7);
+  double sG = m7[0], d2 = 1.0 + X * X + Y * Y;
+  double phi = q[0] / sG, u = q[1] / q[0], v = q[2] / q[0];
+  double f = 2.0 * o->omega * sin_lat(p, X, Y);
+  double pm1 = 2.0 * sG / d2 * (-X * Y * Y * phi * u * u + Y * (1.0 + Y * Y) * phi * u * v);
+  double pm2 = 2.0 * sG / d2 * (X * (1.0 + X * X) * phi * u * v - X * X * Y * phi * v * v);
+  double pc1 = sG * f * (-m7[2] * q[1] + m7[1] * q[2]);
+  double pc2 = sG * f * (-m7[3] * q[1] + m7[2] * q[2]);
+  S[0] = 0.0;
+  S[1] = pm1 + pc1;
+  S[2] = pm2 + pc2;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Tendency (eq. 3.1, reading c6: F_{i+1/2} - F_{i-1/2} over dx = pi/(2N)).    */
+/* ------------------------------------------------------------------------- */
+#define PTS(v, p, j, i, pt) pts[((((size_t)(v) * 6 + (p)) * N + (j)) * N + (i)) * np + (pt)]
+
+static int side_point(int me, int side, int g) { return side * me + g; }
+
+void orc_tendency(orc *o, const double *q, double *dqdt) {
+  int N = o->N, ne = o->ne, np = o->npoc, me = o->me;
+  double dx = o->dx;
+  double *ext = (double *)malloc(sizeof(double) * 3 * 6 * ne * ne);
+  double *pts = (double *)malloc(sizeof(double) * 3 * 6 * (size_t)N * N * np);
+  orc_fill_ghosts(o, q, ext, NULL);
+  orc_reconstruct_all(o, ext, pts);
+  /* edge-averaged fluxes: Fx[v][p][j][i'] i' = 0..N, Fy[v][p][j'][i] j' = 0..N */
+  size_t fe = (size_t)N * (N + 1);
+  double *Fx = (double *)calloc(3 * 6 * fe, sizeof(double));
+  double *Fy = (double *)calloc(3 * 6 * fe, sizeof(double));
+#pragma omp parallel for schedule(static)
+  for (int pj = 0; pj < 6 * N; ++pj) {
+    int p = pj / N, j = pj % N;
+    for (int e = 1; e < N; ++e) { /* interior x-edges of row j, between cells e-1 and e */
+      double acc[3] = {0, 0, 0};
+      for (int g = 0; g < me; ++g) {
+        double qL[3], qR[3], F[3];
+        for (int v = 0; v < 3; ++v) {
+          qL[v] = PTS(v, p, j, e - 1, side_point(me, 1, g));
+          qR[v] = PTS(v, p, j, e, side_point(me, 0, g));
+        }
+        double x = -QPI + e * dx, y = cell_centre(o, j) + o->gx[g] * dx;
+        orc_lmars(o, 0, tan(x), tan(y), qL, qR, F);
+        for (int v = 0; v < 3; ++v) acc[v] += o->gw[g] * F[v];
+      }
+      for (int v = 0; v < 3; ++v) Fx[(v * 6 + p) * fe + (size_t)j * (N + 1) + e] = acc[v];
+    }
+    for (int e = 1; e < N; ++e) { /* interior y-edges of column j (cells (j, e-1) | (j, e)) */
+      int i = j;
+      double acc[3] = {0, 0, 0};
+      for (int g = 0; g < me; ++g) {
+        double qL[3], qR[3], F[3];
+        for (int v = 0; v < 3; ++v) {
+          qL[v] = PTS(v, p, e - 1, i, side_point(me, 3, g));
+          qR[v] = PTS(v, p, e, i, side_point(me, 2, g));
+        }
+        double x = cell_centre(o, i) + o->gx[g] * dx, y = -QPI + e * dx;
+        orc_lmars(o, 1, tan(x), tan(y), qL, qR, F);
+        for (int v = 0; v < 3; ++v) acc[v] += o->gw[g] * F[v];
+      }
+      for (int v = 0; v < 3; ++v) Fy[(v * 6 + p) * fe + (size_t)e * N + i] = acc[v];
+    }
+  }
+  /* panel-boundary edges, reading c10: the flux is computed once, in the      */
+  /* lower-numbered panel's frame, from that panel's boundary-cell             */
+  /* reconstruction and the neighbour panel's own boundary-cell reconstruction */
+  /* converted by eqs. 3.26-3.29; the other panel receives the mass flux with  */
+  /* its orientation sign and the momentum flux converted back by C.           */
+  for (int A = 0; A < 6; ++A)
+    for (int side = 0; side < 4; ++side) {
+      const nbr_t *nb0 = &o->nb[((A * 4 + side) * N + 0) * me];
+      int B = nb0->B;
+      if (B < A) continue;
+      int sideB = nb0->sideB;
+      double sA = (side == 1 || side == 3) ? 1.0 : -1.0;
+      double sB = (sideB == 1 || sideB == 3) ? 1.0 : -1.0;
+      int dirA = side / 2, dirB = sideB / 2;
+      for (int t = 0; t < N; ++t) {
+        double accA[3] = {0, 0, 0};
+        double FB[MAXK][3];
+        int tB = -1;
+        for (int g = 0; g < me; ++g) {
+          const nbr_t *nb = &o->nb[((A * 4 + side) * N + t) * me + g];
+          tB = nb->tB;
+          int ci = side == 0 ? 0 : (side == 1 ? N - 1 : t);
+          int cj = side == 2 ? 0 : (side == 3 ? N - 1 : t);
+          int bi = nb->sideB == 0 ? 0 : (nb->sideB == 1 ? N - 1 : nb->tB);
+          int bj = nb->sideB == 2 ? 0 : (nb->sideB == 3 ? N - 1 : nb->tB);
+          double qin[3], qb[3], qo[3];
+          for (int v = 0; v < 3; ++v) {
+            qin[v] = PTS(v, A, cj, ci, side_point(me, side, g));
+            qb[v] = PTS(v, B, bj, bi, side_point(me, nb->sideB, nb->gB));
+          }
+          qo[0] = nb->ratio * qb[0];
+          qo[1] = nb->C[0] * qb[1] + nb->C[1] * qb[2];
+          qo[2] = nb->C[2] * qb[1] + nb->C[3] * qb[2];
+          double x, y, F[3];
+          edge_point(o, side, t, g, &x, &y);
+          if (sA > 0) orc_lmars(o, dirA, tan(x), tan(y), qin, qo, F);
+          else orc_lmars(o, dirA, tan(x), tan(y), qo, qin, F);
+          for (int v = 0; v < 3; ++v) accA[v] += o->gw[g] * F[v];
+          /* back to B: C_{A->B} is the inverse of C_{B->A} at the same point */
+          double Ci[4];
+          inv2(nb->C, Ci);
+          double sg = -sA * sB;
+          FB[nb->gB][0] = sg * F[0];
+          FB[nb->gB][1] = sg * (Ci[0] * F[1] + Ci[1] * F[2]);
+          FB[nb->gB][2] = sg * (Ci[2] * F[1] + Ci[3] * F[2]);
+        }
+        double accB[3] = {0, 0, 0};
+        for (int g = 0; g < me; ++g)
+          for (int v = 0; v < 3; ++v) accB[v] += o->gw[g] * FB[g][v];
+        accB[0] = -sA * sB * accA[0]; /* the single mass flux, exactly */
+        double *FA = dirA == 0 ? Fx : Fy;
+        double *FBp = dirB == 0 ? Fx : Fy;
+        size_t ia = dirA == 0 ? (size_t)t * (N + 1) + (side == 1 ? N : 0)
+                              : (size_t)(side == 3 ? N : 0) * N + t;
+        size_t ib = dirB == 0 ? (size_t)tB * (N + 1) + (sideB == 1 ? N : 0)
+                              : (size_t)(sideB == 3 ? N : 0) * N + tB;
+        for (int v = 0; v < 3; ++v) {
+          FA[(v * 6 + A) * fe + ia] = accA[v];
+          FBp[(v * 6 + B) * fe + ib] = accB[v];
+        }
+      }
+    }
+  /* sources at the cell points (eq. 3.6) and the tendency */
+#pragma omp parallel for schedule(static)
+  for (int pj = 0; pj < 6 * N; ++pj) {
+    int p = pj / N, j = pj % N;
+    for (int i = 0; i < N; ++i) {
+      double sb[3] = {0, 0, 0};
+      for (int h = 0; h < me; ++h)
+        for (int g = 0; g < me; ++g) {
+          int pt = 4 * me + h * me + g;
+          double qv[3], S[3];
+          for (int v = 0; v < 3; ++v) qv[v] = PTS(v, p, j, i, pt);
+          double x = cell_centre(o, i) + o->gx[g] * dx, y = cell_centre(o, j) + o->gx[h] * dx;
+          orc_sources(o, p, tan(x), tan(y), qv, S);
+          for (int v = 0; v < 3; ++v) sb[v] += o->gw[g] * o->gw[h] * S[v];
+        }
+      for (int v = 0; v < 3; ++v) {
+        const double *fx = Fx + (v * 6 + p) * fe + (size_t)j * (N + 1);
+        const double *fy = Fy + (v * 6 + p) * fe;
+        double d = -(fx[i + 1] - fx[i]) / dx - (fy[(size_t)(j + 1) * N + i] - fy[(size_t)j * N + i]) / dx + sb[v];
+        dqdt[((size_t)(v * 6 + p) * N + j) * N + i] = d;
+      }
+    }
+  }
+  free(ext);
+  free(pts);
+  free(Fx);
+  free(Fy);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Time stepping: SSP-RK3 (Shu-Osher form) and the Wicker-Skamarock RK3 of    */
+/* eqs. 3.39-3.41 (reading c8: the second stage starts from q^n).             */
+/* ------------------------------------------------------------------------- */
+void orc_step(orc *o, double *q, double dt, int nsteps, int rk) {
+  size_t n = (size_t)3 * 6 * o->N * o->N;
+  double *L = (double *)malloc(sizeof(double) * n);
+  double *q1 = (double *)malloc(sizeof(double) * n);
+  double *q2 = (double *)malloc(sizeof(double) * n);
+  for (int s = 0; s < nsteps; ++s) {
+    if (rk == ORC_WSRK3) {
+      orc_tendency(o, q, L);
+      for (size_t i = 0; i < n; ++i) q1[i] = q[i] + dt / 3.0 * L[i];
+      orc_tendency(o, q1, L);
+      for (size_t i = 0; i < n; ++i) q2[i] = q[i] + dt / 2.0 * L[i];
+      orc_tendency(o, q2, L);
+      for (size_t i = 0; i < n; ++i) q[i] = q[i] + dt * L[i];
+    } else {
+      orc_tendency(o, q, L);
+      for (size_t i = 0; i < n; ++i) q1[i] = q[i] + dt * L[i];
+      orc_tendency(o, q1, L);
+      for (size_t i = 0; i < n; ++i) q2[i] = 0.75 * q[i] + 0.25 * (q1[i] + dt * L[i]);
+      orc_tendency(o, q2, L);
+      for (size_t i = 0; i < n; ++i) q[i] = q[i] / 3.0 + 2.0 / 3.0 * (q2[i] + dt * L[i]);
+    }
+  }
+  free(L);
+  free(q1);
+  free(q2);
+}
+
+double orc_mass(const orc *o, const double *q) {
+  long double s = 0.0L;
+  for (size_t i = 0; i < (size_t)6 * o->N * o->N; ++i) s += q[i];
+  return (double)(s * o->dx * o->dx);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Initial conditions (section 5), cell averages by the me x me Gauss rule of  */
+/* sqrtG times the analytic field (reading c15).                               */
+/* ------------------------------------------------------------------------- */
+static double gc_dist(double l1, double t1, double l2, double t2) {
+  double c = sin(t1) * sin(t2) + cos(t1) * cos(t2) * cos(l1 - l2);
+  if (c > 1.0) c = 1.0;
+  if (c < -1.0) c = -1.0;
+  return acos(c);
+}
+
+static void ic_point(const orc *o, int cs, const double *P, int n_extra, const double *ex, double lam,
+                     double th, double *phi, double *us, double *vs) {
+  double a = o->r, Om = o->omega, g = o->g;
+  if (cs == ORC_IC_GEOSTROPHIC || cs == ORC_IC_BUMPS) {
+    double al = P[0], u0 = P[1], phi0 = P[2];
+    double t = -cos(lam) * cos(th) * sin(al) + sin(th) * cos(al);
+    *phi = phi0 - (a * Om * u0 + 0.5 * u0 * u0) * t * t;            /* eq. 5.1 */
+    *us = u0 * (cos(th) * cos(al) + cos(lam) * sin(th) * sin(al));  /* eq. 5.2 */
+    *vs = -u0 * sin(lam) * sin(al);                                 /* eq. 5.3 */
+    if (cs == ORC_IC_BUMPS) {
+      double amp = P[3], rad = P[4];
+      for (int b = 0; b < n_extra / 2; ++b) {
+        double d = gc_dist(lam, th, ex[2 * b], ex[2 * b + 1]);
+        *phi += g * amp * exp(-(d / rad) * (d / rad));
+      }
+    }
+  } else if (cs == ORC_IC_ROSSBY) {
+    double w = P[0], K = P[1], R = P[2], h0 = P[3];
+    double ct = cos(th), st = sin(th);
+    double A = 0.5 * w * (2.0 * Om + w) * ct * ct +
+               0.25 * K * K * pow(ct, 2 * R) * ((R + 1) * ct * ct + 2 * R * R - R - 2 - 2 * R * R / (ct * ct));
+    double B = 2.0 * (Om + w) * K / ((R + 1) * (R + 2)) * pow(ct, R) * (R * R + 2 * R + 2 - (R + 1) * (R + 1) * ct * ct);
+    double C = 0.25 * K * K * pow(ct, 2 * R) * ((R + 1) * ct * ct - R - 2);
+    *phi = g * h0 + a * a * (A + B * cos(R * lam) + C * cos(2 * R * lam));   /* eqs. 5.10, 5.13-5.15 */
+    *us = a * w * ct + a * K * pow(ct, R - 1) * (R * st * st - ct * ct) * cos(R * lam); /* eq. 5.11 */
+    *vs = -a * K * R * pow(ct, R - 1) * st * sin(R * lam);                    /* eq. 5.12 */
+  } else { /* dam break, reading c18: great-circle distance, fluid at rest */
+    double d = gc_dist(lam, th, P[0], P[1]);
+    *phi = g * (d < P[2] ? P[3] : P[4]);
+    *us = 0.0;
+    *vs = 0.0;
+  }
+}
+
+void orc_ic(const orc *o, int cs, const double *P, int n_extra, const double *ex, double *q) {
+  int N = o->N, me = o->me;
+  size_t pi = (size_t)N * N;
+#pragma omp parallel for schedule(static)
+  for (int pj = 0; pj < 6 * N; ++pj) {
+    int p = pj / N, j = pj % N;
+    for (int i = 0; i < N; ++i) {
+      double acc[3] = {0, 0, 0};
+      for (int h = 0; h < me; ++h)
+        for (int g = 0; g < me; ++g) {
+          double X = tan(cell_centre(o, i) + o->gx[g] * o->dx);
+          double Y = tan(cell_centre(o, j) + o->gx[h] * o->dx);
+          double xyz[3], lam, th, phi, us, vs, m7[7], J[4], Ji[4];
+          orc_xyz(p, X, Y, xyz);
+          lonlat(xyz, &lam, &th);
+          ic_point(o, cs, P, n_extra, ex, lam, th, &phi, &us, &vs);
+          orc_metric(X, Y, m7);
+          orc_jacobian(p, X, Y, J);
+          inv2(J, Ji);
+          double u = (Ji[0] * us + Ji[1] * vs) / o->r, v = (Ji[2] * us + Ji[3] * vs) / o->r;
+          double w = o->gw[g] * o->gw[h];
+          acc[0] += w * m7[0] * phi;
+          acc[1] += w * m7[0] * phi * u;
+          acc[2] += w * m7[0] * phi * v;
+        }
+      for (int v = 0; v < 3; ++v) q[(size_t)(v * 6 + p) * pi + (size_t)j * N + i] = acc[v];
+    }
+  }
+}
+
+void orc_cell_sqrtg(const orc *o, double *out) {
+  int N = o->N, me = o->me;
+  for (int p = 0; p < 6; ++p)
+    for (int j = 0; j < N; ++j)
+      for (int i = 0; i < N; ++i) {
+        double acc = 0.0;
+        for (int h = 0; h < me; ++h)
+          for (int g = 0; g < me; ++g) {
+            double m7[7];
+            orc_metric(tan(cell_centre(o, i) + o->gx[g] * o->dx), tan(cell_centre(o, j) + o->gx[h] * o->dx), m7);
+            acc += o->gw[g] * o->gw[h] * m7[0];
+          }
+        out[((size_t)p * N + j) * N + i] = acc;
+      }
+}
+
+/* Error norms of phi (eqs. 5.4-5.7), reading c16: phi = q0 / <sqrtG>, the     */
+/* I() weights are <sqrtG>, the L1 numerator takes absolute values.            */
+void orc_norms(const orc *o, const double *q, const double *qr, double *out) {
+  size_t n = (size_t)6 * o->N * o->N;
+  double *sg = (double *)malloc(sizeof(double) * n);
+  orc_cell_sqrtg(o, sg);
+  long double n1 = 0, d1 = 0, n2 = 0, d2 = 0;
+  double mx = 0, mr = 0;
+  for (size_t c = 0; c < n; ++c) {
+    double ph = q[c] / sg[c], pr = qr[c] / sg[c], d = ph - pr;
+    n1 += sg[c] * fabs(d);
+    d1 += sg[c] * fabs(pr);
+    n2 += sg[c] * d * d;
+    d2 += sg[c] * pr * pr;
+    if (fabs(d) > mx) mx = fabs(d);
+    if (fabs(pr) > mr) mr = fabs(pr);
+  }
+  out[0] = (double)(n1 / d1);
+  out[1] = (double)sqrtl(n2 / d2);
+  out[2] = mx / mr;
+  free(sg);
+}

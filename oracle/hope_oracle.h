@@ -1,0 +1,94 @@
+/*
+ * hope_oracle.h -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain, slow, FP64 CPU reference ("oracle") of the HOPE cubed-sphere
+ * shallow-water spatial operator and its Runge-Kutta stepping
+ * (Zhou, "HOPE: an automatically differentiable high-order non-oscillatory
+ * finite-volume shallow-water dynamic core", arXiv 2411.19185).
+ *
+ * Only the test suite, the package smoke check and the CPU-baseline leg of the
+ * benchmark may load this library.  It shares no code, header, table or
+ * constant generator with the CUDA library; neither includes the other.
+ *
+ * Conventions (identical in meaning to the CUDA library, written separately):
+ *   state q[v][p][j][i]   v = 0..2  (sqrtG*phi, sqrtG*phi*u, sqrtG*phi*v),
+ *                         p = 0..5  (the paper's panels 1..6), j, i = 0..N-1,
+ *                         i (x direction) fastest.
+ *   sqrtG is the unit-sphere metric Jacobian (eq. 2.8 divided by r^2);
+ *   phi in m^2/s^2, (u, v) contravariant in rad/s.
+ *   extended arrays e[v][p][jj][ii], jj, ii = 0..N+2H-1, interior at offset H.
+ *   per-cell reconstruction points (n_poc = 4*me + me*me), in this order:
+ *     [0, me)        west edge   (xi = -1/2, eta = g_r)
+ *     [me, 2me)      east edge   (xi = +1/2, eta = g_r)
+ *     [2me, 3me)     south edge  (xi = g_r,  eta = -1/2)
+ *     [3me, 4me)     north edge  (xi = g_r,  eta = +1/2)
+ *     [4me + h*me + g]  cell point (xi = g_g, eta = g_h)
+ *   with g_r the Gauss-Legendre nodes on [-1/2, 1/2].
+ */
+#ifndef HOPE_ORACLE_H
+#define HOPE_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_TPP 0
+#define ORC_WENO 1
+#define ORC_SSPRK3 0
+#define ORC_WSRK3 1
+
+/* initial-condition cases for orc_ic */
+#define ORC_IC_GEOSTROPHIC 2   /* params: alpha, u0, phi0                         */
+#define ORC_IC_ROSSBY 6        /* params: omega_rh, K, R, h0                      */
+#define ORC_IC_DAMBREAK 7      /* params: lon_c, lat_c, radius_rad, h_in, h_out   */
+#define ORC_IC_BUMPS 8         /* geostrophic + n Gaussian bumps; params: alpha,u0,phi0,amp_m,
+                                  radius_rad; extra = n pairs (lon, lat)          */
+
+typedef struct orc orc;
+
+orc *orc_new(int N, int k, int scheme, double radius, double gravity, double omega,
+             double weno_eps, int ghost_iters);
+void orc_free(orc *o);
+int orc_npoc(const orc *o);
+int orc_halo(const orc *o);
+
+/* One evaluation of the spatial operator L(q) = dq/dt (eq. 3.1). */
+void orc_tendency(orc *o, const double *q, double *dqdt);
+/* nsteps Runge-Kutta steps in place (rk = ORC_SSPRK3 or ORC_WSRK3). */
+void orc_step(orc *o, double *q, double dt, int nsteps, int rk);
+/* Total mass dx*dy*sum(q0) (the I() weighted sum of eq. 5.7), long-double accumulation. */
+double orc_mass(const orc *o, const double *q);
+/* Ghost fill by the iteration of section 3.3.1; ext receives the extended array.
+   resid (may be NULL) receives the 2-norm of the last sweep's increment per variable. */
+void orc_fill_ghosts(orc *o, const double *q, double *ext, double *resid);
+/* Reconstruction at every point of every interior cell from an extended array:
+   pts[v][p][j][i][n_poc]. */
+void orc_reconstruct_all(orc *o, const double *ext, double *pts);
+/* Cell averages of an analytic initial condition by me x me Gauss quadrature. */
+void orc_ic(const orc *o, int ic_case, const double *params, int n_extra, const double *extra,
+            double *q);
+/* Cell-averaged sqrtG (unit sphere) per cell, [p][j][i]. */
+void orc_cell_sqrtg(const orc *o, double *out);
+/* L1, L2, Linf error norms of phi (eqs. 5.4-5.7). */
+void orc_norms(const orc *o, const double *q, const double *qref, double *out3);
+
+/* ---- building blocks exposed for the pin tests ---- */
+void orc_gauss(int m, double *x, double *w);
+void orc_weights_1d(int n, int o0, double xi, double *out);
+void orc_tpp_weights_2d(int k, double xi, double eta, double *out);
+void orc_tpp_weights_2d_literal(int k, double xi, double eta, double *out);
+int orc_weno_gamma(int k, double xi, double eta, double *gam, double *resid);
+double orc_weno_beta(int l, int o0x, int o0y, const double *Qsub);
+double orc_weno_point(const orc *o, const double *stencil, int pt);
+void orc_metric(double X, double Y, double *out7);
+void orc_jacobian(int panel, double X, double Y, double *J4);
+void orc_xyz(int panel, double X, double Y, double *xyz);
+int orc_locate(const double *xyz, double *XY);
+void orc_lmars(const orc *o, int dir, double X, double Y, const double *qL, const double *qR,
+               double *F);
+void orc_sources(const orc *o, int panel, double X, double Y, const double *qv, double *S);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

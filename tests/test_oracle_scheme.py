@@ -1,0 +1,160 @@
+"""Whole-scheme pins of the oracle (no GPU): the paper's Table 5.1, design
+convergence order, exact mass conservation, symmetry, and the ghost-cell
+interpolation against exact extended cell averages of smooth fields.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "table5_1.txt")
+
+
+def _table51():
+    rows = {}
+    for line in open(GOLDEN):
+        if line.startswith("#") or not line.strip():
+            continue
+        s, n, dt, l1, l2, li = line.split()
+        rows[(int(s[3:]), int(n))] = (float(dt), np.array([float(l1), float(l2), float(li)]))
+    return rows
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("k", [3, 5])
+def test_table_5_1_geostrophic_12_days(k):
+    """Table 5.1 (section 5.1): steady geostrophic flow, C30, Wicker-Skamarock RK3,
+    dt = 600 s, 12 days.  The FP64 oracle reproduces the printed L1/L2/Linf errors
+    (quoted to 5 digits) to within 2e-4 relative."""
+    dt, ref = _table51()[(k, 30)]
+    o = O.Oracle(30, k)
+    q0 = o.geostrophic()
+    q = o.step(q0, dt, int(round(12 * 86400 / dt)), O.WSRK3)
+    got = o.norms(q, q0)
+    np.testing.assert_allclose(got, ref, rtol=2e-4)
+
+
+@pytest.mark.parametrize("k", [3, 5, 7])
+def test_design_order_of_steady_state_truncation(k):
+    """The tendency of the exact steady geostrophic state (alpha = pi/4) is the
+    truncation error; it falls at close to the design order k (section 5.1's rates;
+    the RMS tendency error of these coarse grids converges at about k - 1/2)."""
+    errs = []
+    for N in (16, 32):
+        o = O.Oracle(N, k)
+        q = o.geostrophic(alpha=np.pi / 4)
+        d = o.tendency(q)
+        errs.append(np.sqrt(np.mean(d[0] ** 2)) / np.sqrt(np.mean(q[0] ** 2)))
+    rate = np.log2(errs[0] / errs[1])
+    assert rate > k - 1.0, (errs, rate)
+
+
+@pytest.mark.parametrize("k,scheme", [(3, O.TPP), (5, O.TPP), (5, O.WENO)])
+def test_mass_conserved_to_roundoff(k, scheme):
+    """Finite-volume form (eq. 3.1) with a single flux per shared edge point (reading
+    c10): total mass is conserved to round-off."""
+    o = O.Oracle(10, k, scheme=scheme)
+    q = o.rossby_haurwitz()
+    m0 = o.mass(q)
+    q = o.step(q, 900.0, 3)
+    assert abs(o.mass(q) - m0) / m0 < 5e-15
+
+
+def test_mirror_symmetry_z():
+    """Steady zonal flow (alpha = 0) is symmetric under z -> -z: panel 6 cell (i, j)
+    equals panel 5 cell (i, N-1-j) with the y-momentum negated, and each equatorial
+    panel maps to itself with j -> N-1-j; the tendencies inherit the symmetry."""
+    N = 10
+    o = O.Oracle(N, 5)
+    q = o.geostrophic(alpha=0.0)
+    d = o.tendency(q)
+    sgn = np.array([1.0, 1.0, -1.0])[:, None, None]
+    for f in (q, d):
+        scale = np.abs(f).max(axis=(1, 2, 3))[:, None, None] + 1e-300
+        np.testing.assert_allclose(f[:, 5] / scale, sgn * f[:, 4, ::-1, :] / scale, atol=1e-12)
+        for p in range(4):
+            np.testing.assert_allclose(f[:, p] / scale, sgn * f[:, p, ::-1, :] / scale, atol=1e-12)
+
+
+# ------------------------------------------------------------------ ghosts
+_FR = {  # panel frames (n, e1, e2): the documented panel convention
+    0: ((1, 0, 0), (0, 1, 0), (0, 0, 1)), 1: ((0, 1, 0), (-1, 0, 0), (0, 0, 1)),
+    2: ((-1, 0, 0), (0, -1, 0), (0, 0, 1)), 3: ((0, -1, 0), (1, 0, 0), (0, 0, 1)),
+    4: ((0, 0, 1), (0, 1, 0), (-1, 0, 0)), 5: ((0, 0, -1), (0, 1, 0), (1, 0, 0)),
+}
+
+
+def _exact_ext(N, H, f, vel, nq=8):
+    """Exact (nq-point Gauss) cell averages of sqrtG*f and sqrtG*f*(u, v) on every
+    cell of every panel's extended (N+2H)^2 grid, with (u, v) the contravariant
+    components of the tangent field vel, from the tangent vectors dP/dx, dP/dy."""
+    g, w = np.polynomial.legendre.leggauss(nq)
+    g, w = g / 2, w / 2
+    dx = np.pi / (2 * N)
+    ne = N + 2 * H
+    out = np.zeros((3, 6, ne, ne))
+    c = -np.pi / 4 + (np.arange(ne) - H + 0.5) * dx
+    for p in range(6):
+        n, e1, e2 = (np.array(v, float) for v in _FR[p])
+        for jj in range(ne):
+            for ii in range(ne):
+                x = c[ii] + g[:, None] * dx + 0 * g[None, :]
+                y = c[jj] + 0 * g[:, None] + g[None, :] * dx
+                X, Y = np.tan(x), np.tan(y)
+                wv = n[None, None, :] + X[..., None] * e1 + Y[..., None] * e2
+                r = np.linalg.norm(wv, axis=-1)
+                P = wv / r[..., None]
+                sg = (1 + X ** 2) * (1 + Y ** 2) / r ** 3
+                tx = (1 + X ** 2)[..., None] * (e1 - P * (P @ e1)[..., None]) / r[..., None]
+                ty = (1 + Y ** 2)[..., None] * (e2 - P * (P @ e2)[..., None]) / r[..., None]
+                fv = f(P)
+                V = vel(P)
+                # solve V = u tx + v ty (normal equations of the 3x2 system)
+                a11 = np.sum(tx * tx, -1); a12 = np.sum(tx * ty, -1); a22 = np.sum(ty * ty, -1)
+                b1 = np.sum(tx * V, -1); b2 = np.sum(ty * V, -1)
+                det = a11 * a22 - a12 * a12
+                u = (a22 * b1 - a12 * b2) / det
+                v = (a11 * b2 - a12 * b1) / det
+                W = w[:, None] * w[None, :]
+                out[0, p, jj, ii] = np.sum(W * sg * fv)
+                out[1, p, jj, ii] = np.sum(W * sg * fv * u)
+                out[2, p, jj, ii] = np.sum(W * sg * fv * v)
+    return out
+
+
+def _smooth_f(P):
+    return 2.0 + P[..., 0] * P[..., 1] + 0.5 * P[..., 2] ** 2 + 0.3 * P[..., 0]
+
+
+def _smooth_vel(P):
+    ax = np.array([0.3, -0.5, 0.8])
+    return np.cross(np.broadcast_to(ax, P.shape), P)
+
+
+@pytest.mark.parametrize("k", [3, 5])
+def test_ghost_fill_converges_to_exact_extended_averages(k):
+    """Section 3.3 and the appendix: the iterated ghost interpolation (TPP on the
+    owning panel, conversions eqs. 3.26-3.29, Gauss average eq. 3.6) reproduces
+    the exact cell averages of smooth fields on the extended grid (mass and
+    momentum), converging at the design order.  The iteration contracts by about
+    an order of magnitude per sweep: after the paper's 10 sweeps the last increment
+    is below 1e-9 relative (about 1e-11 in practice)."""
+    errs = []
+    for N in (12, 24):
+        H = (k - 1) // 2
+        ex = _exact_ext(N, H, _smooth_f, _smooth_vel)
+        q = np.ascontiguousarray(ex[:, :, H:H + N, H:H + N])
+        o = O.Oracle(N, k)
+        ext, res = o.fill_ghosts(q)
+        mask = np.ones((N + 2 * H, N + 2 * H), bool)
+        mask[H:H + N, H:H + N] = False
+        e = [np.abs(ext[v][:, mask] - ex[v][:, mask]).max() / np.abs(ex[v]).max() for v in range(3)]
+        errs.append(e)
+        norms = [np.linalg.norm(ext[v][:, mask]) for v in range(3)]
+        assert all(res[v] / norms[v] < 1e-9 for v in range(3)), (res, norms)
+    errs = np.array(errs)
+    rates = np.log2(errs[0] / errs[1])
+    assert np.all(errs[1] < 1e-3)
+    assert np.all(rates > k - 0.8), (errs, rates)
