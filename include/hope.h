@@ -1,0 +1,203 @@
+/*
+ * hope.h -- C ABI of the GB300 (sm_103a) implementation of the per-Runge-Kutta-stage
+ * tendency of HOPE's cubed-sphere shallow-water core (Zhou, arXiv 2411.19185).
+ *
+ * The operation
+ *   L(q) = dq/dt  (eq. 3.1): ghost-cell fill across the six panel boundaries
+ *   (section 3.3.1 and appendix eq. 7.12), reconstruction of the three state variables
+ *   at the Gauss points of every cell by tensor-product polynomials (section 3.1,
+ *   eqs. 3.7-3.15) or genuine-2D WENO-Z (section 3.2, eqs. 3.16-3.25), panel conversion
+ *   of boundary states (section 3.3.2, eqs. 3.26-3.29), the LMARS flux at every edge
+ *   Gauss point (section 3.4, eqs. 3.30-3.38), Gauss quadrature of edge fluxes
+ *   (eq. 3.5) and of the metric and Coriolis sources (eqs. 2.2, 2.3, 3.6).
+ *
+ * State layout and units (every state, tendency and adjoint buffer):
+ *   q[var][panel][j][i], var = 0..2, panel = 0..5 (the paper's panels 1..6),
+ *   j, i = 0..N-1 with i (the panel's x direction) fastest; element type double
+ *   (HOPE_FP64) or float (HOPE_FP32) as chosen at init.
+ *   var 0 = sqrtG*phi, var 1 = sqrtG*phi*u, var 2 = sqrtG*phi*v: cell averages, where
+ *   sqrtG = (1+X^2)(1+Y^2)/delta^3 is the unit-sphere metric Jacobian (eq. 2.8 divided by
+ *   r^2), phi = g*h in m^2/s^2 and (u, v) the contravariant wind in rad/s.
+ *   Panel p maps (X, Y) = (tan x, tan y), x, y in [-pi/4, pi/4], to the unit vector
+ *   (n_p + X e1_p + Y e2_p)/delta with (n, e1, e2) =
+ *     p0 ((1,0,0),(0,1,0),(0,0,1))   p1 ((0,1,0),(-1,0,0),(0,0,1))
+ *     p2 ((-1,0,0),(0,-1,0),(0,0,1)) p3 ((0,-1,0),(1,0,0),(0,0,1))
+ *     p4 ((0,0,1),(0,1,0),(-1,0,0))  p5 ((0,0,-1),(0,1,0),(1,0,0)),
+ *   the convention under which the paper's J (eqs. 2.10-2.11) and sin(latitude)
+ *   (eq. 2.5) hold.  Cell (i, j) spans x in [-pi/4 + i dx, -pi/4 + (i+1) dx], dx = pi/(2N).
+ *
+ * Ownership: the caller owns every state/tendency/adjoint buffer (device memory on
+ * the context's device, unless a name ends in _host).  The context owns its tables and
+ * scratch.  Buffers passed to one call must not overlap unless stated.
+ *
+ * Errors: every call returns HOPE_OK (0) or a negative HOPE_E* code; nothing throws or
+ * aborts across the ABI.  hope_strerror() names a code; hope_last_error_message() gives
+ * the detail of the last failure on the calling thread.  Device-side problems (a
+ * non-positive or non-finite phi met by the flux, a non-finite result) set a sticky
+ * status word read and cleared by hope_status().
+ *
+ * Streams: calls taking a stream enqueue work on it and return without synchronising,
+ * except where stated (hope_total_mass and the *_host calls synchronise).  One context
+ * must not be used from two streams at once: its scratch is shared by all its calls.
+ */
+#ifndef HOPE_H
+#define HOPE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hope_ctx *hope_t;
+typedef void *hope_stream_t; /* a cudaStream_t; NULL = the legacy default stream */
+
+/* return codes */
+#define HOPE_OK 0
+#define HOPE_EINVAL -1      /* bad argument (size, order, null pointer, ...) */
+#define HOPE_ECUDA -2       /* a CUDA runtime call failed */
+#define HOPE_ENOMEM -3      /* device or host allocation failed */
+#define HOPE_ENONPHYS -4    /* non-physical state reported by the device */
+#define HOPE_ETIMEOUT -5    /* a bounded device-side wait gave up */
+#define HOPE_EUNSUPPORTED -6
+
+/* schemes, precisions, time steppers */
+#define HOPE_TPP 0     /* tensor-product polynomial reconstruction, section 3.1 */
+#define HOPE_WENO2D 1  /* genuine two-dimensional WENO-Z, section 3.2            */
+#define HOPE_FP64 0
+#define HOPE_FP32 1
+#define HOPE_SSPRK3 0  /* strong-stability-preserving RK3 (Shu-Osher form) */
+#define HOPE_WSRK3 1   /* Wicker-Skamarock RK3 of eqs. 3.39-3.41 */
+
+/* sticky device status bits (hope_status) */
+#define HOPE_STATUS_NONPHYS_PHI 1u /* phi <= 0 where the LMARS flux takes sqrt(phi), eq. 3.35 */
+#define HOPE_STATUS_NAN 2u         /* a non-finite value in a computed tendency or state   */
+
+typedef struct {
+  double radius;   /* sphere radius a (m), default 6.37122e6 (section 5.1) */
+  double gravity;  /* g (m/s^2), default 9.80616 */
+  double omega;    /* rotation rate Omega (1/s), default 7.292e-5; 0 disables Coriolis */
+  int n_gauss;     /* Gauss points per edge m_e; 0 => (order+1)/2, the only value supported */
+  int precision;   /* HOPE_FP64 (default) or HOPE_FP32 */
+  int rk;          /* HOPE_SSPRK3 (default) or HOPE_WSRK3 */
+  int ghost_iters; /* sweeps of the ghost-cell iteration (section 3.3.1), default 10 */
+  double weno_eps; /* epsilon of eq. 3.23; 0 => 1e-40 (FP64) / 1e-12 (FP32) */
+} hope_params;
+
+/* Fill *p with the defaults above. */
+void hope_default_params(hope_params *p);
+
+/*
+ * Create a context for one cubed sphere with N cells per panel edge, stencil width
+ * `order` (odd, 3..11; the design order of TPP, section 3.1) and `scheme`.  All tables
+ * (reconstruction weights eqs. 3.14-3.15, WENO linear weights eqs. 3.19-3.20 and
+ * smoothness forms eq. 3.25, the ghost operator G of eq. 7.12, per-point metric terms
+ * eqs. 2.2-2.8) are built in FP64 and stored on the current CUDA device.  Requires
+ * N >= order.  On failure *out is NULL.
+ */
+int hope_init_grid(int N, int order, int scheme, const hope_params *params, hope_t *out);
+
+/*
+ * Create one context for an ensemble of n_members independent spheres with
+ * N[m] cells per edge (uneven resolutions allowed), sharing order, scheme and params.
+ * Ensemble states concatenate the members' (3,6,N[m],N[m]) blocks in member order;
+ * hope_state_elems() gives the total length.  A stage of the whole ensemble runs as
+ * one persistent launch (work list over all members' tiles).
+ */
+int hope_init_ensemble(int n_members, const int *N, int order, int scheme,
+                       const hope_params *params, hope_t *out);
+
+void hope_destroy(hope_t ctx);
+
+/* Number of elements of one state (3*6*N^2 summed over members). */
+size_t hope_state_elems(hope_t ctx);
+
+/* Element size in bytes of the context's precision (8 or 4). */
+int hope_elem_size(hope_t ctx);
+
+/*
+ * Cell averages of an analytic initial condition (section 5), computed on the device
+ * with the me x me Gauss rule of sqrtG times the field, written to q_dev.
+ *   case 2  steady geostrophic flow, eqs. 5.1-5.3     params: alpha, u0, phi0
+ *   case 6  Rossby-Haurwitz wave, eqs. 5.10-5.15       params: omega_rh, K, R, h0
+ *   case 7  dam break: h_in inside a great-circle cap  params: lon, lat, radius, h_in, h_out
+ *   case 8  case 2 plus Gaussian bumps of phi          params: alpha, u0, phi0, amp_m, radius;
+ *           extra_host: n_extra/2 (lon, lat) centres
+ * For an ensemble every member gets the same case.
+ */
+int hope_initial_state(hope_t ctx, int ic_case, const double *params, int n_params,
+                       const double *extra_host, int n_extra, void *q_dev, hope_stream_t stream);
+
+/* Copy a caller state into / out of the context's own state buffer (device to device). */
+int hope_set_state(hope_t ctx, const void *q_dev, hope_stream_t stream);
+int hope_get_state(hope_t ctx, void *q_dev, hope_stream_t stream);
+
+/*
+ * dqdt_dev = L(q_dev) for one stage (eq. 3.1).  q_dev and dqdt_dev are caller-owned
+ * device buffers of hope_state_elems() elements and must not overlap.  q_dev == NULL
+ * uses the context's own state.
+ */
+int hope_tendency(hope_t ctx, const void *q_dev, void *dqdt_dev, hope_stream_t stream);
+
+/*
+ * nsteps Runge-Kutta steps of size dt (seconds) in place on q_dev (NULL = the context's
+ * own state), with the context's stepper (SSP-RK3 by default).  Each stage fuses the
+ * stage combination into the tendency's final kernel.  Steps are replayed from a CUDA
+ * graph captured on first use for a given (q_dev, dt, stream).
+ */
+int hope_step(hope_t ctx, void *q_dev, double dt, int nsteps, hope_stream_t stream);
+
+/* hope_step with SSP-RK3 regardless of the context's default stepper. */
+int hope_step_ssprk3(hope_t ctx, void *q_dev, double dt, hope_stream_t stream);
+
+/*
+ * End-to-end form of hope_step for callers holding HOST memory: copies q_host_in
+ * (hope_state_elems() elements, ideally pinned) to the device, runs nsteps steps,
+ * copies the result to q_host_out (may equal q_host_in) and synchronises the stream.
+ */
+int hope_step_host(hope_t ctx, const void *q_host_in, void *q_host_out, double dt,
+                   int nsteps, hope_stream_t stream);
+
+/*
+ * Vector-Jacobian products (hand-written adjoints, no tracing).
+ *   hope_tendency_vjp:  lam_q = (dL/dq)^T lam_dqdt at q_dev.
+ *   hope_step_vjp:      lam_n = (dS/dq)^T lam_np1 for one RK step S of size dt taken from
+ *                       qn_dev (the stage states are recomputed).
+ * Output buffers are overwritten; none may overlap an input.
+ */
+int hope_tendency_vjp(hope_t ctx, const void *q_dev, const void *lam_dqdt_dev, void *lam_q_dev,
+                      hope_stream_t stream);
+int hope_step_vjp(hope_t ctx, const void *qn_dev, const void *lam_np1_dev, void *lam_n_dev,
+                  double dt, hope_stream_t stream);
+
+/*
+ * Total mass M = dx*dy*sum(q[0]) (the I() sum of eq. 5.7 times the cell area) of q_dev,
+ * accumulated in FP64 in a fixed order on the device (bitwise reproducible).  For an
+ * ensemble, mass_host receives one value per member.  Synchronises the stream.
+ */
+int hope_total_mass(hope_t ctx, const void *q_dev, double *mass_host, hope_stream_t stream);
+
+/* Read and clear the sticky device status (HOPE_STATUS_* bits).  Synchronises. */
+int hope_status(hope_t ctx, unsigned *device_status);
+
+/* Total nonzeros of the ghost operator G (eq. 7.12) and its row count. */
+int hope_ghost_nnz(hope_t ctx, long long *nnz, long long *rows);
+
+/* Launch configuration introspection for profiling: number of kernel launches one
+   tendency enqueues. */
+int hope_launches_per_stage(hope_t ctx, int *launches);
+
+const char *hope_strerror(int code);
+const char *hope_last_error_message(void);
+
+/*
+ * Microbenchmark of the device's plain-ALU peak (no tensor cores): dependent-chain-free
+ * fused multiply-add loops in FP64 (precision HOPE_FP64) or FP32 on every SM, timed with
+ * CUDA events.  *flops_per_s receives the measured rate (2 flops per FMA).
+ */
+int hope_measure_fma_peak(int precision, double *flops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

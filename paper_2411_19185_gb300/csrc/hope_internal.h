@@ -1,0 +1,85 @@
+// hope_internal.h -- context layout and launch helpers of the HOPE GB300 library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/hope.h"
+
+namespace hope {
+
+// One cube edge shared by panels A < B: A's side sideA meets B's side sideB
+// (0 west x=-pi/4, 1 east, 2 south y=-pi/4, 3 north); along the edge, A's cell t and
+// Gauss node g coincide with B's cell (flip ? N-1-t : t) and node (flip ? me-1-g : g).
+struct CubeEdge {
+  int A, sideA, B, sideB, flip;
+};
+
+// Device tables and scratch of one sphere (one member of an ensemble).
+struct Grid {
+  int N = 0, ne = 0;
+  size_t off = 0;   // element offset of this member in ensemble states
+  // tables (element type = context precision)
+  void *Xg = nullptr;    // [N][me]  tan of the cell Gauss-node coordinates
+  void *t1w = nullptr;   // [N][N][me][me]  2/delta^2 * W_gh at the cell points
+  void *mx = nullptr;    // [N+1][N][me][5] x-edge metric terms (transposed use for y-edges)
+  void *gval = nullptr;  // [nnz][5] ghost operator weights (mass, C00, C01, C10, C11)
+  int *grow = nullptr;   // [rows+1]
+  int *gcol = nullptr;   // [nnz]  source cell p*N*N + j*N + i
+  int *gdst = nullptr;   // [rows] destination p*ne*ne + jj*ne + ii
+  long long rows = 0, nnz = 0;
+  int *bedge = nullptr;  // [12][5] CubeEdge
+  void *bconv = nullptr; // [12][N][me][9] ratio_BA, C_BA[4], C_AB[4]
+  // scratch
+  void *gext = nullptr;  // [3][6][ne][ne] ghost ring (interior unused)
+  void *ep = nullptr;    // [4][3][me][6][N][N] edge-point reconstructions
+  void *fx = nullptr;    // [3][6][N][N+1]
+  void *fy = nullptr;    // [3][6][N+1][N]
+  void *sb = nullptr;    // [2][6][N][N] cell-averaged sources
+  CubeEdge edges[12];
+};
+
+struct GraphKey {
+  const void *q;
+  double dt;
+  int rk;
+  bool operator<(const GraphKey &o) const {
+    if (q != o.q) return q < o.q;
+    if (dt != o.dt) return dt < o.dt;
+    return rk < o.rk;
+  }
+};
+
+}  // namespace hope
+
+struct hope_ctx {
+  int k = 0, H = 0, me = 0, npoc = 0, scheme = 0, prec = 0, rk = 0, ghost_iters = 10;
+  double radius = 0, gravity = 0, omega = 0, eps = 0;
+  int device = 0;
+  int esize = 8;
+  size_t total = 0;  // elements of one (ensemble) state
+  std::vector<hope::Grid> grids;
+  // order-dependent tables (element type = precision)
+  void *w1 = nullptr;   // [me+2][k] 1-D TPP weights at xi = -1/2, +1/2, g_0..g_{me-1}
+  void *gw = nullptr;   // [me] Gauss weights
+  // WENO tables
+  void *wsub = nullptr;   // [me+2][l][l]  1-D sub-stencil weights at the same positions
+  void *gpm = nullptr;    // [npoc][2][s] normalised gamma+/sigma+, gamma-/sigma-
+  void *sig = nullptr;    // [npoc][2] sigma+, sigma-
+  void *bform = nullptr;  // [l][2][l][l] S and B0 1-D forms per sub-stencil offset
+  // buffers
+  void *state = nullptr;  // context-owned state
+  void *q1 = nullptr, *q2 = nullptr, *lbuf = nullptr;
+  unsigned *status = nullptr;
+  double *mass_part = nullptr;
+  double *mass_out = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  std::map<hope::GraphKey, cudaGraphExec_t> graphs;
+};
+
+namespace hope {
+void set_error(const std::string &msg);
+}

@@ -1,0 +1,431 @@
+// hope_kernels.cuh -- per-stage kernels of the HOPE cubed-sphere shallow-water core
+// (arXiv 2411.19185) for sm_103a, templated on the element type T (double / float)
+// and the stencil width K.
+//
+// One stage L(q) = dq/dt runs as
+//   k_ghost      ghost ring = G q                       (appendix eq. 7.12)
+//   k_recon_tpp  per tile: x-pass / y-pass sum-factorised TPP reconstruction at the
+//                4 me edge points and me^2 cell points (eqs. 3.14-3.15, R = r_x (x) r_y),
+//                edge points to global, cell-point sources quadrature (eqs. 2.2, 2.3, 3.6)
+//   k_flux       LMARS at every edge Gauss point (eqs. 3.30-3.38) + edge quadrature
+//                (eq. 3.5); panel-boundary edges once per cube edge with the
+//                conversions of eqs. 3.26-3.29
+//   k_update     flux difference + sources (eq. 3.1) fused with the RK stage combination
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hope {
+
+template <typename T>
+struct Acc;  // edge/tendency accumulator: plain in FP64, compensated (TwoSum) in FP32
+
+template <>
+struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+template <>
+struct Acc<float> {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float x) {
+    float t = s + x;
+    float bp = t - s;
+    c += (s - (t - bp)) + (x - bp);  // Knuth TwoSum error term
+    s = t;
+  }
+  __device__ __forceinline__ float value() const { return s + c; }
+};
+
+template <typename T>
+__device__ __forceinline__ T rcp(T x) { return T(1) / x; }
+
+// ---------------------------------------------------------------------------------
+// Ghost fill: one warp per ghost cell, lanes stride over the row's nonzeros.
+// ---------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_ghost(const T *__restrict__ q, T *__restrict__ gext,
+                                               const int *__restrict__ grow, const int *__restrict__ gcol,
+                                               const T *__restrict__ gval, const int *__restrict__ gdst,
+                                               int rows, int N, int ne) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= rows) return;
+  size_t pn = (size_t)6 * N * N, pe = (size_t)6 * ne * ne;
+  int b = grow[warp], e = grow[warp + 1];
+  T s0 = 0, s1 = 0, s2 = 0;
+  for (int t = b + lane; t < e; t += 32) {
+    int c = gcol[t];
+    const T *w = gval + (size_t)t * 5;
+    T a0 = q[c], a1 = q[pn + c], a2 = q[2 * pn + c];
+    s0 += w[0] * a0;
+    s1 += w[1] * a1 + w[2] * a2;
+    s2 += w[3] * a1 + w[4] * a2;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  if (lane == 0) {
+    int d = gdst[warp];
+    gext[d] = s0;
+    gext[pe + d] = s1;
+    gext[2 * pe + d] = s2;
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// TPP reconstruction + cell-point sources.  Block = TX x TY cells of one panel.
+// ---------------------------------------------------------------------------------
+constexpr int REC_TX = 16;
+constexpr int REC_TY = 8;
+
+template <int K>
+struct Shape {
+  static constexpr int H = (K - 1) / 2;
+  static constexpr int ME = (K + 1) / 2;
+  static constexpr int NPOS = ME + 2;  // x-pass evaluation positions
+  static constexpr int RW = REC_TX + 2 * H;
+  static constexpr int RH = REC_TY + 2 * H;
+};
+
+template <typename T, int K>
+__host__ __device__ constexpr size_t recon_smem_bytes() {
+  using S = Shape<K>;
+  return sizeof(T) * (3 * S::RH * S::RW + 3 * S::NPOS * S::RH * REC_TX + S::NPOS * K);
+}
+
+// Load the extended tile of the 3 variables: interior cells from q, ring cells from gext.
+template <typename T, int K>
+__device__ __forceinline__ void load_tile(T *raw, const T *__restrict__ q, const T *__restrict__ gext,
+                                          int p, int i0, int j0, int N, int ne) {
+  using S = Shape<K>;
+  size_t pn = (size_t)6 * N * N, pe = (size_t)6 * ne * ne;
+  for (int idx = threadIdx.x; idx < 3 * S::RH * S::RW; idx += blockDim.x) {
+    int v = idx / (S::RH * S::RW);
+    int rem = idx - v * S::RH * S::RW;
+    int r = rem / S::RW, c = rem - r * S::RW;
+    int i = i0 + c - S::H, j = j0 + r - S::H;
+    T val = T(0);
+    if (i >= 0 && i < N && j >= 0 && j < N)
+      val = q[v * pn + ((size_t)p * N + j) * N + i];
+    else if (i >= -S::H && i < N + S::H && j >= -S::H && j < N + S::H)
+      val = gext[v * pe + ((size_t)p * ne + (j + S::H)) * ne + (i + S::H)];
+    raw[idx] = val;
+  }
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(REC_TX *REC_TY)
+    k_recon_tpp(const T *__restrict__ q, const T *__restrict__ gext, const T *__restrict__ w1g,
+                const T *__restrict__ Xg, const T *__restrict__ t1w, T *__restrict__ ep,
+                T *__restrict__ sb, int N, int ne, T omega) {
+  using S = Shape<K>;
+  constexpr int ME = S::ME, NPOS = S::NPOS, H = S::H;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *raw = reinterpret_cast<T *>(smem_raw);              // [3][RH][RW]
+  T *xs = raw + 3 * S::RH * S::RW;                        // [3][NPOS][RH][TX]
+  T *w1 = xs + 3 * NPOS * S::RH * REC_TX;                 // [NPOS][K]
+  const int p = blockIdx.z;
+  const int i0 = blockIdx.x * REC_TX, j0 = blockIdx.y * REC_TY;
+  for (int t = threadIdx.x; t < NPOS * K; t += blockDim.x) w1[t] = w1g[t];
+  load_tile<T, K>(raw, q, gext, p, i0, j0, N, ne);
+  __syncthreads();
+  // x-pass: every row of the extended tile, every tile column, NPOS positions
+  for (int idx = threadIdx.x; idx < 3 * S::RH * REC_TX; idx += blockDim.x) {
+    int v = idx / (S::RH * REC_TX);
+    int rem = idx - v * S::RH * REC_TX;
+    int r = rem / REC_TX, c = rem - r * REC_TX;
+    const T *row = raw + (v * S::RH + r) * S::RW + c;
+    T a[K];
+#pragma unroll
+    for (int b = 0; b < K; ++b) a[b] = row[b];
+#pragma unroll
+    for (int t = 0; t < NPOS; ++t) {
+      T s = 0;
+#pragma unroll
+      for (int b = 0; b < K; ++b) s = fma(w1[t * K + b], a[b], s);
+      xs[((v * NPOS + t) * S::RH + r) * REC_TX + c] = s;
+    }
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % REC_TX, ty = threadIdx.x / REC_TX;
+  const int i = i0 + tx, j = j0 + ty;
+  if (i >= N || j >= N) return;
+  const size_t pn = (size_t)6 * N * N;
+  const size_t cell = ((size_t)p * N + j) * N + i;
+  const T sgn_pole = (p == 4) ? T(1) : T(-1);
+  T s1 = 0, s2 = 0;
+#pragma unroll 1
+  for (int t = 0; t < NPOS; ++t) {
+    T col[3][K];
+#pragma unroll
+    for (int v = 0; v < 3; ++v)
+#pragma unroll
+      for (int b = 0; b < K; ++b) col[v][b] = xs[((v * NPOS + t) * S::RH + ty + b) * REC_TX + tx];
+    if (t < 2) {
+      // west (t = 0) / east (t = 1) edge points at the Gauss nodes in y
+#pragma unroll
+      for (int r = 0; r < ME; ++r)
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          T s = 0;
+#pragma unroll
+          for (int b = 0; b < K; ++b) s = fma(w1[(2 + r) * K + b], col[v][b], s);
+          ep[((size_t)(t * 3 + v) * ME + r) * pn + cell] = s;
+        }
+    } else {
+      const int g = t - 2;
+      // south / north edge points at x-node g
+#pragma unroll
+      for (int side = 0; side < 2; ++side)
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          T s = 0;
+#pragma unroll
+          for (int b = 0; b < K; ++b) s = fma(w1[side * K + b], col[v][b], s);
+          ep[((size_t)((2 + side) * 3 + v) * ME + g) * pn + cell] = s;
+        }
+      // cell points (g, h): metric (eq. 2.2) and Coriolis (eq. 2.3) sources
+      const T X = Xg[i * ME + g];
+#pragma unroll 1
+      for (int h = 0; h < ME; ++h) {
+        T qv[3];
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          T s = 0;
+#pragma unroll
+          for (int b = 0; b < K; ++b) s = fma(w1[(2 + h) * K + b], col[v][b], s);
+          qv[v] = s;
+        }
+        const T Y = Xg[j * ME + h];
+        const T tw = t1w[(((size_t)j * N + i) * ME + h) * ME + g];
+        const T sl = (p < 4) ? Y : sgn_pole;  // sin(latitude)*delta, eq. 2.5
+        const T rq = rcp(qv[0]);
+        const T XY = X * Y, X2 = X * X, Y2 = Y * Y;
+        const T os = omega * sl;
+        T a1 = (-XY * Y * qv[1] + Y * (T(1) + Y2) * qv[2]) * qv[1] * rq + os * (-XY * qv[1] + (T(1) + Y2) * qv[2]);
+        T a2 = (X * (T(1) + X2) * qv[1] - X2 * Y * qv[2]) * qv[2] * rq + os * (-(T(1) + X2) * qv[1] + XY * qv[2]);
+        s1 = fma(tw, a1, s1);
+        s2 = fma(tw, a2, s2);
+      }
+    }
+  }
+  sb[cell] = s1;
+  sb[pn + cell] = s2;
+}
+
+// ---------------------------------------------------------------------------------
+// LMARS flux at one edge point (eqs. 3.31-3.38) from table metric terms:
+// m5 = {1/sqrtG, sqrt(G^nn), 1/sqrt(G^nn), sqrtG G^nn/2, sqrtG G^nc/2} (true metric).
+// dir 0: x-edge (normal momentum var 1), 1: y-edge (var 2).
+// ---------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void lmars(const T qL[3], const T qR[3], const T *m5, int dir, T F[3],
+                                      unsigned *status) {
+  const T isg = m5[0], s11 = m5[1], is11 = m5[2], pn = m5[3], pc = m5[4];
+  const T phL = qL[0] * isg, phR = qR[0] * isg;
+  if (!(phL > T(0)) || !(phR > T(0))) atomicOr(status, HOPE_STATUS_NONPHYS_PHI);
+  const int n = 1 + dir;
+  const T uL = qL[n] * rcp(qL[0]) * is11, uR = qR[n] * rcp(qR[0]) * is11;
+  const T c = T(0.5) * (sqrt(phL) + sqrt(phR));
+  const T ms = T(0.5) * (uL + uR - (phR - phL) * rcp(c));
+  const T ph = T(0.5) * (phL + phR - c * (uR - uL));
+  const T m = ms * s11;
+  const T am = fabs(m);
+#pragma unroll
+  for (int v = 0; v < 3; ++v) F[v] = T(0.5) * (m * (qL[v] + qR[v]) - am * (qR[v] - qL[v]));
+  const T p2 = ph * ph;
+  F[1 + dir] += pn * p2;
+  F[2 - dir] += pc * p2;
+}
+
+// ---------------------------------------------------------------------------------
+// Edge fluxes: interior x-edges, interior y-edges, then the 12 cube edges x N cells.
+// ---------------------------------------------------------------------------------
+template <typename T, int ME>
+__global__ void __launch_bounds__(256)
+    k_flux(const T *__restrict__ ep, const T *__restrict__ mx, const T *__restrict__ gwg,
+           const int *__restrict__ bedge, const T *__restrict__ bconv, T *__restrict__ fx,
+           T *__restrict__ fy, int N, unsigned *status) {
+  const long long nx = 6LL * N * (N - 1), ny = nx, nb = 12LL * N;
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nx + ny + nb) return;
+  const size_t pn = (size_t)6 * N * N;
+  const size_t fe = (size_t)6 * N * (N + 1);
+  T gw[ME];
+#pragma unroll
+  for (int g = 0; g < ME; ++g) gw[g] = gwg[g];
+  if (idx < nx + ny) {
+    const int dir = idx < nx ? 0 : 1;
+    long long r = dir ? idx - nx : idx;
+    // x-edge: (p, j, e=1..N-1), e fastest; y-edge: (p, e=1..N-1, i), i fastest
+    int p, a, e;  // a = row j (x) / column i (y)
+    if (dir == 0) {
+      e = 1 + (int)(r % (N - 1));
+      long long t = r / (N - 1);
+      a = (int)(t % N);
+      p = (int)(t / N);
+    } else {
+      a = (int)(r % N);
+      long long t = r / N;
+      e = 1 + (int)(t % (N - 1));
+      p = (int)(t / (N - 1));
+    }
+    size_t cl, cr;  // left / right (below / above) cells
+    if (dir == 0) {
+      cl = ((size_t)p * N + a) * N + (e - 1);
+      cr = cl + 1;
+    } else {
+      cl = ((size_t)p * N + (e - 1)) * N + a;
+      cr = cl + N;
+    }
+    const int sl = dir ? 3 : 1, sr = dir ? 2 : 0;
+    Acc<T> acc[3];
+#pragma unroll
+    for (int g = 0; g < ME; ++g) {
+      T qL[3], qR[3], F[3];
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        qL[v] = ep[((size_t)(sl * 3 + v) * ME + g) * pn + cl];
+        qR[v] = ep[((size_t)(sr * 3 + v) * ME + g) * pn + cr];
+      }
+      lmars(qL, qR, mx + (((size_t)e * N + a) * ME + g) * 5, dir, F, status);
+#pragma unroll
+      for (int v = 0; v < 3; ++v) acc[v].add(gw[g] * F[v]);
+    }
+    if (dir == 0) {
+#pragma unroll
+      for (int v = 0; v < 3; ++v) fx[v * fe + ((size_t)p * N + a) * (N + 1) + e] = acc[v].value();
+    } else {
+#pragma unroll
+      for (int v = 0; v < 3; ++v) fy[v * fe + ((size_t)p * (N + 1) + e) * N + a] = acc[v].value();
+    }
+    return;
+  }
+  // panel-boundary edge: cube edge ce, cell t along it
+  long long r = idx - nx - ny;
+  const int ce = (int)(r / N), t = (int)(r % N);
+  const int A = bedge[ce * 5 + 0], sA = bedge[ce * 5 + 1], B = bedge[ce * 5 + 2], sB = bedge[ce * 5 + 3],
+            flip = bedge[ce * 5 + 4];
+  const int tB = flip ? N - 1 - t : t;
+  auto side_cell = [N](int P, int side, int tt) -> size_t {
+    int ci = side == 0 ? 0 : (side == 1 ? N - 1 : tt);
+    int cj = side == 2 ? 0 : (side == 3 ? N - 1 : tt);
+    return ((size_t)P * N + cj) * N + ci;
+  };
+  const size_t cA = side_cell(A, sA, t), cB = side_cell(B, sB, tB);
+  const int dirA = sA >> 1, dirB = sB >> 1;
+  const T sgA = (sA & 1) ? T(1) : T(-1), sgB = (sB & 1) ? T(1) : T(-1);
+  const T sg = -sgA * sgB;
+  const int eA = (sA & 1) ? N : 0;
+  Acc<T> accA[3], accB[3];
+#pragma unroll
+  for (int g = 0; g < ME; ++g) {
+    const int gB = flip ? ME - 1 - g : g;
+    const T *cv = bconv + (((size_t)ce * N + t) * ME + g) * 9;
+    T qin[3], qb[3], qo[3], F[3];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      qin[v] = ep[((size_t)(sA * 3 + v) * ME + g) * pn + cA];
+      qb[v] = ep[((size_t)(sB * 3 + v) * ME + gB) * pn + cB];
+    }
+    qo[0] = cv[0] * qb[0];
+    qo[1] = cv[1] * qb[1] + cv[2] * qb[2];
+    qo[2] = cv[3] * qb[1] + cv[4] * qb[2];
+    const T *m5 = mx + (((size_t)eA * N + t) * ME + g) * 5;
+    if (sA & 1)
+      lmars(qin, qo, m5, dirA, F, status);
+    else
+      lmars(qo, qin, m5, dirA, F, status);
+#pragma unroll
+    for (int v = 0; v < 3; ++v) accA[v].add(gw[g] * F[v]);
+    accB[1].add(gw[gB] * sg * (cv[5] * F[1] + cv[6] * F[2]));
+    accB[2].add(gw[gB] * sg * (cv[7] * F[1] + cv[8] * F[2]));
+  }
+  const T fA0 = accA[0].value();
+  const T outA[3] = {fA0, accA[1].value(), accA[2].value()};
+  const T outB[3] = {sg * fA0, accB[1].value(), accB[2].value()};
+  const int eB = (sB & 1) ? N : 0;
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    if (dirA == 0)
+      fx[v * fe + ((size_t)A * N + t) * (N + 1) + eA] = outA[v];
+    else
+      fy[v * fe + ((size_t)A * (N + 1) + eA) * N + t] = outA[v];
+    if (dirB == 0)
+      fx[v * fe + ((size_t)B * N + tB) * (N + 1) + eB] = outB[v];
+    else
+      fy[v * fe + ((size_t)B * (N + 1) + eB) * N + tB] = outB[v];
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Tendency (eq. 3.1) and the Runge-Kutta stage combination:
+//   mode 0: out = L
+//   mode 1: out = a*q0 + b*qs + c*L
+// ---------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_update(const T *__restrict__ fx, const T *__restrict__ fy, const T *__restrict__ sb,
+             const T *q0, const T *qs, T *out, int N, T inv_dx, int mode, T a, T b, T c,
+             unsigned *status) {
+  const long long ncell = 6LL * N * N;
+  long long cid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cid >= ncell) return;
+  const int i = (int)(cid % N);
+  const long long pj = cid / N;  // p*N + j
+  const int j = (int)(pj % N), p = (int)(pj / N);
+  const size_t fe = (size_t)6 * N * (N + 1);
+  bool bad = false;
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    const T *fxv = fx + v * fe + (size_t)pj * (N + 1);
+    const T *fyv = fy + v * fe + ((size_t)p * (N + 1) + j) * N + i;
+    Acc<T> acc;
+    acc.add(-(fxv[i + 1] - fxv[i]) * inv_dx);
+    acc.add(-(fyv[N] - fyv[0]) * inv_dx);
+    if (v > 0) acc.add(sb[(v - 1) * ncell + cid]);
+    T L = acc.value();
+    T r;
+    if (mode == 0) {
+      r = L;
+    } else {
+      r = a * q0[v * ncell + cid] + b * qs[v * ncell + cid] + c * L;
+    }
+    bad |= !isfinite(r);
+    out[v * ncell + cid] = r;
+  }
+  if (bad) atomicOr(status, HOPE_STATUS_NAN);
+}
+
+// ---------------------------------------------------------------------------------
+// Deterministic FP64 mass sum: fixed per-block ranges, then an ordered final pass.
+// ---------------------------------------------------------------------------------
+constexpr int MASS_BLOCKS = 152;
+constexpr int MASS_THREADS = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(MASS_THREADS) k_mass_partial(const T *__restrict__ q, long long n,
+                                                               double *__restrict__ part) {
+  __shared__ double red[MASS_THREADS];
+  long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  long long b = blockIdx.x * chunk, e = b + chunk < n ? b + chunk : n;
+  double s = 0.0;
+  for (long long t = b + threadIdx.x; t < e; t += blockDim.x) s += (double)q[t];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = MASS_THREADS / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_mass_final(const double *__restrict__ part, int nparts, double scale, double *out);
+
+}  // namespace hope

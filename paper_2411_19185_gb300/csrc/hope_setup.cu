@@ -1,0 +1,412 @@
+// hope_setup.cu -- per-grid table construction of the HOPE GB300 library (setup only,
+// never on the per-stage path): device-side FP64 tables (1-D reconstruction weights,
+// metric terms), host-side assembly of the ghost operator G (appendix eq. 7.12) and of
+// the cube-edge topology.
+#include <math.h>
+#include <omp.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "hope_internal.h"
+#include "hope_setup.h"
+#include "hope_setup_math.cuh"
+
+namespace hope {
+
+// -------------------------------------------------------------------------------
+// Device setup kernels (FP64), writing tables in the context precision T.
+// -------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_setup_order(int K, int me, T *w1, T *gw, double *nodes_out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double x[HOPE_MAXME], w[HOPE_MAXME], r[HOPE_MAXK];
+  gauss_legendre(me, x, w);
+  const int H = (K - 1) / 2;
+  for (int t = 0; t < me + 2; ++t) {
+    double xi = t == 0 ? -0.5 : (t == 1 ? 0.5 : x[t - 2]);
+    cell_avg_weights(K, -H, xi, r);
+    for (int b = 0; b < K; ++b) w1[t * K + b] = (T)r[b];
+  }
+  for (int g = 0; g < me; ++g) {
+    gw[g] = (T)w[g];
+    nodes_out[g] = x[g];
+    nodes_out[me + g] = w[g];
+  }
+}
+
+template <typename T>
+__global__ void k_setup_grid(int N, int me, double radius, const double *__restrict__ nw, T *Xg, T *t1w,
+                             T *mx) {
+  const double dx = HOPE_PI / (2.0 * N);
+  const double r2 = radius * radius;
+  const long long nX = (long long)N * me, nT = (long long)N * N * me * me, nM = (long long)(N + 1) * N * me;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nX + nT + nM;
+       idx += (long long)gridDim.x * blockDim.x) {
+    if (idx < nX) {
+      int i = (int)(idx / me), g = (int)(idx % me);
+      Xg[idx] = (T)tan(-HOPE_QPI + (i + 0.5 + nw[g]) * dx);
+    } else if (idx < nX + nT) {
+      long long r = idx - nX;
+      int g = (int)(r % me);
+      long long t = r / me;
+      int h = (int)(t % me);
+      t /= me;
+      int i = (int)(t % N), j = (int)(t / N);
+      double X = tan(-HOPE_QPI + (i + 0.5 + nw[g]) * dx);
+      double Y = tan(-HOPE_QPI + (j + 0.5 + nw[h]) * dx);
+      t1w[r] = (T)(2.0 / (1.0 + X * X + Y * Y) * nw[me + g] * nw[me + h]);
+    } else {
+      long long r = idx - nX - nT;
+      int g = (int)(r % me);
+      long long t = r / me;
+      int j = (int)(t % N), e = (int)(t / N);
+      double X = tan(-HOPE_QPI + e * dx);
+      double Y = tan(-HOPE_QPI + (j + 0.5 + nw[g]) * dx);
+      double d2 = 1.0 + X * X + Y * Y, d = sqrt(d2);
+      double sg = (1.0 + X * X) * (1.0 + Y * Y) / (d2 * d);
+      double g11 = d2 / (1.0 + X * X);  // unit-sphere G^11 (eq. 2.6)
+      double s11 = sqrt(g11) / radius;
+      T *o = mx + r * 5;
+      o[0] = (T)(1.0 / sg);
+      o[1] = (T)s11;
+      o[2] = (T)(1.0 / s11);
+      o[3] = (T)(0.5 * (1.0 + Y * Y) / (d * r2));  // sqrtG G^11 / 2 (true metric)
+      o[4] = (T)(0.5 * X * Y / (d * r2));          // sqrtG G^12 / 2
+    }
+  }
+}
+
+template __global__ void k_setup_order<double>(int, int, double *, double *, double *);
+template __global__ void k_setup_order<float>(int, int, float *, float *, double *);
+template __global__ void k_setup_grid<double>(int, int, double, const double *, double *, double *, double *);
+template __global__ void k_setup_grid<float>(int, int, double, const double *, float *, float *, float *);
+
+int setup_order_tables(hope_ctx *ctx, std::vector<double> &nodes, std::vector<double> &weights) {
+  const int K = ctx->k, me = ctx->me;
+  double *d_nw = nullptr;
+  if (cudaMalloc(&d_nw, sizeof(double) * 2 * me) != cudaSuccess) return HOPE_ENOMEM;
+  if (cudaMalloc(&ctx->w1, ctx->esize * (me + 2) * K) != cudaSuccess) return HOPE_ENOMEM;
+  if (cudaMalloc(&ctx->gw, ctx->esize * me) != cudaSuccess) return HOPE_ENOMEM;
+  if (ctx->prec == HOPE_FP64)
+    k_setup_order<double><<<1, 1>>>(K, me, (double *)ctx->w1, (double *)ctx->gw, d_nw);
+  else
+    k_setup_order<float><<<1, 1>>>(K, me, (float *)ctx->w1, (float *)ctx->gw, d_nw);
+  std::vector<double> nw(2 * me);
+  if (cudaMemcpy(nw.data(), d_nw, sizeof(double) * 2 * me, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaFree(d_nw);
+    return HOPE_ECUDA;
+  }
+  cudaFree(d_nw);
+  nodes.assign(nw.begin(), nw.begin() + me);
+  weights.assign(nw.begin() + me, nw.end());
+  return HOPE_OK;
+}
+
+int setup_grid_tables(hope_ctx *ctx, Grid &gr, const std::vector<double> &nodes,
+                      const std::vector<double> &weights) {
+  const int N = gr.N, me = ctx->me;
+  std::vector<double> nw(nodes);
+  nw.insert(nw.end(), weights.begin(), weights.end());
+  double *d_nw = nullptr;
+  if (cudaMalloc(&d_nw, sizeof(double) * 2 * me) != cudaSuccess) return HOPE_ENOMEM;
+  cudaMemcpy(d_nw, nw.data(), sizeof(double) * 2 * me, cudaMemcpyHostToDevice);
+  size_t es = ctx->esize;
+  if (cudaMalloc(&gr.Xg, es * N * me) != cudaSuccess) return HOPE_ENOMEM;
+  if (cudaMalloc(&gr.t1w, es * (size_t)N * N * me * me) != cudaSuccess) return HOPE_ENOMEM;
+  if (cudaMalloc(&gr.mx, es * (size_t)(N + 1) * N * me * 5) != cudaSuccess) return HOPE_ENOMEM;
+  if (ctx->prec == HOPE_FP64)
+    k_setup_grid<double><<<256, 256>>>(N, me, ctx->radius, d_nw, (double *)gr.Xg, (double *)gr.t1w,
+                                       (double *)gr.mx);
+  else
+    k_setup_grid<float><<<256, 256>>>(N, me, ctx->radius, d_nw, (float *)gr.Xg, (float *)gr.t1w,
+                                      (float *)gr.mx);
+  cudaError_t e = cudaDeviceSynchronize();
+  cudaFree(d_nw);
+  return e == cudaSuccess ? HOPE_OK : HOPE_ECUDA;
+}
+
+// -------------------------------------------------------------------------------
+// Host assembly of the ghost operator: the map from interior cells to ghost cells
+// obtained by `iters` Jacobi sweeps of the ghost interpolation from zero
+// (section 3.3.1): each sweep interpolates every ghost Gauss point with the owning
+// panel's central TPP stencil (reading that panel's ghosts of the previous sweep),
+// converts it (eqs. 3.26-3.29) and averages (eq. 3.6).  Composed symbolically: a
+// row of G holds, per source cell, a mass weight and a 2x2 momentum block.
+// -------------------------------------------------------------------------------
+namespace {
+struct Ent {
+  int col;
+  double m, c[4];
+};
+struct LocalEnt {
+  int idx;     // interior cell id, or ghost row id
+  bool ghost;
+  double m, c[4];
+};
+}  // namespace
+
+int build_ghost_operator(const hope_ctx *ctx, int N, const std::vector<double> &nodes,
+                         const std::vector<double> &weights, std::vector<int> &rowptr,
+                         std::vector<int> &cols, std::vector<double> &vals, std::vector<int> &dst) {
+  const int K = ctx->k, H = ctx->H, me = ctx->me, ne = N + 2 * H;
+  const double dx = HOPE_PI / (2.0 * N);
+  // ring enumeration
+  std::vector<int> rowid((size_t)6 * ne * ne, -1);
+  dst.clear();
+  for (int p = 0; p < 6; ++p)
+    for (int jj = 0; jj < ne; ++jj)
+      for (int ii = 0; ii < ne; ++ii) {
+        int i = ii - H, j = jj - H;
+        if (i >= 0 && i < N && j >= 0 && j < N) continue;
+        rowid[((size_t)p * ne + jj) * ne + ii] = (int)dst.size();
+        dst.push_back((p * ne + jj) * ne + ii);
+      }
+  const int rows = (int)dst.size();
+  // local operators
+  std::vector<std::vector<LocalEnt>> loc(rows);
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int r = 0; r < rows; ++r) {
+    int p = dst[r] / (ne * ne), rem = dst[r] % (ne * ne), jj = rem / ne, ii = rem % ne;
+    int i = ii - H, j = jj - H;
+    std::vector<LocalEnt> acc;
+    acc.reserve((K + 2) * (K + 2));
+    for (int h = 0; h < me; ++h)
+      for (int g = 0; g < me; ++g) {
+        double x = -HOPE_QPI + (i + 0.5 + nodes[g]) * dx;
+        double y = -HOPE_QPI + (j + 0.5 + nodes[h]) * dx;
+        double X = tan(x), Y = tan(y), P[3], XB, YB;
+        panel_point(p, X, Y, P);
+        int B = face_of(P, -1);
+        if (B == p) {
+#pragma omp atomic
+          ++bad;
+          continue;
+        }
+        panel_coords(B, P, &XB, &YB);
+        double xb = atan(XB), yb = atan(YB);
+        int ic = (int)floor((xb + HOPE_QPI) / dx), jc = (int)floor((yb + HOPE_QPI) / dx);
+        ic = ic < 0 ? 0 : (ic > N - 1 ? N - 1 : ic);
+        jc = jc < 0 ? 0 : (jc > N - 1 ? N - 1 : jc);
+        double xi = (xb - (-HOPE_QPI + (ic + 0.5) * dx)) / dx;
+        double eta = (yb - (-HOPE_QPI + (jc + 0.5) * dx)) / dx;
+        double wx[HOPE_MAXK], wy[HOPE_MAXK], ratio, C[4];
+        cell_avg_weights(K, -H, xi, wx);
+        cell_avg_weights(K, -H, eta, wy);
+        panel_conversion(p, X, Y, B, XB, YB, &ratio, C);
+        double W = weights[g] * weights[h];
+        for (int b = 0; b < K; ++b)
+          for (int a = 0; a < K; ++a) {
+            int ci = ic + a - H, cj = jc + b - H;
+            double wt = W * wx[a] * wy[b];
+            LocalEnt le;
+            if (ci >= 0 && ci < N && cj >= 0 && cj < N) {
+              le.ghost = false;
+              le.idx = (B * N + cj) * N + ci;
+            } else {
+              le.ghost = true;
+              le.idx = rowid[((size_t)B * ne + (cj + H)) * ne + (ci + H)];
+            }
+            le.m = wt * ratio;
+            for (int t = 0; t < 4; ++t) le.c[t] = wt * C[t];
+            bool merged = false;
+            for (auto &e : acc)
+              if (e.ghost == le.ghost && e.idx == le.idx) {
+                e.m += le.m;
+                for (int t = 0; t < 4; ++t) e.c[t] += le.c[t];
+                merged = true;
+                break;
+              }
+            if (!merged) acc.push_back(le);
+          }
+      }
+    loc[r] = std::move(acc);
+  }
+  if (bad) {
+    set_error("ghost operator: a ghost Gauss point maps back onto its own panel");
+    return HOPE_EINVAL;
+  }
+  // sweeps
+  const int ncell = 6 * N * N;
+  std::vector<std::vector<Ent>> G(rows), Gn(rows);
+  for (int it = 0; it < ctx->ghost_iters; ++it) {
+#pragma omp parallel
+    {
+      std::vector<double> am(ncell, 0.0), ac((size_t)4 * ncell, 0.0);
+      std::vector<int> mark(ncell, 0), touched;
+      touched.reserve(4096);
+#pragma omp for schedule(dynamic, 8)
+      for (int r = 0; r < rows; ++r) {
+        touched.clear();
+        auto add = [&](int col, double m, const double *c) {
+          if (!mark[col]) {
+            mark[col] = 1;
+            touched.push_back(col);
+          }
+          am[col] += m;
+          for (int t = 0; t < 4; ++t) ac[(size_t)4 * col + t] += c[t];
+        };
+        for (const auto &e : loc[r]) {
+          if (!e.ghost) {
+            add(e.idx, e.m, e.c);
+          } else {
+            for (const auto &s : G[e.idx]) {
+              double c[4] = {e.c[0] * s.c[0] + e.c[1] * s.c[2], e.c[0] * s.c[1] + e.c[1] * s.c[3],
+                             e.c[2] * s.c[0] + e.c[3] * s.c[2], e.c[2] * s.c[1] + e.c[3] * s.c[3]};
+              add(s.col, e.m * s.m, c);
+            }
+          }
+        }
+        std::sort(touched.begin(), touched.end());
+        std::vector<Ent> out;
+        out.reserve(touched.size());
+        for (int col : touched) {
+          Ent en;
+          en.col = col;
+          en.m = am[col];
+          for (int t = 0; t < 4; ++t) en.c[t] = ac[(size_t)4 * col + t];
+          bool nz = en.m != 0.0 || en.c[0] != 0.0 || en.c[1] != 0.0 || en.c[2] != 0.0 || en.c[3] != 0.0;
+          if (nz) out.push_back(en);
+          am[col] = 0.0;
+          for (int t = 0; t < 4; ++t) ac[(size_t)4 * col + t] = 0.0;
+          mark[col] = 0;
+        }
+        Gn[r] = std::move(out);
+      }
+    }
+    std::swap(G, Gn);
+  }
+  // Drop the negligible tail of every row: entries whose largest weight is below
+  // drop_rel times the row's largest weight (contributions of deep sweeps, which decay
+  // geometrically).  The dropped weights sum to well under the precision's rounding
+  // unit relative to the row (FP64: 1e-17, FP32: 1e-9 relative cut-off).
+  const double drop_rel = ctx->prec == HOPE_FP64 ? 1e-17 : 1e-9;
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int r = 0; r < rows; ++r) {
+    double mx = 0.0;
+    auto emax = [](const Ent &e) {
+      double m = fabs(e.m);
+      for (int t = 0; t < 4; ++t) m = fmax(m, fabs(e.c[t]));
+      return m;
+    };
+    for (const auto &e : G[r]) mx = fmax(mx, emax(e));
+    std::vector<Ent> kept;
+    kept.reserve(G[r].size());
+    for (const auto &e : G[r])
+      if (emax(e) >= drop_rel * mx) kept.push_back(e);
+    G[r] = std::move(kept);
+  }
+  rowptr.assign(rows + 1, 0);
+  for (int r = 0; r < rows; ++r) rowptr[r + 1] = rowptr[r] + (int)G[r].size();
+  cols.resize(rowptr[rows]);
+  vals.resize((size_t)5 * rowptr[rows]);
+  for (int r = 0; r < rows; ++r) {
+    int o = rowptr[r];
+    for (size_t t = 0; t < G[r].size(); ++t) {
+      cols[o + t] = G[r][t].col;
+      vals[(size_t)5 * (o + t)] = G[r][t].m;
+      for (int u = 0; u < 4; ++u) vals[(size_t)5 * (o + t) + 1 + u] = G[r][t].c[u];
+    }
+  }
+  return HOPE_OK;
+}
+
+// -------------------------------------------------------------------------------
+// Cube-edge topology and per-point conversions for the panel-boundary fluxes.
+// -------------------------------------------------------------------------------
+static void edge_coords(int N, int side, int t, double node, double *x, double *y) {
+  double dx = HOPE_PI / (2.0 * N);
+  double along = -HOPE_QPI + (t + 0.5 + node) * dx;
+  switch (side) {
+    case 0: *x = -HOPE_QPI; *y = along; break;
+    case 1: *x = HOPE_QPI; *y = along; break;
+    case 2: *x = along; *y = -HOPE_QPI; break;
+    default: *x = along; *y = HOPE_QPI; break;
+  }
+}
+
+int build_cube_edges(const hope_ctx *ctx, int N, const std::vector<double> &nodes, CubeEdge edges[12],
+                     std::vector<double> &conv) {
+  const int me = ctx->me;
+  const double dx = HOPE_PI / (2.0 * N);
+  int ne = 0;
+  conv.assign((size_t)12 * N * me * 9, 0.0);
+  for (int A = 0; A < 6; ++A)
+    for (int sA = 0; sA < 4; ++sA) {
+      int B = -1, sB = -1, flip = -1;
+      for (int t = 0; t < N; ++t)
+        for (int g = 0; g < me; ++g) {
+          double x, y, P[3], XB, YB;
+          edge_coords(N, sA, t, nodes[g], &x, &y);
+          double XA = tan(x), YA = tan(y);
+          panel_point(A, XA, YA, P);
+          int b = face_of(P, A);
+          panel_coords(b, P, &XB, &YB);
+          double xb = atan(XB), yb = atan(YB), along;
+          int s;
+          if (fabs(xb) > fabs(yb)) {
+            s = xb < 0 ? 0 : 1;
+            along = yb;
+          } else {
+            s = yb < 0 ? 2 : 3;
+            along = xb;
+          }
+          int tb = (int)floor((along + HOPE_QPI) / dx);
+          tb = tb < 0 ? 0 : (tb > N - 1 ? N - 1 : tb);
+          double eta = (along - (-HOPE_QPI + (tb + 0.5) * dx)) / dx;
+          int gb = 0;
+          for (int u = 1; u < me; ++u)
+            if (fabs(nodes[u] - eta) < fabs(nodes[gb] - eta)) gb = u;
+          if (fabs(nodes[gb] - eta) > 1e-8) {
+            set_error("cube edges: edge Gauss points do not coincide across panels");
+            return HOPE_EINVAL;
+          }
+          int f = (tb == t && gb == g) ? 0 : ((tb == N - 1 - t && gb == me - 1 - g) ? 1 : -1);
+          if (t == 0 && g == 0) {
+            B = b;
+            sB = s;
+            flip = f;
+          }
+          if (b != B || s != sB || f != flip || f < 0) {
+            set_error("cube edges: inconsistent neighbour along a panel side");
+            return HOPE_EINVAL;
+          }
+          if (A < B) {
+            double ratio, C[4], r2, Ci[4];
+            panel_conversion(A, XA, YA, B, XB, YB, &ratio, C);
+            panel_conversion(B, XB, YB, A, XA, YA, &r2, Ci);
+            double *o = &conv[(((size_t)ne * N + t) * me + g) * 9];
+            o[0] = ratio;
+            for (int u = 0; u < 4; ++u) {
+              o[1 + u] = C[u];
+              o[5 + u] = Ci[u];
+            }
+          }
+        }
+      if (A < B) {
+        if (ne >= 12) {
+          set_error("cube edges: more than 12 edges");
+          return HOPE_EINVAL;
+        }
+        edges[ne++] = CubeEdge{A, sA, B, sB, flip};
+      }
+    }
+  if (ne != 12) {
+    set_error("cube edges: expected 12 edges");
+    return HOPE_EINVAL;
+  }
+  return HOPE_OK;
+}
+
+}  // namespace hope
+
+namespace hope {
+int setup_weno_tables(hope_ctx *ctx, const std::vector<double> &nodes) {
+  (void)ctx;
+  (void)nodes;
+  set_error("WENO2D tables are not available in this build");
+  return HOPE_EUNSUPPORTED;
+}
+}  // namespace hope

@@ -1,0 +1,17 @@
+// hope_setup.h -- setup entry points shared between the library's translation units.
+#pragma once
+#include <vector>
+
+#include "hope_internal.h"
+
+namespace hope {
+int setup_order_tables(hope_ctx *ctx, std::vector<double> &nodes, std::vector<double> &weights);
+int setup_grid_tables(hope_ctx *ctx, Grid &gr, const std::vector<double> &nodes,
+                      const std::vector<double> &weights);
+int build_ghost_operator(const hope_ctx *ctx, int N, const std::vector<double> &nodes,
+                         const std::vector<double> &weights, std::vector<int> &rowptr,
+                         std::vector<int> &cols, std::vector<double> &vals, std::vector<int> &dst);
+int build_cube_edges(const hope_ctx *ctx, int N, const std::vector<double> &nodes, CubeEdge edges[12],
+                     std::vector<double> &conv);
+int setup_weno_tables(hope_ctx *ctx, const std::vector<double> &nodes);
+}  // namespace hope

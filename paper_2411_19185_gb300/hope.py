@@ -1,0 +1,146 @@
+"""Thin PyTorch-facing wrapper of the HOPE C ABI (include/hope.h).
+
+PyTorch provides device memory and streams only; every step of the path runs in the
+library's CUDA kernels.  Tensors must be contiguous CUDA tensors of the context's dtype
+with hope_state_elems() elements (shape (3, 6, N, N) for one sphere).
+"""
+import ctypes
+
+import torch
+
+from . import _lib as L
+
+IC_GEOSTROPHIC, IC_ROSSBY, IC_DAMBREAK, IC_BUMPS = 2, 6, 7, 8
+RADIUS, GRAVITY, OMEGA = 6.37122e6, 9.80616, 7.292e-5
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t, ctx):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous() or t.dtype != ctx.dtype or t.numel() != ctx.elems:
+        raise ValueError("expected a contiguous CUDA %s tensor of %d elements" % (ctx.dtype, ctx.elems))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Sphere:
+    """One HOPE context: a cubed sphere (or an ensemble of spheres) with its tables."""
+
+    def __init__(self, N, order, scheme=L.HOPE_TPP, precision=L.HOPE_FP64, rk=L.HOPE_SSPRK3,
+                 ghost_iters=10, radius=RADIUS, gravity=GRAVITY, omega=OMEGA, weno_eps=0.0):
+        lib = L.load()
+        p = L.default_params()
+        p.radius, p.gravity, p.omega = radius, gravity, omega
+        p.precision, p.rk, p.ghost_iters, p.weno_eps = precision, rk, ghost_iters, weno_eps
+        h = ctypes.c_void_p()
+        if isinstance(N, (list, tuple)):
+            arr = (ctypes.c_int * len(N))(*N)
+            L.check(lib.hope_init_ensemble(len(N), arr, order, scheme, ctypes.byref(p), ctypes.byref(h)))
+            self.members = list(N)
+        else:
+            L.check(lib.hope_init_grid(int(N), order, scheme, ctypes.byref(p), ctypes.byref(h)))
+            self.members = [int(N)]
+        self._h = h
+        self.N = self.members[0]
+        self.order, self.scheme, self.precision = order, scheme, precision
+        self.radius, self.gravity, self.omega = radius, gravity, omega
+        self.dtype = torch.float64 if precision == L.HOPE_FP64 else torch.float32
+        self.elems = lib.hope_state_elems(h)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            L.load().hope_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ state
+    @property
+    def shape(self):
+        if len(self.members) == 1:
+            return (3, 6, self.N, self.N)
+        return (self.elems,)
+
+    def empty(self, device="cuda"):
+        return torch.empty(self.shape, dtype=self.dtype, device=device)
+
+    def initial_state(self, case, params, extra=None):
+        q = self.empty()
+        prm = (ctypes.c_double * len(params))(*params)
+        ex = list(extra) if extra is not None else []
+        exa = (ctypes.c_double * max(1, len(ex)))(*ex)
+        L.check(L.load().hope_initial_state(self._h, case, prm, len(params), exa, len(ex),
+                                            ctypes.c_void_p(q.data_ptr()), _stream()))
+        return q
+
+    def geostrophic(self, alpha=0.0, u0=None, phi0=2.94e4):
+        if u0 is None:
+            u0 = 2 * 3.141592653589793 * self.radius / (12 * 86400.0)
+        return self.initial_state(IC_GEOSTROPHIC, [alpha, u0, phi0])
+
+    def rossby_haurwitz(self, w=7.848e-6, K=7.848e-6, R=4.0, h0=8000.0):
+        return self.initial_state(IC_ROSSBY, [w, K, R, h0])
+
+    def dam_break(self, lon=0.0, lat=0.0, radius=0.3490658503988659, h_in=10.0, h_out=1.0):
+        return self.initial_state(IC_DAMBREAK, [lon, lat, radius, h_in, h_out])
+
+    def bumps(self, centres, alpha=0.0, amp=50.0, radius=0.08726646259971647, u0=None, phi0=2.94e4):
+        if u0 is None:
+            u0 = 2 * 3.141592653589793 * self.radius / (12 * 86400.0)
+        flat = [float(v) for c in centres for v in c]
+        return self.initial_state(IC_BUMPS, [alpha, u0, phi0, amp, radius], flat)
+
+    # ------------------------------------------------------------------ operator
+    def tendency(self, q, out=None):
+        if out is None:
+            out = torch.empty_like(q)
+        L.check(L.load().hope_tendency(self._h, _ptr(q, self), _ptr(out, self), _stream()))
+        return out
+
+    def step(self, q, dt, nsteps=1):
+        """nsteps RK steps in place on q (a CUDA tensor)."""
+        L.check(L.load().hope_step(self._h, _ptr(q, self), float(dt), int(nsteps), _stream()))
+        return q
+
+    def step_host(self, q_host, dt, nsteps=1, out=None):
+        """End-to-end step on host memory (copies inside the call); returns out."""
+        if q_host.is_cuda or not q_host.is_contiguous() or q_host.dtype != self.dtype:
+            raise ValueError("expected a contiguous host tensor of the context dtype")
+        if out is None:
+            out = torch.empty_like(q_host)
+        L.check(L.load().hope_step_host(self._h, ctypes.c_void_p(q_host.data_ptr()),
+                                        ctypes.c_void_p(out.data_ptr()), float(dt), int(nsteps), _stream()))
+        return out
+
+    def mass(self, q):
+        m = (ctypes.c_double * len(self.members))()
+        L.check(L.load().hope_total_mass(self._h, _ptr(q, self), m, _stream()))
+        return m[0] if len(self.members) == 1 else list(m)
+
+    def status(self):
+        s = ctypes.c_uint()
+        L.check(L.load().hope_status(self._h, ctypes.byref(s)))
+        return s.value
+
+    def ghost_nnz(self):
+        n, r = ctypes.c_longlong(), ctypes.c_longlong()
+        L.check(L.load().hope_ghost_nnz(self._h, ctypes.byref(n), ctypes.byref(r)))
+        return n.value, r.value
+
+    def launches_per_stage(self):
+        n = ctypes.c_int()
+        L.check(L.load().hope_launches_per_stage(self._h, ctypes.byref(n)))
+        return n.value
+
+
+def measure_fma_peak(precision):
+    r = ctypes.c_double()
+    L.check(L.load().hope_measure_fma_peak(precision, ctypes.byref(r)))
+    return r.value
