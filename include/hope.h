@@ -82,6 +82,11 @@ typedef struct {
   int rk;          /* HOPE_SSPRK3 (default) or HOPE_WSRK3 */
   int ghost_iters; /* sweeps of the ghost-cell iteration (section 3.3.1), default 10 */
   double weno_eps; /* epsilon of eq. 3.23; 0 => 1e-40 (FP64) / 1e-12 (FP32) */
+  double coriolis_tilt; /* tilt alpha_c of the rotation axis, default 0: f = 2 Omega sin(theta)
+                           (eq. 2.5); alpha_c != 0 gives f = 2 Omega (-cos(lambda) cos(theta)
+                           sin(alpha_c) + sin(theta) cos(alpha_c)), the Coriolis parameter
+                           under which the geostrophic case rotated by alpha = alpha_c
+                           (eqs. 5.1-5.3) is steady (Williamson et al. 1992, case 2) */
 } hope_params;
 
 /* Fill *p with the defaults above. */

@@ -449,6 +449,7 @@ typedef struct {
 struct orc {
   int N, k, H, me, npoc, scheme, l, s, ghost_iters, ne;
   double r, g, omega, eps, dx;
+  double alpha_c; /* tilt of the rotation axis (0: f = 2 Omega sin(theta), eq. 2.5) */
   double gx[MAXK], gw[MAXK];
   double *px, *py; /* [npoc] */
   double *R;       /* [npoc][k*k] */
@@ -804,6 +805,21 @@ void orc_lmars(const orc *o, int dir, double X, double Y, const double *qL, cons
   F[2] += 0.5 * sG * G2i * ph * ph;
 }
 
+/* Coriolis parameter.  With alpha_c = 0 it is 2 Omega sin(theta) with sin(theta)   */
+/* of eq. 2.5.  reading c21: for the geostrophic case rotated by alpha (eqs.        */
+/* 5.1-5.3 with alpha != 0) to stay steady, the rotation axis is tilted with it, as */
+/* in Williamson et al. (1992) case 2: f = 2 Omega (-cos(lambda) cos(theta)         */
+/* sin(alpha_c) + sin(theta) cos(alpha_c)).                                         */
+static double coriolis(const orc *o, int p, double X, double Y) {
+  if (o->alpha_c == 0.0) return 2.0 * o->omega * sin_lat(p, X, Y);
+  double xyz[3], lam, th;
+  orc_xyz(p, X, Y, xyz);
+  lonlat(xyz, &lam, &th);
+  return 2.0 * o->omega * (-cos(lam) * cos(th) * sin(o->alpha_c) + sin(th) * cos(o->alpha_c));
+}
+
+void orc_set_coriolis_tilt(orc *o, double alpha_c) { o->alpha_c = alpha_c; }
+
 /* Source terms (eqs. 2.2, 2.3; psi_B = 0 without topography) at one point of */
 /* panel p, unit-sphere scaling (both sides of eq. 2.1 divided by r^2).        */
 void orc_sources(const orc *o, int p, double X, double Y, const double *q, double *S) {
@@ -811,7 +827,7 @@ void orc_sources(const orc *o, int p, double X, double Y, const double *q, doubl
   orc_metric(X, Y, m7);
   double sG = m7[0], d2 = 1.0 + X * X + Y * Y;
   double phi = q[0] / sG, u = q[1] / q[0], v = q[2] / q[0];
-  double f = 2.0 * o->omega * sin_lat(p, X, Y);
+  double f = coriolis(o, p, X, Y);
   double pm1 = 2.0 * sG / d2 * (-X * Y * Y * phi * u * u + Y * (1.0 + Y * Y) * phi * u * v);
   double pm2 = 2.0 * sG / d2 * (X * (1.0 + X * X) * phi * u * v - X * X * Y * phi * v * v);
   double pc1 = sG * f * (-m7[2] * q[1] + m7[1] * q[2]);

@@ -49,6 +49,8 @@ typedef struct orc orc;
 orc *orc_new(int N, int k, int scheme, double radius, double gravity, double omega,
              double weno_eps, int ghost_iters);
 void orc_free(orc *o);
+/* Tilt the rotation axis by alpha_c (Williamson case-2 Coriolis parameter); 0 = eq. 2.5. */
+void orc_set_coriolis_tilt(orc *o, double alpha_c);
 int orc_npoc(const orc *o);
 int orc_halo(const orc *o);
 

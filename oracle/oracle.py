@@ -50,6 +50,7 @@ def lib():
         L.orc_new.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                               ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int]
         L.orc_free.argtypes = [vp]
+        L.orc_set_coriolis_tilt.argtypes = [vp, ctypes.c_double]
         L.orc_npoc.argtypes = [vp]
         L.orc_halo.argtypes = [vp]
         L.orc_tendency.argtypes = [vp, P, P]
@@ -95,12 +96,14 @@ class Oracle:
     """One grid of the oracle: N cells per panel edge, stencil width k (odd), scheme TPP/WENO."""
 
     def __init__(self, N, k, scheme=TPP, radius=RADIUS, gravity=GRAVITY, omega=OMEGA,
-                 weno_eps=1e-40, ghost_iters=10):
+                 weno_eps=1e-40, ghost_iters=10, coriolis_tilt=0.0):
         self.N, self.k, self.scheme = N, k, scheme
         self.radius, self.gravity, self.omega = radius, gravity, omega
         self._h = lib().orc_new(N, k, scheme, radius, gravity, omega, weno_eps, ghost_iters)
         if not self._h:
             raise ValueError("oracle: invalid grid N=%d k=%d" % (N, k))
+        lib().orc_set_coriolis_tilt(self._h, float(coriolis_tilt))
+        self.coriolis_tilt = float(coriolis_tilt)
         self.H = (k - 1) // 2
         self.me = (k + 1) // 2
         self.npoc = lib().orc_npoc(self._h)

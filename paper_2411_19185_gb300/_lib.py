@@ -27,7 +27,8 @@ EXPORTED = [
 class hope_params(ctypes.Structure):
     _fields_ = [("radius", ctypes.c_double), ("gravity", ctypes.c_double), ("omega", ctypes.c_double),
                 ("n_gauss", ctypes.c_int), ("precision", ctypes.c_int), ("rk", ctypes.c_int),
-                ("ghost_iters", ctypes.c_int), ("weno_eps", ctypes.c_double)]
+                ("ghost_iters", ctypes.c_int), ("weno_eps", ctypes.c_double),
+                ("coriolis_tilt", ctypes.c_double)]
 
 
 class HopeError(RuntimeError):

@@ -37,6 +37,13 @@ __global__ void k_mass_final(const double *__restrict__ part, int nparts, double
   }
 }
 
+template <typename T>
+static FCoef<T> fcoef(const hope_ctx *ctx) {
+  FCoef<T> f;
+  for (int t = 0; t < 18; ++t) f.c[t] = (T)ctx->fcoef[t];
+  return f;
+}
+
 // -------------------------------------------------------------------------------
 // One stage on one grid: out = L(qs) (mode 0) or a*q0 + b*qs + c*L(qs) (mode 1).
 // -------------------------------------------------------------------------------
@@ -58,7 +65,7 @@ static int stage_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *q0, T *out, 
     size_t smem = recon_smem_bytes<T, K>();
     k_recon_tpp<T, K><<<grid, REC_TX * REC_TY, smem, st>>>(qs, (const T *)g.gext, (const T *)ctx->w1,
                                                           (const T *)g.Xg, (const T *)g.t1w, (T *)g.ep,
-                                                          (T *)g.sb, N, ne, (T)ctx->omega);
+                                                          (T *)g.sb, N, ne, (T)ctx->omega, fcoef<T>(ctx));
   } else {
     int rc = launch_recon_weno<T, K>(ctx, g, qs, st);
     if (rc) return rc;
@@ -278,6 +285,7 @@ void hope_default_params(hope_params *p) {
   p->rk = HOPE_SSPRK3;
   p->ghost_iters = 10;
   p->weno_eps = 0.0;
+  p->coriolis_tilt = 0.0;
 }
 
 const char *hope_strerror(int code) {
@@ -382,6 +390,18 @@ static int init_impl(int n_members, const int *Ns, int order, int scheme, const 
   ctx->radius = prm.radius;
   ctx->gravity = prm.gravity;
   ctx->omega = prm.omega;
+  ctx->tilt = prm.coriolis_tilt;
+  {
+    // rotation axis (-sin(alpha_c), 0, cos(alpha_c)); per panel, axis . (n + X e1 + Y e2)
+    double ax[3] = {-sin(prm.coriolis_tilt), 0.0, cos(prm.coriolis_tilt)};
+    for (int p = 0; p < 6; ++p) {
+      double n[3], e1[3], e2[3];
+      panel_frame(p, n, e1, e2);
+      ctx->fcoef[3 * p] = dot3(ax, n);
+      ctx->fcoef[3 * p + 1] = dot3(ax, e1);
+      ctx->fcoef[3 * p + 2] = dot3(ax, e2);
+    }
+  }
   ctx->eps = prm.weno_eps != 0.0 ? prm.weno_eps : (prm.precision == HOPE_FP64 ? 1e-40 : 1e-12);
   cudaGetDevice(&ctx->device);
   int rc;

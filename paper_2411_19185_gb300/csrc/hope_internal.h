@@ -57,7 +57,8 @@ struct GraphKey {
 
 struct hope_ctx {
   int k = 0, H = 0, me = 0, npoc = 0, scheme = 0, prec = 0, rk = 0, ghost_iters = 10;
-  double radius = 0, gravity = 0, omega = 0, eps = 0;
+  double radius = 0, gravity = 0, omega = 0, eps = 0, tilt = 0;
+  double fcoef[18] = {0};  // per panel (c0, c1, c2): f*delta/(2 Omega) = c0 + c1 X + c2 Y
   int device = 0;
   int esize = 8;
   size_t total = 0;  // elements of one (ensemble) state

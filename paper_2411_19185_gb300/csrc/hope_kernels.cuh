@@ -42,6 +42,13 @@ struct Acc<float> {
 template <typename T>
 __device__ __forceinline__ T rcp(T x) { return T(1) / x; }
 
+// Coriolis coefficients per panel: sin(latitude about the rotation axis) * delta
+// = c0 + c1 X + c2 Y (eq. 2.5 for an untilted axis: Y, 1 or -1).
+template <typename T>
+struct FCoef {
+  T c[18];
+};
+
 // ---------------------------------------------------------------------------------
 // Ghost fill: one warp per ghost cell, lanes stride over the row's nonzeros.
 // ---------------------------------------------------------------------------------
@@ -123,7 +130,7 @@ template <typename T, int K>
 __global__ void __launch_bounds__(REC_TX *REC_TY)
     k_recon_tpp(const T *__restrict__ q, const T *__restrict__ gext, const T *__restrict__ w1g,
                 const T *__restrict__ Xg, const T *__restrict__ t1w, T *__restrict__ ep,
-                T *__restrict__ sb, int N, int ne, T omega) {
+                T *__restrict__ sb, int N, int ne, T omega, FCoef<T> fc) {
   using S = Shape<K>;
   constexpr int ME = S::ME, NPOS = S::NPOS, H = S::H;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -158,7 +165,7 @@ __global__ void __launch_bounds__(REC_TX *REC_TY)
   if (i >= N || j >= N) return;
   const size_t pn = (size_t)6 * N * N;
   const size_t cell = ((size_t)p * N + j) * N + i;
-  const T sgn_pole = (p == 4) ? T(1) : T(-1);
+  const T fc0 = fc.c[3 * p], fc1 = fc.c[3 * p + 1], fc2 = fc.c[3 * p + 2];
   T s1 = 0, s2 = 0;
 #pragma unroll 1
   for (int t = 0; t < NPOS; ++t) {
@@ -204,7 +211,7 @@ __global__ void __launch_bounds__(REC_TX *REC_TY)
         }
         const T Y = Xg[j * ME + h];
         const T tw = t1w[(((size_t)j * N + i) * ME + h) * ME + g];
-        const T sl = (p < 4) ? Y : sgn_pole;  // sin(latitude)*delta, eq. 2.5
+        const T sl = fc0 + fc1 * X + fc2 * Y;  // sin(latitude)*delta, eq. 2.5
         const T rq = rcp(qv[0]);
         const T XY = X * Y, X2 = X * X, Y2 = Y * Y;
         const T os = omega * sl;

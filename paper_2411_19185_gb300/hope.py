@@ -30,11 +30,13 @@ class Sphere:
     """One HOPE context: a cubed sphere (or an ensemble of spheres) with its tables."""
 
     def __init__(self, N, order, scheme=L.HOPE_TPP, precision=L.HOPE_FP64, rk=L.HOPE_SSPRK3,
-                 ghost_iters=10, radius=RADIUS, gravity=GRAVITY, omega=OMEGA, weno_eps=0.0):
+                 ghost_iters=10, radius=RADIUS, gravity=GRAVITY, omega=OMEGA, weno_eps=0.0,
+                 coriolis_tilt=0.0):
         lib = L.load()
         p = L.default_params()
         p.radius, p.gravity, p.omega = radius, gravity, omega
         p.precision, p.rk, p.ghost_iters, p.weno_eps = precision, rk, ghost_iters, weno_eps
+        p.coriolis_tilt = coriolis_tilt
         h = ctypes.c_void_p()
         if isinstance(N, (list, tuple)):
             arr = (ctypes.c_int * len(N))(*N)
