@@ -1,0 +1,276 @@
+"""Benchmark of the HOPE per-stage tendency on GB300.
+
+Workload (default): C90 cubed sphere (6 x 90 x 90 cells), 11th-order TPP reconstruction
+(11 x 11 stencil, 6 Gauss points per edge), FP64, steady geostrophic flow rotated by
+alpha = pi/4 (with the matching tilted rotation axis), SSP-RK3 with dt = 300 s; one
+benchmark step = one SSP-RK3 time step (three passes of the whole stage: ghost fill,
+reconstruction + sources, LMARS fluxes + quadrature, tendency + RK combination) followed
+by the FP64 mass diagnostic.  --steps defaults to 288 steps = one simulated day.
+
+Metric: cell-stage updates per second (cells x stages / time), whole job.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs an independent replica (the path has no data
+exchange between spheres); timing takes the max over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_CELLS, ORDER, DT = 90, 11, 300.0
+ALPHA = np.pi / 4
+WORKLOAD = "C90 TPP11 geostrophic alpha=pi/4, FP64, SSP-RK3 dt=300s"
+METRIC = "cell-stage updates/s"
+L2_FLUSH_BYTES = 512 << 20
+
+# DRAM bytes per launch of the dominant kernel from the ncu capture summarised in
+# profiles/recon_tpp11_c90_fp64.md (None until captured for the current kernel).
+RECON_TRAFFIC_BYTES = 4058624  # 4.058112 MB read + 512 B written
+
+
+def recon_flops_per_launch(N, K):
+    """Algorithmic FLOPs of one TPP reconstruction + sources launch (one stage):
+    sum-factorised x-pass over N x (N + 2H) cells at me + 2 positions and y-pass at the
+    n_poc = 4 me + me^2 points (K FMAs each, 3 variables), plus 41 flops of metric and
+    Coriolis sources per cell point (eqs. 2.2, 2.3)."""
+    me, H = (K + 1) // 2, (K - 1) // 2
+    npoc = 4 * me + me * me
+    per_panel = 3 * 2 * K * ((me + 2) * N * (N + 2 * H) + npoc * N * N) + 41 * me * me * N * N
+    return 6 * per_panel
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(stages):
+    """The FP64 C oracle (test infrastructure), as it stands, on this host's cores:
+    `stages` tendency evaluations of the full workload."""
+    from oracle import oracle as O
+    o = O.Oracle(N_CELLS, ORDER, coriolis_tilt=ALPHA)
+    q = o.geostrophic(ALPHA)
+    o.tendency(q)  # warm-up (thread pool)
+    t0 = time.perf_counter()
+    for _ in range(stages):
+        o.tendency(q)
+    dt = time.perf_counter() - t0
+    return 6 * N_CELLS * N_CELLS * stages / dt, dt
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    o = O.Oracle(N_CELLS, ORDER, coriolis_tilt=ALPHA)
+    q = o.geostrophic(ALPHA)
+    for _ in range(max(args.warmup, 1)):
+        o.tendency(q)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.tendency(q)
+    el = time.perf_counter() - t0
+    v = 6 * N_CELLS * N_CELLS * args.steps / el
+    cores = os.cpu_count()
+    sample = ("each step is one stage (one tendency evaluation) of the full workload, %d steps, "
+              "C FP64 oracle with OpenMP over %d host threads" % (args.steps, cores))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "cell-stage/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (analytic steady geostrophic flow)",
+            "config": {"workload": WORKLOAD, "N": N_CELLS, "order": ORDER, "scheme": "TPP"},
+            "cpu_baseline": {"value": v, "unit": "cell-stage/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "cell-stage/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=288)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-stages", type=int, default=150)
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2411_19185_gb300 as hp
+
+    fp64_peak = hp.measure_fma_peak(hp.HOPE_FP64)
+    s = hp.Sphere(N_CELLS, ORDER, hp.HOPE_TPP, hp.HOPE_FP64, coriolis_tilt=ALPHA)
+    q = s.geostrophic(ALPHA)
+    m0 = s.mass(q)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+    cells = 6 * N_CELLS * N_CELLS
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            s.step(q, DT)
+        s.set_profiling(True)
+        s.step(q, DT)  # captures the profiled graph
+        s.mass(q)
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        recon_ms = []
+        kernel_sum = np.zeros(4)
+        sampler = ClockSampler(local)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        sampler.start()
+        for k in range(args.steps):
+            flush.zero_()
+            ev0[k].record(stream)
+            s.step(q, DT)
+            s.mass(q)  # FP64 mass diagnostic, read back to the host
+            ev1[k].record(stream)
+            kt = s.kernel_times()
+            recon_ms.extend(st[1] for st in kt)
+            kernel_sum += np.sum(np.array(kt), axis=0)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        clocks = sampler.stop()
+        total_ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+        s.set_profiling(False)
+        # end to end through the C ABI with host buffers (copies inside the call)
+        qh = q.detach().to("cpu").pin_memory()
+        s.step_host(qh, DT, 1, out=qh)
+        e2e_s = 0.0
+        for k in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.step_host(qh, DT, 1, out=qh)
+            e2e_s += time.perf_counter() - t0
+    m1 = s.mass(q)
+    status = s.status()
+    total_ms = reduce_max(total_ms, world)
+    e2e_s = reduce_max(e2e_s, world)
+    value = world * cells * 3 * args.steps / (total_ms * 1e-3)
+    e2e_value = world * cells * 3 * args.steps / e2e_s
+    recon_avg_ms = float(np.mean(recon_ms))
+    flops = recon_flops_per_launch(N_CELLS, ORDER)
+    achieved = flops / (recon_avg_ms * 1e-3)
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "cell-stage/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (analytic steady geostrophic flow, eqs. 5.1-5.3)",
+        "config": {"workload": WORKLOAD, "N": N_CELLS, "order": ORDER, "scheme": "TPP", "dt_s": DT,
+                   "l2": "flushed before every timed step (512 MiB write); state 1.2 MB is L2-resident",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"kernel": "k_recon_tpp<double,11>", "bound": "alu", "achieved": achieved / 1e12,
+                     "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                     "peak_source": "FP64 FMA microbenchmark measured in this run (hope_measure_fma_peak)",
+                     "flops_per_launch": flops, "avg_launch_ms": recon_avg_ms,
+                     "traffic": RECON_TRAFFIC_BYTES},
+        "stage_kernel_ms": {"ghost": kernel_sum[0] / (3 * args.steps), "recon": kernel_sum[1] / (3 * args.steps),
+                            "flux": kernel_sum[2] / (3 * args.steps), "update": kernel_sum[3] / (3 * args.steps)},
+        "e2e": {"value": e2e_value, "unit": "cell-stage/s", "h2d_bytes_per_step": q.numel() * 8,
+                "d2h_bytes_per_step": q.numel() * 8},
+        "gpu_launches": args.steps * (3 * s.launches_per_stage() + 2),
+        "clocks": clocks,
+        "mass_drift": (m1 - m0) / m0,
+        "device_status": status,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        v, el = cpu_baseline(args.cpu_stages)
+        line["cpu_baseline"] = {"value": v, "unit": "cell-stage/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": "%d tendency evaluations (stages) of the full workload, %.1f s" %
+                                          (args.cpu_stages, el)}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

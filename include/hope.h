@@ -192,6 +192,18 @@ int hope_ghost_nnz(hope_t ctx, long long *nnz, long long *rows);
    tendency enqueues. */
 int hope_launches_per_stage(hope_t ctx, int *launches);
 
+/*
+ * Per-kernel timing for profiling.  hope_set_profiling(ctx, 1) makes the graphs that
+ * hope_step captures from then on record a CUDA event before and after every kernel of
+ * the first sphere's stages; hope_kernel_times() then returns, for the most recent step,
+ * the elapsed milliseconds of each kernel in launch order: stage-major, and within a
+ * stage [ghost fill, reconstruction, flux, update] (HOPE_KERNELS_PER_STAGE entries).
+ * It synchronises on the last event.  n_entries receives the number written.
+ */
+#define HOPE_KERNELS_PER_STAGE 4
+int hope_set_profiling(hope_t ctx, int enable);
+int hope_kernel_times(hope_t ctx, float *ms_out, int max_entries, int *n_entries);
+
 const char *hope_strerror(int code);
 const char *hope_last_error_message(void);
 

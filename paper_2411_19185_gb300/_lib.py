@@ -20,7 +20,7 @@ EXPORTED = [
     "hope_elem_size", "hope_initial_state", "hope_set_state", "hope_get_state", "hope_tendency",
     "hope_step", "hope_step_ssprk3", "hope_step_host", "hope_tendency_vjp", "hope_step_vjp",
     "hope_total_mass", "hope_status", "hope_ghost_nnz", "hope_launches_per_stage", "hope_strerror",
-    "hope_last_error_message", "hope_measure_fma_peak",
+    "hope_last_error_message", "hope_measure_fma_peak", "hope_set_profiling", "hope_kernel_times",
 ]
 
 
@@ -74,6 +74,8 @@ def load():
         "hope_strerror": (ctypes.c_char_p, [i]),
         "hope_last_error_message": (ctypes.c_char_p, []),
         "hope_measure_fma_peak": (i, [i, P(d)]),
+        "hope_set_profiling": (i, [vp, i]),
+        "hope_kernel_times": (i, [vp, P(ctypes.c_float), i, P(i)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

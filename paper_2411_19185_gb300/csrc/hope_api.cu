@@ -52,6 +52,11 @@ static int stage_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *q0, T *out, 
                       double b, double c, cudaStream_t st) {
   constexpr int ME = (K + 1) / 2;
   const int N = g.N, ne = g.ne;
+  const bool prof = ctx->prof_stage >= 0 && &g == &ctx->grids[0];
+  auto mark = [&](int t) {
+    if (prof) cudaEventRecordWithFlags(ctx->prof_ev[ctx->prof_stage][t], st, cudaEventRecordExternal);
+  };
+  mark(0);
   // ghost ring
   if (g.rows > 0) {
     long long threads = g.rows * 32;
@@ -59,6 +64,7 @@ static int stage_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *q0, T *out, 
     k_ghost<T><<<blocks, 256, 0, st>>>(qs, (T *)g.gext, g.grow, g.gcol, (const T *)g.gval, g.gdst,
                                        (int)g.rows, N, ne);
   }
+  mark(1);
   // reconstruction + sources
   dim3 grid((N + REC_TX - 1) / REC_TX, (N + REC_TY - 1) / REC_TY, 6);
   if (ctx->scheme == HOPE_TPP) {
@@ -70,6 +76,7 @@ static int stage_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *q0, T *out, 
     int rc = launch_recon_weno<T, K>(ctx, g, qs, st);
     if (rc) return rc;
   }
+  mark(2);
   // fluxes
   {
     long long items = 12LL * N * (N - 1) + 12LL * N;
@@ -77,6 +84,7 @@ static int stage_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *q0, T *out, 
     k_flux<T, ME><<<blocks, 256, 0, st>>>((const T *)g.ep, (const T *)g.mx, (const T *)ctx->gw, g.bedge,
                                           (const T *)g.bconv, (T *)g.fx, (T *)g.fy, N, ctx->status);
   }
+  mark(3);
   // tendency + stage combination
   {
     long long cells = 6LL * N * N;
@@ -84,6 +92,7 @@ static int stage_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *q0, T *out, 
     k_update<T><<<blocks, 256, 0, st>>>((const T *)g.fx, (const T *)g.fy, (const T *)g.sb, q0, qs, out, N,
                                         (T)(2.0 * N / HOPE_PI), mode, (T)a, (T)b, (T)c, ctx->status);
   }
+  mark(4);
   HOPE_CUDA_TRY(cudaGetLastError());
   return HOPE_OK;
 }
@@ -141,19 +150,25 @@ static int set_attrs(const hope_ctx *ctx) {
 }
 
 // RK step sequence (3 stages) on stream st
-static int step_sequence(hope_ctx *ctx, void *q, double dt, int rk, cudaStream_t st) {
+static int step_sequence(hope_ctx *ctx, void *q, double dt, int rk, bool prof, cudaStream_t st) {
   stage_fn f = pick_stage(ctx);
-  int rc;
+  int rc = HOPE_OK;
+  double A[3], B[3], C[3];
+  const void *qs[3] = {q, ctx->q1, ctx->q2};
+  void *out[3] = {ctx->q1, ctx->q2, q};
   if (rk == HOPE_WSRK3) {
-    if ((rc = f(ctx, q, q, ctx->q1, 1, 1.0, 0.0, dt / 3.0, st))) return rc;
-    if ((rc = f(ctx, ctx->q1, q, ctx->q2, 1, 1.0, 0.0, dt / 2.0, st))) return rc;
-    if ((rc = f(ctx, ctx->q2, q, q, 1, 1.0, 0.0, dt, st))) return rc;
+    double a[3] = {1.0, 1.0, 1.0}, b[3] = {0.0, 0.0, 0.0}, c[3] = {dt / 3.0, dt / 2.0, dt};
+    for (int s = 0; s < 3; ++s) { A[s] = a[s]; B[s] = b[s]; C[s] = c[s]; }
   } else {
-    if ((rc = f(ctx, q, q, ctx->q1, 1, 0.0, 1.0, dt, st))) return rc;
-    if ((rc = f(ctx, ctx->q1, q, ctx->q2, 1, 0.75, 0.25, 0.25 * dt, st))) return rc;
-    if ((rc = f(ctx, ctx->q2, q, q, 1, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * dt, st))) return rc;
+    double a[3] = {0.0, 0.75, 1.0 / 3.0}, b[3] = {1.0, 0.25, 2.0 / 3.0}, c[3] = {dt, 0.25 * dt, 2.0 / 3.0 * dt};
+    for (int s = 0; s < 3; ++s) { A[s] = a[s]; B[s] = b[s]; C[s] = c[s]; }
   }
-  return HOPE_OK;
+  for (int s = 0; s < 3 && rc == HOPE_OK; ++s) {
+    ctx->prof_stage = prof ? s : -1;
+    rc = f(ctx, qs[s], q, out[s], 1, A[s], B[s], C[s], st);
+  }
+  ctx->prof_stage = -1;
+  return rc;
 }
 
 // -------------------------------------------------------------------------------
@@ -320,6 +335,9 @@ void hope_destroy(hope_t ctx) {
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  for (int s = 0; s < PROF_STAGES; ++s)
+    for (int t = 0; t <= PROF_KERNELS; ++t)
+      if (ctx->prof_ev[s][t]) cudaEventDestroy(ctx->prof_ev[s][t]);
   delete ctx;
 }
 
@@ -560,13 +578,13 @@ static int step_impl(hope_t ctx, void *q_dev, double dt, int nsteps, int rk, cud
     return HOPE_EINVAL;
   }
   void *q = q_dev ? q_dev : ctx->state;
-  GraphKey key{q, dt, rk};
+  GraphKey key{q, dt, rk, ctx->profiling};
   auto it = ctx->graphs.find(key);
   cudaGraphExec_t exec = nullptr;
   if (it == ctx->graphs.end()) {
     cudaGraph_t graph = nullptr;
     HOPE_CUDA_TRY(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-    int rc = step_sequence(ctx, q, dt, rk, ctx->cap_stream);
+    int rc = step_sequence(ctx, q, dt, rk, ctx->profiling != 0, ctx->cap_stream);
     cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
     if (rc) {
       if (graph) cudaGraphDestroy(graph);
@@ -674,6 +692,31 @@ int hope_step_vjp(hope_t ctx, const void *qn_dev, const void *lam_np1_dev, void 
   (void)ctx; (void)qn_dev; (void)lam_np1_dev; (void)lam_n_dev; (void)dt; (void)stream;
   set_error("hope_step_vjp: not available in this build");
   return HOPE_EUNSUPPORTED;
+}
+
+int hope_set_profiling(hope_t ctx, int enable) {
+  if (!ctx) return HOPE_EINVAL;
+  if (enable && !ctx->prof_ev[0][0]) {
+    for (int s = 0; s < PROF_STAGES; ++s)
+      for (int t = 0; t <= PROF_KERNELS; ++t) HOPE_CUDA_TRY(cudaEventCreate(&ctx->prof_ev[s][t]));
+  }
+  ctx->profiling = enable ? 1 : 0;
+  return HOPE_OK;
+}
+
+int hope_kernel_times(hope_t ctx, float *ms_out, int max_entries, int *n_entries) {
+  if (!ctx || !ms_out || !n_entries || !ctx->prof_ev[0][0]) return HOPE_EINVAL;
+  HOPE_CUDA_TRY(cudaEventSynchronize(ctx->prof_ev[PROF_STAGES - 1][PROF_KERNELS]));
+  int n = 0;
+  for (int s = 0; s < PROF_STAGES; ++s)
+    for (int t = 0; t < PROF_KERNELS; ++t) {
+      if (n >= max_entries) break;
+      float ms = 0.0f;
+      HOPE_CUDA_TRY(cudaEventElapsedTime(&ms, ctx->prof_ev[s][t], ctx->prof_ev[s][t + 1]));
+      ms_out[n++] = ms;
+    }
+  *n_entries = n;
+  return HOPE_OK;
 }
 
 int hope_measure_fma_peak(int precision, double *flops_per_s) {

@@ -46,12 +46,17 @@ struct GraphKey {
   const void *q;
   double dt;
   int rk;
+  int prof;
   bool operator<(const GraphKey &o) const {
     if (q != o.q) return q < o.q;
     if (dt != o.dt) return dt < o.dt;
-    return rk < o.rk;
+    if (rk != o.rk) return rk < o.rk;
+    return prof < o.prof;
   }
 };
+
+constexpr int PROF_STAGES = 3;
+constexpr int PROF_KERNELS = 4;
 
 }  // namespace hope
 
@@ -78,6 +83,10 @@ struct hope_ctx {
   double *mass_part = nullptr;
   double *mass_out = nullptr;
   cudaStream_t cap_stream = nullptr;
+  // profiling: events around the first sphere's kernels of each stage of a step
+  int profiling = 0;
+  int prof_stage = -1;  // stage being captured (-1: no events)
+  cudaEvent_t prof_ev[hope::PROF_STAGES][hope::PROF_KERNELS + 1] = {};
   std::map<hope::GraphKey, cudaGraphExec_t> graphs;
 };
 

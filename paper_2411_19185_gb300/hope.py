@@ -136,6 +136,18 @@ class Sphere:
         L.check(L.load().hope_ghost_nnz(self._h, ctypes.byref(n), ctypes.byref(r)))
         return n.value, r.value
 
+    def set_profiling(self, enable=True):
+        L.check(L.load().hope_set_profiling(self._h, 1 if enable else 0))
+
+    def kernel_times(self):
+        """Per-kernel milliseconds of the most recent profiled step: a list of 3 stages x
+        [ghost, reconstruction, flux, update]."""
+        buf = (ctypes.c_float * 64)()
+        n = ctypes.c_int()
+        L.check(L.load().hope_kernel_times(self._h, buf, 64, ctypes.byref(n)))
+        v = list(buf[:n.value])
+        return [v[i:i + 4] for i in range(0, len(v), 4)]
+
     def launches_per_stage(self):
         n = ctypes.c_int()
         L.check(L.load().hope_launches_per_stage(self._h, ctypes.byref(n)))
