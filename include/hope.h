@@ -182,6 +182,40 @@ int hope_step_vjp(hope_t ctx, const void *qn_dev, const void *lam_np1_dev, void 
  */
 int hope_total_mass(hope_t ctx, const void *q_dev, double *mass_host, hope_stream_t stream);
 
+/*
+ * hope_total_mass_noalloc -- the mass diagnostic of hope_total_mass for one sphere,
+ * without a context and without allocating device memory.  (The paper has no
+ * counterpart: this is an interface for callers that cannot allocate.)
+ *
+ * Who needs it: code that must not call cudaMalloc when it wants the diagnostic -- for
+ * example code running while a CUDA graph is being captured on its stream (allocation is
+ * not a capturable operation), a host framework that fixes its device-memory budget after
+ * start-up, or a monitoring thread that must not change the device's allocation state.
+ * Creating a context allocates its tables, so these callers cannot use hope_total_mass.
+ *
+ *   q_dev      state (3, 6, N, N) of one sphere on the current device, element type
+ *              double (precision HOPE_FP64) or float (HOPE_FP32); caller-owned input.
+ *   mass_dev   device pointer to one double; receives dx*dy*sum(q[0]) (FP64 sum in a fixed
+ *              order); caller-owned output.  Nothing is copied to the host and the call
+ *              does not synchronise.
+ *
+ * Scratch: the per-block partial sums live in a file-scope device array of
+ * HOPE_NOALLOC_MASS_PARTIALS doubles (32 KiB), which every GPU that loads the library holds
+ * until the process exits.  Each partial sums HOPE_NOALLOC_MASS_CHUNK elements, so
+ * N <= HOPE_NOALLOC_MASS_MAX_N; larger N returns HOPE_EINVAL with a message.  Every used
+ * slot is written before it is read, so no clearing is needed between calls.  All calls on
+ * a device share the array, which keeps the last call's partials: calls that overlap on
+ * the GPU (two streams, or two host threads on one device) race and must be serialised by
+ * the caller.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before any stream
+ * capture.  No cudaMalloc, cudaFree or allocating library routine is called.
+ */
+#define HOPE_NOALLOC_MASS_PARTIALS 4096
+#define HOPE_NOALLOC_MASS_CHUNK 2048
+#define HOPE_NOALLOC_MASS_MAX_N 1182
+int hope_total_mass_noalloc(const void *q_dev, int precision, int N, double *mass_dev,
+                            hope_stream_t stream);
+
 /* Read and clear the sticky device status (HOPE_STATUS_* bits).  Synchronises. */
 int hope_status(hope_t ctx, unsigned *device_status);
 

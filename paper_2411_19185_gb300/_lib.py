@@ -21,6 +21,7 @@ EXPORTED = [
     "hope_step", "hope_step_ssprk3", "hope_step_host", "hope_tendency_vjp", "hope_step_vjp",
     "hope_total_mass", "hope_status", "hope_ghost_nnz", "hope_launches_per_stage", "hope_strerror",
     "hope_last_error_message", "hope_measure_fma_peak", "hope_set_profiling", "hope_kernel_times",
+    "hope_total_mass_noalloc",
 ]
 
 
@@ -75,6 +76,7 @@ def load():
         "hope_last_error_message": (ctypes.c_char_p, []),
         "hope_measure_fma_peak": (i, [i, P(d)]),
         "hope_set_profiling": (i, [vp, i]),
+        "hope_total_mass_noalloc": (i, [vp, i, i, P(d), vp]),
         "hope_kernel_times": (i, [vp, P(ctypes.c_float), i, P(i)]),
     }
     for name, (res, args) in sig.items():
