@@ -148,7 +148,13 @@ int hope_tendency(hope_t ctx, const void *q_dev, void *dqdt_dev, hope_stream_t s
  * nsteps Runge-Kutta steps of size dt (seconds) in place on q_dev (NULL = the context's
  * own state), with the context's stepper (SSP-RK3 by default).  Each stage fuses the
  * stage combination into the tendency's final kernel.  Steps are replayed from a CUDA
- * graph captured on first use for a given (q_dev, dt, stream).
+ * graph captured on first use for a given (q_dev, dt).
+ * FP32 contexts step compensated: the context keeps an FP32 low word for the most recently
+ * stepped buffer (zeroed when another buffer is stepped or hope_set_state / hope_step_host
+ * load new contents), and every stage combination is formed with error-free FP32
+ * transformations, so rounding of the FP32 state does not accumulate over long runs.
+ * A caller that overwrites q_dev between calls should step another buffer or call
+ * hope_set_state so that the low word restarts from zero.
  */
 int hope_step(hope_t ctx, void *q_dev, double dt, int nsteps, hope_stream_t stream);
 

@@ -44,12 +44,36 @@ static FCoef<T> fcoef(const hope_ctx *ctx) {
   return f;
 }
 
+template <typename T, int K>
+int launch_recon_weno(hope_ctx *ctx, Grid &g, const T *qs, cudaStream_t st) {
+  using W = WenoShape<T, K>;
+  const int N = g.N;
+  dim3 grid((N + REC_TX - 1) / REC_TX, (N + REC_TY - 1) / REC_TY, 6);
+  size_t smem = sizeof(T) * W::smem_elems();
+  k_recon_weno<T, K><<<grid, REC_TX * REC_TY, smem, st>>>(
+      qs, (const T *)g.gext, (const T *)ctx->wsub, (const T *)ctx->gpm, (const T *)ctx->sig,
+      (const T *)ctx->bform, (const T *)ctx->bcoef, (const T *)g.Xg, (const T *)g.t1w, (T *)g.ep, (T *)g.sb, N, g.ne, (T)ctx->omega,
+      fcoef<T>(ctx), (T)ctx->eps);
+  return HOPE_OK;
+}
+
+template <typename T, int K>
+int weno_set_smem_attr() {
+  size_t smem = sizeof(T) * WenoShape<T, K>::smem_elems();
+  cudaError_t e = cudaFuncSetAttribute(k_recon_weno<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) {
+    set_error(std::string("WENO shared memory attribute: ") + cudaGetErrorString(e));
+    return HOPE_ECUDA;
+  }
+  return HOPE_OK;
+}
+
 // -------------------------------------------------------------------------------
 // One stage on one grid: out = L(qs) (mode 0) or a*q0 + b*qs + c*L(qs) (mode 1).
 // -------------------------------------------------------------------------------
 template <typename T, int K>
 static int stage_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *q0, T *out, int mode, double a,
-                      double b, double c, cudaStream_t st) {
+                      double b, double c, const T *q0l, const T *qsl, T *outl, cudaStream_t st) {
   constexpr int ME = (K + 1) / 2;
   const int N = g.N, ne = g.ne;
   const bool prof = ctx->prof_stage >= 0 && &g == &ctx->grids[0];
@@ -90,25 +114,33 @@ static int stage_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *q0, T *out, 
     long long cells = 6LL * N * N;
     int blocks = (int)((cells + 255) / 256);
     k_update<T><<<blocks, 256, 0, st>>>((const T *)g.fx, (const T *)g.fy, (const T *)g.sb, q0, qs, out, N,
-                                        (T)(2.0 * N / HOPE_PI), mode, (T)a, (T)b, (T)c, ctx->status);
+                                        (T)(2.0 * N / HOPE_PI), mode, (T)a, (T)b, (T)c, q0l, qsl, outl,
+                                        ctx->status);
   }
   mark(4);
   HOPE_CUDA_TRY(cudaGetLastError());
   return HOPE_OK;
 }
 
+// Low words of the three stage states for compensated FP32 stepping (all null in FP64).
+struct LoWords {
+  const void *q0l = nullptr, *qsl = nullptr;
+  void *outl = nullptr;
+};
+
 template <typename T, int K>
 static int stage_all(hope_ctx *ctx, const void *qs, const void *q0, void *out, int mode, double a, double b,
-                     double c, cudaStream_t st) {
+                     double c, LoWords lw, cudaStream_t st) {
   for (auto &g : ctx->grids) {
-    int rc = stage_grid<T, K>(ctx, g, (const T *)qs + g.off, q0 ? (const T *)q0 + g.off : nullptr,
-                              (T *)out + g.off, mode, a, b, c, st);
+    auto off = [&](const void *p) -> const T * { return p ? (const T *)p + g.off : nullptr; };
+    int rc = stage_grid<T, K>(ctx, g, (const T *)qs + g.off, off(q0), (T *)out + g.off, mode, a, b, c,
+                              off(lw.q0l), off(lw.qsl), lw.outl ? (T *)lw.outl + g.off : nullptr, st);
     if (rc) return rc;
   }
   return HOPE_OK;
 }
 
-typedef int (*stage_fn)(hope_ctx *, const void *, const void *, void *, int, double, double, double,
+typedef int (*stage_fn)(hope_ctx *, const void *, const void *, void *, int, double, double, double, LoWords,
                         cudaStream_t);
 
 template <typename T>
@@ -163,9 +195,19 @@ static int step_sequence(hope_ctx *ctx, void *q, double dt, int rk, bool prof, c
     double a[3] = {0.0, 0.75, 1.0 / 3.0}, b[3] = {1.0, 0.25, 2.0 / 3.0}, c[3] = {dt, 0.25 * dt, 2.0 / 3.0 * dt};
     for (int s = 0; s < 3; ++s) { A[s] = a[s]; B[s] = b[s]; C[s] = c[s]; }
   }
+  // FP32: compensated state words (the context's carry belongs to q)
+  const bool comp = ctx->prec == HOPE_FP32;
+  const void *qsl[3] = {ctx->carry, ctx->q1l, ctx->q2l};
+  void *outl[3] = {ctx->q1l, ctx->q2l, ctx->carry};
   for (int s = 0; s < 3 && rc == HOPE_OK; ++s) {
     ctx->prof_stage = prof ? s : -1;
-    rc = f(ctx, qs[s], q, out[s], 1, A[s], B[s], C[s], st);
+    LoWords lw;
+    if (comp) {
+      lw.q0l = ctx->carry;
+      lw.qsl = qsl[s];
+      lw.outl = outl[s];
+    }
+    rc = f(ctx, qs[s], q, out[s], 1, A[s], B[s], C[s], lw, st);
   }
   ctx->prof_stage = -1;
   return rc;
@@ -330,8 +372,9 @@ void hope_destroy(hope_t ctx) {
   if (!ctx) return;
   for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
   for (auto &g : ctx->grids) free_grid(g);
-  void *ptrs[] = {ctx->w1, ctx->gw, ctx->wsub, ctx->gpm, ctx->sig, ctx->bform, ctx->state,
-                  ctx->q1, ctx->q2, ctx->lbuf, ctx->status, ctx->mass_part, ctx->mass_out};
+  void *ptrs[] = {ctx->w1, ctx->gw, ctx->wsub, ctx->gpm, ctx->sig, ctx->bform, ctx->bcoef, ctx->state,
+                  ctx->q1, ctx->q2, ctx->lbuf, ctx->status, ctx->mass_part, ctx->mass_out,
+                  ctx->carry, ctx->q1l, ctx->q2l};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -480,6 +523,12 @@ static int init_impl(int n_members, const int *Ns, int order, int scheme, const 
   TRY(alloc(&ctx->q1, es * off));
   TRY(alloc(&ctx->q2, es * off));
   TRY(alloc(&ctx->lbuf, es * off));
+  if (ctx->prec == HOPE_FP32) {
+    TRY(alloc(&ctx->carry, es * off));
+    TRY(alloc(&ctx->q1l, es * off));
+    TRY(alloc(&ctx->q2l, es * off));
+    cudaMemset(ctx->carry, 0, es * off);
+  }
   TRY(alloc((void **)&ctx->status, sizeof(unsigned)));
   cudaMemset(ctx->status, 0, sizeof(unsigned));
   TRY(alloc((void **)&ctx->mass_part, sizeof(double) * MASS_BLOCKS));
@@ -547,6 +596,7 @@ int hope_initial_state(hope_t ctx, int ic_case, const double *params, int n_para
 
 int hope_set_state(hope_t ctx, const void *q_dev, hope_stream_t stream) {
   if (!ctx || !q_dev) return HOPE_EINVAL;
+  if (ctx->carry_owner == ctx->state) ctx->carry_owner = nullptr;  // new contents: fresh carry
   HOPE_CUDA_TRY(cudaMemcpyAsync(ctx->state, q_dev, ctx->esize * ctx->total, cudaMemcpyDeviceToDevice,
                                 (cudaStream_t)stream));
   return HOPE_OK;
@@ -569,7 +619,7 @@ int hope_tendency(hope_t ctx, const void *q_dev, void *dqdt_dev, hope_stream_t s
     set_error("hope_tendency: q and dqdt must not overlap");
     return HOPE_EINVAL;
   }
-  return pick_stage(ctx)(ctx, q, nullptr, dqdt_dev, 0, 0.0, 0.0, 0.0, (cudaStream_t)stream);
+  return pick_stage(ctx)(ctx, q, nullptr, dqdt_dev, 0, 0.0, 0.0, 0.0, LoWords(), (cudaStream_t)stream);
 }
 
 static int step_impl(hope_t ctx, void *q_dev, double dt, int nsteps, int rk, cudaStream_t st) {
@@ -578,6 +628,11 @@ static int step_impl(hope_t ctx, void *q_dev, double dt, int nsteps, int rk, cud
     return HOPE_EINVAL;
   }
   void *q = q_dev ? q_dev : ctx->state;
+  if (ctx->prec == HOPE_FP32 && ctx->carry_owner != q) {
+    // a new state buffer: its compensation word starts at zero
+    HOPE_CUDA_TRY(cudaMemsetAsync(ctx->carry, 0, ctx->esize * ctx->total, st));
+    ctx->carry_owner = q;
+  }
   GraphKey key{q, dt, rk, ctx->profiling};
   auto it = ctx->graphs.find(key);
   cudaGraphExec_t exec = nullptr;
@@ -627,6 +682,7 @@ int hope_step_host(hope_t ctx, const void *q_host_in, void *q_host_out, double d
   cudaStream_t st = (cudaStream_t)stream;
   size_t bytes = ctx->esize * ctx->total;
   HOPE_CUDA_TRY(cudaMemcpyAsync(ctx->state, q_host_in, bytes, cudaMemcpyHostToDevice, st));
+  if (ctx->carry_owner == ctx->state) ctx->carry_owner = nullptr;  // new contents: fresh carry
   int rc = step_impl(ctx, ctx->state, dt, nsteps, ctx->rk, st);
   if (rc) return rc;
   HOPE_CUDA_TRY(cudaMemcpyAsync(q_host_out, ctx->state, bytes, cudaMemcpyDeviceToHost, st));

@@ -75,10 +75,14 @@ struct hope_ctx {
   void *wsub = nullptr;   // [me+2][l][l]  1-D sub-stencil weights at the same positions
   void *gpm = nullptr;    // [npoc][2][s] normalised gamma+/sigma+, gamma-/sigma-
   void *sig = nullptr;    // [npoc][2] sigma+, sigma-
-  void *bform = nullptr;  // [l][2][l][l] S and B0 1-D forms per sub-stencil offset
+  void *bform = nullptr;  // [l][l*l + l] Winv and its row sums per sub-stencil offset
+  void *bcoef = nullptr;  // [l][l][l][l] indicator mode weights
   // buffers
   void *state = nullptr;  // context-owned state
   void *q1 = nullptr, *q2 = nullptr, *lbuf = nullptr;
+  // FP32 compensated stepping: low words of the caller's state (carry) and of q1, q2
+  void *carry = nullptr, *q1l = nullptr, *q2l = nullptr;
+  const void *carry_owner = nullptr;
   unsigned *status = nullptr;
   double *mass_part = nullptr;
   double *mass_out = nullptr;

@@ -375,12 +375,38 @@ __global__ void __launch_bounds__(256)
 // Tendency (eq. 3.1) and the Runge-Kutta stage combination:
 //   mode 0: out = L
 //   mode 1: out = a*q0 + b*qs + c*L
+// With low-word pointers (FP32 contexts) every state is the unevaluated sum hi + lo of two
+// floats, and the combination is formed with error-free transformations (TwoProd by
+// fma, TwoSum), so the FP32 state keeps the low-order part of each stage increment.
 // ---------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void two_sum(T a, T b, T &s, T &e) {
+  s = a + b;
+  T bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
+template <typename T>
+__device__ __forceinline__ T combine(T a, T q0, T b, T qs, T c, T L, const T *q0l, const T *qsl, T *outl,
+                                     long long idx) {
+  if (q0l == nullptr) return a * q0 + b * qs + c * L;
+  const T p1 = a * q0, e1 = fma(a, q0, -p1);
+  const T p2 = b * qs, e2 = fma(b, qs, -p2);
+  const T p3 = c * L, e3 = fma(c, L, -p3);
+  T s, r1, s2, r2;
+  two_sum(p1, p2, s, r1);
+  two_sum(s, p3, s2, r2);
+  T lo = ((r1 + r2) + (e1 + e2 + e3)) + (a * q0l[idx] + b * qsl[idx]);
+  T hi = s2 + lo;
+  outl[idx] = lo - (hi - s2);
+  return hi;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_update(const T *__restrict__ fx, const T *__restrict__ fy, const T *__restrict__ sb,
              const T *q0, const T *qs, T *out, int N, T inv_dx, int mode, T a, T b, T c,
-             unsigned *status) {
+             const T *q0l, const T *qsl, T *outl, unsigned *status) {
   const long long ncell = 6LL * N * N;
   long long cid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (cid >= ncell) return;
@@ -402,7 +428,8 @@ __global__ void __launch_bounds__(256)
     if (mode == 0) {
       r = L;
     } else {
-      r = a * q0[v * ncell + cid] + b * qs[v * ncell + cid] + c * L;
+      const long long idx = v * ncell + cid;
+      r = combine(a, q0[idx], b, qs[idx], c, L, q0l, qsl, outl, idx);
     }
     bad |= !isfinite(r);
     out[v * ncell + cid] = r;

@@ -363,13 +363,13 @@ int build_cube_edges(const hope_ctx *ctx, int N, const std::vector<double> &node
             set_error("cube edges: edge Gauss points do not coincide across panels");
             return HOPE_EINVAL;
           }
-          int f = (tb == t && gb == g) ? 0 : ((tb == N - 1 - t && gb == me - 1 - g) ? 1 : -1);
           if (t == 0 && g == 0) {
             B = b;
             sB = s;
-            flip = f;
+            flip = (tb == 0 && gb == 0) ? 0 : ((tb == N - 1 && gb == me - 1) ? 1 : -1);
           }
-          if (b != B || s != sB || f != flip || f < 0) {
+          const int tb_exp = flip ? N - 1 - t : t, gb_exp = flip ? me - 1 - g : g;
+          if (b != B || s != sB || flip < 0 || tb != tb_exp || gb != gb_exp) {
             set_error("cube edges: inconsistent neighbour along a panel side");
             return HOPE_EINVAL;
           }
@@ -403,10 +403,100 @@ int build_cube_edges(const hope_ctx *ctx, int N, const std::vector<double> &node
 }  // namespace hope
 
 namespace hope {
+// WENO2D tables (section 3.2), FP64 on the host, stored in the context precision:
+//   wsub [me+2][l][l]  1-D sub-stencil weights at xi = -1/2, +1/2, g_0..g_{me-1}
+//   gpm  [npoc][2][s]  gamma+ and gamma- of eq. 3.20 (theta = 3) at every point, gamma the
+//                      tensor product of the 1-D least-squares weights (eq. 3.19)
+//   sig  [npoc][2]     sigma+- = sum of gamma+-
+//   bform [l][l*l + l] per sub-stencil offset: Winv (l x l) of the simultaneous
+//                      diagonalisation of the smoothness forms (eq. 3.25), its row sums
+//   bcoef [l][l][l][l] mode weights lam_y lam_x - 1 of the indicator
+static int upload_t(hope_ctx *ctx, void **dst, const std::vector<double> &v) {
+  size_t bytes = (size_t)ctx->esize * v.size();
+  if (cudaMalloc(dst, bytes) != cudaSuccess) return HOPE_ENOMEM;
+  cudaError_t e;
+  if (ctx->esize == 8) {
+    e = cudaMemcpy(*dst, v.data(), bytes, cudaMemcpyHostToDevice);
+  } else {
+    std::vector<float> f(v.begin(), v.end());
+    e = cudaMemcpy(*dst, f.data(), bytes, cudaMemcpyHostToDevice);
+  }
+  return e == cudaSuccess ? HOPE_OK : HOPE_ECUDA;
+}
+
 int setup_weno_tables(hope_ctx *ctx, const std::vector<double> &nodes) {
-  (void)ctx;
-  (void)nodes;
-  set_error("WENO2D tables are not available in this build");
-  return HOPE_EUNSUPPORTED;
+  const int K = ctx->k, H = ctx->H, me = ctx->me, l = (K + 1) / 2, S = l * l, np = ctx->npoc;
+  std::vector<double> pos(me + 2);
+  pos[0] = -0.5;
+  pos[1] = 0.5;
+  for (int g = 0; g < me; ++g) pos[2 + g] = nodes[g];
+  std::vector<double> wsub((size_t)(me + 2) * l * l), g1((size_t)(me + 2) * l);
+  for (int t = 0; t < me + 2; ++t) {
+    for (int sb = 0; sb < l; ++sb) cell_avg_weights(l, sb - H, pos[t], &wsub[((size_t)t * l + sb) * l]);
+    double res = weno_linear_weights_1d(K, pos[t], &g1[(size_t)t * l]);
+    if (res > 1e-10) {
+      set_error("WENO linear weights: least-squares residual too large");
+      return HOPE_EINVAL;
+    }
+  }
+  std::vector<double> gpm((size_t)np * 2 * S), sig((size_t)np * 2);
+  auto ptpos = [me](int pt, int *tx, int *ty) {
+    if (pt < me) { *tx = 0; *ty = 2 + pt; }
+    else if (pt < 2 * me) { *tx = 1; *ty = 2 + pt - me; }
+    else if (pt < 3 * me) { *tx = 2 + pt - 2 * me; *ty = 0; }
+    else if (pt < 4 * me) { *tx = 2 + pt - 3 * me; *ty = 1; }
+    else { int c = pt - 4 * me; *tx = 2 + c % me; *ty = 2 + c / me; }
+  };
+  for (int pt = 0; pt < np; ++pt) {
+    int tx, ty;
+    ptpos(pt, &tx, &ty);
+    double sp = 0.0, sm = 0.0;
+    for (int sy = 0; sy < l; ++sy)
+      for (int sx = 0; sx < l; ++sx) {
+        double gm = g1[(size_t)tx * l + sx] * g1[(size_t)ty * l + sy];
+        double gpl = 0.5 * (3.0 * fabs(gm) + gm), gmi = 0.5 * (3.0 * fabs(gm) - gm);
+        gpm[((size_t)pt * 2 + 0) * S + sy * l + sx] = gpl;
+        gpm[((size_t)pt * 2 + 1) * S + sy * l + sx] = gmi;
+        sp += gpl;
+        sm += gmi;
+      }
+    sig[(size_t)pt * 2] = sp;
+    sig[(size_t)pt * 2 + 1] = sm;
+  }
+  // bform per sub-stencil offset: Winv (l x l) and its row sums (l); the indicator uses
+  // Q minus the cell's own value (beta is blind to constants), whose transform is
+  // Winv Q - q_c * rowsum.  bcoef[sy][k][sx][k'] = lam_y,k lam_x,k' - 1, set to exactly 0
+  // for the constant mode (|.| < 1e-12) and clamped at 0, so beta >= 0 in any precision.
+  std::vector<double> bf((size_t)l * (l * l + l)), lam((size_t)l * l);
+  for (int sb = 0; sb < l; ++sb) {
+    double Sm[HOPE_MAXME * HOPE_MAXME], B0[HOPE_MAXME * HOPE_MAXME];
+    weno_beta_forms_1d(l, sb - H, Sm, B0);
+    double *W = &bf[(size_t)sb * (l * l + l)];
+    if (weno_beta_diag(l, Sm, B0, W, &lam[(size_t)sb * l])) {
+      set_error("WENO smoothness forms: Cholesky failed");
+      return HOPE_EINVAL;
+    }
+    for (int k = 0; k < l; ++k) {
+      double rs = 0.0;
+      for (int a = 0; a < l; ++a) rs += W[k * l + a];
+      W[l * l + k] = rs;
+    }
+  }
+  std::vector<double> bcoef((size_t)l * l * l * l);
+  for (int sy = 0; sy < l; ++sy)
+    for (int k = 0; k < l; ++k)
+      for (int sx = 0; sx < l; ++sx)
+        for (int kp = 0; kp < l; ++kp) {
+          double c = lam[(size_t)sy * l + k] * lam[(size_t)sx * l + kp] - 1.0;
+          if (c < 1e-12) c = 0.0;
+          bcoef[(((size_t)sy * l + k) * l + sx) * l + kp] = c;
+        }
+  int rc;
+  if ((rc = upload_t(ctx, &ctx->wsub, wsub))) return rc;
+  if ((rc = upload_t(ctx, &ctx->gpm, gpm))) return rc;
+  if ((rc = upload_t(ctx, &ctx->sig, sig))) return rc;
+  if ((rc = upload_t(ctx, &ctx->bform, bf))) return rc;
+  if ((rc = upload_t(ctx, &ctx->bcoef, bcoef))) return rc;
+  return HOPE_OK;
 }
 }  // namespace hope

@@ -290,4 +290,77 @@ HOPE_HD void weno_beta_forms_1d(int l, int o0, double *S, double *B0) {
   }
 }
 
+// Simultaneous diagonalisation of the smoothness forms of one sub-stencil: with
+// B0 = L L^T (Cholesky) and L^{-1} S L^{-T} = U diag(lam) U^T (cyclic Jacobi), the matrix
+// Winv = U^T L^T gives q^T B0 q = |Winv q|^2 and q^T S q = sum_k lam_k (Winv q)_k^2, so the
+// 2-D indicator is beta = sum_{k,k'} (lam_y,k lam_x,k' - 1) Z_{k k'}^2, Z = Winv_y Q Winv_x^T.
+// Returns 0 on success.
+inline int weno_beta_diag(int l, const double *S, const double *B0, double *Winv, double *lam) {
+  double L[HOPE_MAXME][HOPE_MAXME] = {}, Li[HOPE_MAXME][HOPE_MAXME] = {};
+  for (int i = 0; i < l; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double s = B0[i * l + j];
+      for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+      if (i == j) {
+        if (!(s > 0)) return -1;
+        L[i][i] = sqrt(s);
+      } else {
+        L[i][j] = s / L[j][j];
+      }
+    }
+  for (int c = 0; c < l; ++c) {  // Li = L^{-1} by forward substitution
+    for (int i = 0; i < l; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) s -= L[i][k] * Li[k][c];
+      Li[i][c] = s / L[i][i];
+    }
+  }
+  double M[HOPE_MAXME][HOPE_MAXME], U[HOPE_MAXME][HOPE_MAXME];
+  for (int i = 0; i < l; ++i)
+    for (int j = 0; j < l; ++j) {
+      double s = 0.0;
+      for (int a = 0; a < l; ++a)
+        for (int b = 0; b < l; ++b) s += Li[i][a] * S[a * l + b] * Li[j][b];
+      M[i][j] = s;
+      U[i][j] = (i == j) ? 1.0 : 0.0;
+    }
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < l; ++p)
+      for (int q = p + 1; q < l; ++q) off += M[p][q] * M[p][q];
+    if (off < 1e-32) break;
+    for (int p = 0; p < l; ++p)
+      for (int q = p + 1; q < l; ++q) {
+        if (fabs(M[p][q]) < 1e-300) continue;
+        double th = (M[q][q] - M[p][p]) / (2.0 * M[p][q]);
+        double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < l; ++k) {  // M <- J^T M J
+          double mkp = M[k][p], mkq = M[k][q];
+          M[k][p] = c * mkp - s * mkq;
+          M[k][q] = s * mkp + c * mkq;
+        }
+        for (int k = 0; k < l; ++k) {
+          double mpk = M[p][k], mqk = M[q][k];
+          M[p][k] = c * mpk - s * mqk;
+          M[q][k] = s * mpk + c * mqk;
+        }
+        for (int k = 0; k < l; ++k) {
+          double ukp = U[k][p], ukq = U[k][q];
+          U[k][p] = c * ukp - s * ukq;
+          U[k][q] = s * ukp + c * ukq;
+        }
+      }
+  }
+  for (int k = 0; k < l; ++k) {
+    lam[k] = M[k][k];
+    for (int a = 0; a < l; ++a) {  // Winv = U^T L^T: row k = sum_i U[i][k] L[a][i]
+      double s = 0.0;
+      for (int i = 0; i < l; ++i) s += U[i][k] * L[a][i];
+      Winv[k * l + a] = s;
+    }
+  }
+  return 0;
+}
+
 }  // namespace hope

@@ -1,19 +1,211 @@
-// hope_weno.cuh -- genuine-2D WENO-Z reconstruction kernels (section 3.2).
+// hope_weno.cuh -- genuine two-dimensional WENO-Z reconstruction (section 3.2) with the
+// cell-point sources, one thread per cell, for sm_103a.
+//
+// Per cell and variable, with the k x k stencil Q staged in shared memory:
+//   beta_i   smoothness indicator of each of the s = l^2 sub-stencils (eq. 3.25 read as
+//            the sum of squared mixed derivatives), through the simultaneous
+//            diagonalisation of the 1-D forms: beta = sum (lam_y lam_x - 1) Z^2 with
+//            Z = Winv_y Q_i Winv_x^T, sum-factorised over the sub-stencil rows;
+//   tau      eq. 3.24; f_i = 1 + tau / (beta_i + eps) (eq. 3.23);
+//   p_i(pt)  the sub-stencil TPP values at every point, x-pass per sub-stencil column,
+//            then y-pass per sub-stencil row;
+//   q(pt)    = sigma+ sum(gamma+ f p)/sum(gamma+ f) - sigma- sum(gamma- f p)/sum(gamma- f)
+//            (eqs. 3.20-3.23 with the sigma+- normalisation of the split weights).
+// Edge points go to the edge-point buffer; the me^2 cell points of the three variables
+// are staged in shared memory for the sources (eqs. 2.2, 2.3, 3.6).
 #pragma once
 #include "hope_internal.h"
+#include "hope_kernels.cuh"
 
 namespace hope {
 
 template <typename T, int K>
-int launch_recon_weno(hope_ctx *ctx, Grid &g, const T *qs, cudaStream_t st) {
-  (void)ctx; (void)g; (void)qs; (void)st;
-  set_error("WENO2D reconstruction is not available in this build");
-  return HOPE_EUNSUPPORTED;
+struct WenoShape {
+  static constexpr int L = (K + 1) / 2;
+  static constexpr int S = L * L;
+  static constexpr int ME = L;
+  static constexpr int NPOS = ME + 2;
+  static constexpr int NPOC = 4 * ME + ME * ME;
+  static constexpr int NT = REC_TX * REC_TY;
+  static constexpr size_t smem_elems() {
+    return 3 * Shape<K>::RH * Shape<K>::RW + NPOS * L * L + NPOC * 2 * S + NPOC * 2 + L * (L * L + L) +
+           S * S + 3 * ME * ME * NT;
+  }
+};
+
+template <typename T, int K>
+__global__ void __launch_bounds__(REC_TX *REC_TY)
+    k_recon_weno(const T *__restrict__ q, const T *__restrict__ gext, const T *__restrict__ wsub_g,
+                 const T *__restrict__ gpm_g, const T *__restrict__ sig_g, const T *__restrict__ bform_g,
+                 const T *__restrict__ bcoef_g, const T *__restrict__ Xg, const T *__restrict__ t1w, T *__restrict__ ep, T *__restrict__ sb,
+                 int N, int ne, T omega, FCoef<T> fc, T eps) {
+  using W = WenoShape<T, K>;
+  using SH = Shape<K>;
+  constexpr int L = W::L, S = W::S, ME = W::ME, NPOS = W::NPOS, NPOC = W::NPOC, NT = W::NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *raw = reinterpret_cast<T *>(smem_raw);        // [3][RH][RW]
+  T *wsub = raw + 3 * SH::RH * SH::RW;             // [NPOS][L][L]
+  T *gpm = wsub + NPOS * L * L;                    // [NPOC][2][S]
+  T *sig = gpm + NPOC * 2 * S;                     // [NPOC][2]
+  T *bform = sig + NPOC * 2;                       // [L][L*L + L] Winv, row sums
+  T *bcoef = bform + L * (L * L + L);              // [L][L][L][L]
+  T *cq = bcoef + S * S;                           // [3][ME*ME][NT]
+  const int p = blockIdx.z;
+  const int i0 = blockIdx.x * REC_TX, j0 = blockIdx.y * REC_TY;
+  for (int t = threadIdx.x; t < NPOS * L * L; t += blockDim.x) wsub[t] = wsub_g[t];
+  for (int t = threadIdx.x; t < NPOC * 2 * S; t += blockDim.x) gpm[t] = gpm_g[t];
+  for (int t = threadIdx.x; t < NPOC * 2; t += blockDim.x) sig[t] = sig_g[t];
+  for (int t = threadIdx.x; t < L * (L * L + L); t += blockDim.x) bform[t] = bform_g[t];
+  for (int t = threadIdx.x; t < S * S; t += blockDim.x) bcoef[t] = bcoef_g[t];
+  load_tile<T, K>(raw, q, gext, p, i0, j0, N, ne);
+  __syncthreads();
+  const int tid = threadIdx.x;
+  const int tx = tid % REC_TX, ty = tid / REC_TX;
+  const int i = i0 + tx, j = j0 + ty;
+  if (i >= N || j >= N) return;
+  const size_t pn = (size_t)6 * N * N;
+  const size_t cell = ((size_t)p * N + j) * N + i;
+  const T tau_scale = T(2) / (T(S + 1) * T(S));
+
+#pragma unroll 1
+  for (int v = 0; v < 3; ++v) {
+    const T *Qv = raw + (v * SH::RH + ty) * SH::RW + tx;  // Q(r, c) = Qv[r * RW + c]
+    // ---------------------------------------------------------------- beta (eq. 3.25)
+    // on Q - q_c (beta ignores constants): Zx = Winv_x (Q - q_c) row-wise, then Winv_y.
+    const T qc = Qv[SH::H * SH::RW + SH::H];
+    T f[S];
+#pragma unroll
+    for (int t = 0; t < S; ++t) f[t] = T(0);
+#pragma unroll
+    for (int sx = 0; sx < L; ++sx) {
+      const T *Wx = bform + sx * (L * L + L);
+#pragma unroll 1
+      for (int kp = 0; kp < L; ++kp) {
+        T Zx[K];
+        const T rs = Wx[L * L + kp];
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+          T s = -qc * rs;
+#pragma unroll
+          for (int a = 0; a < L; ++a) s = fma(Wx[kp * L + a], Qv[r * SH::RW + sx + a], s);
+          Zx[r] = s;
+        }
+#pragma unroll
+        for (int sy = 0; sy < L; ++sy) {
+          const T *Wy = bform + sy * (L * L + L);
+#pragma unroll
+          for (int k = 0; k < L; ++k) {
+            T z = 0;
+#pragma unroll
+            for (int b = 0; b < L; ++b) z = fma(Wy[k * L + b], Zx[sy + b], z);
+            const T c = bcoef[((sy * L + k) * L + sx) * L + kp];
+            f[sy * L + sx] = fma(c * z, z, f[sy * L + sx]);
+          }
+        }
+      }
+    }
+    // ---------------------------------------------------------------- tau (eq. 3.24), f
+    T tsum = 0;
+#pragma unroll
+    for (int e = 0; e < S - 1; ++e)
+#pragma unroll
+      for (int ps = e + 1; ps < S; ++ps) tsum += fabs(f[ps] - f[e]);
+    const T tau = tsum * tau_scale;
+#pragma unroll
+    for (int t = 0; t < S; ++t) f[t] = T(1) + tau / (f[t] + eps);
+    // ---------------------------------------------------------------- points
+#pragma unroll 1
+    for (int t = 0; t < NPOS; ++t) {
+      const int npt = t < 2 ? ME : ME + 2;
+      const int g = t - 2;
+      T Ap[ME + 2], Am[ME + 2];
+#pragma unroll
+      for (int jj = 0; jj < ME + 2; ++jj) Ap[jj] = Am[jj] = T(0);
+#pragma unroll
+      for (int sx = 0; sx < L; ++sx) {
+        T Xc[K];
+        const T *wx = wsub + (t * L + sx) * L;
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+          T s = 0;
+#pragma unroll
+          for (int a = 0; a < L; ++a) s = fma(wx[a], Qv[r * SH::RW + sx + a], s);
+          Xc[r] = s;
+        }
+#pragma unroll
+        for (int jj = 0; jj < ME + 2; ++jj) {
+          if (jj < npt) {
+            const int tyi = t < 2 ? 2 + jj : jj;
+            const int pt = t < 2 ? t * ME + jj : (jj == 0 ? 2 * ME + g : (jj == 1 ? 3 * ME + g : 4 * ME + (jj - 2) * ME + g));
+            const T *gp = gpm + pt * 2 * S;
+#pragma unroll
+            for (int sy = 0; sy < L; ++sy) {
+              const T *wy = wsub + (tyi * L + sy) * L;
+              T pv = 0;
+#pragma unroll
+              for (int b = 0; b < L; ++b) pv = fma(wy[b], Xc[sy + b], pv);
+              const int ii = sy * L + sx;
+              const T fp = f[ii] * pv;
+              Ap[jj] = fma(gp[ii], fp, Ap[jj]);
+              Am[jj] = fma(gp[S + ii], fp, Am[jj]);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int jj = 0; jj < ME + 2; ++jj) {
+        if (jj < npt) {
+          const int pt = t < 2 ? t * ME + jj : (jj == 0 ? 2 * ME + g : (jj == 1 ? 3 * ME + g : 4 * ME + (jj - 2) * ME + g));
+          const T *gp = gpm + pt * 2 * S;
+          T Dp = 0, Dm = 0;
+#pragma unroll
+          for (int ii = 0; ii < S; ++ii) {
+            Dp = fma(gp[ii], f[ii], Dp);
+            Dm = fma(gp[S + ii], f[ii], Dm);
+          }
+          const T val = sig[2 * pt] * Ap[jj] / Dp - sig[2 * pt + 1] * Am[jj] / Dm;
+          if (t < 2) {
+            ep[((size_t)(t * 3 + v) * ME + jj) * pn + cell] = val;
+          } else if (jj < 2) {
+            ep[((size_t)((2 + jj) * 3 + v) * ME + g) * pn + cell] = val;
+          } else {
+            cq[(v * ME * ME + (jj - 2) * ME + g) * NT + tid] = val;
+          }
+        }
+      }
+    }
+  }
+  // ------------------------------------------------------------------ sources
+  const T fc0 = fc.c[3 * p], fc1 = fc.c[3 * p + 1], fc2 = fc.c[3 * p + 2];
+  T s1 = 0, s2 = 0;
+#pragma unroll 1
+  for (int h = 0; h < ME; ++h) {
+    const T Y = Xg[j * ME + h];
+#pragma unroll
+    for (int g = 0; g < ME; ++g) {
+      const T X = Xg[i * ME + g];
+      const T q0 = cq[(0 * ME * ME + h * ME + g) * NT + tid];
+      const T q1 = cq[(1 * ME * ME + h * ME + g) * NT + tid];
+      const T q2 = cq[(2 * ME * ME + h * ME + g) * NT + tid];
+      const T tw = t1w[(((size_t)j * N + i) * ME + h) * ME + g];
+      const T sl = fc0 + fc1 * X + fc2 * Y;
+      const T rq = rcp(q0);
+      const T XY = X * Y, X2 = X * X, Y2 = Y * Y;
+      const T os = omega * sl;
+      T a1 = (-XY * Y * q1 + Y * (T(1) + Y2) * q2) * q1 * rq + os * (-XY * q1 + (T(1) + Y2) * q2);
+      T a2 = (X * (T(1) + X2) * q1 - X2 * Y * q2) * q2 * rq + os * (-(T(1) + X2) * q1 + XY * q2);
+      s1 = fma(tw, a1, s1);
+      s2 = fma(tw, a2, s2);
+    }
+  }
+  sb[cell] = s1;
+  sb[pn + cell] = s2;
 }
 
 template <typename T, int K>
-int weno_set_smem_attr() {
-  return HOPE_OK;
-}
+int launch_recon_weno(hope_ctx *ctx, Grid &g, const T *qs, cudaStream_t st);
+
+template <typename T, int K>
+int weno_set_smem_attr();
 
 }  // namespace hope

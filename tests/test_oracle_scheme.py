@@ -158,3 +158,16 @@ def test_ghost_fill_converges_to_exact_extended_averages(k):
     rates = np.log2(errs[0] / errs[1])
     assert np.all(errs[1] < 1e-3)
     assert np.all(rates > k - 0.8), (errs, rates)
+
+
+def test_weno_dam_break_positivity_depends_on_jump_ratio():
+    """Reading of the dam-break workload: with the paper's 2:1 jump (eq. 5.19) the genuine
+    2-D WENO-Z reconstruction stays positive; a 10:1 jump undershoots below phi = 0 at
+    edge points (negative linear weights split with theta = 3, eq. 3.20, give no
+    positivity guarantee), so that case cannot run without a limiter."""
+    o = O.Oracle(17, 5, scheme=O.WENO, omega=0.0)
+    for h_out, positive in ((5.0, True), (1.0, False)):
+        q = o.dam_break(h_in=10.0, h_out=h_out)
+        ext, _ = o.fill_ghosts(q)
+        pts = o.reconstruct_all(ext)
+        assert (pts[0].min() > 0.0) == positive, (h_out, pts[0].min())
