@@ -1,0 +1,405 @@
+// hope_adjoint.cuh -- hand-written vector-Jacobian products of one stage L(q)
+// (eq. 3.1) for sm_103a.  Given lam (the adjoint of dq/dt) the kernels compute
+// (dL/dq)^T lam, in reverse order of the forward stage:
+//   k_flux_adj     edge quadrature (eq. 3.5) and LMARS (eqs. 3.31-3.38) adjoints, per
+//                  edge, from lam of the two adjacent cells; panel-boundary edges with
+//                  the transposed conversions (eqs. 3.26-3.29); writes lam at every
+//                  edge point of every cell (each point has exactly one writer)
+//   k_recon_*_adj  per cell: adjoint of the cell-point sources (eqs. 2.2, 2.3, 3.6),
+//                  then of the reconstruction (TPP: transposed sum factorisation), giving
+//                  the gradient with respect to the k x k stencil values
+//   k_gather_adj   per extended cell: sum of the stencil gradients of every cell whose
+//                  stencil covers it (deterministic, no atomics)
+//   k_ghost_adj    interior cells += G^T lam_ring (transposed ghost operator, eq. 7.12),
+//                  fused with the Runge-Kutta combination of adjoint states
+#pragma once
+#include "hope_kernels.cuh"
+
+namespace hope {
+
+// LMARS flux and its vector-Jacobian product at one edge point (same arithmetic as lmars()).
+template <typename T>
+__device__ __forceinline__ void lmars_vjp(const T qL[3], const T qR[3], const T *m5, int dir, const T lF[3],
+                                          T lqL[3], T lqR[3]) {
+  const T isg = m5[0], s11 = m5[1], is11 = m5[2], pn = m5[3], pc = m5[4];
+  const int n = 1 + dir;
+  const T phL = qL[0] * isg, phR = qR[0] * isg;
+  const T rL = rcp(qL[0]), rR = rcp(qR[0]);
+  const T uL = qL[n] * rL * is11, uR = qR[n] * rR * is11;
+  const T sL = sqrt(phL), sR = sqrt(phR);
+  const T c = T(0.5) * (sL + sR);
+  const T ic = rcp(c);
+  const T ms = T(0.5) * (uL + uR - (phR - phL) * ic);
+  const T ph = T(0.5) * (phL + phR - c * (uR - uL));
+  const T m = ms * s11;
+  const T am = fabs(m);
+  const T sg = m > T(0) ? T(1) : (m < T(0) ? T(-1) : T(0));
+  // F_v = 1/2 (m (qL + qR) - |m| (qR - qL)) + P
+  T lm = 0;
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    lqL[v] = T(0.5) * (m + am) * lF[v];
+    lqR[v] = T(0.5) * (m - am) * lF[v];
+    lm += T(0.5) * ((qL[v] + qR[v]) - sg * (qR[v] - qL[v])) * lF[v];
+  }
+  const T lph = T(2) * ph * (pn * lF[1 + dir] + pc * lF[2 - dir]);
+  const T lms = lm * s11;
+  T luL = T(0.5) * lms, luR = T(0.5) * lms;
+  T lphL = T(0.5) * ic * lms, lphR = -T(0.5) * ic * lms;
+  const T lic = -T(0.5) * (phR - phL) * lms;
+  lphL += T(0.5) * lph;
+  lphR += T(0.5) * lph;
+  T lc = -T(0.5) * (uR - uL) * lph;
+  luR -= T(0.5) * c * lph;
+  luL += T(0.5) * c * lph;
+  lc -= ic * ic * lic;
+  const T lsL = T(0.5) * lc, lsR = T(0.5) * lc;
+  lphL += lsL / (T(2) * sL);
+  lphR += lsR / (T(2) * sR);
+  lqL[n] += rL * is11 * luL;
+  lqR[n] += rR * is11 * luR;
+  lqL[0] += -rL * rL * (qL[n] * is11 * luL) + isg * lphL;
+  lqR[0] += -rR * rR * (qR[n] * is11 * luR) + isg * lphR;
+}
+
+// ---------------------------------------------------------------------------------
+// Flux adjoint.  lamL: adjoint of the tendency [3][6][N][N]; lep: [4][3][me][6][N][N].
+// ---------------------------------------------------------------------------------
+template <typename T, int ME>
+__global__ void __launch_bounds__(256)
+    k_flux_adj(const T *__restrict__ ep, const T *__restrict__ mx, const T *__restrict__ gwg,
+               const int *__restrict__ bedge, const T *__restrict__ bconv, const T *__restrict__ lamL,
+               T *__restrict__ lep, int N, T inv_dx) {
+  const long long nx = 6LL * N * (N - 1), ny = nx, nb = 12LL * N;
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nx + ny + nb) return;
+  const size_t pn = (size_t)6 * N * N;
+  T gw[ME];
+#pragma unroll
+  for (int g = 0; g < ME; ++g) gw[g] = gwg[g];
+  if (idx < nx + ny) {
+    const int dir = idx < nx ? 0 : 1;
+    long long r = dir ? idx - nx : idx;
+    int p, a, e;
+    if (dir == 0) {
+      e = 1 + (int)(r % (N - 1));
+      long long t = r / (N - 1);
+      a = (int)(t % N);
+      p = (int)(t / N);
+    } else {
+      a = (int)(r % N);
+      long long t = r / N;
+      e = 1 + (int)(t % (N - 1));
+      p = (int)(t / (N - 1));
+    }
+    size_t cl, cr;
+    if (dir == 0) {
+      cl = ((size_t)p * N + a) * N + (e - 1);
+      cr = cl + 1;
+    } else {
+      cl = ((size_t)p * N + (e - 1)) * N + a;
+      cr = cl + N;
+    }
+    const int sl = dir ? 3 : 1, sr = dir ? 2 : 0;
+    T lFbar[3];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) lFbar[v] = (lamL[v * pn + cr] - lamL[v * pn + cl]) * inv_dx;
+#pragma unroll
+    for (int g = 0; g < ME; ++g) {
+      T qL[3], qR[3], lF[3], lqL[3], lqR[3];
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        qL[v] = ep[((size_t)(sl * 3 + v) * ME + g) * pn + cl];
+        qR[v] = ep[((size_t)(sr * 3 + v) * ME + g) * pn + cr];
+        lF[v] = gw[g] * lFbar[v];
+      }
+      lmars_vjp(qL, qR, mx + (((size_t)e * N + a) * ME + g) * 5, dir, lF, lqL, lqR);
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        lep[((size_t)(sl * 3 + v) * ME + g) * pn + cl] = lqL[v];
+        lep[((size_t)(sr * 3 + v) * ME + g) * pn + cr] = lqR[v];
+      }
+    }
+    return;
+  }
+  long long r = idx - nx - ny;
+  const int ce = (int)(r / N), t = (int)(r % N);
+  const int A = bedge[ce * 5 + 0], sA = bedge[ce * 5 + 1], B = bedge[ce * 5 + 2], sB = bedge[ce * 5 + 3],
+            flip = bedge[ce * 5 + 4];
+  const int tB = flip ? N - 1 - t : t;
+  auto side_cell = [N](int P, int side, int tt) -> size_t {
+    int ci = side == 0 ? 0 : (side == 1 ? N - 1 : tt);
+    int cj = side == 2 ? 0 : (side == 3 ? N - 1 : tt);
+    return ((size_t)P * N + cj) * N + ci;
+  };
+  const size_t cA = side_cell(A, sA, t), cB = side_cell(B, sB, tB);
+  const int dirA = sA >> 1;
+  const T sgA = (sA & 1) ? T(1) : T(-1), sgB = (sB & 1) ? T(1) : T(-1);
+  const T sg = -sgA * sgB;
+  const int eA = (sA & 1) ? N : 0;
+  // d L(cell) / d Fbar(edge) = -1/dx on the cell's east/north edge, +1/dx on west/south
+  T lFA[3], lFB[3];
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    lFA[v] = -sgA * lamL[v * pn + cA] * inv_dx;
+    lFB[v] = -sgB * lamL[v * pn + cB] * inv_dx;
+  }
+#pragma unroll
+  for (int g = 0; g < ME; ++g) {
+    const int gB = flip ? ME - 1 - g : g;
+    const T *cv = bconv + (((size_t)ce * N + t) * ME + g) * 9;
+    T qin[3], qb[3], qo[3], lF[3], l1[3], l2[3];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      qin[v] = ep[((size_t)(sA * 3 + v) * ME + g) * pn + cA];
+      qb[v] = ep[((size_t)(sB * 3 + v) * ME + gB) * pn + cB];
+    }
+    qo[0] = cv[0] * qb[0];
+    qo[1] = cv[1] * qb[1] + cv[2] * qb[2];
+    qo[2] = cv[3] * qb[1] + cv[4] * qb[2];
+    // Fbar_A = sum_g w_g F_g; Fbar_B,0 = sg Fbar_A,0; Fbar_B,mom = sum_g w_gB sg C_AB F_g,mom
+    lF[0] = gw[g] * (lFA[0] + sg * lFB[0]);
+    lF[1] = gw[g] * lFA[1] + gw[gB] * sg * (cv[5] * lFB[1] + cv[7] * lFB[2]);
+    lF[2] = gw[g] * lFA[2] + gw[gB] * sg * (cv[6] * lFB[1] + cv[8] * lFB[2]);
+    const T *m5 = mx + (((size_t)eA * N + t) * ME + g) * 5;
+    T lin[3], lo[3];
+    if (sA & 1) {
+      lmars_vjp(qin, qo, m5, dirA, lF, l1, l2);
+#pragma unroll
+      for (int v = 0; v < 3; ++v) { lin[v] = l1[v]; lo[v] = l2[v]; }
+    } else {
+      lmars_vjp(qo, qin, m5, dirA, lF, l1, l2);
+#pragma unroll
+      for (int v = 0; v < 3; ++v) { lo[v] = l1[v]; lin[v] = l2[v]; }
+    }
+    T lb[3];
+    lb[0] = cv[0] * lo[0];
+    lb[1] = cv[1] * lo[1] + cv[3] * lo[2];
+    lb[2] = cv[2] * lo[1] + cv[4] * lo[2];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      lep[((size_t)(sA * 3 + v) * ME + g) * pn + cA] = lin[v];
+      lep[((size_t)(sB * 3 + v) * ME + gB) * pn + cB] = lb[v];
+    }
+  }
+}
+
+// Vector-Jacobian product of the cell-point source (same arithmetic as the forward).
+template <typename T>
+__device__ __forceinline__ void source_vjp(const T q[3], T X, T Y, T os, T tw, T l1, T l2, T lq[3]) {
+  const T rq = rcp(q[0]);
+  const T XY = X * Y, X2 = X * X, Y2 = Y * Y;
+  const T A1 = -XY * Y * q[1] + Y * (T(1) + Y2) * q[2];
+  const T A2 = X * (T(1) + X2) * q[1] - X2 * Y * q[2];
+  const T la1 = tw * l1, la2 = tw * l2;
+  // a1 = A1 q1 / q0 + os (-XY q1 + (1+Y2) q2); a2 = A2 q2 / q0 + os (-(1+X2) q1 + XY q2)
+  lq[0] = -(la1 * A1 * q[1] + la2 * A2 * q[2]) * rq * rq;
+  lq[1] = la1 * ((-XY * Y) * q[1] * rq + A1 * rq - os * XY) + la2 * (X * (T(1) + X2) * q[2] * rq - os * (T(1) + X2));
+  lq[2] = la1 * (Y * (T(1) + Y2) * q[1] * rq + os * (T(1) + Y2)) + la2 * ((-X2 * Y) * q[2] * rq + A2 * rq + os * XY);
+}
+
+// ---------------------------------------------------------------------------------
+// TPP reconstruction + sources adjoint: per cell, the gradient with respect to its
+// K x K stencil, grad[v][b*K + a][cell] (a: x offset + H, b: y offset + H).
+// ---------------------------------------------------------------------------------
+template <typename T, int K>
+__global__ void __launch_bounds__(REC_TX *REC_TY)
+    k_recon_tpp_adj(const T *__restrict__ q, const T *__restrict__ gext, const T *__restrict__ w1g,
+                    const T *__restrict__ Xg, const T *__restrict__ t1w, const T *__restrict__ lep,
+                    const T *__restrict__ lamL, T *__restrict__ grad, int N, int ne, T omega, FCoef<T> fc) {
+  using S = Shape<K>;
+  constexpr int ME = S::ME, NPOS = S::NPOS, NT = REC_TX * REC_TY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *raw = reinterpret_cast<T *>(smem_raw);              // [3][RH][RW]
+  T *xs = raw + 3 * S::RH * S::RW;                        // [3][NPOS][RH][TX]
+  T *w1 = xs + 3 * NPOS * S::RH * REC_TX;                 // [NPOS][K]
+  T *lcq = w1 + NPOS * K;                                 // [3][ME*ME][NT] adjoint at cell points
+  const int p = blockIdx.z;
+  const int i0 = blockIdx.x * REC_TX, j0 = blockIdx.y * REC_TY;
+  for (int t = threadIdx.x; t < NPOS * K; t += blockDim.x) w1[t] = w1g[t];
+  load_tile<T, K>(raw, q, gext, p, i0, j0, N, ne);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 3 * S::RH * REC_TX; idx += blockDim.x) {
+    int v = idx / (S::RH * REC_TX);
+    int rem = idx - v * S::RH * REC_TX;
+    int r = rem / REC_TX, c = rem - r * REC_TX;
+    const T *row = raw + (v * S::RH + r) * S::RW + c;
+#pragma unroll
+    for (int t = 0; t < NPOS; ++t) {
+      T s = 0;
+#pragma unroll
+      for (int b = 0; b < K; ++b) s = fma(w1[t * K + b], row[b], s);
+      xs[((v * NPOS + t) * S::RH + r) * REC_TX + c] = s;
+    }
+  }
+  __syncthreads();
+  const int tid = threadIdx.x;
+  const int tx = tid % REC_TX, ty = tid / REC_TX;
+  const int i = i0 + tx, j = j0 + ty;
+  if (i >= N || j >= N) return;
+  const size_t pn = (size_t)6 * N * N;
+  const size_t cell = ((size_t)p * N + j) * N + i;
+  const T fc0 = fc.c[3 * p], fc1 = fc.c[3 * p + 1], fc2 = fc.c[3 * p + 2];
+  const T lS1 = lamL[pn + cell], lS2 = lamL[2 * pn + cell];
+  // phase 1: adjoint at the cell points (recomputed values, source VJP)
+#pragma unroll 1
+  for (int g = 0; g < ME; ++g) {
+    const T X = Xg[i * ME + g];
+    T col[3][K];
+#pragma unroll
+    for (int v = 0; v < 3; ++v)
+#pragma unroll
+      for (int b = 0; b < K; ++b) col[v][b] = xs[((v * NPOS + 2 + g) * S::RH + ty + b) * REC_TX + tx];
+#pragma unroll 1
+    for (int h = 0; h < ME; ++h) {
+      T qv[3];
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        T s = 0;
+#pragma unroll
+        for (int b = 0; b < K; ++b) s = fma(w1[(2 + h) * K + b], col[v][b], s);
+        qv[v] = s;
+      }
+      const T Y = Xg[j * ME + h];
+      const T tw = t1w[(((size_t)j * N + i) * ME + h) * ME + g];
+      const T os = omega * (fc0 + fc1 * X + fc2 * Y);
+      T lq[3];
+      source_vjp(qv, X, Y, os, tw, lS1, lS2, lq);
+#pragma unroll
+      for (int v = 0; v < 3; ++v) lcq[(v * ME * ME + h * ME + g) * NT + tid] = lq[v];
+    }
+  }
+  // phase 2: per stencil row b, gt[v][t] = sum over points at x-position t of
+  // w1[ty(pt)][b] lam(pt), then grad[v][b][a] = sum_t w1[t][a] gt[v][t]
+#pragma unroll 1
+  for (int b = 0; b < K; ++b) {
+    T gacc[3][K];
+#pragma unroll
+    for (int v = 0; v < 3; ++v)
+#pragma unroll
+      for (int a = 0; a < K; ++a) gacc[v][a] = T(0);
+#pragma unroll 1
+    for (int t = 0; t < NPOS; ++t) {
+      T gt[3] = {0, 0, 0};
+      if (t < 2) {
+#pragma unroll
+        for (int r = 0; r < ME; ++r) {
+          const T w = w1[(2 + r) * K + b];
+#pragma unroll
+          for (int v = 0; v < 3; ++v) gt[v] = fma(w, lep[((size_t)(t * 3 + v) * ME + r) * pn + cell], gt[v]);
+        }
+      } else {
+        const int g = t - 2;
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+          const T w = w1[side * K + b];
+#pragma unroll
+          for (int v = 0; v < 3; ++v)
+            gt[v] = fma(w, lep[((size_t)((2 + side) * 3 + v) * ME + g) * pn + cell], gt[v]);
+        }
+#pragma unroll
+        for (int h = 0; h < ME; ++h) {
+          const T w = w1[(2 + h) * K + b];
+#pragma unroll
+          for (int v = 0; v < 3; ++v) gt[v] = fma(w, lcq[(v * ME * ME + h * ME + g) * NT + tid], gt[v]);
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < K; ++a) {
+        const T w = w1[t * K + a];
+#pragma unroll
+        for (int v = 0; v < 3; ++v) gacc[v][a] = fma(w, gt[v], gacc[v][a]);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 3; ++v)
+#pragma unroll
+      for (int a = 0; a < K; ++a) grad[((size_t)v * K * K + b * K + a) * pn + cell] = gacc[v][a];
+  }
+}
+
+template <typename T, int K>
+__host__ __device__ constexpr size_t recon_adj_smem_bytes() {
+  return recon_smem_bytes<T, K>() + sizeof(T) * 3 * Shape<K>::ME * Shape<K>::ME * REC_TX * REC_TY;
+}
+
+// ---------------------------------------------------------------------------------
+// Gather: lam at every extended cell (xi, yj) (interior coordinates in [-H, N+H)):
+// sum over cells c = (xi + H - a, yj + H - b) of grad[c][b][a].  Interior cells go to
+// lam_direct[3][6][N][N], ring cells to lam_ring[3][6][ne][ne].
+// ---------------------------------------------------------------------------------
+template <typename T, int K>
+__global__ void __launch_bounds__(256)
+    k_gather_adj(const T *__restrict__ grad, T *__restrict__ lam_direct, T *__restrict__ lam_ring, int N) {
+  constexpr int H = (K - 1) / 2;
+  const int ne = N + 2 * H;
+  const long long total = 6LL * ne * ne;
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int ii = (int)(idx % ne);
+  const long long pj = idx / ne;
+  const int jj = (int)(pj % ne), p = (int)(pj / ne);
+  const int xi = ii - H, yj = jj - H;
+  const size_t pn = (size_t)6 * N * N, pe = (size_t)6 * ne * ne;
+  T s[3] = {0, 0, 0};
+#pragma unroll
+  for (int b = 0; b < K; ++b) {
+    const int cj = yj + H - b;
+    if (cj < 0 || cj >= N) continue;
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+      const int ci = xi + H - a;
+      if (ci < 0 || ci >= N) continue;
+      const size_t cell = ((size_t)p * N + cj) * N + ci;
+#pragma unroll
+      for (int v = 0; v < 3; ++v) s[v] += grad[((size_t)v * K * K + b * K + a) * pn + cell];
+    }
+  }
+  if (xi >= 0 && xi < N && yj >= 0 && yj < N) {
+    const size_t cell = ((size_t)p * N + yj) * N + xi;
+#pragma unroll
+    for (int v = 0; v < 3; ++v) lam_direct[v * pn + cell] = s[v];
+  } else {
+#pragma unroll
+    for (int v = 0; v < 3; ++v) lam_ring[v * pe + idx] = s[v];
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Transposed ghost operator + Runge-Kutta adjoint combination, per interior cell:
+//   Lt = lam_direct + sum_rows G^T lam_ring
+//   out = a*x + b*y + d*z + c*Lt   (x, y, z may be null)
+// gtp/gtr/gtv: G^T in CSR over interior cells (row index = ghost row, weights as G).
+// ---------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_ghost_adj(const T *__restrict__ lam_direct, const T *__restrict__ lam_ring, const int *__restrict__ gtp,
+                const int *__restrict__ gtr, const T *__restrict__ gtv, const int *__restrict__ gdst,
+                const T *x, const T *y, const T *z, T *out, T a, T b, T d, T c, int N, int ne) {
+  const long long ncell = 6LL * N * N;
+  long long cid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cid >= ncell) return;
+  const size_t pe = (size_t)6 * ne * ne;
+  T s0 = lam_direct[cid], s1 = lam_direct[ncell + cid], s2 = lam_direct[2 * ncell + cid];
+  for (int t = gtp[cid]; t < gtp[cid + 1]; ++t) {
+    const int r = gtr[t];
+    const int dpos = gdst[r];
+    const T *w = gtv + (size_t)t * 5;
+    const T g0 = lam_ring[dpos], g1 = lam_ring[pe + dpos], g2 = lam_ring[2 * pe + dpos];
+    s0 += w[0] * g0;
+    s1 += w[1] * g1 + w[3] * g2;
+    s2 += w[2] * g1 + w[4] * g2;
+  }
+  T r3[3] = {s0, s1, s2};
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    const long long k = v * ncell + cid;
+    T o = c * r3[v];
+    if (x) o += a * x[k];
+    if (y) o += b * y[k];
+    if (z) o += d * z[k];
+    out[k] = o;
+  }
+}
+
+}  // namespace hope

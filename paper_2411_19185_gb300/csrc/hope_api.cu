@@ -14,6 +14,7 @@
 #include "hope_setup.h"
 #include "hope_setup_math.cuh"
 #include "hope_weno.cuh"
+#include "hope_adjoint.cuh"
 
 namespace hope {
 
@@ -66,6 +67,13 @@ int weno_set_smem_attr() {
     return HOPE_ECUDA;
   }
   return HOPE_OK;
+}
+
+template <typename T, int K>
+int launch_recon_weno_adj(hope_ctx *ctx, Grid &g, const T *qs, const T *lamL, cudaStream_t st) {
+  (void)ctx; (void)g; (void)qs; (void)lamL; (void)st;
+  set_error("the WENO2D adjoint is not available in this build");
+  return HOPE_EUNSUPPORTED;
 }
 
 // -------------------------------------------------------------------------------
@@ -163,6 +171,8 @@ template <typename T, int K>
 static int set_smem_attr() {
   size_t smem = recon_smem_bytes<T, K>();
   HOPE_CUDA_TRY(cudaFuncSetAttribute(k_recon_tpp<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  HOPE_CUDA_TRY(cudaFuncSetAttribute(k_recon_tpp_adj<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)recon_adj_smem_bytes<T, K>()));
   return weno_set_smem_attr<T, K>();
 }
 
@@ -179,6 +189,116 @@ static int set_attrs(const hope_ctx *ctx) {
   }
 #undef CASE_K
   return HOPE_EINVAL;
+}
+
+// -------------------------------------------------------------------------------
+// One stage VJP on one grid:  out = a*x + b*y + d*z + c*(dL/dq at qs)^T lamL.
+// -------------------------------------------------------------------------------
+static int ensure_adjoint_scratch(hope_ctx *ctx) {
+  for (auto &g : ctx->grids) {
+    if (g.lep) continue;
+    const size_t N = g.N, ne = g.ne, es = ctx->esize, me = ctx->me, K = ctx->k;
+    if (cudaMalloc(&g.lep, es * 4 * 3 * me * 6 * N * N) != cudaSuccess ||
+        cudaMalloc(&g.grad, es * 3 * K * K * 6 * N * N) != cudaSuccess ||
+        cudaMalloc(&g.lring, es * 3 * 6 * ne * ne) != cudaSuccess ||
+        cudaMalloc(&g.ldir, es * 3 * 6 * N * N) != cudaSuccess) {
+      set_error("adjoint scratch allocation failed");
+      return HOPE_ENOMEM;
+    }
+    cudaMemset(g.lring, 0, es * 3 * 6 * ne * ne);
+  }
+  if (!ctx->lam_a) {
+    if (cudaMalloc(&ctx->lam_a, ctx->esize * ctx->total) != cudaSuccess ||
+        cudaMalloc(&ctx->lam_b, ctx->esize * ctx->total) != cudaSuccess) {
+      set_error("adjoint scratch allocation failed");
+      return HOPE_ENOMEM;
+    }
+  }
+  return HOPE_OK;
+}
+
+struct VjpComb {
+  const void *x = nullptr, *y = nullptr, *z = nullptr;
+  double a = 0, b = 0, d = 0, c = 1;
+};
+
+template <typename T, int K>
+static int stage_vjp_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *lamL, const T *x, const T *y, const T *z,
+                          T *out, const VjpComb &cb, cudaStream_t st) {
+  constexpr int ME = (K + 1) / 2;
+  const int N = g.N, ne = g.ne;
+  if (g.rows > 0) {
+    int blocks = (int)((g.rows * 32 + 255) / 256);
+    k_ghost<T><<<blocks, 256, 0, st>>>(qs, (T *)g.gext, g.grow, g.gcol, (const T *)g.gval, g.gdst, (int)g.rows, N,
+                                       ne);
+  }
+  dim3 grid((N + REC_TX - 1) / REC_TX, (N + REC_TY - 1) / REC_TY, 6);
+  if (ctx->scheme == HOPE_TPP) {
+    k_recon_tpp<T, K><<<grid, REC_TX * REC_TY, recon_smem_bytes<T, K>(), st>>>(
+        qs, (const T *)g.gext, (const T *)ctx->w1, (const T *)g.Xg, (const T *)g.t1w, (T *)g.ep, (T *)g.sb, N, ne,
+        (T)ctx->omega, fcoef<T>(ctx));
+  } else {
+    int rc = launch_recon_weno<T, K>(ctx, g, qs, st);
+    if (rc) return rc;
+  }
+  const T inv_dx = (T)(2.0 * N / HOPE_PI);
+  {
+    long long items = 12LL * N * (N - 1) + 12LL * N;
+    k_flux_adj<T, ME><<<(int)((items + 255) / 256), 256, 0, st>>>((const T *)g.ep, (const T *)g.mx,
+                                                                   (const T *)ctx->gw, g.bedge, (const T *)g.bconv,
+                                                                   lamL, (T *)g.lep, N, inv_dx);
+  }
+  if (ctx->scheme == HOPE_TPP) {
+    k_recon_tpp_adj<T, K><<<grid, REC_TX * REC_TY, recon_adj_smem_bytes<T, K>(), st>>>(
+        qs, (const T *)g.gext, (const T *)ctx->w1, (const T *)g.Xg, (const T *)g.t1w, (const T *)g.lep, lamL,
+        (T *)g.grad, N, ne, (T)ctx->omega, fcoef<T>(ctx));
+  } else {
+    int rc = launch_recon_weno_adj<T, K>(ctx, g, qs, lamL, st);
+    if (rc) return rc;
+  }
+  {
+    long long total = 6LL * ne * ne;
+    k_gather_adj<T, K><<<(int)((total + 255) / 256), 256, 0, st>>>((const T *)g.grad, (T *)g.ldir, (T *)g.lring,
+                                                                    N);
+  }
+  {
+    long long cells = 6LL * N * N;
+    k_ghost_adj<T><<<(int)((cells + 255) / 256), 256, 0, st>>>((const T *)g.ldir, (const T *)g.lring, g.gtp, g.gtr,
+                                                               (const T *)g.gtv, g.gdst, x, y, z, out, (T)cb.a,
+                                                               (T)cb.b, (T)cb.d, (T)cb.c, N, ne);
+  }
+  HOPE_CUDA_TRY(cudaGetLastError());
+  return HOPE_OK;
+}
+
+template <typename T, int K>
+static int stage_vjp_all(hope_ctx *ctx, const void *qs, const void *lamL, void *out, const VjpComb &cb,
+                         cudaStream_t st) {
+  for (auto &g : ctx->grids) {
+    auto off = [&](const void *p) -> const T * { return p ? (const T *)p + g.off : nullptr; };
+    int rc = stage_vjp_grid<T, K>(ctx, g, off(qs), off(lamL), off(cb.x), off(cb.y), off(cb.z), (T *)out + g.off,
+                                  cb, st);
+    if (rc) return rc;
+  }
+  return HOPE_OK;
+}
+
+typedef int (*vjp_fn)(hope_ctx *, const void *, const void *, void *, const VjpComb &, cudaStream_t);
+
+template <typename T>
+static vjp_fn pick_vjp_t(int k) {
+  switch (k) {
+    case 3: return stage_vjp_all<T, 3>;
+    case 5: return stage_vjp_all<T, 5>;
+    case 7: return stage_vjp_all<T, 7>;
+    case 9: return stage_vjp_all<T, 9>;
+    case 11: return stage_vjp_all<T, 11>;
+  }
+  return nullptr;
+}
+
+static vjp_fn pick_vjp(const hope_ctx *ctx) {
+  return ctx->prec == HOPE_FP64 ? pick_vjp_t<double>(ctx->k) : pick_vjp_t<float>(ctx->k);
 }
 
 // RK step sequence (3 stages) on stream st
@@ -362,7 +482,7 @@ const char *hope_last_error_message(void) { return g_err.c_str(); }
 
 static void free_grid(Grid &g) {
   void *ptrs[] = {g.Xg, g.t1w, g.mx, g.gval, g.grow, g.gcol, g.gdst, g.bedge, g.bconv,
-                  g.gext, g.ep, g.fx, g.fy, g.sb};
+                  g.gext, g.ep, g.fx, g.fy, g.sb, g.gtp, g.gtr, g.gtv, g.lep, g.grad, g.lring, g.ldir};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   g = Grid();
@@ -374,7 +494,7 @@ void hope_destroy(hope_t ctx) {
   for (auto &g : ctx->grids) free_grid(g);
   void *ptrs[] = {ctx->w1, ctx->gw, ctx->wsub, ctx->gpm, ctx->sig, ctx->bform, ctx->bcoef, ctx->state,
                   ctx->q1, ctx->q2, ctx->lbuf, ctx->status, ctx->mass_part, ctx->mass_out,
-                  ctx->carry, ctx->q1l, ctx->q2l};
+                  ctx->carry, ctx->q1l, ctx->q2l, ctx->lam_a, ctx->lam_b};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -497,6 +617,24 @@ static int init_impl(int n_members, const int *Ns, int order, int scheme, const 
     TRY(upload_int(&gr.gcol, cols));
     TRY(upload_int(&gr.gdst, dst));
     TRY(upload(&gr.gval, vals, ctx->esize));
+    {
+      // transposed ghost operator for the adjoint: CSR over interior cells
+      const int ncell = 6 * gr.N * gr.N;
+      std::vector<int> tp(ncell + 1, 0), tr(cols.size());
+      std::vector<double> tv(vals.size());
+      for (size_t t = 0; t < cols.size(); ++t) tp[cols[t] + 1]++;
+      for (int c = 0; c < ncell; ++c) tp[c + 1] += tp[c];
+      std::vector<int> fill(tp.begin(), tp.end() - 1);
+      for (int r = 0; r + 1 < (int)rowptr.size(); ++r)
+        for (int t = rowptr[r]; t < rowptr[r + 1]; ++t) {
+          int o = fill[cols[t]]++;
+          tr[o] = r;
+          for (int u = 0; u < 5; ++u) tv[(size_t)5 * o + u] = vals[(size_t)5 * t + u];
+        }
+      TRY(upload_int(&gr.gtp, tp));
+      TRY(upload_int(&gr.gtr, tr));
+      TRY(upload(&gr.gtv, tv, ctx->esize));
+    }
     std::vector<double> conv;
     TRY(build_cube_edges(ctx, gr.N, nodes, gr.edges, conv));
     std::vector<int> be;
@@ -738,16 +876,61 @@ int hope_launches_per_stage(hope_t ctx, int *launches) {
 
 int hope_tendency_vjp(hope_t ctx, const void *q_dev, const void *lam_dqdt_dev, void *lam_q_dev,
                       hope_stream_t stream) {
-  (void)ctx; (void)q_dev; (void)lam_dqdt_dev; (void)lam_q_dev; (void)stream;
-  set_error("hope_tendency_vjp: not available in this build");
-  return HOPE_EUNSUPPORTED;
+  if (!ctx || !q_dev || !lam_dqdt_dev || !lam_q_dev || lam_q_dev == q_dev || lam_q_dev == lam_dqdt_dev) {
+    set_error("hope_tendency_vjp: invalid or overlapping arguments");
+    return HOPE_EINVAL;
+  }
+  int rc = ensure_adjoint_scratch(ctx);
+  if (rc) return rc;
+  VjpComb cb;
+  return pick_vjp(ctx)(ctx, q_dev, lam_dqdt_dev, lam_q_dev, cb, (cudaStream_t)stream);
 }
 
 int hope_step_vjp(hope_t ctx, const void *qn_dev, const void *lam_np1_dev, void *lam_n_dev, double dt,
                   hope_stream_t stream) {
-  (void)ctx; (void)qn_dev; (void)lam_np1_dev; (void)lam_n_dev; (void)dt; (void)stream;
-  set_error("hope_step_vjp: not available in this build");
-  return HOPE_EUNSUPPORTED;
+  if (!ctx || !qn_dev || !lam_np1_dev || !lam_n_dev || lam_n_dev == qn_dev || lam_n_dev == lam_np1_dev ||
+      !(dt == dt)) {
+    set_error("hope_step_vjp: invalid or overlapping arguments");
+    return HOPE_EINVAL;
+  }
+  int rc = ensure_adjoint_scratch(ctx);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  stage_fn f = pick_stage(ctx);
+  vjp_fn v = pick_vjp(ctx);
+  // recompute the stage states q1, q2 from q^n
+  if (ctx->rk == HOPE_WSRK3) {
+    if ((rc = f(ctx, qn_dev, qn_dev, ctx->q1, 1, 1.0, 0.0, dt / 3.0, LoWords(), st))) return rc;
+    if ((rc = f(ctx, ctx->q1, qn_dev, ctx->q2, 1, 1.0, 0.0, dt / 2.0, LoWords(), st))) return rc;
+    VjpComb c3;  // lam** = dt L^T(q**) lam
+    c3.c = dt;
+    if ((rc = v(ctx, ctx->q2, lam_np1_dev, ctx->lam_b, c3, st))) return rc;
+    VjpComb c2;  // lam* = dt/2 L^T(q*) lam**
+    c2.c = dt / 2.0;
+    if ((rc = v(ctx, ctx->q1, ctx->lam_b, ctx->lam_a, c2, st))) return rc;
+    VjpComb c1;  // lam_n = lam + lam** + lam* + dt/3 L^T(q) lam*
+    c1.x = lam_np1_dev; c1.a = 1.0;
+    c1.y = ctx->lam_b; c1.b = 1.0;
+    c1.z = ctx->lam_a; c1.d = 1.0;
+    c1.c = dt / 3.0;
+    return v(ctx, qn_dev, ctx->lam_a, lam_n_dev, c1, st);
+  }
+  if ((rc = f(ctx, qn_dev, qn_dev, ctx->q1, 1, 0.0, 1.0, dt, LoWords(), st))) return rc;
+  if ((rc = f(ctx, ctx->q1, qn_dev, ctx->q2, 1, 0.75, 0.25, 0.25 * dt, LoWords(), st))) return rc;
+  VjpComb c3;  // lam2 = 2/3 lam + 2/3 dt L^T(q2) lam
+  c3.x = lam_np1_dev; c3.a = 2.0 / 3.0;
+  c3.c = 2.0 / 3.0 * dt;
+  if ((rc = v(ctx, ctx->q2, lam_np1_dev, ctx->lam_b, c3, st))) return rc;
+  VjpComb c2;  // lam1 = 1/4 lam2 + 1/4 dt L^T(q1) lam2
+  c2.x = ctx->lam_b; c2.a = 0.25;
+  c2.c = 0.25 * dt;
+  if ((rc = v(ctx, ctx->q1, ctx->lam_b, ctx->lam_a, c2, st))) return rc;
+  VjpComb c1;  // lam_n = 1/3 lam + 3/4 lam2 + lam1 + dt L^T(q) lam1
+  c1.x = lam_np1_dev; c1.a = 1.0 / 3.0;
+  c1.y = ctx->lam_b; c1.b = 0.75;
+  c1.z = ctx->lam_a; c1.d = 1.0;
+  c1.c = dt;
+  return v(ctx, qn_dev, ctx->lam_a, lam_n_dev, c1, st);
 }
 
 int hope_set_profiling(hope_t ctx, int enable) {

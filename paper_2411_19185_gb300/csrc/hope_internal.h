@@ -40,6 +40,15 @@ struct Grid {
   void *fy = nullptr;    // [3][6][N+1][N]
   void *sb = nullptr;    // [2][6][N][N] cell-averaged sources
   CubeEdge edges[12];
+  // transposed ghost operator (adjoint): CSR over interior cells
+  int *gtp = nullptr;    // [6*N*N + 1]
+  int *gtr = nullptr;    // [nnz] ghost row
+  void *gtv = nullptr;   // [nnz][5]
+  // adjoint scratch (allocated on the first VJP call)
+  void *lep = nullptr;    // like ep
+  void *grad = nullptr;   // [3][k*k][6][N][N]
+  void *lring = nullptr;  // like gext
+  void *ldir = nullptr;   // [3][6][N][N]
 };
 
 struct GraphKey {
@@ -82,6 +91,8 @@ struct hope_ctx {
   void *q1 = nullptr, *q2 = nullptr, *lbuf = nullptr;
   // FP32 compensated stepping: low words of the caller's state (carry) and of q1, q2
   void *carry = nullptr, *q1l = nullptr, *q2l = nullptr;
+  // adjoint stage states
+  void *lam_a = nullptr, *lam_b = nullptr;
   const void *carry_owner = nullptr;
   unsigned *status = nullptr;
   double *mass_part = nullptr;

@@ -208,4 +208,7 @@ int launch_recon_weno(hope_ctx *ctx, Grid &g, const T *qs, cudaStream_t st);
 template <typename T, int K>
 int weno_set_smem_attr();
 
+template <typename T, int K>
+int launch_recon_weno_adj(hope_ctx *ctx, Grid &g, const T *qs, const T *lamL, cudaStream_t st);
+
 }  // namespace hope

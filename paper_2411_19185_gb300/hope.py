@@ -121,6 +121,27 @@ class Sphere:
                                         ctypes.c_void_p(out.data_ptr()), float(dt), int(nsteps), _stream()))
         return out
 
+    def tendency_vjp(self, q, lam, out=None):
+        """(dL/dq)^T lam at q (hand-written adjoint kernels)."""
+        if out is None:
+            out = torch.empty_like(q)
+        L.check(L.load().hope_tendency_vjp(self._h, _ptr(q, self), _ptr(lam, self), _ptr(out, self), _stream()))
+        return out
+
+    def step_vjp(self, qn, lam_np1, dt, out=None):
+        """(dS/dq)^T lam_np1 for one RK step S of size dt taken from qn."""
+        if out is None:
+            out = torch.empty_like(qn)
+        L.check(L.load().hope_step_vjp(self._h, _ptr(qn, self), _ptr(lam_np1, self), _ptr(out, self), float(dt),
+                                       _stream()))
+        return out
+
+    def rollout(self, q0, dt, nsteps, checkpoint_every=10):
+        """Differentiable nsteps-step integration: returns q(T) with a backward pass that
+        recomputes from checkpoints every `checkpoint_every` steps and applies the
+        hand-written step adjoints in reverse."""
+        return _Rollout.apply(q0, self, float(dt), int(nsteps), int(checkpoint_every))
+
     def mass(self, q):
         m = (ctypes.c_double * len(self.members))()
         L.check(L.load().hope_total_mass(self._h, _ptr(q, self), m, _stream()))
@@ -158,3 +179,38 @@ def measure_fma_peak(precision):
     r = ctypes.c_double()
     L.check(L.load().hope_measure_fma_peak(precision, ctypes.byref(r)))
     return r.value
+
+
+class _Rollout(torch.autograd.Function):
+    """q(T) = S^n(q0) with checkpointed recompute and hand-written step adjoints."""
+
+    @staticmethod
+    def forward(ctx, q0, sphere, dt, nsteps, every):
+        work = q0.detach().clone().contiguous()
+        ckpts = [work.clone()]
+        for s in range(nsteps):
+            sphere.step(work, dt)
+            if (s + 1) % every == 0 and s + 1 < nsteps:
+                ckpts.append(work.clone())
+        ctx.sphere, ctx.dt, ctx.nsteps, ctx.every, ctx.ckpts = sphere, dt, nsteps, every, ckpts
+        return work
+
+    @staticmethod
+    def backward(ctx, lam):
+        sphere, dt, nsteps, every = ctx.sphere, ctx.dt, ctx.nsteps, ctx.every
+        lam = lam.detach().contiguous().clone()
+        work = torch.empty_like(lam)
+        buf = torch.empty_like(lam)
+        for seg in reversed(range(len(ctx.ckpts))):
+            start = seg * every
+            n = min(every, nsteps - start)
+            work.copy_(ctx.ckpts[seg])
+            states = [work.clone()]
+            for _ in range(n - 1):
+                sphere.step(work, dt)
+                states.append(work.clone())
+            for s in reversed(range(n)):
+                sphere.step_vjp(states[s], lam, dt, out=buf)
+                lam, buf = buf, lam
+        ctx.ckpts = None
+        return lam, None, None, None, None
