@@ -1129,3 +1129,40 @@ void orc_norms(const orc *o, const double *q, const double *qr, double *out) {
   out[2] = mx / mr;
   free(sg);
 }
+
+/* ------------------------------------------------------------------------- */
+/* Table exports for the PyTorch reference composition (test infrastructure). */
+/* ------------------------------------------------------------------------- */
+int orc_ghost_count(const orc *o) { return o->nring; }
+
+void orc_ghost_tables(const orc *o, int *ring, int *B, int *ic, int *jc, double *wx, double *wy,
+                      double *ratio, double *C) {
+  int me = o->me, k = o->k;
+  for (int c = 0; c < o->nring; ++c) ring[c] = o->ring[c];
+  for (size_t r = 0; r < (size_t)6 * o->nring * me * me; ++r) {
+    const gqp_t *g = &o->gq[r];
+    B[r] = g->B;
+    ic[r] = g->ic;
+    jc[r] = g->jc;
+    for (int a = 0; a < k; ++a) {
+      wx[r * k + a] = g->wx[a];
+      wy[r * k + a] = g->wy[a];
+    }
+    ratio[r] = g->ratio;
+    for (int t = 0; t < 4; ++t) C[r * 4 + t] = g->C[t];
+  }
+}
+
+void orc_edge_tables(const orc *o, int *B, int *sideB, int *tB, int *gB, double *ratio, double *C) {
+  for (size_t r = 0; r < (size_t)6 * 4 * o->N * o->me; ++r) {
+    const nbr_t *n = &o->nb[r];
+    B[r] = n->B;
+    sideB[r] = n->sideB;
+    tB[r] = n->tB;
+    gB[r] = n->gB;
+    ratio[r] = n->ratio;
+    for (int t = 0; t < 4; ++t) C[r * 4 + t] = n->C[t];
+  }
+}
+
+double orc_coriolis(const orc *o, int p, double X, double Y) { return coriolis(o, p, X, Y); }

@@ -90,6 +90,13 @@ void orc_lmars(const orc *o, int dir, double X, double Y, const double *qL, cons
                double *F);
 void orc_sources(const orc *o, int panel, double X, double Y, const double *qv, double *S);
 
+/* ---- table exports for the PyTorch reference composition ---- */
+int orc_ghost_count(const orc *o);
+void orc_ghost_tables(const orc *o, int *ring, int *B, int *ic, int *jc, double *wx, double *wy,
+                      double *ratio, double *C);
+void orc_edge_tables(const orc *o, int *B, int *sideB, int *tB, int *gB, double *ratio, double *C);
+double orc_coriolis(const orc *o, int panel, double X, double Y);
+
 #ifdef __cplusplus
 }
 #endif

@@ -79,6 +79,13 @@ def lib():
         L.orc_locate.argtypes = [P, P]
         L.orc_lmars.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, P, P, P]
         L.orc_sources.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, P, P]
+        Pi = ctypes.POINTER(ctypes.c_int)
+        L.orc_ghost_count.restype = ctypes.c_int
+        L.orc_ghost_count.argtypes = [vp]
+        L.orc_ghost_tables.argtypes = [vp, Pi, Pi, Pi, Pi, P, P, P, P]
+        L.orc_edge_tables.argtypes = [vp, Pi, Pi, Pi, Pi, P, P]
+        L.orc_coriolis.restype = ctypes.c_double
+        L.orc_coriolis.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
         _lib = L
     return _lib
 
@@ -194,6 +201,32 @@ class Oracle:
         S = np.empty(3)
         lib().orc_sources(self._h, int(panel), float(X), float(Y), _p(_f64(q)), _p(S))
         return S
+
+    def ghost_tables(self):
+        """Per ghost Gauss point (panel, ring cell, h, g): owning panel, containing cell,
+        1-D weights, mass ratio and momentum matrix; plus the ring cell list."""
+        nr = lib().orc_ghost_count(self._h)
+        n = 6 * nr * self.me * self.me
+        ring = np.empty(nr, np.int32)
+        B, ic, jc = (np.empty(n, np.int32) for _ in range(3))
+        wx, wy = np.empty((n, self.k)), np.empty((n, self.k))
+        ratio, C = np.empty(n), np.empty((n, 4))
+        ip = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        lib().orc_ghost_tables(self._h, ip(ring), ip(B), ip(ic), ip(jc), _p(wx), _p(wy), _p(ratio), _p(C))
+        return dict(ring=ring, B=B, ic=ic, jc=jc, wx=wx, wy=wy, ratio=ratio, C=C)
+
+    def edge_tables(self):
+        """Per (panel, side, cell, node): neighbour panel, side, cell, node and the B->A
+        conversion (mass ratio, momentum matrix) at the shared edge point."""
+        n = 6 * 4 * self.N * self.me
+        B, sB, tB, gB = (np.empty(n, np.int32) for _ in range(4))
+        ratio, C = np.empty(n), np.empty((n, 4))
+        ip = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        lib().orc_edge_tables(self._h, ip(B), ip(sB), ip(tB), ip(gB), _p(ratio), _p(C))
+        return dict(B=B, sideB=sB, tB=tB, gB=gB, ratio=ratio, C=C)
+
+    def coriolis(self, panel, X, Y):
+        return lib().orc_coriolis(self._h, int(panel), float(X), float(Y))
 
     def points(self):
         """Local unit-cell coordinates (xi, eta) of the n_poc reconstruction points."""

@@ -61,6 +61,15 @@ int launch_recon_weno(hope_ctx *ctx, Grid &g, const T *qs, cudaStream_t st) {
 template <typename T, int K>
 int weno_set_smem_attr() {
   size_t smem = sizeof(T) * WenoShape<T, K>::smem_elems();
+  size_t smem_adj = sizeof(T) * WenoAdjShape<T, K>::smem_elems();
+  if (smem_adj <= 227 * 1024) {
+    cudaError_t e2 = cudaFuncSetAttribute(k_recon_weno_adj<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem_adj);
+    if (e2 != cudaSuccess) {
+      set_error(std::string("WENO adjoint shared memory attribute: ") + cudaGetErrorString(e2));
+      return HOPE_ECUDA;
+    }
+  }
   cudaError_t e = cudaFuncSetAttribute(k_recon_weno<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) {
     set_error(std::string("WENO shared memory attribute: ") + cudaGetErrorString(e));
@@ -71,9 +80,18 @@ int weno_set_smem_attr() {
 
 template <typename T, int K>
 int launch_recon_weno_adj(hope_ctx *ctx, Grid &g, const T *qs, const T *lamL, cudaStream_t st) {
-  (void)ctx; (void)g; (void)qs; (void)lamL; (void)st;
-  set_error("the WENO2D adjoint is not available in this build");
-  return HOPE_EUNSUPPORTED;
+  const int N = g.N;
+  dim3 grid((N + REC_TX - 1) / REC_TX, (N + REC_TY - 1) / REC_TY, 6);
+  size_t smem = sizeof(T) * WenoAdjShape<T, K>::smem_elems();
+  if (smem > 227 * 1024) {
+    set_error("WENO adjoint: order too high for the per-cell shared-memory staging");
+    return HOPE_EUNSUPPORTED;
+  }
+  k_recon_weno_adj<T, K><<<grid, REC_TX * REC_TY, smem, st>>>(
+      qs, (const T *)g.gext, (const T *)ctx->wsub, (const T *)ctx->gpm, (const T *)ctx->sig, (const T *)ctx->bform,
+      (const T *)ctx->bcoef, (const T *)g.Xg, (const T *)g.t1w, (const T *)g.lep, lamL, (T *)g.grad, N, g.ne,
+      (T)ctx->omega, fcoef<T>(ctx), (T)ctx->eps);
+  return HOPE_OK;
 }
 
 // -------------------------------------------------------------------------------

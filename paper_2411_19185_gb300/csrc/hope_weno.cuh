@@ -16,6 +16,7 @@
 #pragma once
 #include "hope_internal.h"
 #include "hope_kernels.cuh"
+#include "hope_adjoint.cuh"
 
 namespace hope {
 
@@ -210,5 +211,371 @@ int weno_set_smem_attr();
 
 template <typename T, int K>
 int launch_recon_weno_adj(hope_ctx *ctx, Grid &g, const T *qs, const T *lamL, cudaStream_t st);
+
+}  // namespace hope
+
+namespace hope {
+
+// ---------------------------------------------------------------------------------
+// WENO2D reconstruction + sources adjoint: per cell, recomputes the forward (indicators,
+// nonlinear weights, cell-point values), applies the source VJP at the cell points, then
+// back-propagates every point's adjoint through the WENO combination, the nonlinear
+// weights (eqs. 3.22-3.24; d|x|/dx = sign(x), 0 at 0), the indicators (eq. 3.25) and the
+// sub-stencil reconstructions into grad[v][b*K + a][cell] (the cell's own slice, no
+// atomics).
+// ---------------------------------------------------------------------------------
+template <typename T, int K>
+struct WenoAdjShape {
+  static constexpr size_t smem_elems() {
+    using W = WenoShape<T, K>;
+    return W::smem_elems() + 3 * W::ME * W::ME * W::NT;  // + adjoint at the cell points
+  }
+};
+
+template <typename T, int K>
+__device__ __forceinline__ void weno_indicators(const T *Qv, const T *bform, const T *bcoef, T *beta) {
+  constexpr int L = (K + 1) / 2, S = L * L, H = (K - 1) / 2, RW = Shape<K>::RW;
+  const T qc = Qv[H * RW + H];
+#pragma unroll
+  for (int t = 0; t < S; ++t) beta[t] = T(0);
+#pragma unroll
+  for (int sx = 0; sx < L; ++sx) {
+    const T *Wx = bform + sx * (L * L + L);
+#pragma unroll 1
+    for (int kp = 0; kp < L; ++kp) {
+      T Zx[K];
+      const T rs = Wx[L * L + kp];
+#pragma unroll
+      for (int r = 0; r < K; ++r) {
+        T s = -qc * rs;
+#pragma unroll
+        for (int a = 0; a < L; ++a) s = fma(Wx[kp * L + a], Qv[r * RW + sx + a], s);
+        Zx[r] = s;
+      }
+#pragma unroll
+      for (int sy = 0; sy < L; ++sy) {
+        const T *Wy = bform + sy * (L * L + L);
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+          T z = 0;
+#pragma unroll
+          for (int b = 0; b < L; ++b) z = fma(Wy[k * L + b], Zx[sy + b], z);
+          beta[sy * L + sx] = fma(bcoef[((sy * L + k) * L + sx) * L + kp] * z, z, beta[sy * L + sx]);
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(REC_TX *REC_TY)
+    k_recon_weno_adj(const T *__restrict__ q, const T *__restrict__ gext, const T *__restrict__ wsub_g,
+                     const T *__restrict__ gpm_g, const T *__restrict__ sig_g, const T *__restrict__ bform_g,
+                     const T *__restrict__ bcoef_g, const T *__restrict__ Xg, const T *__restrict__ t1w,
+                     const T *__restrict__ lep, const T *__restrict__ lamL, T *__restrict__ grad, int N, int ne,
+                     T omega, FCoef<T> fc, T eps) {
+  using W = WenoShape<T, K>;
+  using SH = Shape<K>;
+  constexpr int L = W::L, S = W::S, ME = W::ME, NPOS = W::NPOS, NPOC = W::NPOC, NT = W::NT, RW = SH::RW;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *raw = reinterpret_cast<T *>(smem_raw);
+  T *wsub = raw + 3 * SH::RH * SH::RW;
+  T *gpm = wsub + NPOS * L * L;
+  T *sig = gpm + NPOC * 2 * S;
+  T *bform = sig + NPOC * 2;
+  T *bcoef = bform + L * (L * L + L);
+  T *cq = bcoef + S * S;       // [3][ME*ME][NT] forward values at the cell points
+  T *lcq = cq + 3 * ME * ME * NT;  // [3][ME*ME][NT] adjoint at the cell points
+  const int p = blockIdx.z;
+  const int i0 = blockIdx.x * REC_TX, j0 = blockIdx.y * REC_TY;
+  for (int t = threadIdx.x; t < NPOS * L * L; t += blockDim.x) wsub[t] = wsub_g[t];
+  for (int t = threadIdx.x; t < NPOC * 2 * S; t += blockDim.x) gpm[t] = gpm_g[t];
+  for (int t = threadIdx.x; t < NPOC * 2; t += blockDim.x) sig[t] = sig_g[t];
+  for (int t = threadIdx.x; t < L * (L * L + L); t += blockDim.x) bform[t] = bform_g[t];
+  for (int t = threadIdx.x; t < S * S; t += blockDim.x) bcoef[t] = bcoef_g[t];
+  load_tile<T, K>(raw, q, gext, p, i0, j0, N, ne);
+  __syncthreads();
+  const int tid = threadIdx.x;
+  const int tx = tid % REC_TX, ty = tid / REC_TX;
+  const int i = i0 + tx, j = j0 + ty;
+  if (i >= N || j >= N) return;
+  const size_t pn = (size_t)6 * N * N;
+  const size_t cell = ((size_t)p * N + j) * N + i;
+  const T tau_scale = T(2) / (T(S + 1) * T(S));
+  auto ptidx = [](int t, int jj) -> int {
+    const int g = t - 2;
+    return t < 2 ? t * ME + jj : (jj == 0 ? 2 * ME + g : (jj == 1 ? 3 * ME + g : 4 * ME + (jj - 2) * ME + g));
+  };
+  // ---------------- phase A: forward values at the cell points (all variables)
+#pragma unroll 1
+  for (int v = 0; v < 3; ++v) {
+    const T *Qv = raw + (v * SH::RH + ty) * SH::RW + tx;
+    T f[S];
+    weno_indicators<T, K>(Qv, bform, bcoef, f);
+    T tsum = 0;
+#pragma unroll
+    for (int e = 0; e < S - 1; ++e)
+#pragma unroll
+      for (int ps = e + 1; ps < S; ++ps) tsum += fabs(f[ps] - f[e]);
+    const T tau = tsum * tau_scale;
+#pragma unroll
+    for (int t = 0; t < S; ++t) f[t] = T(1) + tau / (f[t] + eps);
+#pragma unroll 1
+    for (int g = 0; g < ME; ++g) {
+      const int t = 2 + g;
+      T Ap[ME], Am[ME];
+#pragma unroll
+      for (int h = 0; h < ME; ++h) Ap[h] = Am[h] = T(0);
+#pragma unroll
+      for (int sx = 0; sx < L; ++sx) {
+        T Xc[K];
+        const T *wx = wsub + (t * L + sx) * L;
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+          T s = 0;
+#pragma unroll
+          for (int a = 0; a < L; ++a) s = fma(wx[a], Qv[r * RW + sx + a], s);
+          Xc[r] = s;
+        }
+#pragma unroll
+        for (int h = 0; h < ME; ++h) {
+          const T *gp = gpm + (4 * ME + h * ME + g) * 2 * S;
+#pragma unroll
+          for (int sy = 0; sy < L; ++sy) {
+            const T *wy = wsub + ((2 + h) * L + sy) * L;
+            T pv = 0;
+#pragma unroll
+            for (int b = 0; b < L; ++b) pv = fma(wy[b], Xc[sy + b], pv);
+            const int ii = sy * L + sx;
+            const T fp = f[ii] * pv;
+            Ap[h] = fma(gp[ii], fp, Ap[h]);
+            Am[h] = fma(gp[S + ii], fp, Am[h]);
+          }
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < ME; ++h) {
+        const int pt = 4 * ME + h * ME + g;
+        const T *gp = gpm + pt * 2 * S;
+        T Dp = 0, Dm = 0;
+#pragma unroll
+        for (int ii = 0; ii < S; ++ii) {
+          Dp = fma(gp[ii], f[ii], Dp);
+          Dm = fma(gp[S + ii], f[ii], Dm);
+        }
+        cq[(v * ME * ME + h * ME + g) * NT + tid] = sig[2 * pt] * Ap[h] / Dp - sig[2 * pt + 1] * Am[h] / Dm;
+      }
+    }
+  }
+  // ---------------- phase B: source adjoint at the cell points
+  {
+    const T fc0 = fc.c[3 * p], fc1 = fc.c[3 * p + 1], fc2 = fc.c[3 * p + 2];
+    const T lS1 = lamL[pn + cell], lS2 = lamL[2 * pn + cell];
+#pragma unroll 1
+    for (int h = 0; h < ME; ++h) {
+      const T Y = Xg[j * ME + h];
+#pragma unroll 1
+      for (int g = 0; g < ME; ++g) {
+        const T X = Xg[i * ME + g];
+        T qv[3], lq[3];
+#pragma unroll
+        for (int v = 0; v < 3; ++v) qv[v] = cq[(v * ME * ME + h * ME + g) * NT + tid];
+        const T tw = t1w[(((size_t)j * N + i) * ME + h) * ME + g];
+        const T os = omega * (fc0 + fc1 * X + fc2 * Y);
+        source_vjp(qv, X, Y, os, tw, lS1, lS2, lq);
+#pragma unroll
+        for (int v = 0; v < 3; ++v) lcq[(v * ME * ME + h * ME + g) * NT + tid] = lq[v];
+      }
+    }
+  }
+  // ---------------- phase C: per variable, back through WENO into the stencil gradient
+#pragma unroll 1
+  for (int v = 0; v < 3; ++v) {
+    const T *Qv = raw + (v * SH::RH + ty) * SH::RW + tx;
+    T *gv = grad + (size_t)v * K * K * pn + cell;  // gv[(b*K + a) * pn]
+#pragma unroll 1
+    for (int t = 0; t < K * K; ++t) gv[(size_t)t * pn] = T(0);
+    T beta[S], f[S], lf[S];
+    weno_indicators<T, K>(Qv, bform, bcoef, beta);
+    T tsum = 0;
+#pragma unroll
+    for (int e = 0; e < S - 1; ++e)
+#pragma unroll
+      for (int ps = e + 1; ps < S; ++ps) tsum += fabs(beta[ps] - beta[e]);
+    const T tau = tsum * tau_scale;
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      f[t] = T(1) + tau / (beta[t] + eps);
+      lf[t] = T(0);
+    }
+#pragma unroll 1
+    for (int t = 0; t < NPOS; ++t) {
+      const int npt = t < 2 ? ME : ME + 2;
+      const int g = t - 2;
+      // pass 1: forward sums of the points at x-position t
+      T Ap[ME + 2], Am[ME + 2];
+#pragma unroll
+      for (int jj = 0; jj < ME + 2; ++jj) Ap[jj] = Am[jj] = T(0);
+#pragma unroll
+      for (int sx = 0; sx < L; ++sx) {
+        T Xc[K];
+        const T *wx = wsub + (t * L + sx) * L;
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+          T s = 0;
+#pragma unroll
+          for (int a = 0; a < L; ++a) s = fma(wx[a], Qv[r * RW + sx + a], s);
+          Xc[r] = s;
+        }
+#pragma unroll
+        for (int jj = 0; jj < ME + 2; ++jj) {
+          if (jj < npt) {
+            const int tyi = t < 2 ? 2 + jj : jj;
+            const T *gp = gpm + ptidx(t, jj) * 2 * S;
+#pragma unroll
+            for (int sy = 0; sy < L; ++sy) {
+              const T *wy = wsub + (tyi * L + sy) * L;
+              T pv = 0;
+#pragma unroll
+              for (int b = 0; b < L; ++b) pv = fma(wy[b], Xc[sy + b], pv);
+              const int ii = sy * L + sx;
+              const T fp = f[ii] * pv;
+              Ap[jj] = fma(gp[ii], fp, Ap[jj]);
+              Am[jj] = fma(gp[S + ii], fp, Am[jj]);
+            }
+          }
+        }
+      }
+      // adjoints of A+-, D+- at each point
+      T lAp[ME + 2], lAm[ME + 2], lDp[ME + 2], lDm[ME + 2];
+#pragma unroll
+      for (int jj = 0; jj < ME + 2; ++jj) {
+        lAp[jj] = lAm[jj] = lDp[jj] = lDm[jj] = T(0);
+        if (jj < npt) {
+          const int pt = ptidx(t, jj);
+          const T *gp = gpm + pt * 2 * S;
+          T Dp = 0, Dm = 0;
+#pragma unroll
+          for (int ii = 0; ii < S; ++ii) {
+            Dp = fma(gp[ii], f[ii], Dp);
+            Dm = fma(gp[S + ii], f[ii], Dm);
+          }
+          T lv;
+          if (t < 2)
+            lv = lep[((size_t)(t * 3 + v) * ME + jj) * pn + cell];
+          else if (jj < 2)
+            lv = lep[((size_t)((2 + jj) * 3 + v) * ME + g) * pn + cell];
+          else
+            lv = lcq[(v * ME * ME + (jj - 2) * ME + g) * NT + tid];
+          const T sp = sig[2 * pt], sm = sig[2 * pt + 1];
+          lAp[jj] = sp / Dp * lv;
+          lAm[jj] = -sm / Dm * lv;
+          lDp[jj] = -sp * Ap[jj] / (Dp * Dp) * lv;
+          lDm[jj] = sm * Am[jj] / (Dm * Dm) * lv;
+          // dD+-/df_i = gamma+-_i
+#pragma unroll
+          for (int ii = 0; ii < S; ++ii) lf[ii] = fma(gp[ii], lDp[jj], fma(gp[S + ii], lDm[jj], lf[ii]));
+        }
+      }
+      // pass 2: p-dependent parts -> lf and the stencil gradient
+#pragma unroll
+      for (int sx = 0; sx < L; ++sx) {
+        T Xc[K], lXc[K];
+        const T *wx = wsub + (t * L + sx) * L;
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+          T s = 0;
+#pragma unroll
+          for (int a = 0; a < L; ++a) s = fma(wx[a], Qv[r * RW + sx + a], s);
+          Xc[r] = s;
+          lXc[r] = T(0);
+        }
+#pragma unroll
+        for (int jj = 0; jj < ME + 2; ++jj) {
+          if (jj < npt) {
+            const int tyi = t < 2 ? 2 + jj : jj;
+            const T *gp = gpm + ptidx(t, jj) * 2 * S;
+#pragma unroll
+            for (int sy = 0; sy < L; ++sy) {
+              const T *wy = wsub + (tyi * L + sy) * L;
+              T pv = 0;
+#pragma unroll
+              for (int b = 0; b < L; ++b) pv = fma(wy[b], Xc[sy + b], pv);
+              const int ii = sy * L + sx;
+              const T gl = gp[ii] * lAp[jj] + gp[S + ii] * lAm[jj];
+              lf[ii] = fma(gl, pv, lf[ii]);
+              const T lp = gl * f[ii];
+#pragma unroll
+              for (int b = 0; b < L; ++b) lXc[sy + b] = fma(wy[b], lp, lXc[sy + b]);
+            }
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < K; ++r)
+#pragma unroll
+          for (int a = 0; a < L; ++a) gv[(size_t)(r * K + sx + a) * pn] += wx[a] * lXc[r];
+      }
+    }
+    // f_i = 1 + tau / (beta_i + eps)
+    T ltau = 0;
+#pragma unroll
+    for (int ii = 0; ii < S; ++ii) {
+      const T ib = T(1) / (beta[ii] + eps);
+      ltau = fma(lf[ii], ib, ltau);
+      lf[ii] = -lf[ii] * tau * ib * ib;  // now d/d beta_i (direct part)
+    }
+    // tau = ts sum_{e<p} |beta_p - beta_e|
+    const T lt = ltau * tau_scale;
+#pragma unroll
+    for (int e = 0; e < S - 1; ++e)
+#pragma unroll
+      for (int ps = e + 1; ps < S; ++ps) {
+        const T d = beta[ps] - beta[e];
+        const T sgn = d > T(0) ? T(1) : (d < T(0) ? T(-1) : T(0));
+        lf[ps] += lt * sgn;
+        lf[e] -= lt * sgn;
+      }
+    // beta = sum c z^2 on Q - q_c
+    const T qc = Qv[SH::H * RW + SH::H];
+    T lqc = 0;
+#pragma unroll
+    for (int sx = 0; sx < L; ++sx) {
+      const T *Wx = bform + sx * (L * L + L);
+#pragma unroll 1
+      for (int kp = 0; kp < L; ++kp) {
+        T Zx[K], lZx[K];
+        const T rs = Wx[L * L + kp];
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+          T s = -qc * rs;
+#pragma unroll
+          for (int a = 0; a < L; ++a) s = fma(Wx[kp * L + a], Qv[r * RW + sx + a], s);
+          Zx[r] = s;
+          lZx[r] = T(0);
+        }
+#pragma unroll
+        for (int sy = 0; sy < L; ++sy) {
+          const T *Wy = bform + sy * (L * L + L);
+#pragma unroll
+          for (int k = 0; k < L; ++k) {
+            T z = 0;
+#pragma unroll
+            for (int b = 0; b < L; ++b) z = fma(Wy[k * L + b], Zx[sy + b], z);
+            const T lz = T(2) * bcoef[((sy * L + k) * L + sx) * L + kp] * z * lf[sy * L + sx];
+#pragma unroll
+            for (int b = 0; b < L; ++b) lZx[sy + b] = fma(Wy[k * L + b], lz, lZx[sy + b]);
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+          lqc -= rs * lZx[r];
+#pragma unroll
+          for (int a = 0; a < L; ++a) gv[(size_t)(r * K + sx + a) * pn] += Wx[kp * L + a] * lZx[r];
+        }
+      }
+    }
+    gv[(size_t)(SH::H * K + SH::H) * pn] += lqc;
+  }
+}
 
 }  // namespace hope
