@@ -72,6 +72,7 @@ typedef void *hope_stream_t; /* a cudaStream_t; NULL = the legacy default stream
 /* sticky device status bits (hope_status) */
 #define HOPE_STATUS_NONPHYS_PHI 1u /* phi <= 0 where the LMARS flux takes sqrt(phi), eq. 3.35 */
 #define HOPE_STATUS_NAN 2u         /* a non-finite value in a computed tendency or state   */
+#define HOPE_STATUS_TIMEOUT 4u     /* a bounded grid-wide wait of the persistent ensemble stage gave up */
 
 typedef struct {
   double radius;   /* sphere radius a (m), default 6.37122e6 (section 5.1) */
@@ -94,7 +95,8 @@ void hope_default_params(hope_params *p);
 
 /*
  * Create a context for one cubed sphere with N cells per panel edge, stencil width
- * `order` (odd, 3..11; the design order of TPP, section 3.1) and `scheme`.  All tables
+ * `order` (odd; 3..11 for TPP, the design order of section 3.1; 3..9 for WENO2D, whose
+ * adjoint is available up to 7) and `scheme`.  All tables
  * (reconstruction weights eqs. 3.14-3.15, WENO linear weights eqs. 3.19-3.20 and
  * smoothness forms eq. 3.25, the ghost operator G of eq. 7.12, per-point metric terms
  * eqs. 2.2-2.8) are built in FP64 and stored on the current CUDA device.  Requires
@@ -224,6 +226,26 @@ int hope_total_mass_noalloc(const void *q_dev, int precision, int N, double *mas
 
 /* Read and clear the sticky device status (HOPE_STATUS_* bits).  Synchronises. */
 int hope_status(hope_t ctx, unsigned *device_status);
+
+/*
+ * Ensembles (hope_init_ensemble, TPP): each stage is one persistent cooperative launch over
+ * all members' work lists.  hope_autotune times the compiled tile shapes (TX x TY cells per
+ * work item: 16x8, 16x4, 32x4) for reps stages on the context's scratch buffers and keeps
+ * the fastest; it runs once at hope_init_ensemble.  ms_out (3 floats, may be NULL) gets the
+ * per-shape stage times, tx/ty/grid the chosen shape and resident grid size.  Returns
+ * HOPE_EUNSUPPORTED for contexts without the persistent path (one sphere, WENO2D).
+ */
+int hope_autotune(hope_t ctx, int reps, float *ms_out, int *tx, int *ty, int *grid);
+
+/*
+ * Failure-path hook for tests: HOPE_INJECT_BARRIER_TIMEOUT makes the next persistent stage
+ * launch of an ensemble expect one block more at its grid barriers than it launches, so
+ * no block is released; every block gives up after the bounded wait (about one second),
+ * HOPE_STATUS_TIMEOUT is set and the launch returns.  The context stays usable: the next
+ * hope_status() reads and clears the bit and resets the barrier.  No GPU fault is made.
+ */
+#define HOPE_INJECT_BARRIER_TIMEOUT 1
+int hope_inject_fault(hope_t ctx, int what);
 
 /* Total nonzeros of the ghost operator G (eq. 7.12) and its row count. */
 int hope_ghost_nnz(hope_t ctx, long long *nnz, long long *rows);

@@ -13,7 +13,7 @@ HOPE_OK = 0
 HOPE_TPP, HOPE_WENO2D = 0, 1
 HOPE_FP64, HOPE_FP32 = 0, 1
 HOPE_SSPRK3, HOPE_WSRK3 = 0, 1
-HOPE_STATUS_NONPHYS_PHI, HOPE_STATUS_NAN = 1, 2
+HOPE_STATUS_NONPHYS_PHI, HOPE_STATUS_NAN, HOPE_STATUS_TIMEOUT = 1, 2, 4
 
 EXPORTED = [
     "hope_default_params", "hope_init_grid", "hope_init_ensemble", "hope_destroy", "hope_state_elems",
@@ -21,7 +21,7 @@ EXPORTED = [
     "hope_step", "hope_step_ssprk3", "hope_step_host", "hope_tendency_vjp", "hope_step_vjp",
     "hope_total_mass", "hope_status", "hope_ghost_nnz", "hope_launches_per_stage", "hope_strerror",
     "hope_last_error_message", "hope_measure_fma_peak", "hope_set_profiling", "hope_kernel_times",
-    "hope_total_mass_noalloc",
+    "hope_total_mass_noalloc", "hope_autotune", "hope_inject_fault",
 ]
 
 
@@ -77,6 +77,8 @@ def load():
         "hope_measure_fma_peak": (i, [i, P(d)]),
         "hope_set_profiling": (i, [vp, i]),
         "hope_total_mass_noalloc": (i, [vp, i, i, P(d), vp]),
+        "hope_autotune": (i, [vp, i, P(ctypes.c_float), P(i), P(i), P(i)]),
+        "hope_inject_fault": (i, [vp, i]),
         "hope_kernel_times": (i, [vp, P(ctypes.c_float), i, P(i)]),
     }
     for name, (res, args) in sig.items():

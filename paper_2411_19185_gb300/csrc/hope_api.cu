@@ -6,29 +6,20 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
+#include "hope_ensemble.h"
 #include "hope_internal.h"
-#include "hope_kernels.cuh"
 #include "hope_setup.h"
-#include "hope_setup_math.cuh"
-#include "hope_weno.cuh"
-#include "hope_adjoint.cuh"
+#include "hope_stage.cuh"
 
 namespace hope {
 
 static thread_local std::string g_err;
 void set_error(const std::string &msg) { g_err = msg; }
 
-#define HOPE_CUDA_TRY(expr)                                                              \
-  do {                                                                                   \
-    cudaError_t _e = (expr);                                                             \
-    if (_e != cudaSuccess) {                                                             \
-      set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));                     \
-      return HOPE_ECUDA;                                                                 \
-    }                                                                                    \
-  } while (0)
 
 __global__ void k_mass_final(const double *__restrict__ part, int nparts, double scale, double *out) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -38,180 +29,10 @@ __global__ void k_mass_final(const double *__restrict__ part, int nparts, double
   }
 }
 
-template <typename T>
-static FCoef<T> fcoef(const hope_ctx *ctx) {
-  FCoef<T> f;
-  for (int t = 0; t < 18; ++t) f.c[t] = (T)ctx->fcoef[t];
-  return f;
-}
+static stage_fn pick_stage(const hope_ctx *ctx) { return stage_entry(ctx->prec, ctx->k); }
+static vjp_fn pick_vjp(const hope_ctx *ctx) { return vjp_entry(ctx->prec, ctx->k); }
+static int set_attrs(const hope_ctx *ctx) { return smem_attr_entry(ctx->prec, ctx->k); }
 
-template <typename T, int K>
-int launch_recon_weno(hope_ctx *ctx, Grid &g, const T *qs, cudaStream_t st) {
-  using W = WenoShape<T, K>;
-  const int N = g.N;
-  dim3 grid((N + REC_TX - 1) / REC_TX, (N + REC_TY - 1) / REC_TY, 6);
-  size_t smem = sizeof(T) * W::smem_elems();
-  k_recon_weno<T, K><<<grid, REC_TX * REC_TY, smem, st>>>(
-      qs, (const T *)g.gext, (const T *)ctx->wsub, (const T *)ctx->gpm, (const T *)ctx->sig,
-      (const T *)ctx->bform, (const T *)ctx->bcoef, (const T *)g.Xg, (const T *)g.t1w, (T *)g.ep, (T *)g.sb, N, g.ne, (T)ctx->omega,
-      fcoef<T>(ctx), (T)ctx->eps);
-  return HOPE_OK;
-}
-
-template <typename T, int K>
-int weno_set_smem_attr() {
-  size_t smem = sizeof(T) * WenoShape<T, K>::smem_elems();
-  size_t smem_adj = sizeof(T) * WenoAdjShape<T, K>::smem_elems();
-  if (smem_adj <= 227 * 1024) {
-    cudaError_t e2 = cudaFuncSetAttribute(k_recon_weno_adj<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem_adj);
-    if (e2 != cudaSuccess) {
-      set_error(std::string("WENO adjoint shared memory attribute: ") + cudaGetErrorString(e2));
-      return HOPE_ECUDA;
-    }
-  }
-  cudaError_t e = cudaFuncSetAttribute(k_recon_weno<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) {
-    set_error(std::string("WENO shared memory attribute: ") + cudaGetErrorString(e));
-    return HOPE_ECUDA;
-  }
-  return HOPE_OK;
-}
-
-template <typename T, int K>
-int launch_recon_weno_adj(hope_ctx *ctx, Grid &g, const T *qs, const T *lamL, cudaStream_t st) {
-  const int N = g.N;
-  dim3 grid((N + REC_TX - 1) / REC_TX, (N + REC_TY - 1) / REC_TY, 6);
-  size_t smem = sizeof(T) * WenoAdjShape<T, K>::smem_elems();
-  if (smem > 227 * 1024) {
-    set_error("WENO adjoint: order too high for the per-cell shared-memory staging");
-    return HOPE_EUNSUPPORTED;
-  }
-  k_recon_weno_adj<T, K><<<grid, REC_TX * REC_TY, smem, st>>>(
-      qs, (const T *)g.gext, (const T *)ctx->wsub, (const T *)ctx->gpm, (const T *)ctx->sig, (const T *)ctx->bform,
-      (const T *)ctx->bcoef, (const T *)g.Xg, (const T *)g.t1w, (const T *)g.lep, lamL, (T *)g.grad, N, g.ne,
-      (T)ctx->omega, fcoef<T>(ctx), (T)ctx->eps);
-  return HOPE_OK;
-}
-
-// -------------------------------------------------------------------------------
-// One stage on one grid: out = L(qs) (mode 0) or a*q0 + b*qs + c*L(qs) (mode 1).
-// -------------------------------------------------------------------------------
-template <typename T, int K>
-static int stage_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *q0, T *out, int mode, double a,
-                      double b, double c, const T *q0l, const T *qsl, T *outl, cudaStream_t st) {
-  constexpr int ME = (K + 1) / 2;
-  const int N = g.N, ne = g.ne;
-  const bool prof = ctx->prof_stage >= 0 && &g == &ctx->grids[0];
-  auto mark = [&](int t) {
-    if (prof) cudaEventRecordWithFlags(ctx->prof_ev[ctx->prof_stage][t], st, cudaEventRecordExternal);
-  };
-  mark(0);
-  // ghost ring
-  if (g.rows > 0) {
-    long long threads = g.rows * 32;
-    int blocks = (int)((threads + 255) / 256);
-    k_ghost<T><<<blocks, 256, 0, st>>>(qs, (T *)g.gext, g.grow, g.gcol, (const T *)g.gval, g.gdst,
-                                       (int)g.rows, N, ne);
-  }
-  mark(1);
-  // reconstruction + sources
-  dim3 grid((N + REC_TX - 1) / REC_TX, (N + REC_TY - 1) / REC_TY, 6);
-  if (ctx->scheme == HOPE_TPP) {
-    size_t smem = recon_smem_bytes<T, K>();
-    k_recon_tpp<T, K><<<grid, REC_TX * REC_TY, smem, st>>>(qs, (const T *)g.gext, (const T *)ctx->w1,
-                                                          (const T *)g.Xg, (const T *)g.t1w, (T *)g.ep,
-                                                          (T *)g.sb, N, ne, (T)ctx->omega, fcoef<T>(ctx));
-  } else {
-    int rc = launch_recon_weno<T, K>(ctx, g, qs, st);
-    if (rc) return rc;
-  }
-  mark(2);
-  // fluxes
-  {
-    long long items = 12LL * N * (N - 1) + 12LL * N;
-    int blocks = (int)((items + 255) / 256);
-    k_flux<T, ME><<<blocks, 256, 0, st>>>((const T *)g.ep, (const T *)g.mx, (const T *)ctx->gw, g.bedge,
-                                          (const T *)g.bconv, (T *)g.fx, (T *)g.fy, N, ctx->status);
-  }
-  mark(3);
-  // tendency + stage combination
-  {
-    long long cells = 6LL * N * N;
-    int blocks = (int)((cells + 255) / 256);
-    k_update<T><<<blocks, 256, 0, st>>>((const T *)g.fx, (const T *)g.fy, (const T *)g.sb, q0, qs, out, N,
-                                        (T)(2.0 * N / HOPE_PI), mode, (T)a, (T)b, (T)c, q0l, qsl, outl,
-                                        ctx->status);
-  }
-  mark(4);
-  HOPE_CUDA_TRY(cudaGetLastError());
-  return HOPE_OK;
-}
-
-// Low words of the three stage states for compensated FP32 stepping (all null in FP64).
-struct LoWords {
-  const void *q0l = nullptr, *qsl = nullptr;
-  void *outl = nullptr;
-};
-
-template <typename T, int K>
-static int stage_all(hope_ctx *ctx, const void *qs, const void *q0, void *out, int mode, double a, double b,
-                     double c, LoWords lw, cudaStream_t st) {
-  for (auto &g : ctx->grids) {
-    auto off = [&](const void *p) -> const T * { return p ? (const T *)p + g.off : nullptr; };
-    int rc = stage_grid<T, K>(ctx, g, (const T *)qs + g.off, off(q0), (T *)out + g.off, mode, a, b, c,
-                              off(lw.q0l), off(lw.qsl), lw.outl ? (T *)lw.outl + g.off : nullptr, st);
-    if (rc) return rc;
-  }
-  return HOPE_OK;
-}
-
-typedef int (*stage_fn)(hope_ctx *, const void *, const void *, void *, int, double, double, double, LoWords,
-                        cudaStream_t);
-
-template <typename T>
-static stage_fn pick_stage_t(int k) {
-  switch (k) {
-    case 3: return stage_all<T, 3>;
-    case 5: return stage_all<T, 5>;
-    case 7: return stage_all<T, 7>;
-    case 9: return stage_all<T, 9>;
-    case 11: return stage_all<T, 11>;
-  }
-  return nullptr;
-}
-
-static stage_fn pick_stage(const hope_ctx *ctx) {
-  return ctx->prec == HOPE_FP64 ? pick_stage_t<double>(ctx->k) : pick_stage_t<float>(ctx->k);
-}
-
-template <typename T, int K>
-static int set_smem_attr() {
-  size_t smem = recon_smem_bytes<T, K>();
-  HOPE_CUDA_TRY(cudaFuncSetAttribute(k_recon_tpp<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  HOPE_CUDA_TRY(cudaFuncSetAttribute(k_recon_tpp_adj<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)recon_adj_smem_bytes<T, K>()));
-  return weno_set_smem_attr<T, K>();
-}
-
-static int set_attrs(const hope_ctx *ctx) {
-#define CASE_K(KK)                                                                             \
-  case KK:                                                                                     \
-    return ctx->prec == HOPE_FP64 ? set_smem_attr<double, KK>() : set_smem_attr<float, KK>();
-  switch (ctx->k) {
-    CASE_K(3)
-    CASE_K(5)
-    CASE_K(7)
-    CASE_K(9)
-    CASE_K(11)
-  }
-#undef CASE_K
-  return HOPE_EINVAL;
-}
-
-// -------------------------------------------------------------------------------
-// One stage VJP on one grid:  out = a*x + b*y + d*z + c*(dL/dq at qs)^T lamL.
-// -------------------------------------------------------------------------------
 static int ensure_adjoint_scratch(hope_ctx *ctx) {
   for (auto &g : ctx->grids) {
     if (g.lep) continue;
@@ -233,90 +54,6 @@ static int ensure_adjoint_scratch(hope_ctx *ctx) {
     }
   }
   return HOPE_OK;
-}
-
-struct VjpComb {
-  const void *x = nullptr, *y = nullptr, *z = nullptr;
-  double a = 0, b = 0, d = 0, c = 1;
-};
-
-template <typename T, int K>
-static int stage_vjp_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *lamL, const T *x, const T *y, const T *z,
-                          T *out, const VjpComb &cb, cudaStream_t st) {
-  constexpr int ME = (K + 1) / 2;
-  const int N = g.N, ne = g.ne;
-  if (g.rows > 0) {
-    int blocks = (int)((g.rows * 32 + 255) / 256);
-    k_ghost<T><<<blocks, 256, 0, st>>>(qs, (T *)g.gext, g.grow, g.gcol, (const T *)g.gval, g.gdst, (int)g.rows, N,
-                                       ne);
-  }
-  dim3 grid((N + REC_TX - 1) / REC_TX, (N + REC_TY - 1) / REC_TY, 6);
-  if (ctx->scheme == HOPE_TPP) {
-    k_recon_tpp<T, K><<<grid, REC_TX * REC_TY, recon_smem_bytes<T, K>(), st>>>(
-        qs, (const T *)g.gext, (const T *)ctx->w1, (const T *)g.Xg, (const T *)g.t1w, (T *)g.ep, (T *)g.sb, N, ne,
-        (T)ctx->omega, fcoef<T>(ctx));
-  } else {
-    int rc = launch_recon_weno<T, K>(ctx, g, qs, st);
-    if (rc) return rc;
-  }
-  const T inv_dx = (T)(2.0 * N / HOPE_PI);
-  {
-    long long items = 12LL * N * (N - 1) + 12LL * N;
-    k_flux_adj<T, ME><<<(int)((items + 255) / 256), 256, 0, st>>>((const T *)g.ep, (const T *)g.mx,
-                                                                   (const T *)ctx->gw, g.bedge, (const T *)g.bconv,
-                                                                   lamL, (T *)g.lep, N, inv_dx);
-  }
-  if (ctx->scheme == HOPE_TPP) {
-    k_recon_tpp_adj<T, K><<<grid, REC_TX * REC_TY, recon_adj_smem_bytes<T, K>(), st>>>(
-        qs, (const T *)g.gext, (const T *)ctx->w1, (const T *)g.Xg, (const T *)g.t1w, (const T *)g.lep, lamL,
-        (T *)g.grad, N, ne, (T)ctx->omega, fcoef<T>(ctx));
-  } else {
-    int rc = launch_recon_weno_adj<T, K>(ctx, g, qs, lamL, st);
-    if (rc) return rc;
-  }
-  {
-    long long total = 6LL * ne * ne;
-    k_gather_adj<T, K><<<(int)((total + 255) / 256), 256, 0, st>>>((const T *)g.grad, (T *)g.ldir, (T *)g.lring,
-                                                                    N);
-  }
-  {
-    long long cells = 6LL * N * N;
-    k_ghost_adj<T><<<(int)((cells + 255) / 256), 256, 0, st>>>((const T *)g.ldir, (const T *)g.lring, g.gtp, g.gtr,
-                                                               (const T *)g.gtv, g.gdst, x, y, z, out, (T)cb.a,
-                                                               (T)cb.b, (T)cb.d, (T)cb.c, N, ne);
-  }
-  HOPE_CUDA_TRY(cudaGetLastError());
-  return HOPE_OK;
-}
-
-template <typename T, int K>
-static int stage_vjp_all(hope_ctx *ctx, const void *qs, const void *lamL, void *out, const VjpComb &cb,
-                         cudaStream_t st) {
-  for (auto &g : ctx->grids) {
-    auto off = [&](const void *p) -> const T * { return p ? (const T *)p + g.off : nullptr; };
-    int rc = stage_vjp_grid<T, K>(ctx, g, off(qs), off(lamL), off(cb.x), off(cb.y), off(cb.z), (T *)out + g.off,
-                                  cb, st);
-    if (rc) return rc;
-  }
-  return HOPE_OK;
-}
-
-typedef int (*vjp_fn)(hope_ctx *, const void *, const void *, void *, const VjpComb &, cudaStream_t);
-
-template <typename T>
-static vjp_fn pick_vjp_t(int k) {
-  switch (k) {
-    case 3: return stage_vjp_all<T, 3>;
-    case 5: return stage_vjp_all<T, 5>;
-    case 7: return stage_vjp_all<T, 7>;
-    case 9: return stage_vjp_all<T, 9>;
-    case 11: return stage_vjp_all<T, 11>;
-  }
-  return nullptr;
-}
-
-static vjp_fn pick_vjp(const hope_ctx *ctx) {
-  return ctx->prec == HOPE_FP64 ? pick_vjp_t<double>(ctx->k) : pick_vjp_t<float>(ctx->k);
 }
 
 // RK step sequence (3 stages) on stream st
@@ -345,7 +82,10 @@ static int step_sequence(hope_ctx *ctx, void *q, double dt, int rk, bool prof, c
       lw.qsl = qsl[s];
       lw.outl = outl[s];
     }
-    rc = f(ctx, qs[s], q, out[s], 1, A[s], B[s], C[s], lw, st);
+    if (ctx->ens)
+      rc = stage_persistent(ctx, qs[s], q, out[s], 1, A[s], B[s], C[s], lw.q0l, lw.qsl, lw.outl, st);
+    else
+      rc = f(ctx, qs[s], q, out[s], 1, A[s], B[s], C[s], lw, st);
   }
   ctx->prof_stage = -1;
   return rc;
@@ -499,9 +239,13 @@ const char *hope_strerror(int code) {
 const char *hope_last_error_message(void) { return g_err.c_str(); }
 
 static void free_grid(Grid &g) {
-  void *ptrs[] = {g.Xg, g.t1w, g.mx, g.gval, g.grow, g.gcol, g.gdst, g.bedge, g.bconv,
-                  g.gext, g.ep, g.fx, g.fy, g.sb, g.gtp, g.gtr, g.gtv, g.lep, g.grad, g.lring, g.ldir};
-  for (void *p : ptrs)
+  if (g.owns_tables) {
+    void *tables[] = {g.Xg, g.t1w, g.mx, g.gval, g.grow, g.gcol, g.gdst, g.bedge, g.bconv, g.gtp, g.gtr, g.gtv};
+    for (void *p : tables)
+      if (p) cudaFree(p);
+  }
+  void *scratch[] = {g.gext, g.ep, g.fx, g.fy, g.sb, g.lep, g.grad, g.lring, g.ldir};
+  for (void *p : scratch)
     if (p) cudaFree(p);
   g = Grid();
 }
@@ -516,6 +260,7 @@ void hope_destroy(hope_t ctx) {
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  ensemble_free(ctx);
   for (int s = 0; s < PROF_STAGES; ++s)
     for (int t = 0; t <= PROF_KERNELS; ++t)
       if (ctx->prof_ev[s][t]) cudaEventDestroy(ctx->prof_ev[s][t]);
@@ -571,6 +316,10 @@ static int init_impl(int n_members, const int *Ns, int order, int scheme, const 
     set_error("invalid order/scheme/precision/params");
     return HOPE_EINVAL;
   }
+  if (scheme == HOPE_WENO2D && order > HOPE_WENO_MAXK) {
+    set_error("WENO2D supports orders 3..9");
+    return HOPE_EUNSUPPORTED;
+  }
   for (int m = 0; m < n_members; ++m)
     if (Ns[m] < order || Ns[m] > 8192) {
       set_error("N must satisfy order <= N <= 8192");
@@ -617,54 +366,70 @@ static int init_impl(int n_members, const int *Ns, int order, int scheme, const 
   TRY(setup_order_tables(ctx, nodes, weights));
   if (scheme == HOPE_WENO2D) TRY(setup_weno_tables(ctx, nodes));
   size_t off = 0;
+  std::map<int, int> first_of_N;  // members with equal N share one set of tables
   for (int m = 0; m < n_members; ++m) {
     Grid g;
     g.N = Ns[m];
     g.ne = Ns[m] + 2 * ctx->H;
     g.off = off;
     off += (size_t)3 * 6 * Ns[m] * Ns[m];
-    ctx->grids.push_back(g);
+    auto it = first_of_N.find(Ns[m]);
+    if (it != first_of_N.end()) {
+      const Grid &src = ctx->grids[it->second];
+      g.Xg = src.Xg; g.t1w = src.t1w; g.mx = src.mx;
+      g.gval = src.gval; g.grow = src.grow; g.gcol = src.gcol; g.gdst = src.gdst;
+      g.rows = src.rows; g.nnz = src.nnz;
+      g.bedge = src.bedge; g.bconv = src.bconv;
+      g.gtp = src.gtp; g.gtr = src.gtr; g.gtv = src.gtv;
+      for (int e = 0; e < 12; ++e) g.edges[e] = src.edges[e];
+      g.owns_tables = false;
+      ctx->grids.push_back(g);
+    } else {
+      first_of_N[Ns[m]] = (int)ctx->grids.size();
+      ctx->grids.push_back(g);
+      Grid &gr = ctx->grids.back();
+      TRY(setup_grid_tables(ctx, gr, nodes, weights));
+      std::vector<int> rowptr, cols, dst;
+      std::vector<double> vals;
+      TRY(build_ghost_operator(ctx, gr.N, nodes, weights, rowptr, cols, vals, dst));
+      gr.rows = (long long)dst.size();
+      gr.nnz = rowptr.back();
+      TRY(upload_int(&gr.grow, rowptr));
+      TRY(upload_int(&gr.gcol, cols));
+      TRY(upload_int(&gr.gdst, dst));
+      TRY(upload(&gr.gval, vals, ctx->esize));
+      {
+        // transposed ghost operator for the adjoint: CSR over interior cells
+        const int ncell = 6 * gr.N * gr.N;
+        std::vector<int> tp(ncell + 1, 0), tr(cols.size());
+        std::vector<double> tv(vals.size());
+        for (size_t t = 0; t < cols.size(); ++t) tp[cols[t] + 1]++;
+        for (int c = 0; c < ncell; ++c) tp[c + 1] += tp[c];
+        std::vector<int> fill(tp.begin(), tp.end() - 1);
+        for (int r = 0; r + 1 < (int)rowptr.size(); ++r)
+          for (int t = rowptr[r]; t < rowptr[r + 1]; ++t) {
+            int o = fill[cols[t]]++;
+            tr[o] = r;
+            for (int u = 0; u < 5; ++u) tv[(size_t)5 * o + u] = vals[(size_t)5 * t + u];
+          }
+        TRY(upload_int(&gr.gtp, tp));
+        TRY(upload_int(&gr.gtr, tr));
+        TRY(upload(&gr.gtv, tv, ctx->esize));
+      }
+      std::vector<double> conv;
+      TRY(build_cube_edges(ctx, gr.N, nodes, gr.edges, conv));
+      std::vector<int> be;
+      for (int e = 0; e < 12; ++e) {
+        be.push_back(gr.edges[e].A);
+        be.push_back(gr.edges[e].sideA);
+        be.push_back(gr.edges[e].B);
+        be.push_back(gr.edges[e].sideB);
+        be.push_back(gr.edges[e].flip);
+      }
+      TRY(upload_int(&gr.bedge, be));
+      TRY(upload(&gr.bconv, conv, ctx->esize));
+    }
     Grid &gr = ctx->grids.back();
-    TRY(setup_grid_tables(ctx, gr, nodes, weights));
-    std::vector<int> rowptr, cols, dst;
-    std::vector<double> vals;
-    TRY(build_ghost_operator(ctx, gr.N, nodes, weights, rowptr, cols, vals, dst));
-    gr.rows = (long long)dst.size();
-    gr.nnz = rowptr.back();
-    TRY(upload_int(&gr.grow, rowptr));
-    TRY(upload_int(&gr.gcol, cols));
-    TRY(upload_int(&gr.gdst, dst));
-    TRY(upload(&gr.gval, vals, ctx->esize));
-    {
-      // transposed ghost operator for the adjoint: CSR over interior cells
-      const int ncell = 6 * gr.N * gr.N;
-      std::vector<int> tp(ncell + 1, 0), tr(cols.size());
-      std::vector<double> tv(vals.size());
-      for (size_t t = 0; t < cols.size(); ++t) tp[cols[t] + 1]++;
-      for (int c = 0; c < ncell; ++c) tp[c + 1] += tp[c];
-      std::vector<int> fill(tp.begin(), tp.end() - 1);
-      for (int r = 0; r + 1 < (int)rowptr.size(); ++r)
-        for (int t = rowptr[r]; t < rowptr[r + 1]; ++t) {
-          int o = fill[cols[t]]++;
-          tr[o] = r;
-          for (int u = 0; u < 5; ++u) tv[(size_t)5 * o + u] = vals[(size_t)5 * t + u];
-        }
-      TRY(upload_int(&gr.gtp, tp));
-      TRY(upload_int(&gr.gtr, tr));
-      TRY(upload(&gr.gtv, tv, ctx->esize));
-    }
-    std::vector<double> conv;
-    TRY(build_cube_edges(ctx, gr.N, nodes, gr.edges, conv));
-    std::vector<int> be;
-    for (int e = 0; e < 12; ++e) {
-      be.push_back(gr.edges[e].A);
-      be.push_back(gr.edges[e].sideA);
-      be.push_back(gr.edges[e].B);
-      be.push_back(gr.edges[e].sideB);
-      be.push_back(gr.edges[e].flip);
-    }
-    TRY(upload_int(&gr.bedge, be));
-    TRY(upload(&gr.bconv, conv, ctx->esize));
     const size_t N = gr.N, ne = gr.ne, es = ctx->esize, me = ctx->me;
     TRY(alloc(&gr.gext, es * 3 * 6 * ne * ne));
     cudaMemset(gr.gext, 0, es * 3 * 6 * ne * ne);
@@ -698,6 +463,20 @@ static int init_impl(int n_members, const int *Ns, int order, int scheme, const 
     set_error(std::string("setup: ") + cudaGetErrorString(cudaGetLastError()));
     hope_destroy(ctx);
     return HOPE_ECUDA;
+  }
+  if (n_members > 1 && scheme == HOPE_TPP) {
+    TRY(ensemble_init(ctx));
+    // tune the tile shape on a benign state (steady geostrophic flow) in the scratch buffers
+    const double u0 = 2.0 * HOPE_PI * ctx->radius / (12.0 * 86400.0);
+    const double prm[3] = {0.0, u0, 2.94e4};
+    TRY(hope_initial_state(ctx, 2, prm, 3, nullptr, 0, ctx->q1, nullptr));
+    TRY(ensemble_autotune(ctx, ctx->q1, ctx->lbuf, 3, nullptr, nullptr));
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+      set_error(std::string("ensemble autotune: ") + cudaGetErrorString(cudaGetLastError()));
+      hope_destroy(ctx);
+      return HOPE_ECUDA;
+    }
+    cudaMemset(ctx->status, 0, sizeof(unsigned));
   }
 #undef TRY
   *out = ctx;
@@ -775,6 +554,9 @@ int hope_tendency(hope_t ctx, const void *q_dev, void *dqdt_dev, hope_stream_t s
     set_error("hope_tendency: q and dqdt must not overlap");
     return HOPE_EINVAL;
   }
+  if (ctx->ens)
+    return stage_persistent(ctx, q, nullptr, dqdt_dev, 0, 0.0, 0.0, 0.0, nullptr, nullptr, nullptr,
+                            (cudaStream_t)stream);
   return pick_stage(ctx)(ctx, q, nullptr, dqdt_dev, 0, 0.0, 0.0, 0.0, LoWords(), (cudaStream_t)stream);
 }
 
@@ -872,6 +654,7 @@ int hope_status(hope_t ctx, unsigned *device_status) {
   HOPE_CUDA_TRY(cudaDeviceSynchronize());
   HOPE_CUDA_TRY(cudaMemcpy(device_status, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
   HOPE_CUDA_TRY(cudaMemset(ctx->status, 0, sizeof(unsigned)));
+  if (*device_status & HOPE_STATUS_TIMEOUT) ensemble_reset_barrier(ctx);
   return HOPE_OK;
 }
 
@@ -888,7 +671,7 @@ int hope_ghost_nnz(hope_t ctx, long long *nnz, long long *rows) {
 
 int hope_launches_per_stage(hope_t ctx, int *launches) {
   if (!ctx || !launches) return HOPE_EINVAL;
-  *launches = 4 * (int)ctx->grids.size();
+  *launches = ctx->ens ? 1 : 4 * (int)ctx->grids.size();
   return HOPE_OK;
 }
 
@@ -949,6 +732,33 @@ int hope_step_vjp(hope_t ctx, const void *qn_dev, const void *lam_np1_dev, void 
   c1.z = ctx->lam_a; c1.d = 1.0;
   c1.c = dt;
   return v(ctx, qn_dev, ctx->lam_a, lam_n_dev, c1, st);
+}
+
+int hope_autotune(hope_t ctx, int reps, float *ms_out, int *tx, int *ty, int *grid) {
+  if (!ctx || reps < 1) return HOPE_EINVAL;
+  if (!ctx->ens) {
+    set_error("hope_autotune: only ensembles of TPP spheres use the persistent stage");
+    return HOPE_EUNSUPPORTED;
+  }
+  int rc = ensemble_autotune(ctx, ctx->q1, ctx->lbuf, reps, ms_out, nullptr);
+  if (rc) return rc;
+  HOPE_CUDA_TRY(cudaDeviceSynchronize());
+  int a = 0, b = 0, c = 0;
+  ensemble_shape(ctx, &a, &b, &c);
+  if (tx) *tx = a;
+  if (ty) *ty = b;
+  if (grid) *grid = c;
+  return HOPE_OK;
+}
+
+int hope_inject_fault(hope_t ctx, int what) {
+  if (!ctx || what != HOPE_INJECT_BARRIER_TIMEOUT) return HOPE_EINVAL;
+  if (!ctx->ens) {
+    set_error("hope_inject_fault: only the persistent ensemble stage has grid barriers");
+    return HOPE_EUNSUPPORTED;
+  }
+  ctx->ens->inject_timeout = 1;
+  return HOPE_OK;
 }
 
 int hope_set_profiling(hope_t ctx, int enable) {

@@ -1,0 +1,359 @@
+// hope_ensemble.cu -- one persistent launch per Runge-Kutta stage for an ensemble of
+// cubed spheres at uneven resolutions (TPP reconstruction).
+//
+// The four phases of a stage (ghost fill, reconstruction + sources, edge fluxes, tendency
+// + stage combination) become work lists over all members, walked by a cooperative grid
+// of resident blocks and separated by grid-wide barriers.  Every barrier wait is bounded:
+// a block that waits longer than the limit sets HOPE_STATUS_TIMEOUT and the launch
+// returns instead of hanging.  The tile shape (TX x TY cells per work item) is chosen by
+// timing the compiled candidates (hope_autotune).
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "hope_ensemble.h"
+#include "hope_kernels.cuh"
+
+namespace hope {
+
+template <typename T>
+struct MemberDev {
+  int N, ne;
+  long long off;  // element offset of the member in ensemble states
+  const int *grow, *gcol, *gdst;
+  const T *gval;
+  T *gext;
+  const T *Xg, *t1w, *mx, *bconv;
+  const int *bedge;
+  T *ep, *sb, *fx, *fy;
+  long long b_ghost, b_tile, b_flux, b_cell;  // first global item of each phase
+  int tiles_x, tiles_y;
+};
+
+template <typename T>
+struct StageArgs {
+  const T *qs, *q0;
+  T *out;
+  const T *q0l, *qsl;
+  T *outl;
+  T a, b, c;
+  int mode;
+  T omega;
+  FCoef<T> fc;
+  const T *gw, *w1;
+};
+
+constexpr long long BARRIER_WAIT_CYCLES = 2000000000ll;  // about one second of SM clock
+
+// Grid-wide barrier over the co-resident blocks of a cooperative launch.  bar[0] counts
+// arrivals, bar[1] is the generation.  Returns false (and sets the timeout bit) if the
+// wait exceeded the limit or another block already timed out.
+// `extra` raises the expected arrival count (fault injection for the timeout path: no
+// block releases the barrier, every block gives up after the bounded wait).
+__device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned *status, unsigned extra) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned *vgen = bar + 1;
+    const unsigned g = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+    if (arrived == gridDim.x + extra) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == g) {
+        if (clock64() - t0 > BARRIER_WAIT_CYCLES) {
+          atomicOr(status, HOPE_STATUS_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(256);
+      }
+    }
+    __threadfence();
+    if (*(volatile unsigned *)status & HOPE_STATUS_TIMEOUT) ok = 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// member owning global item `it` of a phase (begin offsets ascending by member)
+template <typename T>
+__device__ __forceinline__ int find_member(const MemberDev<T> *mem, int nmem, long long it, int phase) {
+  int lo = 0, hi = nmem - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    const long long b = phase == 0 ? mem[mid].b_ghost
+                        : phase == 1 ? mem[mid].b_tile
+                        : phase == 2 ? mem[mid].b_flux
+                                     : mem[mid].b_cell;
+    if (b <= it)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T, int K, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY)
+    k_stage_persistent(const MemberDev<T> *__restrict__ mem, int nmem, long long n_ghost, long long n_tile,
+                       long long n_flux, long long n_cell, StageArgs<T> sa, unsigned *bar, unsigned *status,
+                       unsigned inject) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int ME = (K + 1) / 2;
+  constexpr int NT = TX * TY, WPB = NT / 32;
+  // phase 1: ghost rows, one warp each
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (long long it = (long long)blockIdx.x * WPB + warp; it < n_ghost; it += (long long)gridDim.x * WPB) {
+      const MemberDev<T> &m = mem[find_member(mem, nmem, it, 0)];
+      ghost_row(int(it - m.b_ghost), lane, sa.qs + m.off, m.gext, m.grow, m.gcol, m.gval, m.gdst, m.N, m.ne);
+    }
+  }
+  if (!grid_sync(bar, status, inject)) return;
+  // phase 2: reconstruction tiles, one block each
+  for (long long it = blockIdx.x; it < n_tile; it += gridDim.x) {
+    const MemberDev<T> &m = mem[find_member(mem, nmem, it, 1)];
+    const int local = int(it - m.b_tile);
+    const int p = local / (m.tiles_x * m.tiles_y);
+    const int rem = local - p * m.tiles_x * m.tiles_y;
+    const int ty = rem / m.tiles_x, tx = rem - ty * m.tiles_x;
+    recon_tpp_tile<T, K, TX, TY>(smem_raw, p, tx * TX, ty * TY, sa.qs + m.off, m.gext, sa.w1, m.Xg, m.t1w, m.ep,
+                                 m.sb, m.N, m.ne, sa.omega, sa.fc);
+  }
+  if (!grid_sync(bar, status, inject)) return;
+  // phase 3: edge fluxes, one thread per edge
+  for (long long it = (long long)blockIdx.x * NT + threadIdx.x; it < n_flux; it += (long long)gridDim.x * NT) {
+    const MemberDev<T> &m = mem[find_member(mem, nmem, it, 2)];
+    flux_item<T, ME>(it - m.b_flux, m.ep, m.mx, sa.gw, m.bedge, m.bconv, m.fx, m.fy, m.N, status);
+  }
+  if (!grid_sync(bar, status, inject)) return;
+  // phase 4: tendency and stage combination, one thread per cell
+  for (long long it = (long long)blockIdx.x * NT + threadIdx.x; it < n_cell; it += (long long)gridDim.x * NT) {
+    const MemberDev<T> &m = mem[find_member(mem, nmem, it, 3)];
+    auto off = [&](const T *p) -> const T * { return p ? p + m.off : nullptr; };
+    update_cell(it - m.b_cell, m.fx, m.fy, m.sb, off(sa.q0), sa.qs + m.off, sa.out + m.off, m.N,
+                (T)(2.0 * m.N / 3.14159265358979323846), sa.mode, sa.a, sa.b, sa.c, off(sa.q0l), off(sa.qsl),
+                sa.outl ? sa.outl + m.off : nullptr, status);
+  }
+}
+
+// -------------------------------------------------------------------------------------
+// host side
+// -------------------------------------------------------------------------------------
+template <typename T>
+static int build_members(hope_ctx *ctx, int TX, int TY, std::vector<MemberDev<T>> &out, long long n[4]) {
+  out.clear();
+  long long bg = 0, bt = 0, bf = 0, bc = 0;
+  for (auto &g : ctx->grids) {
+    MemberDev<T> m{};
+    m.N = g.N;
+    m.ne = g.ne;
+    m.off = (long long)g.off;
+    m.grow = g.grow;
+    m.gcol = g.gcol;
+    m.gdst = g.gdst;
+    m.gval = (const T *)g.gval;
+    m.gext = (T *)g.gext;
+    m.Xg = (const T *)g.Xg;
+    m.t1w = (const T *)g.t1w;
+    m.mx = (const T *)g.mx;
+    m.bconv = (const T *)g.bconv;
+    m.bedge = g.bedge;
+    m.ep = (T *)g.ep;
+    m.sb = (T *)g.sb;
+    m.fx = (T *)g.fx;
+    m.fy = (T *)g.fy;
+    m.tiles_x = (g.N + TX - 1) / TX;
+    m.tiles_y = (g.N + TY - 1) / TY;
+    m.b_ghost = bg;
+    m.b_tile = bt;
+    m.b_flux = bf;
+    m.b_cell = bc;
+    bg += g.rows;
+    bt += 6LL * m.tiles_x * m.tiles_y;
+    bf += 12LL * g.N * (g.N - 1) + 12LL * g.N;
+    bc += 6LL * g.N * g.N;
+    out.push_back(m);
+  }
+  n[0] = bg;
+  n[1] = bt;
+  n[2] = bf;
+  n[3] = bc;
+  return HOPE_OK;
+}
+
+struct PersistentShape {
+  int TX, TY;
+};
+static const PersistentShape kShapes[] = {{16, 8}, {16, 4}, {32, 4}};
+static const int kNumShapes = 3;
+
+template <typename T, int K, int TX, int TY>
+static int launch_shape(hope_ctx *ctx, EnsembleState &es, const StageArgs<T> &sa, cudaStream_t st) {
+  auto kern = k_stage_persistent<T, K, TX, TY>;
+  const size_t smem = recon_smem_bytes<T, K, TX, TY>();
+  if (es.grid[es.shape] == 0) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      set_error("persistent stage: shared-memory attribute failed");
+      return HOPE_ECUDA;
+    }
+    int per_sm = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, smem);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (per_sm < 1) {
+      set_error("persistent stage: no resident block fits");
+      return HOPE_EUNSUPPORTED;
+    }
+    es.grid[es.shape] = per_sm * sms;
+  }
+  const MemberDev<T> *mem = (const MemberDev<T> *)es.members[es.shape];
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(es.grid[es.shape]);
+  cfg.blockDim = dim3(TX * TY);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const long long *n = es.items[es.shape];
+  const unsigned inject = es.inject_timeout ? 1u : 0u;
+  es.inject_timeout = 0;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, mem, (int)ctx->grids.size(), n[0], n[1], n[2], n[3], sa,
+                                     es.barrier, ctx->status, inject);
+  if (e != cudaSuccess) {
+    set_error(std::string("persistent stage launch: ") + cudaGetErrorString(e));
+    return HOPE_ECUDA;
+  }
+  return HOPE_OK;
+}
+
+template <typename T, int K>
+static int launch_any(hope_ctx *ctx, EnsembleState &es, const StageArgs<T> &sa, cudaStream_t st) {
+  switch (es.shape) {
+    case 0: return launch_shape<T, K, 16, 8>(ctx, es, sa, st);
+    case 1: return launch_shape<T, K, 16, 4>(ctx, es, sa, st);
+    default: return launch_shape<T, K, 32, 4>(ctx, es, sa, st);
+  }
+}
+
+template <typename T>
+static int stage_persistent_t(hope_ctx *ctx, const void *qs, const void *q0, void *out, int mode, double a, double b,
+                              double c, const void *q0l, const void *qsl, void *outl, cudaStream_t st) {
+  EnsembleState &es = *ctx->ens;
+  StageArgs<T> sa;
+  sa.qs = (const T *)qs;
+  sa.q0 = (const T *)q0;
+  sa.out = (T *)out;
+  sa.q0l = (const T *)q0l;
+  sa.qsl = (const T *)qsl;
+  sa.outl = (T *)outl;
+  sa.a = (T)a;
+  sa.b = (T)b;
+  sa.c = (T)c;
+  sa.mode = mode;
+  sa.omega = (T)ctx->omega;
+  for (int t = 0; t < 18; ++t) sa.fc.c[t] = (T)ctx->fcoef[t];
+  sa.gw = (const T *)ctx->gw;
+  sa.w1 = (const T *)ctx->w1;
+  switch (ctx->k) {
+    case 3: return launch_any<T, 3>(ctx, es, sa, st);
+    case 5: return launch_any<T, 5>(ctx, es, sa, st);
+    case 7: return launch_any<T, 7>(ctx, es, sa, st);
+    case 9: return launch_any<T, 9>(ctx, es, sa, st);
+    case 11: return launch_any<T, 11>(ctx, es, sa, st);
+  }
+  return HOPE_EINVAL;
+}
+
+int stage_persistent(hope_ctx *ctx, const void *qs, const void *q0, void *out, int mode, double a, double b,
+                     double c, const void *q0l, const void *qsl, void *outl, cudaStream_t st) {
+  if (ctx->prec == HOPE_FP64)
+    return stage_persistent_t<double>(ctx, qs, q0, out, mode, a, b, c, q0l, qsl, outl, st);
+  return stage_persistent_t<float>(ctx, qs, q0, out, mode, a, b, c, q0l, qsl, outl, st);
+}
+
+template <typename T>
+static int ensemble_init_t(hope_ctx *ctx) {
+  EnsembleState *es = new EnsembleState();
+  ctx->ens = es;
+  for (int s = 0; s < kNumShapes; ++s) {
+    std::vector<MemberDev<T>> mv;
+    build_members<T>(ctx, kShapes[s].TX, kShapes[s].TY, mv, es->items[s]);
+    if (cudaMalloc(&es->members[s], sizeof(MemberDev<T>) * mv.size()) != cudaSuccess) return HOPE_ENOMEM;
+    cudaMemcpy(es->members[s], mv.data(), sizeof(MemberDev<T>) * mv.size(), cudaMemcpyHostToDevice);
+  }
+  if (cudaMalloc(&es->barrier, 2 * sizeof(unsigned)) != cudaSuccess) return HOPE_ENOMEM;
+  cudaMemset(es->barrier, 0, 2 * sizeof(unsigned));
+  return HOPE_OK;
+}
+
+int ensemble_init(hope_ctx *ctx) {
+  return ctx->prec == HOPE_FP64 ? ensemble_init_t<double>(ctx) : ensemble_init_t<float>(ctx);
+}
+
+void ensemble_free(hope_ctx *ctx) {
+  if (!ctx->ens) return;
+  for (int s = 0; s < kNumShapes; ++s)
+    if (ctx->ens->members[s]) cudaFree(ctx->ens->members[s]);
+  if (ctx->ens->barrier) cudaFree(ctx->ens->barrier);
+  delete ctx->ens;
+  ctx->ens = nullptr;
+}
+
+void ensemble_reset_barrier(hope_ctx *ctx) {
+  if (ctx->ens && ctx->ens->barrier) cudaMemset(ctx->ens->barrier, 0, 2 * sizeof(unsigned));
+}
+
+// Time `reps` tendency stages of every candidate shape on the scratch buffers and keep
+// the fastest.  ms_out (may be null) receives the per-shape times.
+int ensemble_autotune(hope_ctx *ctx, const void *qs, void *out, int reps, float *ms_out, cudaStream_t st) {
+  EnsembleState &es = *ctx->ens;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_s = 0;
+  for (int s = 0; s < kNumShapes; ++s) {
+    es.shape = s;
+    int rc = stage_persistent(ctx, qs, nullptr, out, 0, 0, 0, 0, nullptr, nullptr, nullptr, st);
+    if (rc) {
+      if (ms_out) ms_out[s] = -1.0f;
+      continue;
+    }
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps; ++r) stage_persistent(ctx, qs, nullptr, out, 0, 0, 0, 0, nullptr, nullptr, nullptr, st);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    if (ms_out) ms_out[s] = ms;
+    if (ms < best) {
+      best = ms;
+      best_s = s;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  es.shape = best_s;
+  es.tuned = 1;
+  return cudaGetLastError() == cudaSuccess ? HOPE_OK : HOPE_ECUDA;
+}
+
+void ensemble_shape(const hope_ctx *ctx, int *tx, int *ty, int *grid) {
+  const EnsembleState &es = *ctx->ens;
+  *tx = kShapes[es.shape].TX;
+  *ty = kShapes[es.shape].TY;
+  *grid = es.grid[es.shape];
+}
+
+}  // namespace hope

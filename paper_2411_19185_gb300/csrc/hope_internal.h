@@ -9,7 +9,12 @@
 
 #include "../../include/hope.h"
 
+#define HOPE_WENO_MAXK 9      // highest WENO2D order compiled
+#define HOPE_WENO_ADJ_MAXK 7  // highest WENO2D order with a compiled adjoint
+
 namespace hope {
+
+struct EnsembleState;
 
 // One cube edge shared by panels A < B: A's side sideA meets B's side sideB
 // (0 west x=-pi/4, 1 east, 2 south y=-pi/4, 3 north); along the edge, A's cell t and
@@ -22,6 +27,7 @@ struct CubeEdge {
 struct Grid {
   int N = 0, ne = 0;
   size_t off = 0;   // element offset of this member in ensemble states
+  bool owns_tables = true;  // false: tables shared with an earlier member of equal N
   // tables (element type = context precision)
   void *Xg = nullptr;    // [N][me]  tan of the cell Gauss-node coordinates
   void *t1w = nullptr;   // [N][N][me][me]  2/delta^2 * W_gh at the cell points
@@ -99,6 +105,7 @@ struct hope_ctx {
   double *mass_out = nullptr;
   cudaStream_t cap_stream = nullptr;
   // profiling: events around the first sphere's kernels of each stage of a step
+  hope::EnsembleState *ens = nullptr;  // persistent per-stage launch (TPP ensembles)
   int profiling = 0;
   int prof_stage = -1;  // stage being captured (-1: no events)
   cudaEvent_t prof_ev[hope::PROF_STAGES][hope::PROF_KERNELS + 1] = {};

@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/hope.h"
+
 namespace hope {
 
 template <typename T>
@@ -53,15 +55,11 @@ struct FCoef {
 // Ghost fill: one warp per ghost cell, lanes stride over the row's nonzeros.
 // ---------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_ghost(const T *__restrict__ q, T *__restrict__ gext,
-                                               const int *__restrict__ grow, const int *__restrict__ gcol,
-                                               const T *__restrict__ gval, const int *__restrict__ gdst,
-                                               int rows, int N, int ne) {
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (warp >= rows) return;
+__device__ __forceinline__ void ghost_row(int row, int lane, const T *__restrict__ q, T *__restrict__ gext,
+                                          const int *__restrict__ grow, const int *__restrict__ gcol,
+                                          const T *__restrict__ gval, const int *__restrict__ gdst, int N, int ne) {
   size_t pn = (size_t)6 * N * N, pe = (size_t)6 * ne * ne;
-  int b = grow[warp], e = grow[warp + 1];
+  int b = grow[row], e = grow[row + 1];
   T s0 = 0, s1 = 0, s2 = 0;
   for (int t = b + lane; t < e; t += 32) {
     int c = gcol[t];
@@ -78,11 +76,21 @@ __global__ void __launch_bounds__(256) k_ghost(const T *__restrict__ q, T *__res
     s2 += __shfl_xor_sync(0xffffffffu, s2, o);
   }
   if (lane == 0) {
-    int d = gdst[warp];
+    int d = gdst[row];
     gext[d] = s0;
     gext[pe + d] = s1;
     gext[2 * pe + d] = s2;
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_ghost(const T *__restrict__ q, T *__restrict__ gext,
+                                               const int *__restrict__ grow, const int *__restrict__ gcol,
+                                               const T *__restrict__ gval, const int *__restrict__ gdst,
+                                               int rows, int N, int ne) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (warp >= rows) return;
+  ghost_row(warp, threadIdx.x & 31, q, gext, grow, gcol, gval, gdst, N, ne);
 }
 
 // ---------------------------------------------------------------------------------
@@ -91,26 +99,30 @@ __global__ void __launch_bounds__(256) k_ghost(const T *__restrict__ q, T *__res
 constexpr int REC_TX = 16;
 constexpr int REC_TY = 8;
 
-template <int K>
-struct Shape {
+template <int K, int TX = REC_TX, int TY = REC_TY>
+struct Tile {
   static constexpr int H = (K - 1) / 2;
   static constexpr int ME = (K + 1) / 2;
   static constexpr int NPOS = ME + 2;  // x-pass evaluation positions
-  static constexpr int RW = REC_TX + 2 * H;
-  static constexpr int RH = REC_TY + 2 * H;
+  static constexpr int RW = TX + 2 * H;
+  static constexpr int RH = TY + 2 * H;
+  static constexpr int NT = TX * TY;
 };
 
-template <typename T, int K>
+template <int K>
+using Shape = Tile<K, REC_TX, REC_TY>;
+
+template <typename T, int K, int TX = REC_TX, int TY = REC_TY>
 __host__ __device__ constexpr size_t recon_smem_bytes() {
-  using S = Shape<K>;
-  return sizeof(T) * (3 * S::RH * S::RW + 3 * S::NPOS * S::RH * REC_TX + S::NPOS * K);
+  using S = Tile<K, TX, TY>;
+  return sizeof(T) * (3 * S::RH * S::RW + 3 * S::NPOS * S::RH * TX + S::NPOS * K);
 }
 
 // Load the extended tile of the 3 variables: interior cells from q, ring cells from gext.
-template <typename T, int K>
+template <typename T, int K, int TX = REC_TX, int TY = REC_TY>
 __device__ __forceinline__ void load_tile(T *raw, const T *__restrict__ q, const T *__restrict__ gext,
                                           int p, int i0, int j0, int N, int ne) {
-  using S = Shape<K>;
+  using S = Tile<K, TX, TY>;
   size_t pn = (size_t)6 * N * N, pe = (size_t)6 * ne * ne;
   for (int idx = threadIdx.x; idx < 3 * S::RH * S::RW; idx += blockDim.x) {
     int v = idx / (S::RH * S::RW);
@@ -126,27 +138,28 @@ __device__ __forceinline__ void load_tile(T *raw, const T *__restrict__ q, const
   }
 }
 
-template <typename T, int K>
-__global__ void __launch_bounds__(REC_TX *REC_TY)
-    k_recon_tpp(const T *__restrict__ q, const T *__restrict__ gext, const T *__restrict__ w1g,
-                const T *__restrict__ Xg, const T *__restrict__ t1w, T *__restrict__ ep,
-                T *__restrict__ sb, int N, int ne, T omega, FCoef<T> fc) {
-  using S = Shape<K>;
-  constexpr int ME = S::ME, NPOS = S::NPOS, H = S::H;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+// One tile of TX x TY cells of panel p with its first cell at (i0, j0); called by all
+// threads of a block of TX*TY threads; ends with a barrier so the shared memory can be
+// reused for the next tile.
+template <typename T, int K, int TX, int TY>
+__device__ __forceinline__ void recon_tpp_tile(unsigned char *smem_raw, int p, int i0, int j0,
+                                               const T *__restrict__ q, const T *__restrict__ gext,
+                                               const T *__restrict__ w1g, const T *__restrict__ Xg,
+                                               const T *__restrict__ t1w, T *__restrict__ ep, T *__restrict__ sb,
+                                               int N, int ne, T omega, const FCoef<T> &fc) {
+  using S = Tile<K, TX, TY>;
+  constexpr int ME = S::ME, NPOS = S::NPOS;
   T *raw = reinterpret_cast<T *>(smem_raw);              // [3][RH][RW]
   T *xs = raw + 3 * S::RH * S::RW;                        // [3][NPOS][RH][TX]
-  T *w1 = xs + 3 * NPOS * S::RH * REC_TX;                 // [NPOS][K]
-  const int p = blockIdx.z;
-  const int i0 = blockIdx.x * REC_TX, j0 = blockIdx.y * REC_TY;
+  T *w1 = xs + 3 * NPOS * S::RH * TX;                     // [NPOS][K]
   for (int t = threadIdx.x; t < NPOS * K; t += blockDim.x) w1[t] = w1g[t];
-  load_tile<T, K>(raw, q, gext, p, i0, j0, N, ne);
+  load_tile<T, K, TX, TY>(raw, q, gext, p, i0, j0, N, ne);
   __syncthreads();
   // x-pass: every row of the extended tile, every tile column, NPOS positions
-  for (int idx = threadIdx.x; idx < 3 * S::RH * REC_TX; idx += blockDim.x) {
-    int v = idx / (S::RH * REC_TX);
-    int rem = idx - v * S::RH * REC_TX;
-    int r = rem / REC_TX, c = rem - r * REC_TX;
+  for (int idx = threadIdx.x; idx < 3 * S::RH * TX; idx += blockDim.x) {
+    int v = idx / (S::RH * TX);
+    int rem = idx - v * S::RH * TX;
+    int r = rem / TX, c = rem - r * TX;
     const T *row = raw + (v * S::RH + r) * S::RW + c;
     T a[K];
 #pragma unroll
@@ -156,74 +169,86 @@ __global__ void __launch_bounds__(REC_TX *REC_TY)
       T s = 0;
 #pragma unroll
       for (int b = 0; b < K; ++b) s = fma(w1[t * K + b], a[b], s);
-      xs[((v * NPOS + t) * S::RH + r) * REC_TX + c] = s;
+      xs[((v * NPOS + t) * S::RH + r) * TX + c] = s;
     }
   }
   __syncthreads();
-  const int tx = threadIdx.x % REC_TX, ty = threadIdx.x / REC_TX;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int i = i0 + tx, j = j0 + ty;
-  if (i >= N || j >= N) return;
-  const size_t pn = (size_t)6 * N * N;
-  const size_t cell = ((size_t)p * N + j) * N + i;
-  const T fc0 = fc.c[3 * p], fc1 = fc.c[3 * p + 1], fc2 = fc.c[3 * p + 2];
-  T s1 = 0, s2 = 0;
+  if (i < N && j < N) {
+    const size_t pn = (size_t)6 * N * N;
+    const size_t cell = ((size_t)p * N + j) * N + i;
+    const T fc0 = fc.c[3 * p], fc1 = fc.c[3 * p + 1], fc2 = fc.c[3 * p + 2];
+    T s1 = 0, s2 = 0;
 #pragma unroll 1
-  for (int t = 0; t < NPOS; ++t) {
-    T col[3][K];
+    for (int t = 0; t < NPOS; ++t) {
+      T col[3][K];
 #pragma unroll
-    for (int v = 0; v < 3; ++v)
+      for (int v = 0; v < 3; ++v)
 #pragma unroll
-      for (int b = 0; b < K; ++b) col[v][b] = xs[((v * NPOS + t) * S::RH + ty + b) * REC_TX + tx];
-    if (t < 2) {
-      // west (t = 0) / east (t = 1) edge points at the Gauss nodes in y
+        for (int b = 0; b < K; ++b) col[v][b] = xs[((v * NPOS + t) * S::RH + ty + b) * TX + tx];
+      if (t < 2) {
+        // west (t = 0) / east (t = 1) edge points at the Gauss nodes in y
 #pragma unroll
-      for (int r = 0; r < ME; ++r)
+        for (int r = 0; r < ME; ++r)
 #pragma unroll
-        for (int v = 0; v < 3; ++v) {
-          T s = 0;
+          for (int v = 0; v < 3; ++v) {
+            T s = 0;
 #pragma unroll
-          for (int b = 0; b < K; ++b) s = fma(w1[(2 + r) * K + b], col[v][b], s);
-          ep[((size_t)(t * 3 + v) * ME + r) * pn + cell] = s;
-        }
-    } else {
-      const int g = t - 2;
-      // south / north edge points at x-node g
+            for (int b = 0; b < K; ++b) s = fma(w1[(2 + r) * K + b], col[v][b], s);
+            ep[((size_t)(t * 3 + v) * ME + r) * pn + cell] = s;
+          }
+      } else {
+        const int g = t - 2;
+        // south / north edge points at x-node g
 #pragma unroll
-      for (int side = 0; side < 2; ++side)
+        for (int side = 0; side < 2; ++side)
 #pragma unroll
-        for (int v = 0; v < 3; ++v) {
-          T s = 0;
+          for (int v = 0; v < 3; ++v) {
+            T s = 0;
 #pragma unroll
-          for (int b = 0; b < K; ++b) s = fma(w1[side * K + b], col[v][b], s);
-          ep[((size_t)((2 + side) * 3 + v) * ME + g) * pn + cell] = s;
-        }
-      // cell points (g, h): metric (eq. 2.2) and Coriolis (eq. 2.3) sources
-      const T X = Xg[i * ME + g];
+            for (int b = 0; b < K; ++b) s = fma(w1[side * K + b], col[v][b], s);
+            ep[((size_t)((2 + side) * 3 + v) * ME + g) * pn + cell] = s;
+          }
+        // cell points (g, h): metric (eq. 2.2) and Coriolis (eq. 2.3) sources
+        const T X = Xg[i * ME + g];
 #pragma unroll 1
-      for (int h = 0; h < ME; ++h) {
-        T qv[3];
+        for (int h = 0; h < ME; ++h) {
+          T qv[3];
 #pragma unroll
-        for (int v = 0; v < 3; ++v) {
-          T s = 0;
+          for (int v = 0; v < 3; ++v) {
+            T s = 0;
 #pragma unroll
-          for (int b = 0; b < K; ++b) s = fma(w1[(2 + h) * K + b], col[v][b], s);
-          qv[v] = s;
+            for (int b = 0; b < K; ++b) s = fma(w1[(2 + h) * K + b], col[v][b], s);
+            qv[v] = s;
+          }
+          const T Y = Xg[j * ME + h];
+          const T tw = t1w[(((size_t)j * N + i) * ME + h) * ME + g];
+          const T sl = fc0 + fc1 * X + fc2 * Y;  // sin(latitude)*delta, eq. 2.5
+          const T rq = rcp(qv[0]);
+          const T XY = X * Y, X2 = X * X, Y2 = Y * Y;
+          const T os = omega * sl;
+          T a1 = (-XY * Y * qv[1] + Y * (T(1) + Y2) * qv[2]) * qv[1] * rq + os * (-XY * qv[1] + (T(1) + Y2) * qv[2]);
+          T a2 = (X * (T(1) + X2) * qv[1] - X2 * Y * qv[2]) * qv[2] * rq + os * (-(T(1) + X2) * qv[1] + XY * qv[2]);
+          s1 = fma(tw, a1, s1);
+          s2 = fma(tw, a2, s2);
         }
-        const T Y = Xg[j * ME + h];
-        const T tw = t1w[(((size_t)j * N + i) * ME + h) * ME + g];
-        const T sl = fc0 + fc1 * X + fc2 * Y;  // sin(latitude)*delta, eq. 2.5
-        const T rq = rcp(qv[0]);
-        const T XY = X * Y, X2 = X * X, Y2 = Y * Y;
-        const T os = omega * sl;
-        T a1 = (-XY * Y * qv[1] + Y * (T(1) + Y2) * qv[2]) * qv[1] * rq + os * (-XY * qv[1] + (T(1) + Y2) * qv[2]);
-        T a2 = (X * (T(1) + X2) * qv[1] - X2 * Y * qv[2]) * qv[2] * rq + os * (-(T(1) + X2) * qv[1] + XY * qv[2]);
-        s1 = fma(tw, a1, s1);
-        s2 = fma(tw, a2, s2);
       }
     }
+    sb[cell] = s1;
+    sb[pn + cell] = s2;
   }
-  sb[cell] = s1;
-  sb[pn + cell] = s2;
+  __syncthreads();
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(REC_TX *REC_TY)
+    k_recon_tpp(const T *__restrict__ q, const T *__restrict__ gext, const T *__restrict__ w1g,
+                const T *__restrict__ Xg, const T *__restrict__ t1w, T *__restrict__ ep,
+                T *__restrict__ sb, int N, int ne, T omega, FCoef<T> fc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  recon_tpp_tile<T, K, REC_TX, REC_TY>(smem_raw, blockIdx.z, blockIdx.x * REC_TX, blockIdx.y * REC_TY, q, gext, w1g,
+                                       Xg, t1w, ep, sb, N, ne, omega, fc);
 }
 
 // ---------------------------------------------------------------------------------
@@ -255,13 +280,11 @@ __device__ __forceinline__ void lmars(const T qL[3], const T qR[3], const T *m5,
 // Edge fluxes: interior x-edges, interior y-edges, then the 12 cube edges x N cells.
 // ---------------------------------------------------------------------------------
 template <typename T, int ME>
-__global__ void __launch_bounds__(256)
-    k_flux(const T *__restrict__ ep, const T *__restrict__ mx, const T *__restrict__ gwg,
-           const int *__restrict__ bedge, const T *__restrict__ bconv, T *__restrict__ fx,
-           T *__restrict__ fy, int N, unsigned *status) {
-  const long long nx = 6LL * N * (N - 1), ny = nx, nb = 12LL * N;
-  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nx + ny + nb) return;
+__device__ __forceinline__ void flux_item(long long idx, const T *__restrict__ ep, const T *__restrict__ mx,
+                                          const T *__restrict__ gwg, const int *__restrict__ bedge,
+                                          const T *__restrict__ bconv, T *__restrict__ fx, T *__restrict__ fy,
+                                          int N, unsigned *status) {
+  const long long nx = 6LL * N * (N - 1), ny = nx;
   const size_t pn = (size_t)6 * N * N;
   const size_t fe = (size_t)6 * N * (N + 1);
   T gw[ME];
@@ -371,6 +394,17 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+template <typename T, int ME>
+__global__ void __launch_bounds__(256)
+    k_flux(const T *__restrict__ ep, const T *__restrict__ mx, const T *__restrict__ gwg,
+           const int *__restrict__ bedge, const T *__restrict__ bconv, T *__restrict__ fx,
+           T *__restrict__ fy, int N, unsigned *status) {
+  const long long n = 12LL * N * (N - 1) + 12LL * N;
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  flux_item<T, ME>(idx, ep, mx, gwg, bedge, bconv, fx, fy, N, status);
+}
+
 // ---------------------------------------------------------------------------------
 // Tendency (eq. 3.1) and the Runge-Kutta stage combination:
 //   mode 0: out = L
@@ -403,13 +437,11 @@ __device__ __forceinline__ T combine(T a, T q0, T b, T qs, T c, T L, const T *q0
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256)
-    k_update(const T *__restrict__ fx, const T *__restrict__ fy, const T *__restrict__ sb,
-             const T *q0, const T *qs, T *out, int N, T inv_dx, int mode, T a, T b, T c,
-             const T *q0l, const T *qsl, T *outl, unsigned *status) {
+__device__ __forceinline__ void update_cell(long long cid, const T *__restrict__ fx, const T *__restrict__ fy,
+                                            const T *__restrict__ sb, const T *q0, const T *qs, T *out, int N,
+                                            T inv_dx, int mode, T a, T b, T c, const T *q0l, const T *qsl, T *outl,
+                                            unsigned *status) {
   const long long ncell = 6LL * N * N;
-  long long cid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (cid >= ncell) return;
   const int i = (int)(cid % N);
   const long long pj = cid / N;  // p*N + j
   const int j = (int)(pj % N), p = (int)(pj / N);
@@ -435,6 +467,16 @@ __global__ void __launch_bounds__(256)
     out[v * ncell + cid] = r;
   }
   if (bad) atomicOr(status, HOPE_STATUS_NAN);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_update(const T *__restrict__ fx, const T *__restrict__ fy, const T *__restrict__ sb,
+             const T *q0, const T *qs, T *out, int N, T inv_dx, int mode, T a, T b, T c,
+             const T *q0l, const T *qsl, T *outl, unsigned *status) {
+  long long cid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cid >= 6LL * N * N) return;
+  update_cell(cid, fx, fy, sb, q0, qs, out, N, inv_dx, mode, a, b, c, q0l, qsl, outl, status);
 }
 
 // ---------------------------------------------------------------------------------

@@ -1,0 +1,262 @@
+// hope_stage.cuh -- per-stage launch sequences (forward stage, stage VJP) of the HOPE
+// GB300 library, templated on precision and order; instantiated per (precision, order
+// group) in hope_stage_*.cu so the heavy kernels compile in parallel.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "hope_adjoint.cuh"
+#include "hope_internal.h"
+#include "hope_kernels.cuh"
+#include "hope_setup_math.cuh"
+#include "hope_weno.cuh"
+
+namespace hope {
+
+#define HOPE_CUDA_TRY(expr)                                                              \
+  do {                                                                                   \
+    cudaError_t _e = (expr);                                                             \
+    if (_e != cudaSuccess) {                                                             \
+      set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));                     \
+      return HOPE_ECUDA;                                                                 \
+    }                                                                                    \
+  } while (0)
+
+template <typename T>
+inline FCoef<T> fcoef(const hope_ctx *ctx) {
+  FCoef<T> f;
+  for (int t = 0; t < 18; ++t) f.c[t] = (T)ctx->fcoef[t];
+  return f;
+}
+
+template <typename T, int K>
+int launch_recon_weno(hope_ctx *ctx, Grid &g, const T *qs, cudaStream_t st) {
+  if constexpr (K > HOPE_WENO_MAXK) {
+    (void)ctx; (void)g; (void)qs; (void)st;
+    set_error("WENO2D supports orders up to 9");
+    return HOPE_EUNSUPPORTED;
+  } else {
+  using W = WenoShape<T, K>;
+  const int N = g.N;
+  dim3 grid((N + REC_TX - 1) / REC_TX, (N + REC_TY - 1) / REC_TY, 6);
+  size_t smem = sizeof(T) * W::smem_elems();
+  k_recon_weno<T, K><<<grid, REC_TX * REC_TY, smem, st>>>(
+      qs, (const T *)g.gext, (const T *)ctx->wsub, (const T *)ctx->gpm, (const T *)ctx->sig,
+      (const T *)ctx->bform, (const T *)ctx->bcoef, (const T *)g.Xg, (const T *)g.t1w, (T *)g.ep, (T *)g.sb, N, g.ne, (T)ctx->omega,
+      fcoef<T>(ctx), (T)ctx->eps);
+  return HOPE_OK;
+  }
+}
+
+template <typename T, int K>
+int weno_set_smem_attr() {
+  if constexpr (K > HOPE_WENO_MAXK) {
+    return HOPE_OK;
+  } else {
+  size_t smem = sizeof(T) * WenoShape<T, K>::smem_elems();
+  size_t smem_adj = sizeof(T) * WenoAdjShape<T, K>::smem_elems();
+  if (K <= HOPE_WENO_ADJ_MAXK && smem_adj <= 227 * 1024) {
+    cudaError_t e2 = cudaFuncSetAttribute(k_recon_weno_adj<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem_adj);
+    if (e2 != cudaSuccess) {
+      set_error(std::string("WENO adjoint shared memory attribute: ") + cudaGetErrorString(e2));
+      return HOPE_ECUDA;
+    }
+  }
+  cudaError_t e = cudaFuncSetAttribute(k_recon_weno<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) {
+    set_error(std::string("WENO shared memory attribute: ") + cudaGetErrorString(e));
+    return HOPE_ECUDA;
+  }
+  return HOPE_OK;
+  }
+}
+
+template <typename T, int K>
+int launch_recon_weno_adj(hope_ctx *ctx, Grid &g, const T *qs, const T *lamL, cudaStream_t st) {
+  if constexpr (K > HOPE_WENO_ADJ_MAXK) {
+    (void)ctx; (void)g; (void)qs; (void)lamL; (void)st;
+    set_error("the WENO2D adjoint supports orders up to 7");
+    return HOPE_EUNSUPPORTED;
+  } else {
+  const int N = g.N;
+  dim3 grid((N + REC_TX - 1) / REC_TX, (N + REC_TY - 1) / REC_TY, 6);
+  size_t smem = sizeof(T) * WenoAdjShape<T, K>::smem_elems();
+  if (smem > 227 * 1024) {
+    set_error("WENO adjoint: order too high for the per-cell shared-memory staging");
+    return HOPE_EUNSUPPORTED;
+  }
+  k_recon_weno_adj<T, K><<<grid, REC_TX * REC_TY, smem, st>>>(
+      qs, (const T *)g.gext, (const T *)ctx->wsub, (const T *)ctx->gpm, (const T *)ctx->sig, (const T *)ctx->bform,
+      (const T *)ctx->bcoef, (const T *)g.Xg, (const T *)g.t1w, (const T *)g.lep, lamL, (T *)g.grad, N, g.ne,
+      (T)ctx->omega, fcoef<T>(ctx), (T)ctx->eps);
+  return HOPE_OK;
+  }
+}
+
+// -------------------------------------------------------------------------------
+// One stage on one grid: out = L(qs) (mode 0) or a*q0 + b*qs + c*L(qs) (mode 1).
+// -------------------------------------------------------------------------------
+template <typename T, int K>
+inline int stage_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *q0, T *out, int mode, double a,
+                      double b, double c, const T *q0l, const T *qsl, T *outl, cudaStream_t st) {
+  constexpr int ME = (K + 1) / 2;
+  const int N = g.N, ne = g.ne;
+  const bool prof = ctx->prof_stage >= 0 && &g == &ctx->grids[0];
+  auto mark = [&](int t) {
+    if (prof) cudaEventRecordWithFlags(ctx->prof_ev[ctx->prof_stage][t], st, cudaEventRecordExternal);
+  };
+  mark(0);
+  // ghost ring
+  if (g.rows > 0) {
+    long long threads = g.rows * 32;
+    int blocks = (int)((threads + 255) / 256);
+    k_ghost<T><<<blocks, 256, 0, st>>>(qs, (T *)g.gext, g.grow, g.gcol, (const T *)g.gval, g.gdst,
+                                       (int)g.rows, N, ne);
+  }
+  mark(1);
+  // reconstruction + sources
+  dim3 grid((N + REC_TX - 1) / REC_TX, (N + REC_TY - 1) / REC_TY, 6);
+  if (ctx->scheme == HOPE_TPP) {
+    size_t smem = recon_smem_bytes<T, K>();
+    k_recon_tpp<T, K><<<grid, REC_TX * REC_TY, smem, st>>>(qs, (const T *)g.gext, (const T *)ctx->w1,
+                                                          (const T *)g.Xg, (const T *)g.t1w, (T *)g.ep,
+                                                          (T *)g.sb, N, ne, (T)ctx->omega, fcoef<T>(ctx));
+  } else {
+    int rc = launch_recon_weno<T, K>(ctx, g, qs, st);
+    if (rc) return rc;
+  }
+  mark(2);
+  // fluxes
+  {
+    long long items = 12LL * N * (N - 1) + 12LL * N;
+    int blocks = (int)((items + 255) / 256);
+    k_flux<T, ME><<<blocks, 256, 0, st>>>((const T *)g.ep, (const T *)g.mx, (const T *)ctx->gw, g.bedge,
+                                          (const T *)g.bconv, (T *)g.fx, (T *)g.fy, N, ctx->status);
+  }
+  mark(3);
+  // tendency + stage combination
+  {
+    long long cells = 6LL * N * N;
+    int blocks = (int)((cells + 255) / 256);
+    k_update<T><<<blocks, 256, 0, st>>>((const T *)g.fx, (const T *)g.fy, (const T *)g.sb, q0, qs, out, N,
+                                        (T)(2.0 * N / HOPE_PI), mode, (T)a, (T)b, (T)c, q0l, qsl, outl,
+                                        ctx->status);
+  }
+  mark(4);
+  HOPE_CUDA_TRY(cudaGetLastError());
+  return HOPE_OK;
+}
+
+// Low words of the three stage states for compensated FP32 stepping (all null in FP64).
+struct LoWords {
+  const void *q0l = nullptr, *qsl = nullptr;
+  void *outl = nullptr;
+};
+
+template <typename T, int K>
+inline int stage_all(hope_ctx *ctx, const void *qs, const void *q0, void *out, int mode, double a, double b,
+                     double c, LoWords lw, cudaStream_t st) {
+  for (auto &g : ctx->grids) {
+    auto off = [&](const void *p) -> const T * { return p ? (const T *)p + g.off : nullptr; };
+    int rc = stage_grid<T, K>(ctx, g, (const T *)qs + g.off, off(q0), (T *)out + g.off, mode, a, b, c,
+                              off(lw.q0l), off(lw.qsl), lw.outl ? (T *)lw.outl + g.off : nullptr, st);
+    if (rc) return rc;
+  }
+  return HOPE_OK;
+}
+
+typedef int (*stage_fn)(hope_ctx *, const void *, const void *, void *, int, double, double, double, LoWords,
+                        cudaStream_t);
+
+template <typename T, int K>
+inline int set_smem_attr() {
+  size_t smem = recon_smem_bytes<T, K>();
+  HOPE_CUDA_TRY(cudaFuncSetAttribute(k_recon_tpp<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  HOPE_CUDA_TRY(cudaFuncSetAttribute(k_recon_tpp_adj<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)recon_adj_smem_bytes<T, K>()));
+  return weno_set_smem_attr<T, K>();
+}
+
+// -------------------------------------------------------------------------------
+// One stage VJP on one grid:  out = a*x + b*y + d*z + c*(dL/dq at qs)^T lamL.
+// -------------------------------------------------------------------------------
+struct VjpComb {
+  const void *x = nullptr, *y = nullptr, *z = nullptr;
+  double a = 0, b = 0, d = 0, c = 1;
+};
+
+template <typename T, int K>
+inline int stage_vjp_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *lamL, const T *x, const T *y, const T *z,
+                          T *out, const VjpComb &cb, cudaStream_t st) {
+  constexpr int ME = (K + 1) / 2;
+  const int N = g.N, ne = g.ne;
+  if (g.rows > 0) {
+    int blocks = (int)((g.rows * 32 + 255) / 256);
+    k_ghost<T><<<blocks, 256, 0, st>>>(qs, (T *)g.gext, g.grow, g.gcol, (const T *)g.gval, g.gdst, (int)g.rows, N,
+                                       ne);
+  }
+  dim3 grid((N + REC_TX - 1) / REC_TX, (N + REC_TY - 1) / REC_TY, 6);
+  if (ctx->scheme == HOPE_TPP) {
+    k_recon_tpp<T, K><<<grid, REC_TX * REC_TY, recon_smem_bytes<T, K>(), st>>>(
+        qs, (const T *)g.gext, (const T *)ctx->w1, (const T *)g.Xg, (const T *)g.t1w, (T *)g.ep, (T *)g.sb, N, ne,
+        (T)ctx->omega, fcoef<T>(ctx));
+  } else {
+    int rc = launch_recon_weno<T, K>(ctx, g, qs, st);
+    if (rc) return rc;
+  }
+  const T inv_dx = (T)(2.0 * N / HOPE_PI);
+  {
+    long long items = 12LL * N * (N - 1) + 12LL * N;
+    k_flux_adj<T, ME><<<(int)((items + 255) / 256), 256, 0, st>>>((const T *)g.ep, (const T *)g.mx,
+                                                                   (const T *)ctx->gw, g.bedge, (const T *)g.bconv,
+                                                                   lamL, (T *)g.lep, N, inv_dx);
+  }
+  if (ctx->scheme == HOPE_TPP) {
+    k_recon_tpp_adj<T, K><<<grid, REC_TX * REC_TY, recon_adj_smem_bytes<T, K>(), st>>>(
+        qs, (const T *)g.gext, (const T *)ctx->w1, (const T *)g.Xg, (const T *)g.t1w, (const T *)g.lep, lamL,
+        (T *)g.grad, N, ne, (T)ctx->omega, fcoef<T>(ctx));
+  } else {
+    int rc = launch_recon_weno_adj<T, K>(ctx, g, qs, lamL, st);
+    if (rc) return rc;
+  }
+  {
+    long long total = 6LL * ne * ne;
+    k_gather_adj<T, K><<<(int)((total + 255) / 256), 256, 0, st>>>((const T *)g.grad, (T *)g.ldir, (T *)g.lring,
+                                                                    N);
+  }
+  {
+    long long cells = 6LL * N * N;
+    k_ghost_adj<T><<<(int)((cells + 255) / 256), 256, 0, st>>>((const T *)g.ldir, (const T *)g.lring, g.gtp, g.gtr,
+                                                               (const T *)g.gtv, g.gdst, x, y, z, out, (T)cb.a,
+                                                               (T)cb.b, (T)cb.d, (T)cb.c, N, ne);
+  }
+  HOPE_CUDA_TRY(cudaGetLastError());
+  return HOPE_OK;
+}
+
+template <typename T, int K>
+inline int stage_vjp_all(hope_ctx *ctx, const void *qs, const void *lamL, void *out, const VjpComb &cb,
+                         cudaStream_t st) {
+  for (auto &g : ctx->grids) {
+    auto off = [&](const void *p) -> const T * { return p ? (const T *)p + g.off : nullptr; };
+    int rc = stage_vjp_grid<T, K>(ctx, g, off(qs), off(lamL), off(cb.x), off(cb.y), off(cb.z), (T *)out + g.off,
+                                  cb, st);
+    if (rc) return rc;
+  }
+  return HOPE_OK;
+}
+
+typedef int (*vjp_fn)(hope_ctx *, const void *, const void *, void *, const VjpComb &, cudaStream_t);
+
+
+
+
+
+// Per-(precision, order) entry points, defined in hope_stage_<tag>.cu.
+stage_fn stage_entry(int prec, int k);
+vjp_fn vjp_entry(int prec, int k);
+int smem_attr_entry(int prec, int k);
+
+}  // namespace hope

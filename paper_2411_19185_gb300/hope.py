@@ -46,6 +46,9 @@ class Sphere:
             L.check(lib.hope_init_grid(int(N), order, scheme, ctypes.byref(p), ctypes.byref(h)))
             self.members = [int(N)]
         self._h = h
+        self.offsets = [0]
+        for n in self.members:
+            self.offsets.append(self.offsets[-1] + 18 * n * n)
         self.N = self.members[0]
         self.order, self.scheme, self.precision = order, scheme, precision
         self.radius, self.gravity, self.omega = radius, gravity, omega
@@ -69,6 +72,11 @@ class Sphere:
         if len(self.members) == 1:
             return (3, 6, self.N, self.N)
         return (self.elems,)
+
+    def member(self, q, m):
+        """View of member m of an ensemble state as (3, 6, N_m, N_m)."""
+        n = self.members[m]
+        return q.view(-1)[self.offsets[m]:self.offsets[m + 1]].view(3, 6, n, n)
 
     def empty(self, device="cuda"):
         return torch.empty(self.shape, dtype=self.dtype, device=device)
@@ -168,6 +176,14 @@ class Sphere:
         L.check(L.load().hope_kernel_times(self._h, buf, 64, ctypes.byref(n)))
         v = list(buf[:n.value])
         return [v[i:i + 4] for i in range(0, len(v), 4)]
+
+    def autotune(self, reps=5):
+        """Re-time the persistent stage's tile shapes (ensembles); returns
+        (per-shape ms, (tx, ty), grid)."""
+        ms = (ctypes.c_float * 3)()
+        tx, ty, grid = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        L.check(L.load().hope_autotune(self._h, reps, ms, ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(grid)))
+        return list(ms), (tx.value, ty.value), grid.value
 
     def launches_per_stage(self):
         n = ctypes.c_int()
