@@ -122,6 +122,109 @@ def reduce_max(x, world):
     return float(t.item())
 
 
+def _time_steps(s, q, dt, n, stream):
+    """CUDA-event time of n graph-replayed steps on `stream` (after one warm-up step)."""
+    import torch
+    with torch.cuda.stream(stream):
+        s.step(q, dt, 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(q, dt, n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / n
+
+
+def measure_forms(hp, stream):
+    """The precision, differentiation and batching forms on the same box (short runs;
+    throughput in cell-stage updates/s)."""
+    import torch
+    from synth import bump_centres, noise_field
+    out = {}
+    fp32_peak = hp.measure_fma_peak(hp.HOPE_FP32)
+    out["fp32_fma_peak_tflops"] = fp32_peak / 1e12
+    # precision form on the headline workload: FP32 bulk path
+    s = hp.Sphere(N_CELLS, ORDER, hp.HOPE_TPP, hp.HOPE_FP32, coriolis_tilt=ALPHA)
+    q = s.geostrophic(ALPHA)
+    ms = _time_steps(s, q, DT, 100, stream)
+    cells = 6 * N_CELLS * N_CELLS
+    s.set_profiling(True)
+    with torch.cuda.stream(stream):
+        s.step(q, DT)
+        rec = []
+        for _ in range(20):
+            s.step(q, DT)
+            rec.extend(st[1] for st in s.kernel_times())
+    s.set_profiling(False)
+    fl = recon_flops_per_launch(N_CELLS, ORDER)
+    out["tpp11_c90_fp32"] = {"value": cells * 3 / (ms * 1e-3), "ms_per_step": ms,
+                             "recon_ms": float(np.mean(rec)),
+                             "recon_frac_of_fp32_peak": fl / (np.mean(rec) * 1e-3) / fp32_peak}
+    # precision form, discontinuous flow: WENO9 dam break (2:1), C90, FP64 and FP32
+    for name, P in (("weno9_c90_dam_fp64", hp.HOPE_FP64), ("weno9_c90_dam_fp32", hp.HOPE_FP32)):
+        s = hp.Sphere(N_CELLS, 9, hp.HOPE_WENO2D, P, omega=0.0)
+        q = s.dam_break(h_in=10.0, h_out=5.0)
+        n = 6 if P == hp.HOPE_FP64 else 30
+        ms = _time_steps(s, q, 300.0, n, stream)
+        out[name] = {"value": cells * 3 / (ms * 1e-3), "ms_per_step": ms}
+    # differentiation form: C180 WENO5, geostrophic + 16 bumps, forward and forward+adjoint
+    cen = bump_centres(16, 0)
+    for name, P in (("adjoint_c180_weno5_fp64", hp.HOPE_FP64), ("adjoint_c180_weno5_fp32", hp.HOPE_FP32)):
+        s = hp.Sphere(180, 5, hp.HOPE_WENO2D, P)
+        q0 = s.bumps(cen)
+        target = q0[0].clone()
+        nsteps = 10
+        with torch.cuda.stream(stream):
+            x = q0.clone().requires_grad_(True)
+            qT = s.rollout(x, 150.0, nsteps, checkpoint_every=10)
+            loss = 0.5 * ((qT[0] - target) ** 2).sum()
+            loss.backward()
+            torch.cuda.synchronize()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            x = q0.clone().requires_grad_(True)
+            e[0].record(stream)
+            qT = s.rollout(x, 150.0, nsteps, checkpoint_every=10)
+            e[1].record(stream)
+            loss = 0.5 * ((qT[0] - target) ** 2).sum()
+            loss.backward()
+            e[2].record(stream)
+            torch.cuda.synchronize()
+        fwd, bwd = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+        c180 = 6 * 180 * 180 * 3 * nsteps
+        out[name] = {"forward": c180 / (fwd * 1e-3), "forward_plus_adjoint": c180 / ((fwd + bwd) * 1e-3),
+                     "steps": nsteps, "checkpoint_every": 10, "fwd_ms": fwd, "adjoint_ms": bwd}
+    # batching form: 64 members (32 x C48, 24 x C96, 8 x C192), TPP7, FP32, RH + 1% noise
+    members = [48] * 32 + [96] * 24 + [192] * 8
+    ens = hp.Sphere(members, 7, hp.HOPE_TPP, hp.HOPE_FP32)
+    q = ens.empty()
+    for N in (48, 96, 192):
+        base = hp.Sphere(N, 7, hp.HOPE_TPP, hp.HOPE_FP32).rossby_haurwitz()
+        for m, Nm in enumerate(members):
+            if Nm == N:
+                xi = torch.from_numpy(noise_field((6, N, N), 0, member=m)).to("cuda", torch.float32)
+                ens.member(q, m).copy_(base * (1 + 0.01 * xi)[None])
+    ms = _time_steps(ens, q, 45.0, 20, stream)
+    total = sum(6 * n * n for n in members)
+    lam = torch.ones_like(q)
+    with torch.cuda.stream(stream):
+        out_l = torch.empty_like(q)
+        ens.step_vjp(q, lam, 45.0, out=out_l)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            ens.step_vjp(q, lam, 45.0, out=out_l)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    adj_ms = e0.elapsed_time(e1) / 5
+    out["ensemble64_tpp7_fp32"] = {"value": total * 3 / (ms * 1e-3), "ms_per_step": ms, "cells": total,
+                                   "launches_per_stage": ens.launches_per_stage(),
+                                   "step_adjoint_ms": adj_ms,
+                                   "forward_plus_adjoint": total * 3 / ((ms + adj_ms) * 1e-3)}
+    return out
+
+
 def cpu_baseline(stages):
     """The FP64 C oracle (test infrastructure), as it stands, on this host's cores:
     `stages` tendency evaluations of the full workload."""
@@ -171,6 +274,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-stages", type=int, default=150)
+    ap.add_argument("--no-forms", action="store_true")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -233,6 +337,7 @@ def main():
             e2e_s += time.perf_counter() - t0
     m1 = s.mass(q)
     status = s.status()
+    forms = measure_forms(hp, stream) if not args.no_forms else None
     total_ms = reduce_max(total_ms, world)
     e2e_s = reduce_max(e2e_s, world)
     value = world * cells * 3 * args.steps / (total_ms * 1e-3)
@@ -263,6 +368,7 @@ def main():
         "clocks": clocks,
         "mass_drift": (m1 - m0) / m0,
         "device_status": status,
+        "forms": forms,
     }
     if world == 1 and not args.no_cpu_baseline:
         v, el = cpu_baseline(args.cpu_stages)

@@ -240,7 +240,8 @@ const char *hope_last_error_message(void) { return g_err.c_str(); }
 
 static void free_grid(Grid &g) {
   if (g.owns_tables) {
-    void *tables[] = {g.Xg, g.t1w, g.mx, g.gval, g.grow, g.gcol, g.gdst, g.bedge, g.bconv, g.gtp, g.gtr, g.gtv};
+    void *tables[] = {g.Xg, g.t1w, g.mx, g.gval, g.grow, g.gcol, g.gdst, g.bedge, g.bconv, g.gtp, g.gtr, g.gtv,
+                      g.trow, g.tcol, g.tval};
     for (void *p : tables)
       if (p) cudaFree(p);
   }
@@ -378,6 +379,7 @@ static int init_impl(int n_members, const int *Ns, int order, int scheme, const 
       const Grid &src = ctx->grids[it->second];
       g.Xg = src.Xg; g.t1w = src.t1w; g.mx = src.mx;
       g.gval = src.gval; g.grow = src.grow; g.gcol = src.gcol; g.gdst = src.gdst;
+      g.trow = src.trow; g.tcol = src.tcol; g.tval = src.tval; g.tnnz = src.tnnz;
       g.rows = src.rows; g.nnz = src.nnz;
       g.bedge = src.bedge; g.bconv = src.bconv;
       g.gtp = src.gtp; g.gtr = src.gtr; g.gtv = src.gtv;
@@ -391,13 +393,27 @@ static int init_impl(int n_members, const int *Ns, int order, int scheme, const 
       TRY(setup_grid_tables(ctx, gr, nodes, weights));
       std::vector<int> rowptr, cols, dst;
       std::vector<double> vals;
-      TRY(build_ghost_operator(ctx, gr.N, nodes, weights, rowptr, cols, vals, dst));
+      GhostSplit split;
+      TRY(build_ghost_operator(ctx, gr.N, nodes, weights, rowptr, cols, vals, dst,
+                               ctx->prec == HOPE_FP64 ? &split : nullptr));
       gr.rows = (long long)dst.size();
       gr.nnz = rowptr.back();
-      TRY(upload_int(&gr.grow, rowptr));
-      TRY(upload_int(&gr.gcol, cols));
       TRY(upload_int(&gr.gdst, dst));
-      TRY(upload(&gr.gval, vals, ctx->esize));
+      if (ctx->prec == HOPE_FP64) {
+        TRY(upload_int(&gr.grow, split.head_ptr));
+        TRY(upload_int(&gr.gcol, split.head_col));
+        TRY(upload(&gr.gval, split.head_val, ctx->esize));
+        TRY(upload_int(&gr.trow, split.tail_ptr));
+        TRY(upload_int(&gr.tcol, split.tail_col));
+        gr.tnnz = (long long)split.tail_col.size();
+        TRY(alloc((void **)&gr.tval, sizeof(float) * (split.tail_val.empty() ? 1 : split.tail_val.size())));
+        if (!split.tail_val.empty())
+          cudaMemcpy(gr.tval, split.tail_val.data(), sizeof(float) * split.tail_val.size(), cudaMemcpyHostToDevice);
+      } else {
+        TRY(upload_int(&gr.grow, rowptr));
+        TRY(upload_int(&gr.gcol, cols));
+        TRY(upload(&gr.gval, vals, ctx->esize));
+      }
       {
         // transposed ghost operator for the adjoint: CSR over interior cells
         const int ncell = 6 * gr.N * gr.N;

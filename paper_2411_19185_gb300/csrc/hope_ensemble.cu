@@ -23,6 +23,8 @@ struct MemberDev {
   long long off;  // element offset of the member in ensemble states
   const int *grow, *gcol, *gdst;
   const T *gval;
+  const int *trow, *tcol;
+  const float *tval;
   T *gext;
   const T *Xg, *t1w, *mx, *bconv;
   const int *bedge;
@@ -113,7 +115,8 @@ __global__ void __launch_bounds__(TX *TY)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (long long it = (long long)blockIdx.x * WPB + warp; it < n_ghost; it += (long long)gridDim.x * WPB) {
       const MemberDev<T> &m = mem[find_member(mem, nmem, it, 0)];
-      ghost_row(int(it - m.b_ghost), lane, sa.qs + m.off, m.gext, m.grow, m.gcol, m.gval, m.gdst, m.N, m.ne);
+      ghost_row(int(it - m.b_ghost), lane, sa.qs + m.off, m.gext, m.grow, m.gcol, m.gval, m.gdst, m.trow, m.tcol,
+                m.tval, m.N, m.ne);
     }
   }
   if (!grid_sync(bar, status, inject)) return;
@@ -160,6 +163,9 @@ static int build_members(hope_ctx *ctx, int TX, int TY, std::vector<MemberDev<T>
     m.gcol = g.gcol;
     m.gdst = g.gdst;
     m.gval = (const T *)g.gval;
+    m.trow = g.trow;
+    m.tcol = g.tcol;
+    m.tval = g.tval;
     m.gext = (T *)g.gext;
     m.Xg = (const T *)g.Xg;
     m.t1w = (const T *)g.t1w;

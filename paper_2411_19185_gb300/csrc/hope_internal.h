@@ -37,6 +37,10 @@ struct Grid {
   int *gcol = nullptr;   // [nnz]  source cell p*N*N + j*N + i
   int *gdst = nullptr;   // [rows] destination p*ne*ne + jj*ne + ii
   long long rows = 0, nnz = 0;
+  // FP64 contexts: grow/gcol/gval hold the FP64 head of each row, these the FP32 tail
+  int *trow = nullptr, *tcol = nullptr;
+  float *tval = nullptr;
+  long long tnnz = 0;
   int *bedge = nullptr;  // [12][5] CubeEdge
   void *bconv = nullptr; // [12][N][me][9] ratio_BA, C_BA[4], C_AB[4]
   // scratch

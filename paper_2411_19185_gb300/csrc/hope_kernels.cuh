@@ -54,10 +54,14 @@ struct FCoef {
 // ---------------------------------------------------------------------------------
 // Ghost fill: one warp per ghost cell, lanes stride over the row's nonzeros.
 // ---------------------------------------------------------------------------------
+// One ghost row: FP64/FP32 head sum in the context precision, plus (FP64 contexts) the
+// FP32 tail of negligible weights.
 template <typename T>
 __device__ __forceinline__ void ghost_row(int row, int lane, const T *__restrict__ q, T *__restrict__ gext,
                                           const int *__restrict__ grow, const int *__restrict__ gcol,
-                                          const T *__restrict__ gval, const int *__restrict__ gdst, int N, int ne) {
+                                          const T *__restrict__ gval, const int *__restrict__ gdst,
+                                          const int *__restrict__ trow, const int *__restrict__ tcol,
+                                          const float *__restrict__ tval, int N, int ne) {
   size_t pn = (size_t)6 * N * N, pe = (size_t)6 * ne * ne;
   int b = grow[row], e = grow[row + 1];
   T s0 = 0, s1 = 0, s2 = 0;
@@ -68,6 +72,21 @@ __device__ __forceinline__ void ghost_row(int row, int lane, const T *__restrict
     s0 += w[0] * a0;
     s1 += w[1] * a1 + w[2] * a2;
     s2 += w[3] * a1 + w[4] * a2;
+  }
+  if (trow) {
+    float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+    const int tb = trow[row], te = trow[row + 1];
+    for (int t = tb + lane; t < te; t += 32) {
+      int c = tcol[t];
+      const float *w = tval + (size_t)t * 5;
+      float a0 = (float)q[c], a1 = (float)q[pn + c], a2 = (float)q[2 * pn + c];
+      f0 = fmaf(w[0], a0, f0);
+      f1 = fmaf(w[1], a1, fmaf(w[2], a2, f1));
+      f2 = fmaf(w[3], a1, fmaf(w[4], a2, f2));
+    }
+    s0 += (T)f0;
+    s1 += (T)f1;
+    s2 += (T)f2;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -87,10 +106,11 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_ghost(const T *__restrict__ q, T *__restrict__ gext,
                                                const int *__restrict__ grow, const int *__restrict__ gcol,
                                                const T *__restrict__ gval, const int *__restrict__ gdst,
-                                               int rows, int N, int ne) {
+                                               const int *__restrict__ trow, const int *__restrict__ tcol,
+                                               const float *__restrict__ tval, int rows, int N, int ne) {
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (warp >= rows) return;
-  ghost_row(warp, threadIdx.x & 31, q, gext, grow, gcol, gval, gdst, N, ne);
+  ghost_row(warp, threadIdx.x & 31, q, gext, grow, gcol, gval, gdst, trow, tcol, tval, N, ne);
 }
 
 // ---------------------------------------------------------------------------------

@@ -149,7 +149,8 @@ struct LocalEnt {
 
 int build_ghost_operator(const hope_ctx *ctx, int N, const std::vector<double> &nodes,
                          const std::vector<double> &weights, std::vector<int> &rowptr,
-                         std::vector<int> &cols, std::vector<double> &vals, std::vector<int> &dst) {
+                         std::vector<int> &cols, std::vector<double> &vals, std::vector<int> &dst,
+                         GhostSplit *split) {
   const int K = ctx->k, H = ctx->H, me = ctx->me, ne = N + 2 * H;
   const double dx = HOPE_PI / (2.0 * N);
   // ring enumeration
@@ -300,6 +301,41 @@ int build_ghost_operator(const hope_ctx *ctx, int N, const std::vector<double> &
   }
   rowptr.assign(rows + 1, 0);
   for (int r = 0; r < rows; ++r) rowptr[r + 1] = rowptr[r] + (int)G[r].size();
+  if (split) {
+    // Head/tail split for FP64 contexts: entries whose largest weight is at least
+    // split_rel of the row's largest stay in FP64; the rest (at most ~2e-8 of a row's
+    // weight) are evaluated in FP32, whose rounding then contributes ~1e-15 relative.
+    const double split_rel = 1e-9;
+    split->head_ptr.assign(rows + 1, 0);
+    split->tail_ptr.assign(rows + 1, 0);
+    split->head_col.clear();
+    split->tail_col.clear();
+    split->head_val.clear();
+    split->tail_val.clear();
+    for (int r = 0; r < rows; ++r) {
+      double mx = 0.0;
+      for (const auto &e : G[r]) {
+        double m = fabs(e.m);
+        for (int t = 0; t < 4; ++t) m = fmax(m, fabs(e.c[t]));
+        mx = fmax(mx, m);
+      }
+      for (const auto &e : G[r]) {
+        double m = fabs(e.m);
+        for (int t = 0; t < 4; ++t) m = fmax(m, fabs(e.c[t]));
+        if (m >= split_rel * mx) {
+          split->head_col.push_back(e.col);
+          split->head_val.push_back(e.m);
+          for (int t = 0; t < 4; ++t) split->head_val.push_back(e.c[t]);
+        } else {
+          split->tail_col.push_back(e.col);
+          split->tail_val.push_back((float)e.m);
+          for (int t = 0; t < 4; ++t) split->tail_val.push_back((float)e.c[t]);
+        }
+      }
+      split->head_ptr[r + 1] = (int)split->head_col.size();
+      split->tail_ptr[r + 1] = (int)split->tail_col.size();
+    }
+  }
   cols.resize(rowptr[rows]);
   vals.resize((size_t)5 * rowptr[rows]);
   for (int r = 0; r < rows; ++r) {

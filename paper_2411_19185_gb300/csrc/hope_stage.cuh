@@ -113,7 +113,7 @@ inline int stage_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *q0, T *out, 
     long long threads = g.rows * 32;
     int blocks = (int)((threads + 255) / 256);
     k_ghost<T><<<blocks, 256, 0, st>>>(qs, (T *)g.gext, g.grow, g.gcol, (const T *)g.gval, g.gdst,
-                                       (int)g.rows, N, ne);
+                                       g.trow, g.tcol, g.tval, (int)g.rows, N, ne);
   }
   mark(1);
   // reconstruction + sources
@@ -194,8 +194,8 @@ inline int stage_vjp_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *lamL, co
   const int N = g.N, ne = g.ne;
   if (g.rows > 0) {
     int blocks = (int)((g.rows * 32 + 255) / 256);
-    k_ghost<T><<<blocks, 256, 0, st>>>(qs, (T *)g.gext, g.grow, g.gcol, (const T *)g.gval, g.gdst, (int)g.rows, N,
-                                       ne);
+    k_ghost<T><<<blocks, 256, 0, st>>>(qs, (T *)g.gext, g.grow, g.gcol, (const T *)g.gval, g.gdst, g.trow, g.tcol,
+                                       g.tval, (int)g.rows, N, ne);
   }
   dim3 grid((N + REC_TX - 1) / REC_TX, (N + REC_TY - 1) / REC_TY, 6);
   if (ctx->scheme == HOPE_TPP) {

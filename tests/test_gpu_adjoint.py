@@ -103,11 +103,12 @@ def smooth_generic_state(N, seed):
 
 @pytest.mark.parametrize("k,N", [(3, 10), (5, 11)])
 def test_weno_tendency_vjp_matches_central_differences(hp, k, N):
-    """WENO-Z is piecewise smooth: tau (eq. 3.24) has kinks where two indicators are equal.
-    A 1%-noise state puts some of the ~10^5 indicator pairs within the finite-difference
-    step of a kink, and the unperturbed wave ties pairs exactly by symmetry; the smooth
-    asymmetric state keeps every pair far from a kink (the autograd comparison below
-    covers the noisy state at 1e-10)."""
+    """WENO-Z is only piecewise smooth: tau (eq. 3.24) has a kink wherever two indicators
+    are equal, and on smooth data the indicators of one cell differ by O(dx) only, so a
+    central difference of step h crosses about (pairs x h / dx) kinks -- close to one
+    here.  Central differences therefore bound the WENO adjoint only to 1e-4; the exact
+    check is the 1e-10 comparison with autograd through the PyTorch reference below.
+    The smooth asymmetric state avoids exact ties by symmetry."""
     s = hp.Sphere(N, k, scheme=hp.HOPE_WENO2D)
     q = smooth_generic_state(N, 41)
     d = torch.from_numpy(fd_direction(q.shape, 12)).cuda() * q.abs().mean(dim=(1, 2, 3), keepdim=True)
@@ -115,7 +116,7 @@ def test_weno_tendency_vjp_matches_central_differences(hp, k, N):
     h = 1e-6
     fd = torch.sum(lam * directional(lambda x: s.tendency(x.contiguous()), q, d, h)).item()
     adj = torch.sum(s.tendency_vjp(q, lam) * d).item()
-    assert abs(adj - fd) <= 1e-6 * abs(fd), (adj, fd)
+    assert abs(adj - fd) <= 1e-4 * abs(fd), (adj, fd)
 
 
 # ------------------------------------------------------------------ autograd reference
@@ -154,6 +155,31 @@ def test_rollout_gradient_matches_torch_autograd_reference(hp):
     ref = qc.grad.numpy()
     xg = q0.clone().requires_grad_(True)
     qT = s.rollout(xg, dt, n, checkpoint_every=3)
+    (0.5 * ((qT[0] - target) ** 2).sum()).backward()
+    got = xg.grad.cpu().numpy()
+    err = [np.linalg.norm(got[v] - ref[v]) / np.linalg.norm(ref[v]) for v in range(3)]
+    assert max(err) < 1e-10, err
+
+
+def test_weno_rollout_gradient_matches_torch_autograd_reference(hp):
+    """Differentiation form in small: gradient of 0.5 |h_T - h_target|^2 after 3 SSP-RK3
+    steps of WENO5 (geostrophic flow plus Gaussian bumps) against autograd through the
+    PyTorch reference: relative 1e-10."""
+    from oracle.torch_ref import TorchReference
+    from synth import bump_centres
+    N, k, dt, n = 9, 5, 900.0, 3
+    R = TorchReference(N, k, O.WENO)
+    s = hp.Sphere(N, k, scheme=hp.HOPE_WENO2D)
+    q0 = torch.from_numpy(np.ascontiguousarray(R.o.bumps(bump_centres(16, 0)))).cuda()
+    target = torch.from_numpy(np.ascontiguousarray(R.o.bumps(bump_centres(16, 7))))[0].cuda()
+    qc = q0.cpu().clone().requires_grad_(True)
+    x = qc
+    for _ in range(n):
+        x = R.step(x, dt)
+    (0.5 * ((x[0] - target.cpu()) ** 2).sum()).backward()
+    ref = qc.grad.numpy()
+    xg = q0.clone().requires_grad_(True)
+    qT = s.rollout(xg, dt, n, checkpoint_every=2)
     (0.5 * ((qT[0] - target) ** 2).sum()).backward()
     got = xg.grad.cpu().numpy()
     err = [np.linalg.norm(got[v] - ref[v]) / np.linalg.norm(ref[v]) for v in range(3)]
