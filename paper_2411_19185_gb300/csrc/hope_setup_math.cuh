@@ -1,7 +1,7 @@
 // hope_setup_math.cuh -- FP64 setup mathematics shared by the host-side table
 // assembly and the device-side setup kernels of the HOPE GB300 library.
 //
-// Everything here is evaluated once per grid; nothing runs per stage.
+// Everything here is evaluated once per grid at set-up; nothing runs per stage.
 // Routes are chosen for conditioning in FP64:
 //   * cell-average reconstruction weights through the derivative of the Lagrange
 //     interpolant of the primitive function at the cell interfaces (the unique
