@@ -69,7 +69,7 @@ def test_tendency_tpp_fp64(hp, k, N, tilt):
     assert s.status() == 0
 
 
-def test_config1_c32_tpp5_10_steps(hp):
+def test_c32_tpp5_geostrophic_10_steps(hp):
     """C32, TPP5, steady geostrophic flow (alpha = 0), SSP-RK3 dt = 600 s, 10 steps."""
     N, k = 32, 5
     s = hp.Sphere(N, k)
@@ -99,7 +99,7 @@ def test_wsrk3_steps(hp):
     assert max(rel_l2(q.cpu().numpy(), ref)) < 1e-12
 
 
-def test_config2_c90_tpp11_full_size_one_step(hp):
+def test_c90_tpp11_geostrophic_full_size_one_step(hp):
     """Full-size C90 TPP11 (alpha = pi/4), the benchmark's launch configuration
     (graph-replayed SSP-RK3 step, dt = 300 s): one step against the oracle."""
     N, k = 90, 11
@@ -214,7 +214,7 @@ def test_fp32_tendency_vs_oracle(hp, scheme):
     assert max(err) < 1e-4, err
 
 
-def test_config3_weno9_dam_break_fp32_vs_fp64_one_day(hp):
+def test_c90_weno9_dam_break_fp32_vs_fp64_one_day(hp):
     """Precision form at full size: C90, WENO9, dam break (h = 10 m inside a 20 degree cap
     at (0, 0), 5 m outside -- the 2:1 ratio of eq. 5.19 --, at rest, Omega = 0), SSP-RK3
     dt = 300 s for one simulated day.
