@@ -240,7 +240,7 @@ const char *hope_last_error_message(void) { return g_err.c_str(); }
 
 static void free_grid(Grid &g) {
   if (g.owns_tables) {
-    void *tables[] = {g.Xg, g.t1w, g.mx, g.gval, g.grow, g.gcol, g.gdst, g.bedge, g.bconv, g.gtp, g.gtr, g.gtv,
+    void *tables[] = {g.Xg, g.t1w, g.mx, g.src8, g.gval, g.grow, g.gcol, g.gdst, g.bedge, g.bconv, g.gtp, g.gtr, g.gtv,
                       g.trow, g.tcol, g.tval};
     for (void *p : tables)
       if (p) cudaFree(p);
@@ -377,7 +377,7 @@ static int init_impl(int n_members, const int *Ns, int order, int scheme, const 
     auto it = first_of_N.find(Ns[m]);
     if (it != first_of_N.end()) {
       const Grid &src = ctx->grids[it->second];
-      g.Xg = src.Xg; g.t1w = src.t1w; g.mx = src.mx;
+      g.Xg = src.Xg; g.t1w = src.t1w; g.mx = src.mx; g.src8 = src.src8;
       g.gval = src.gval; g.grow = src.grow; g.gcol = src.gcol; g.gdst = src.gdst;
       g.trow = src.trow; g.tcol = src.tcol; g.tval = src.tval; g.tnnz = src.tnnz;
       g.rows = src.rows; g.nnz = src.nnz;

@@ -32,6 +32,7 @@ struct Grid {
   void *Xg = nullptr;    // [N][me]  tan of the cell Gauss-node coordinates
   void *t1w = nullptr;   // [N][N][me][me]  2/delta^2 * W_gh at the cell points
   void *mx = nullptr;    // [N+1][N][me][5] x-edge metric terms (transposed use for y-edges)
+  void *src8 = nullptr;  // [N][N][me][me][8] source polynomials times the cell-point weight
   void *gval = nullptr;  // [nnz][5] ghost operator weights (mass, C00, C01, C10, C11)
   int *grow = nullptr;   // [rows+1]
   int *gcol = nullptr;   // [nnz]  source cell p*N*N + j*N + i

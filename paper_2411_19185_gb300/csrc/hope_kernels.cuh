@@ -165,7 +165,7 @@ template <typename T, int K, int TX, int TY>
 __device__ __forceinline__ void recon_tpp_tile(unsigned char *smem_raw, int p, int i0, int j0,
                                                const T *__restrict__ q, const T *__restrict__ gext,
                                                const T *__restrict__ w1g, const T *__restrict__ Xg,
-                                               const T *__restrict__ t1w, T *__restrict__ ep, T *__restrict__ sb,
+                                               const T *__restrict__ src8, T *__restrict__ ep, T *__restrict__ sb,
                                                int N, int ne, T omega, const FCoef<T> &fc) {
   using S = Tile<K, TX, TY>;
   constexpr int ME = S::ME, NPOS = S::NPOS;
@@ -243,15 +243,11 @@ __device__ __forceinline__ void recon_tpp_tile(unsigned char *smem_raw, int p, i
             qv[v] = s;
           }
           const T Y = Xg[j * ME + h];
-          const T tw = t1w[(((size_t)j * N + i) * ME + h) * ME + g];
-          const T sl = fc0 + fc1 * X + fc2 * Y;  // sin(latitude)*delta, eq. 2.5
+          const T *c8 = src8 + ((((size_t)j * N + i) * ME + h) * ME + g) * 8;
+          const T os = omega * (fc0 + fc1 * X + fc2 * Y);  // Omega sin(latitude) delta, eq. 2.5
           const T rq = rcp(qv[0]);
-          const T XY = X * Y, X2 = X * X, Y2 = Y * Y;
-          const T os = omega * sl;
-          T a1 = (-XY * Y * qv[1] + Y * (T(1) + Y2) * qv[2]) * qv[1] * rq + os * (-XY * qv[1] + (T(1) + Y2) * qv[2]);
-          T a2 = (X * (T(1) + X2) * qv[1] - X2 * Y * qv[2]) * qv[2] * rq + os * (-(T(1) + X2) * qv[1] + XY * qv[2]);
-          s1 = fma(tw, a1, s1);
-          s2 = fma(tw, a2, s2);
+          s1 += fma(c8[0], qv[1], c8[1] * qv[2]) * qv[1] * rq + os * fma(c8[4], qv[1], c8[5] * qv[2]);
+          s2 += fma(c8[2], qv[1], c8[3] * qv[2]) * qv[2] * rq + os * fma(c8[6], qv[1], c8[7] * qv[2]);
         }
       }
     }
@@ -264,11 +260,11 @@ __device__ __forceinline__ void recon_tpp_tile(unsigned char *smem_raw, int p, i
 template <typename T, int K>
 __global__ void __launch_bounds__(REC_TX *REC_TY)
     k_recon_tpp(const T *__restrict__ q, const T *__restrict__ gext, const T *__restrict__ w1g,
-                const T *__restrict__ Xg, const T *__restrict__ t1w, T *__restrict__ ep,
+                const T *__restrict__ Xg, const T *__restrict__ src8, T *__restrict__ ep,
                 T *__restrict__ sb, int N, int ne, T omega, FCoef<T> fc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   recon_tpp_tile<T, K, REC_TX, REC_TY>(smem_raw, blockIdx.z, blockIdx.x * REC_TX, blockIdx.y * REC_TY, q, gext, w1g,
-                                       Xg, t1w, ep, sb, N, ne, omega, fc);
+                                       Xg, src8, ep, sb, N, ne, omega, fc);
 }
 
 // ---------------------------------------------------------------------------------
@@ -283,7 +279,8 @@ __device__ __forceinline__ void lmars(const T qL[3], const T qR[3], const T *m5,
   const T phL = qL[0] * isg, phR = qR[0] * isg;
   if (!(phL > T(0)) || !(phR > T(0))) atomicOr(status, HOPE_STATUS_NONPHYS_PHI);
   const int n = 1 + dir;
-  const T uL = qL[n] * rcp(qL[0]) * is11, uR = qR[n] * rcp(qR[0]) * is11;
+  const T rLR = rcp(qL[0] * qR[0]);  // one reciprocal for both states
+  const T uL = qL[n] * (qR[0] * rLR) * is11, uR = qR[n] * (qL[0] * rLR) * is11;
   const T c = T(0.5) * (sqrt(phL) + sqrt(phR));
   const T ms = T(0.5) * (uL + uR - (phR - phL) * rcp(c));
   const T ph = T(0.5) * (phL + phR - c * (uR - uL));

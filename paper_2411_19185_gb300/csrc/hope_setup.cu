@@ -38,7 +38,7 @@ __global__ void k_setup_order(int K, int me, T *w1, T *gw, double *nodes_out) {
 
 template <typename T>
 __global__ void k_setup_grid(int N, int me, double radius, const double *__restrict__ nw, T *Xg, T *t1w,
-                             T *mx) {
+                             T *mx, T *src8) {
   const double dx = HOPE_PI / (2.0 * N);
   const double r2 = radius * radius;
   const long long nX = (long long)N * me, nT = (long long)N * N * me * me, nM = (long long)(N + 1) * N * me;
@@ -56,7 +56,20 @@ __global__ void k_setup_grid(int N, int me, double radius, const double *__restr
       int i = (int)(t % N), j = (int)(t / N);
       double X = tan(-HOPE_QPI + (i + 0.5 + nw[g]) * dx);
       double Y = tan(-HOPE_QPI + (j + 0.5 + nw[h]) * dx);
-      t1w[r] = (T)(2.0 / (1.0 + X * X + Y * Y) * nw[me + g] * nw[me + h]);
+      const double tw = 2.0 / (1.0 + X * X + Y * Y) * nw[me + g] * nw[me + h];
+      t1w[r] = (T)tw;
+      // source polynomials with the weight folded in (eqs. 2.2, 2.3 times W_gh 2/delta^2):
+      //   a1 = (c1 q1 + c2 q2) q1/q0 + os (e1 q1 + e2 q2)
+      //   a2 = (c3 q1 + c4 q2) q2/q0 + os (e3 q1 + e4 q2),  os = Omega sin(lat) delta
+      T *o = src8 + r * 8;
+      o[0] = (T)(-tw * X * Y * Y);
+      o[1] = (T)(tw * Y * (1.0 + Y * Y));
+      o[2] = (T)(tw * X * (1.0 + X * X));
+      o[3] = (T)(-tw * X * X * Y);
+      o[4] = (T)(-tw * X * Y);
+      o[5] = (T)(tw * (1.0 + Y * Y));
+      o[6] = (T)(-tw * (1.0 + X * X));
+      o[7] = (T)(tw * X * Y);
     } else {
       long long r = idx - nX - nT;
       int g = (int)(r % me);
@@ -80,8 +93,9 @@ __global__ void k_setup_grid(int N, int me, double radius, const double *__restr
 
 template __global__ void k_setup_order<double>(int, int, double *, double *, double *);
 template __global__ void k_setup_order<float>(int, int, float *, float *, double *);
-template __global__ void k_setup_grid<double>(int, int, double, const double *, double *, double *, double *);
-template __global__ void k_setup_grid<float>(int, int, double, const double *, float *, float *, float *);
+template __global__ void k_setup_grid<double>(int, int, double, const double *, double *, double *, double *,
+                                              double *);
+template __global__ void k_setup_grid<float>(int, int, double, const double *, float *, float *, float *, float *);
 
 int setup_order_tables(hope_ctx *ctx, std::vector<double> &nodes, std::vector<double> &weights) {
   const int K = ctx->k, me = ctx->me;
@@ -116,12 +130,13 @@ int setup_grid_tables(hope_ctx *ctx, Grid &gr, const std::vector<double> &nodes,
   if (cudaMalloc(&gr.Xg, es * N * me) != cudaSuccess) return HOPE_ENOMEM;
   if (cudaMalloc(&gr.t1w, es * (size_t)N * N * me * me) != cudaSuccess) return HOPE_ENOMEM;
   if (cudaMalloc(&gr.mx, es * (size_t)(N + 1) * N * me * 5) != cudaSuccess) return HOPE_ENOMEM;
+  if (cudaMalloc(&gr.src8, es * (size_t)N * N * me * me * 8) != cudaSuccess) return HOPE_ENOMEM;
   if (ctx->prec == HOPE_FP64)
     k_setup_grid<double><<<256, 256>>>(N, me, ctx->radius, d_nw, (double *)gr.Xg, (double *)gr.t1w,
-                                       (double *)gr.mx);
+                                       (double *)gr.mx, (double *)gr.src8);
   else
     k_setup_grid<float><<<256, 256>>>(N, me, ctx->radius, d_nw, (float *)gr.Xg, (float *)gr.t1w,
-                                      (float *)gr.mx);
+                                      (float *)gr.mx, (float *)gr.src8);
   cudaError_t e = cudaDeviceSynchronize();
   cudaFree(d_nw);
   return e == cudaSuccess ? HOPE_OK : HOPE_ECUDA;
