@@ -26,7 +26,7 @@ struct MemberDev {
   const int *trow, *tcol;
   const float *tval;
   T *gext;
-  const T *Xg, *src8, *mx, *bconv;
+  const T *Xg, *t1w, *src8, *mx, *bconv;
   const int *bedge;
   T *ep, *sb, *fx, *fy;
   long long b_ghost, b_tile, b_flux, b_cell;  // first global item of each phase
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(TX *TY)
     const int p = local / (m.tiles_x * m.tiles_y);
     const int rem = local - p * m.tiles_x * m.tiles_y;
     const int ty = rem / m.tiles_x, tx = rem - ty * m.tiles_x;
-    recon_tpp_tile<T, K, TX, TY>(smem_raw, p, tx * TX, ty * TY, sa.qs + m.off, m.gext, sa.w1, m.Xg, m.src8, m.ep,
+    recon_tpp_tile<T, K, TX, TY>(smem_raw, p, tx * TX, ty * TY, sa.qs + m.off, m.gext, sa.w1, m.Xg, m.t1w, m.src8, m.ep,
                                  m.sb, m.N, m.ne, sa.omega, sa.fc);
   }
   if (!grid_sync(bar, status, inject)) return;
@@ -168,6 +168,7 @@ static int build_members(hope_ctx *ctx, int TX, int TY, std::vector<MemberDev<T>
     m.tval = g.tval;
     m.gext = (T *)g.gext;
     m.Xg = (const T *)g.Xg;
+    m.t1w = (const T *)g.t1w;
     m.src8 = (const T *)g.src8;
     m.mx = (const T *)g.mx;
     m.bconv = (const T *)g.bconv;

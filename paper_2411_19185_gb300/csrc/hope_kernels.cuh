@@ -165,8 +165,9 @@ template <typename T, int K, int TX, int TY>
 __device__ __forceinline__ void recon_tpp_tile(unsigned char *smem_raw, int p, int i0, int j0,
                                                const T *__restrict__ q, const T *__restrict__ gext,
                                                const T *__restrict__ w1g, const T *__restrict__ Xg,
-                                               const T *__restrict__ src8, T *__restrict__ ep, T *__restrict__ sb,
-                                               int N, int ne, T omega, const FCoef<T> &fc) {
+                                               const T *__restrict__ t1w, const T *__restrict__ src8,
+                                               T *__restrict__ ep, T *__restrict__ sb, int N, int ne, T omega,
+                                               const FCoef<T> &fc) {
   using S = Tile<K, TX, TY>;
   constexpr int ME = S::ME, NPOS = S::NPOS;
   T *raw = reinterpret_cast<T *>(smem_raw);              // [3][RH][RW]
@@ -243,11 +244,25 @@ __device__ __forceinline__ void recon_tpp_tile(unsigned char *smem_raw, int p, i
             qv[v] = s;
           }
           const T Y = Xg[j * ME + h];
-          const T *c8 = src8 + ((((size_t)j * N + i) * ME + h) * ME + g) * 8;
+          const size_t pt = (((size_t)j * N + i) * ME + h) * ME + g;
           const T os = omega * (fc0 + fc1 * X + fc2 * Y);  // Omega sin(latitude) delta, eq. 2.5
           const T rq = rcp(qv[0]);
-          s1 += fma(c8[0], qv[1], c8[1] * qv[2]) * qv[1] * rq + os * fma(c8[4], qv[1], c8[5] * qv[2]);
-          s2 += fma(c8[2], qv[1], c8[3] * qv[2]) * qv[2] * rq + os * fma(c8[6], qv[1], c8[7] * qv[2]);
+          if constexpr (sizeof(T) == 8) {
+            // FP64: the FP64 pipe is the bound, so the eight weighted polynomials are loaded
+            const T *c8 = src8 + pt * 8;
+            s1 += fma(c8[0], qv[1], c8[1] * qv[2]) * qv[1] * rq + os * fma(c8[4], qv[1], c8[5] * qv[2]);
+            s2 += fma(c8[2], qv[1], c8[3] * qv[2]) * qv[2] * rq + os * fma(c8[6], qv[1], c8[7] * qv[2]);
+          } else {
+            // FP32: arithmetic is cheap next to load latency, so the polynomials are evaluated
+            const T XY = X * Y, X2 = X * X, Y2 = Y * Y;
+            const T a1 = (-XY * Y * qv[1] + Y * (T(1) + Y2) * qv[2]) * qv[1] * rq +
+                         os * (-XY * qv[1] + (T(1) + Y2) * qv[2]);
+            const T a2 = (X * (T(1) + X2) * qv[1] - X2 * Y * qv[2]) * qv[2] * rq +
+                         os * (-(T(1) + X2) * qv[1] + XY * qv[2]);
+            const T tw = t1w[pt];
+            s1 = fma(tw, a1, s1);
+            s2 = fma(tw, a2, s2);
+          }
         }
       }
     }
@@ -260,11 +275,11 @@ __device__ __forceinline__ void recon_tpp_tile(unsigned char *smem_raw, int p, i
 template <typename T, int K>
 __global__ void __launch_bounds__(REC_TX *REC_TY)
     k_recon_tpp(const T *__restrict__ q, const T *__restrict__ gext, const T *__restrict__ w1g,
-                const T *__restrict__ Xg, const T *__restrict__ src8, T *__restrict__ ep,
-                T *__restrict__ sb, int N, int ne, T omega, FCoef<T> fc) {
+                const T *__restrict__ Xg, const T *__restrict__ t1w, const T *__restrict__ src8,
+                T *__restrict__ ep, T *__restrict__ sb, int N, int ne, T omega, FCoef<T> fc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   recon_tpp_tile<T, K, REC_TX, REC_TY>(smem_raw, blockIdx.z, blockIdx.x * REC_TX, blockIdx.y * REC_TY, q, gext, w1g,
-                                       Xg, src8, ep, sb, N, ne, omega, fc);
+                                       Xg, t1w, src8, ep, sb, N, ne, omega, fc);
 }
 
 // ---------------------------------------------------------------------------------

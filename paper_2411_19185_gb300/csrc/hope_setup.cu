@@ -61,6 +61,7 @@ __global__ void k_setup_grid(int N, int me, double radius, const double *__restr
       // source polynomials with the weight folded in (eqs. 2.2, 2.3 times W_gh 2/delta^2):
       //   a1 = (c1 q1 + c2 q2) q1/q0 + os (e1 q1 + e2 q2)
       //   a2 = (c3 q1 + c4 q2) q2/q0 + os (e3 q1 + e4 q2),  os = Omega sin(lat) delta
+      if (!src8) continue;
       T *o = src8 + r * 8;
       o[0] = (T)(-tw * X * Y * Y);
       o[1] = (T)(tw * Y * (1.0 + Y * Y));
@@ -130,7 +131,10 @@ int setup_grid_tables(hope_ctx *ctx, Grid &gr, const std::vector<double> &nodes,
   if (cudaMalloc(&gr.Xg, es * N * me) != cudaSuccess) return HOPE_ENOMEM;
   if (cudaMalloc(&gr.t1w, es * (size_t)N * N * me * me) != cudaSuccess) return HOPE_ENOMEM;
   if (cudaMalloc(&gr.mx, es * (size_t)(N + 1) * N * me * 5) != cudaSuccess) return HOPE_ENOMEM;
-  if (cudaMalloc(&gr.src8, es * (size_t)N * N * me * me * 8) != cudaSuccess) return HOPE_ENOMEM;
+  // the tabulated source polynomials serve only the FP64 TPP reconstruction
+  if (ctx->prec == HOPE_FP64 && ctx->scheme == HOPE_TPP &&
+      cudaMalloc(&gr.src8, es * (size_t)N * N * me * me * 8) != cudaSuccess)
+    return HOPE_ENOMEM;
   if (ctx->prec == HOPE_FP64)
     k_setup_grid<double><<<256, 256>>>(N, me, ctx->radius, d_nw, (double *)gr.Xg, (double *)gr.t1w,
                                        (double *)gr.mx, (double *)gr.src8);

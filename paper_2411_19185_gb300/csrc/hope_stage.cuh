@@ -121,7 +121,7 @@ inline int stage_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *q0, T *out, 
   if (ctx->scheme == HOPE_TPP) {
     size_t smem = recon_smem_bytes<T, K>();
     k_recon_tpp<T, K><<<grid, REC_TX * REC_TY, smem, st>>>(qs, (const T *)g.gext, (const T *)ctx->w1,
-                                                          (const T *)g.Xg, (const T *)g.src8, (T *)g.ep,
+                                                          (const T *)g.Xg, (const T *)g.t1w, (const T *)g.src8, (T *)g.ep,
                                                           (T *)g.sb, N, ne, (T)ctx->omega, fcoef<T>(ctx));
   } else {
     int rc = launch_recon_weno<T, K>(ctx, g, qs, st);
@@ -200,7 +200,7 @@ inline int stage_vjp_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *lamL, co
   dim3 grid((N + REC_TX - 1) / REC_TX, (N + REC_TY - 1) / REC_TY, 6);
   if (ctx->scheme == HOPE_TPP) {
     k_recon_tpp<T, K><<<grid, REC_TX * REC_TY, recon_smem_bytes<T, K>(), st>>>(
-        qs, (const T *)g.gext, (const T *)ctx->w1, (const T *)g.Xg, (const T *)g.src8, (T *)g.ep, (T *)g.sb, N, ne,
+        qs, (const T *)g.gext, (const T *)ctx->w1, (const T *)g.Xg, (const T *)g.t1w, (const T *)g.src8, (T *)g.ep, (T *)g.sb, N, ne,
         (T)ctx->omega, fcoef<T>(ctx));
   } else {
     int rc = launch_recon_weno<T, K>(ctx, g, qs, st);
