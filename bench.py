@@ -136,19 +136,47 @@ def _time_steps(s, q, dt, n, stream):
     return e0.elapsed_time(e1) / n
 
 
+def _run(s, q, dt, n, stream):
+    """CUDA-event milliseconds of one n-step run on `stream` (graphs captured beforehand
+    by the caller's warm-up)."""
+    import torch
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(q, dt, n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def _rel(a, b):
+    import torch
+    return float(torch.linalg.norm((a - b).double()) / torch.linalg.norm(b.double()))
+
+
 def measure_forms(hp, stream):
-    """The precision, differentiation and batching forms on the same box (short runs;
-    throughput in cell-stage updates/s)."""
+    """The precision, differentiation and batching forms on the same box, each at the length
+    its workload states, with its error (throughput in cell-stage updates/s)."""
     import torch
     from synth import bump_centres, noise_field
     out = {}
     fp32_peak = hp.measure_fma_peak(hp.HOPE_FP32)
     out["fp32_fma_peak_tflops"] = fp32_peak / 1e12
-    # precision form on the headline workload: FP32 bulk path
-    s = hp.Sphere(N_CELLS, ORDER, hp.HOPE_TPP, hp.HOPE_FP32, coriolis_tilt=ALPHA)
-    q = s.geostrophic(ALPHA)
-    ms = _time_steps(s, q, DT, 100, stream)
     cells = 6 * N_CELLS * N_CELLS
+    day = int(round(86400.0 / DT))
+    # precision form on the headline workload: FP32 bulk path, one day against FP64
+    s64 = hp.Sphere(N_CELLS, ORDER, hp.HOPE_TPP, hp.HOPE_FP64, coriolis_tilt=ALPHA)
+    s = hp.Sphere(N_CELLS, ORDER, hp.HOPE_TPP, hp.HOPE_FP32, coriolis_tilt=ALPHA)
+    qa = s64.geostrophic(ALPHA)
+    q64, q32 = qa.clone(), qa.float().contiguous()
+    m0 = s.mass(q32)
+    with torch.cuda.stream(stream):
+        s64.step(q64, DT, day)
+        s.step(q32, DT, day)
+    torch.cuda.synchronize()
+    q = q32.clone()
+    ms = _time_steps(s, q, DT, 100, stream)
     s.set_profiling(True)
     with torch.cuda.stream(stream):
         s.step(q, DT)
@@ -160,41 +188,73 @@ def measure_forms(hp, stream):
     fl = recon_flops_per_launch(N_CELLS, ORDER)
     out["tpp11_c90_fp32"] = {"value": cells * 3 / (ms * 1e-3), "ms_per_step": ms,
                              "recon_ms": float(np.mean(rec)),
-                             "recon_frac_of_fp32_peak": fl / (np.mean(rec) * 1e-3) / fp32_peak}
-    # precision form, discontinuous flow: WENO9 dam break (2:1), C90, FP64 and FP32
-    for name, P in (("weno9_c90_dam_fp64", hp.HOPE_FP64), ("weno9_c90_dam_fp32", hp.HOPE_FP32)):
-        s = hp.Sphere(N_CELLS, 9, hp.HOPE_WENO2D, P, omega=0.0)
-        q = s.dam_break(h_in=10.0, h_out=5.0)
-        n = 6 if P == hp.HOPE_FP64 else 30
-        ms = _time_steps(s, q, 300.0, n, stream)
-        out[name] = {"value": cells * 3 / (ms * 1e-3), "ms_per_step": ms}
-    # differentiation form: C180 WENO5, geostrophic + 16 bumps, forward and forward+adjoint
-    cen = bump_centres(16, 0)
+                             "recon_frac_of_fp32_peak": fl / (np.mean(rec) * 1e-3) / fp32_peak,
+                             "days": day * DT / 86400.0,
+                             "rel_l2_h_vs_fp64": _rel(q32[0], q64[0]),
+                             "rel_l2_h_vs_analytic": _rel(q32[0], qa[0]),
+                             "fp64_rel_l2_h_vs_analytic": _rel(q64[0], qa[0]),
+                             "mass_drift": (s.mass(q32) - m0) / m0,
+                             "status": s.status() | s64.status()}
+    del s64, s, q64, q32, q, qa
+    # precision form, discontinuous flow: WENO9 dam break (2:1), C90, two days; FP64 with
+    # epsilon 1e-40 and with 1e-12 (the FP32 epsilon: same scheme, arithmetic error alone)
+    nd = 2 * day
+    runs = {}
+    for name, P, eps in (("fp64", hp.HOPE_FP64, 1e-40), ("fp64_eps12", hp.HOPE_FP64, 1e-12),
+                         ("fp32", hp.HOPE_FP32, 1e-12)):
+        sw = hp.Sphere(N_CELLS, 9, hp.HOPE_WENO2D, P, omega=0.0, weno_eps=eps)
+        qw = sw.dam_break(h_in=10.0, h_out=5.0)
+        m0 = sw.mass(qw)
+        warm = qw.clone()
+        with torch.cuda.stream(stream):
+            sw.step(warm, 300.0, 1)
+        ms_run = _run(sw, qw, 300.0, nd, stream)
+        runs[name] = (qw, ms_run / nd, (sw.mass(qw) - m0) / m0, sw.status())
+        del sw
+    h64, h64b, h32 = runs["fp64"][0][0], runs["fp64_eps12"][0][0], runs["fp32"][0][0]
+    for name in ("fp64", "fp32"):
+        qw, msr, drift, st = runs[name]
+        out["weno9_c90_dam_" + name] = {"value": cells * 3 / (msr * 1e-3), "ms_per_step": msr,
+                                        "days": nd * 300.0 / 86400.0, "mass_drift": drift, "status": st}
+    out["weno9_c90_dam_fp32"].update({"rel_l2_h_vs_fp64": _rel(h32, h64),
+                                      "rel_l2_h_vs_fp64_same_eps": _rel(h32, h64b),
+                                      "rel_l2_h_fp64_eps_1e-12_vs_1e-40": _rel(h64b, h64)})
+    del runs, h64, h64b, h32
+    # differentiation form: C180 WENO5, geostrophic + 16 bumps of 50 m, 50 steps of 150 s
+    # with recompute from checkpoints every 10 steps; loss 0.5 |h_T - h_target|^2
+    cen, cen_t = bump_centres(16, 0), bump_centres(16, 1)
+    nsteps, every = 50, 10
+    grads = {}
     for name, P in (("adjoint_c180_weno5_fp64", hp.HOPE_FP64), ("adjoint_c180_weno5_fp32", hp.HOPE_FP32)):
         s = hp.Sphere(180, 5, hp.HOPE_WENO2D, P)
         q0 = s.bumps(cen)
-        target = q0[0].clone()
-        nsteps = 10
+        target = s.bumps(cen_t)[0].clone()
+        times = []
         with torch.cuda.stream(stream):
-            x = q0.clone().requires_grad_(True)
-            qT = s.rollout(x, 150.0, nsteps, checkpoint_every=10)
-            loss = 0.5 * ((qT[0] - target) ** 2).sum()
-            loss.backward()
-            torch.cuda.synchronize()
-            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-            x = q0.clone().requires_grad_(True)
-            e[0].record(stream)
-            qT = s.rollout(x, 150.0, nsteps, checkpoint_every=10)
-            e[1].record(stream)
-            loss = 0.5 * ((qT[0] - target) ** 2).sum()
-            loss.backward()
-            e[2].record(stream)
-            torch.cuda.synchronize()
-        fwd, bwd = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+            for rep in range(2):  # the first pass captures the step graphs
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                x = q0.clone().requires_grad_(True)
+                torch.cuda.synchronize()
+                e[0].record(stream)
+                qT = s.rollout(x, 150.0, nsteps, checkpoint_every=every)
+                e[1].record(stream)
+                loss = 0.5 * ((qT[0] - target) ** 2).sum()
+                loss.backward()
+                e[2].record(stream)
+                torch.cuda.synchronize()
+                times.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])))
+        fwd, bwd = times[-1]
+        grads[name] = x.grad.double()
         c180 = 6 * 180 * 180 * 3 * nsteps
         out[name] = {"forward": c180 / (fwd * 1e-3), "forward_plus_adjoint": c180 / ((fwd + bwd) * 1e-3),
-                     "steps": nsteps, "checkpoint_every": 10, "fwd_ms": fwd, "adjoint_ms": bwd}
-    # batching form: 64 members (32 x C48, 24 x C96, 8 x C192), TPP7, FP32, RH + 1% noise
+                     "steps": nsteps, "checkpoint_every": every, "fwd_ms": fwd, "adjoint_ms": bwd,
+                     "status": s.status()}
+        del s
+    out["adjoint_c180_weno5_fp32"]["rel_l2_grad_vs_fp64"] = _rel(grads["adjoint_c180_weno5_fp32"],
+                                                                 grads["adjoint_c180_weno5_fp64"])
+    del grads
+    # batching form: 64 members (32 x C48, 24 x C96, 8 x C192), TPP7, FP32, RH + 1% noise;
+    # one simulated day of 45 s steps, then the adjoint of the last 20 steps
     members = [48] * 32 + [96] * 24 + [192] * 8
     ens = hp.Sphere(members, 7, hp.HOPE_TPP, hp.HOPE_FP32)
     q = ens.empty()
@@ -204,24 +264,34 @@ def measure_forms(hp, stream):
             if Nm == N:
                 xi = torch.from_numpy(noise_field((6, N, N), 0, member=m)).to("cuda", torch.float32)
                 ens.member(q, m).copy_(base * (1 + 0.01 * xi)[None])
-    ms = _time_steps(ens, q, 45.0, 20, stream)
+    dte, nday, nadj = 45.0, int(round(86400.0 / 45.0)), 20
+    m0 = ens.mass(q)
+    warm = q.clone()
+    ms = _time_steps(ens, warm, dte, 20, stream)
+    day_ms = _run(ens, q, dte, nday - nadj, stream)
     total = sum(6 * n * n for n in members)
-    lam = torch.ones_like(q)
     with torch.cuda.stream(stream):
-        out_l = torch.empty_like(q)
-        ens.step_vjp(q, lam, 45.0, out=out_l)
+        target = q[:].clone()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        x = q.clone().requires_grad_(True)
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(5):
-            ens.step_vjp(q, lam, 45.0, out=out_l)
-        e1.record(stream)
+        e[0].record(stream)
+        qT = ens.rollout(x, dte, nadj, checkpoint_every=10)
+        e[1].record(stream)
+        loss = 0.5 * ((qT - target) ** 2).sum()
+        loss.backward()
+        e[2].record(stream)
         torch.cuda.synchronize()
-    adj_ms = e0.elapsed_time(e1) / 5
+    fwd20, adj20 = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    m1 = ens.mass(qT.detach())
     out["ensemble64_tpp7_fp32"] = {"value": total * 3 / (ms * 1e-3), "ms_per_step": ms, "cells": total,
                                    "launches_per_stage": ens.launches_per_stage(),
-                                   "step_adjoint_ms": adj_ms,
-                                   "forward_plus_adjoint": total * 3 / ((ms + adj_ms) * 1e-3)}
+                                   "day_s": (day_ms + fwd20) * 1e-3, "steps": nday,
+                                   "day_value": total * 3 * nday / ((day_ms + fwd20) * 1e-3),
+                                   "adjoint_steps": nadj, "adjoint_ms": adj20,
+                                   "forward_plus_adjoint": total * 3 * nadj / ((fwd20 + adj20) * 1e-3),
+                                   "max_member_mass_drift": max(abs(b - a) / a for a, b in zip(m0, m1)),
+                                   "status": ens.status()}
     return out
 
 

@@ -238,6 +238,22 @@ int hope_status(hope_t ctx, unsigned *device_status);
 int hope_autotune(hope_t ctx, int reps, float *ms_out, int *tx, int *ty, int *grid);
 
 /*
+ * Tile shape of the per-kernel TPP reconstruction (single spheres; Section 4 describes the
+ * reconstruction, the tiling is this library's).  One block reconstructs tx x ty cells of
+ * one panel: it stages the tile with its (k-1)/2 halo in shared memory, runs the x-pass
+ * over the tile's extended rows and one thread per cell runs the y-pass and the sources.
+ * hope_init_grid picks the shape: for FP64 the one that minimises a model of the FP64-pipe
+ * time of the most loaded SM (tiles of 64..512 cells), for FP32 16 x 8.  The results do
+ * not depend on the shape (every point value is the same sum in the same order).
+ * hope_set_recon_tile overrides it (1 <= tx*ty <= 512 and the tile's shared memory,
+ * 8 (FP64) or 4 (FP32) bytes x (3 (ty+k-1)(tx+k-1) + 3 ((k+1)/2+2)(ty+k-1) tx + ((k+1)/2+2) k),
+ * within the device's per-block limit; else HOPE_EINVAL) and drops the captured step graphs;
+ * HOPE_EINVAL for WENO2D contexts.  hope_recon_tile reads the current shape.
+ */
+int hope_set_recon_tile(hope_t ctx, int tx, int ty);
+int hope_recon_tile(hope_t ctx, int *tx, int *ty);
+
+/*
  * Failure-path hook for tests: HOPE_INJECT_BARRIER_TIMEOUT makes the next persistent stage
  * launch of an ensemble expect one block more at its grid barriers than it launches, so
  * no block is released; every block gives up after the bounded wait (about one second),

@@ -21,7 +21,7 @@ EXPORTED = [
     "hope_step", "hope_step_ssprk3", "hope_step_host", "hope_tendency_vjp", "hope_step_vjp",
     "hope_total_mass", "hope_status", "hope_ghost_nnz", "hope_launches_per_stage", "hope_strerror",
     "hope_last_error_message", "hope_measure_fma_peak", "hope_set_profiling", "hope_kernel_times",
-    "hope_total_mass_noalloc", "hope_autotune", "hope_inject_fault",
+    "hope_total_mass_noalloc", "hope_autotune", "hope_inject_fault", "hope_set_recon_tile", "hope_recon_tile",
 ]
 
 
@@ -80,6 +80,8 @@ def load():
         "hope_autotune": (i, [vp, i, P(ctypes.c_float), P(i), P(i), P(i)]),
         "hope_inject_fault": (i, [vp, i]),
         "hope_kernel_times": (i, [vp, P(ctypes.c_float), i, P(i)]),
+        "hope_set_recon_tile": (i, [vp, i, i]),
+        "hope_recon_tile": (i, [vp, P(i), P(i)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -17,24 +17,25 @@
 
 namespace hope {
 
-// LMARS flux and its vector-Jacobian product at one edge point (same arithmetic as lmars()).
+// LMARS flux and its vector-Jacobian product at one edge point (same arithmetic as lmars():
+// interface velocity 1/2 (uL + uR) - (sR - sL), s = sqrt(phi)).
 template <typename T>
 __device__ __forceinline__ void lmars_vjp(const T qL[3], const T qR[3], const T *m5, int dir, const T lF[3],
                                           T lqL[3], T lqR[3]) {
   const T isg = m5[0], s11 = m5[1], is11 = m5[2], pn = m5[3], pc = m5[4];
-  const int n = 1 + dir;
+  const T qnL = dir ? qL[2] : qL[1], qnR = dir ? qR[2] : qR[1];
   const T phL = qL[0] * isg, phR = qR[0] * isg;
-  const T rL = rcp(qL[0]), rR = rcp(qR[0]);
-  const T uL = qL[n] * rL * is11, uR = qR[n] * rR * is11;
+  const T rLR = rcp(qL[0] * qR[0]);
+  const T rL = qR[0] * rLR, rR = qL[0] * rLR;
+  const T uL = qnL * rL * is11, uR = qnR * rR * is11;
   const T sL = sqrt(phL), sR = sqrt(phR);
   const T c = T(0.5) * (sL + sR);
-  const T ic = rcp(c);
-  const T ms = T(0.5) * (uL + uR - (phR - phL) * ic);
+  const T ms = T(0.5) * (uL + uR) - (sR - sL);
   const T ph = T(0.5) * (phL + phR - c * (uR - uL));
   const T m = ms * s11;
   const T am = fabs(m);
   const T sg = m > T(0) ? T(1) : (m < T(0) ? T(-1) : T(0));
-  // F_v = 1/2 (m (qL + qR) - |m| (qR - qL)) + P
+  // F_v = 1/2 (m (qL + qR) - |m| (qR - qL)) + P_v,  P_1 = a1 ph^2, P_2 = a2 ph^2
   T lm = 0;
 #pragma unroll
   for (int v = 0; v < 3; ++v) {
@@ -42,24 +43,26 @@ __device__ __forceinline__ void lmars_vjp(const T qL[3], const T qR[3], const T 
     lqR[v] = T(0.5) * (m - am) * lF[v];
     lm += T(0.5) * ((qL[v] + qR[v]) - sg * (qR[v] - qL[v])) * lF[v];
   }
-  const T lph = T(2) * ph * (pn * lF[1 + dir] + pc * lF[2 - dir]);
+  const T a1 = dir ? pc : pn, a2 = dir ? pn : pc;
+  const T lph = T(2) * ph * (a1 * lF[1] + a2 * lF[2]);
   const T lms = lm * s11;
   T luL = T(0.5) * lms, luR = T(0.5) * lms;
-  T lphL = T(0.5) * ic * lms, lphR = -T(0.5) * ic * lms;
-  const T lic = -T(0.5) * (phR - phL) * lms;
-  lphL += T(0.5) * lph;
-  lphR += T(0.5) * lph;
-  T lc = -T(0.5) * (uR - uL) * lph;
+  T lsL = lms, lsR = -lms;
+  T lphL = T(0.5) * lph, lphR = T(0.5) * lph;
+  const T lc = -T(0.5) * (uR - uL) * lph;
   luR -= T(0.5) * c * lph;
   luL += T(0.5) * c * lph;
-  lc -= ic * ic * lic;
-  const T lsL = T(0.5) * lc, lsR = T(0.5) * lc;
+  lsL += T(0.5) * lc;
+  lsR += T(0.5) * lc;
   lphL += lsL / (T(2) * sL);
   lphR += lsR / (T(2) * sR);
-  lqL[n] += rL * is11 * luL;
-  lqR[n] += rR * is11 * luR;
-  lqL[0] += -rL * rL * (qL[n] * is11 * luL) + isg * lphL;
-  lqR[0] += -rR * rR * (qR[n] * is11 * luR) + isg * lphR;
+  const T dL = rL * is11 * luL, dR = rR * is11 * luR;
+  lqL[1] += dir ? T(0) : dL;
+  lqL[2] += dir ? dL : T(0);
+  lqR[1] += dir ? T(0) : dR;
+  lqR[2] += dir ? dR : T(0);
+  lqL[0] += -rL * (qnL * rL * is11 * luL) + isg * lphL;
+  lqR[0] += -rR * (qnR * rR * is11 * luR) + isg * lphR;
 }
 
 // ---------------------------------------------------------------------------------

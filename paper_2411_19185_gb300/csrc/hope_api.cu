@@ -6,7 +6,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
+#include <queue>
 #include <string>
 #include <vector>
 
@@ -32,6 +34,67 @@ __global__ void k_mass_final(const double *__restrict__ part, int nparts, double
 static stage_fn pick_stage(const hope_ctx *ctx) { return stage_entry(ctx->prec, ctx->k); }
 static vjp_fn pick_vjp(const hope_ctx *ctx) { return vjp_entry(ctx->prec, ctx->k); }
 static int set_attrs(const hope_ctx *ctx) { return smem_attr_entry(ctx->prec, ctx->k); }
+
+// Modelled FP64-pipe time (in warp instructions of the most loaded SM) of the TPP
+// reconstruction with TX x TY tiles on an N x N panel: a tile's x-pass issues NPOS*K FMAs
+// per (variable, extended row, valid column) item, its cell phase a fixed count per
+// 32 valid cells (the edge- and cell-point y-pass and the sources), plus its loads; tiles
+// go in launch order to the least loaded SM.
+static double recon_tile_cost(int N, int K, int TX, int TY, int nsm) {
+  const int H = (K - 1) / 2, me = (K + 1) / 2, npos = me + 2;
+  const int threads = (TX * TY + 31) / 32 * 32;
+  const double per_item = (double)npos * K;
+  const double per_warp_cells = (double)(4 * me + me * me) * 3 * K + (double)me * me * 22;
+  const int nbx = (N + TX - 1) / TX, nby = (N + TY - 1) / TY;
+  std::vector<double> load(nsm, 0.0);
+  std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>, std::greater<>> heap;
+  for (int s = 0; s < nsm; ++s) heap.push({0.0, s});
+  double worst = 0.0;
+  for (int p = 0; p < 6; ++p)
+    for (int by = 0; by < nby; ++by)
+      for (int bx = 0; bx < nbx; ++bx) {
+        const int vx = std::min(TX, N - bx * TX), vy = std::min(TY, N - by * TY);
+        const int items = 3 * (vy + 2 * H) * vx;
+        const int loads = 3 * (vy + 2 * H) * (vx + 2 * H);
+        const double xw = (double)(items / threads) * (threads / 32) + (items % threads + 31) / 32;
+        const double cost = xw * per_item + ((vx * vy + 31) / 32) * per_warp_cells +
+                            50.0 * ((loads + threads - 1) / threads);
+        auto top = heap.top();
+        heap.pop();
+        top.first += cost;
+        worst = std::max(worst, top.first);
+        heap.push(top);
+      }
+  return worst;
+}
+
+// Tile shape of the per-kernel TPP reconstruction.  The FP64 kernel is bound by the FP64
+// pipe, so its shape minimises recon_tile_cost over tiles of 64..512 cells that fit the
+// shared memory; the FP32 kernel is latency-bound at these sizes and keeps 16 x 8.
+static void choose_recon_tile(const hope_ctx *ctx, Grid &g) {
+  g.rtx = REC_TX;
+  g.rty = REC_TY;
+  if (ctx->scheme != HOPE_TPP || ctx->prec != HOPE_FP64) return;
+  int nsm = 0, optin = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+  if (nsm < 1) return;
+  const int K = ctx->k;
+  const int me = (K + 1) / 2, npos = me + 2;
+  double best = recon_tile_cost(g.N, K, g.rtx, g.rty, nsm);
+  for (int TY = 4; TY <= 32; ++TY)
+    for (int TX = 8; TX <= 32; ++TX) {
+      if (TX * TY < 64 || TX * TY > REC_MAX_THREADS) continue;
+      const size_t smem = sizeof(double) * (3 * (TY + K - 1) * (TX + K - 1) + 3 * npos * (TY + K - 1) * TX + npos * K);
+      if (smem > (size_t)optin) continue;
+      const double c = recon_tile_cost(g.N, K, TX, TY, nsm);
+      if (c < best * 0.999) {
+        best = c;
+        g.rtx = TX;
+        g.rty = TY;
+      }
+    }
+}
 
 static int ensure_adjoint_scratch(hope_ctx *ctx) {
   for (auto &g : ctx->grids) {
@@ -353,6 +416,8 @@ static int init_impl(int n_members, const int *Ns, int order, int scheme, const 
   }
   ctx->eps = prm.weno_eps != 0.0 ? prm.weno_eps : (prm.precision == HOPE_FP64 ? 1e-40 : 1e-12);
   cudaGetDevice(&ctx->device);
+  cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (ctx->nsm < 1) ctx->nsm = 1;
   int rc;
   std::vector<double> nodes, weights;
 #define TRY(x)          \
@@ -453,6 +518,7 @@ static int init_impl(int n_members, const int *Ns, int order, int scheme, const 
     TRY(alloc(&gr.fx, es * 3 * 6 * N * (N + 1)));
     TRY(alloc(&gr.fy, es * 3 * 6 * (N + 1) * N));
     TRY(alloc(&gr.sb, es * 2 * 6 * N * N));
+    choose_recon_tile(ctx, gr);
   }
   ctx->total = off;
   const size_t es = ctx->esize;
@@ -748,6 +814,39 @@ int hope_step_vjp(hope_t ctx, const void *qn_dev, const void *lam_np1_dev, void 
   c1.z = ctx->lam_a; c1.d = 1.0;
   c1.c = dt;
   return v(ctx, qn_dev, ctx->lam_a, lam_n_dev, c1, st);
+}
+
+static void drop_graphs(hope_ctx *ctx) {
+  for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+  ctx->graphs.clear();
+}
+
+int hope_set_recon_tile(hope_t ctx, int tx, int ty) {
+  if (!ctx || ctx->scheme != HOPE_TPP || tx < 1 || ty < 1 || tx * ty > REC_MAX_THREADS) {
+    set_error("hope_set_recon_tile: needs a TPP context and 1 <= tx*ty <= 512");
+    return HOPE_EINVAL;
+  }
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+  const int K = ctx->k, npos = (K + 1) / 2 + 2;
+  const size_t smem = (size_t)ctx->esize * (3 * (ty + K - 1) * (tx + K - 1) + 3 * npos * (ty + K - 1) * tx + npos * K);
+  if (smem > (size_t)optin) {
+    set_error("hope_set_recon_tile: the tile's shared memory exceeds the per-block limit");
+    return HOPE_EINVAL;
+  }
+  for (auto &g : ctx->grids) {
+    g.rtx = tx;
+    g.rty = ty;
+  }
+  drop_graphs(ctx);
+  return HOPE_OK;
+}
+
+int hope_recon_tile(hope_t ctx, int *tx, int *ty) {
+  if (!ctx || !tx || !ty) return HOPE_EINVAL;
+  *tx = ctx->grids[0].rtx;
+  *ty = ctx->grids[0].rty;
+  return HOPE_OK;
 }
 
 int hope_autotune(hope_t ctx, int reps, float *ms_out, int *tx, int *ty, int *grid) {

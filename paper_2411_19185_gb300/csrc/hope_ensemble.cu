@@ -39,7 +39,7 @@ struct StageArgs {
   T *out;
   const T *q0l, *qsl;
   T *outl;
-  T a, b, c;
+  T a, b, c, alo, blo, clo;  // stage coefficients and their rounding residuals
   int mode;
   T omega;
   FCoef<T> fc;
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(TX *TY)
     const int p = local / (m.tiles_x * m.tiles_y);
     const int rem = local - p * m.tiles_x * m.tiles_y;
     const int ty = rem / m.tiles_x, tx = rem - ty * m.tiles_x;
-    recon_tpp_tile<T, K, TX, TY>(smem_raw, p, tx * TX, ty * TY, sa.qs + m.off, m.gext, sa.w1, m.Xg, m.t1w, m.src8, m.ep,
+    recon_tpp_tile<T, K>(smem_raw, p, tx * TX, ty * TY, TX, TY, sa.qs + m.off, m.gext, sa.w1, m.Xg, m.t1w, m.src8, m.ep,
                                  m.sb, m.N, m.ne, sa.omega, sa.fc);
   }
   if (!grid_sync(bar, status, inject)) return;
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(TX *TY)
     const MemberDev<T> &m = mem[find_member(mem, nmem, it, 3)];
     auto off = [&](const T *p) -> const T * { return p ? p + m.off : nullptr; };
     update_cell(it - m.b_cell, m.fx, m.fy, m.sb, off(sa.q0), sa.qs + m.off, sa.out + m.off, m.N,
-                (T)(2.0 * m.N / 3.14159265358979323846), sa.mode, sa.a, sa.b, sa.c, off(sa.q0l), off(sa.qsl),
+                (T)(2.0 * m.N / 3.14159265358979323846), sa.mode, sa.a, sa.b, sa.c, sa.alo, sa.blo, sa.clo, off(sa.q0l), off(sa.qsl),
                 sa.outl ? sa.outl + m.off : nullptr, status);
   }
 }
@@ -266,6 +266,9 @@ static int stage_persistent_t(hope_ctx *ctx, const void *qs, const void *q0, voi
   sa.a = (T)a;
   sa.b = (T)b;
   sa.c = (T)c;
+  sa.alo = coef_lo<T>(a);
+  sa.blo = coef_lo<T>(b);
+  sa.clo = coef_lo<T>(c);
   sa.mode = mode;
   sa.omega = (T)ctx->omega;
   for (int t = 0; t < 18; ++t) sa.fc.c[t] = (T)ctx->fcoef[t];

@@ -26,6 +26,8 @@ struct CubeEdge {
 // Device tables and scratch of one sphere (one member of an ensemble).
 struct Grid {
   int N = 0, ne = 0;
+  int rtx = 16, rty = 8;  // TPP reconstruction tile (cells) of the per-kernel path
+  int ghost_grid = 0, flux_grid = 0, flux_tpb = 0;  // launch shapes, set on first use
   size_t off = 0;   // element offset of this member in ensemble states
   bool owns_tables = true;  // false: tables shared with an earlier member of equal N
   // tables (element type = context precision)
@@ -85,6 +87,7 @@ struct hope_ctx {
   double radius = 0, gravity = 0, omega = 0, eps = 0, tilt = 0;
   double fcoef[18] = {0};  // per panel (c0, c1, c2): f*delta/(2 Omega) = c0 + c1 X + c2 Y
   int device = 0;
+  int nsm = 1;  // streaming multiprocessors of the device (launch balancing)
   int esize = 8;
   size_t total = 0;  // elements of one (ensemble) state
   std::vector<hope::Grid> grids;

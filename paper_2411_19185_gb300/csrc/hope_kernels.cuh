@@ -54,6 +54,20 @@ struct FCoef {
 // ---------------------------------------------------------------------------------
 // Ghost fill: one warp per ghost cell, lanes stride over the row's nonzeros.
 // ---------------------------------------------------------------------------------
+// FP64 -> FP32 by truncating the significand with integer operations, so the FP32 tail
+// of the ghost rows costs no FP64-pipe conversion.  Values outside the normal FP32 range
+// become 0 (below it) or +-inf (above it, NaN included); the tail's weights are below
+// 1e-9 of their row's largest, so truncation (2^-23 relative) is far below FP64 rounding.
+__device__ __forceinline__ float f64_to_f32_trunc(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const int e = (int)((hi >> 20) & 0x7FFu) - (1023 - 127);
+  const unsigned sign = hi & 0x80000000u;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
+  return __uint_as_float(sign | ((unsigned)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+}
+
 // One ghost row: FP64/FP32 head sum in the context precision, plus (FP64 contexts) the
 // FP32 tail of negligible weights.
 template <typename T>
@@ -69,17 +83,18 @@ __device__ __forceinline__ void ghost_row(int row, int lane, const T *__restrict
     int c = gcol[t];
     const T *w = gval + (size_t)t * 5;
     T a0 = q[c], a1 = q[pn + c], a2 = q[2 * pn + c];
-    s0 += w[0] * a0;
-    s1 += w[1] * a1 + w[2] * a2;
-    s2 += w[3] * a1 + w[4] * a2;
+    s0 = fma(w[0], a0, s0);
+    s1 = fma(w[1], a1, fma(w[2], a2, s1));
+    s2 = fma(w[3], a1, fma(w[4], a2, s2));
   }
-  if (trow) {
+  if constexpr (sizeof(T) == 8) {
+    if (trow) {
     float f0 = 0.f, f1 = 0.f, f2 = 0.f;
     const int tb = trow[row], te = trow[row + 1];
     for (int t = tb + lane; t < te; t += 32) {
       int c = tcol[t];
       const float *w = tval + (size_t)t * 5;
-      float a0 = (float)q[c], a1 = (float)q[pn + c], a2 = (float)q[2 * pn + c];
+      float a0 = f64_to_f32_trunc(q[c]), a1 = f64_to_f32_trunc(q[pn + c]), a2 = f64_to_f32_trunc(q[2 * pn + c]);
       f0 = fmaf(w[0], a0, f0);
       f1 = fmaf(w[1], a1, fmaf(w[2], a2, f1));
       f2 = fmaf(w[3], a1, fmaf(w[4], a2, f2));
@@ -87,6 +102,7 @@ __device__ __forceinline__ void ghost_row(int row, int lane, const T *__restrict
     s0 += (T)f0;
     s1 += (T)f1;
     s2 += (T)f2;
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -108,9 +124,10 @@ __global__ void __launch_bounds__(256) k_ghost(const T *__restrict__ q, T *__res
                                                const T *__restrict__ gval, const int *__restrict__ gdst,
                                                const int *__restrict__ trow, const int *__restrict__ tcol,
                                                const float *__restrict__ tval, int rows, int N, int ne) {
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (warp >= rows) return;
-  ghost_row(warp, threadIdx.x & 31, q, gext, grow, gcol, gval, gdst, trow, tcol, tval, N, ne);
+  // grid of resident blocks; warps stride over the rows so every SM gets an equal share
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows; row += nwarps)
+    ghost_row(row, threadIdx.x & 31, q, gext, grow, gcol, gval, gdst, trow, tcol, tval, N, ne);
 }
 
 // ---------------------------------------------------------------------------------
@@ -158,30 +175,58 @@ __device__ __forceinline__ void load_tile(T *raw, const T *__restrict__ q, const
   }
 }
 
-// One tile of TX x TY cells of panel p with its first cell at (i0, j0); called by all
-// threads of a block of TX*TY threads; ends with a barrier so the shared memory can be
-// reused for the next tile.
-template <typename T, int K, int TX, int TY>
-__device__ __forceinline__ void recon_tpp_tile(unsigned char *smem_raw, int p, int i0, int j0,
-                                               const T *__restrict__ q, const T *__restrict__ gext,
+// Shared memory of one TPP reconstruction tile of TX x TY cells (runtime shape).
+template <typename T, int K>
+__host__ __device__ constexpr size_t recon_tile_smem_bytes(int TX, int TY) {
+  return sizeof(T) * (3 * (TY + K - 1) * (TX + K - 1) + 3 * ((K + 1) / 2 + 2) * (TY + K - 1) * TX + ((K + 1) / 2 + 2) * K);
+}
+
+// Largest thread count of a TPP reconstruction block (one thread per cell of the tile).
+constexpr int REC_MAX_THREADS = 512;
+
+// One tile of at most TX x TY cells of panel p with its first cell at (i0, j0); called by
+// all threads of a block of at least TX*TY threads; ends with a barrier so the shared
+// memory can be reused for the next tile.  Tiles cut by the panel's edge only load,
+// sweep and evaluate their vx x vy valid cells, and the cell phase packs those cells onto
+// the first vx*vy threads so the idle warps of a ragged tile issue nothing.
+template <typename T, int K>
+__device__ __forceinline__ void recon_tpp_tile(unsigned char *smem_raw, int p, int i0, int j0, const int TX,
+                                               const int TY, const T *__restrict__ q, const T *__restrict__ gext,
                                                const T *__restrict__ w1g, const T *__restrict__ Xg,
                                                const T *__restrict__ t1w, const T *__restrict__ src8,
                                                T *__restrict__ ep, T *__restrict__ sb, int N, int ne, T omega,
                                                const FCoef<T> &fc) {
-  using S = Tile<K, TX, TY>;
-  constexpr int ME = S::ME, NPOS = S::NPOS;
-  T *raw = reinterpret_cast<T *>(smem_raw);              // [3][RH][RW]
-  T *xs = raw + 3 * S::RH * S::RW;                        // [3][NPOS][RH][TX]
-  T *w1 = xs + 3 * NPOS * S::RH * TX;                     // [NPOS][K]
+  constexpr int H = (K - 1) / 2, ME = (K + 1) / 2, NPOS = ME + 2;
+  const int RW = TX + 2 * H, RH = TY + 2 * H;
+  const int vx = min(TX, N - i0), vy = min(TY, N - j0);
+  const int vw = vx + 2 * H, vh = vy + 2 * H;
+  T *raw = reinterpret_cast<T *>(smem_raw);  // [3][RH][RW]
+  T *xs = raw + 3 * RH * RW;                  // [3][NPOS][RH][TX]
+  T *w1 = xs + 3 * NPOS * RH * TX;            // [NPOS][K]
   for (int t = threadIdx.x; t < NPOS * K; t += blockDim.x) w1[t] = w1g[t];
-  load_tile<T, K, TX, TY>(raw, q, gext, p, i0, j0, N, ne);
+  {
+    // extended tile of the 3 variables: interior cells from q, ring cells from gext
+    const size_t pn = (size_t)6 * N * N, pe = (size_t)6 * ne * ne;
+    for (int idx = threadIdx.x; idx < 3 * vh * vw; idx += blockDim.x) {
+      const int v = idx / (vh * vw);
+      const int rem = idx - v * vh * vw;
+      const int r = rem / vw, c = rem - r * vw;
+      const int i = i0 + c - H, j = j0 + r - H;
+      T val = T(0);
+      if (i >= 0 && i < N && j >= 0 && j < N)
+        val = q[v * pn + ((size_t)p * N + j) * N + i];
+      else if (i >= -H && i < N + H && j >= -H && j < N + H)
+        val = gext[v * pe + ((size_t)p * ne + (j + H)) * ne + (i + H)];
+      raw[(v * RH + r) * RW + c] = val;
+    }
+  }
   __syncthreads();
-  // x-pass: every row of the extended tile, every tile column, NPOS positions
-  for (int idx = threadIdx.x; idx < 3 * S::RH * TX; idx += blockDim.x) {
-    int v = idx / (S::RH * TX);
-    int rem = idx - v * S::RH * TX;
-    int r = rem / TX, c = rem - r * TX;
-    const T *row = raw + (v * S::RH + r) * S::RW + c;
+  // x-pass: every row of the extended tile, every valid tile column, NPOS positions
+  for (int idx = threadIdx.x; idx < 3 * vh * vx; idx += blockDim.x) {
+    const int v = idx / (vh * vx);
+    const int rem = idx - v * vh * vx;
+    const int r = rem / vx, c = rem - r * vx;
+    const T *row = raw + (v * RH + r) * RW + c;
     T a[K];
 #pragma unroll
     for (int b = 0; b < K; ++b) a[b] = row[b];
@@ -190,13 +235,13 @@ __device__ __forceinline__ void recon_tpp_tile(unsigned char *smem_raw, int p, i
       T s = 0;
 #pragma unroll
       for (int b = 0; b < K; ++b) s = fma(w1[t * K + b], a[b], s);
-      xs[((v * NPOS + t) * S::RH + r) * TX + c] = s;
+      xs[((v * NPOS + t) * RH + r) * TX + c] = s;
     }
   }
   __syncthreads();
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int i = i0 + tx, j = j0 + ty;
-  if (i < N && j < N) {
+  if ((int)threadIdx.x < vx * vy) {
+    const int ty = threadIdx.x / vx, tx = threadIdx.x - ty * vx;
+    const int i = i0 + tx, j = j0 + ty;
     const size_t pn = (size_t)6 * N * N;
     const size_t cell = ((size_t)p * N + j) * N + i;
     const T fc0 = fc.c[3 * p], fc1 = fc.c[3 * p + 1], fc2 = fc.c[3 * p + 2];
@@ -207,7 +252,7 @@ __device__ __forceinline__ void recon_tpp_tile(unsigned char *smem_raw, int p, i
 #pragma unroll
       for (int v = 0; v < 3; ++v)
 #pragma unroll
-        for (int b = 0; b < K; ++b) col[v][b] = xs[((v * NPOS + t) * S::RH + ty + b) * TX + tx];
+        for (int b = 0; b < K; ++b) col[v][b] = xs[((v * NPOS + t) * RH + ty + b) * TX + tx];
       if (t < 2) {
         // west (t = 0) / east (t = 1) edge points at the Gauss nodes in y
 #pragma unroll
@@ -272,14 +317,16 @@ __device__ __forceinline__ void recon_tpp_tile(unsigned char *smem_raw, int p, i
   __syncthreads();
 }
 
+// One block per tile of TX x TY cells (blockIdx.x, blockIdx.y: tile column and row,
+// blockIdx.z: panel); TX*TY <= blockDim.x <= REC_MAX_THREADS.
 template <typename T, int K>
-__global__ void __launch_bounds__(REC_TX *REC_TY)
+__global__ void __launch_bounds__(REC_MAX_THREADS)
     k_recon_tpp(const T *__restrict__ q, const T *__restrict__ gext, const T *__restrict__ w1g,
                 const T *__restrict__ Xg, const T *__restrict__ t1w, const T *__restrict__ src8,
-                T *__restrict__ ep, T *__restrict__ sb, int N, int ne, T omega, FCoef<T> fc) {
+                T *__restrict__ ep, T *__restrict__ sb, int N, int ne, int TX, int TY, T omega, FCoef<T> fc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  recon_tpp_tile<T, K, REC_TX, REC_TY>(smem_raw, blockIdx.z, blockIdx.x * REC_TX, blockIdx.y * REC_TY, q, gext, w1g,
-                                       Xg, t1w, src8, ep, sb, N, ne, omega, fc);
+  recon_tpp_tile<T, K>(smem_raw, blockIdx.z, blockIdx.x * TX, blockIdx.y * TY, TX, TY, q, gext, w1g, Xg, t1w, src8,
+                       ep, sb, N, ne, omega, fc);
 }
 
 // ---------------------------------------------------------------------------------
@@ -293,19 +340,22 @@ __device__ __forceinline__ void lmars(const T qL[3], const T qR[3], const T *m5,
   const T isg = m5[0], s11 = m5[1], is11 = m5[2], pn = m5[3], pc = m5[4];
   const T phL = qL[0] * isg, phR = qR[0] * isg;
   if (!(phL > T(0)) || !(phR > T(0))) atomicOr(status, HOPE_STATUS_NONPHYS_PHI);
-  const int n = 1 + dir;
+  // normal momentum component (selects, not a runtime index, keep the arrays in registers)
+  const T qnL = dir ? qL[2] : qL[1], qnR = dir ? qR[2] : qR[1];
   const T rLR = rcp(qL[0] * qR[0]);  // one reciprocal for both states
-  const T uL = qL[n] * (qR[0] * rLR) * is11, uR = qR[n] * (qL[0] * rLR) * is11;
-  const T c = T(0.5) * (sqrt(phL) + sqrt(phR));
-  const T ms = T(0.5) * (uL + uR - (phR - phL) * rcp(c));
+  const T uL = qnL * (qR[0] * rLR) * is11, uR = qnR * (qL[0] * rLR) * is11;
+  const T sL = sqrt(phL), sR = sqrt(phR);
+  const T c = T(0.5) * (sL + sR);
+  // (phR - phL) / (2 c) = sR - sL exactly, so the interface velocity needs no division
+  const T ms = T(0.5) * (uL + uR) - (sR - sL);
   const T ph = T(0.5) * (phL + phR - c * (uR - uL));
   const T m = ms * s11;
   const T am = fabs(m);
 #pragma unroll
   for (int v = 0; v < 3; ++v) F[v] = T(0.5) * (m * (qL[v] + qR[v]) - am * (qR[v] - qL[v]));
   const T p2 = ph * ph;
-  F[1 + dir] += pn * p2;
-  F[2 - dir] += pc * p2;
+  F[1] += (dir ? pc : pn) * p2;
+  F[2] += (dir ? pn : pc) * p2;
 }
 
 // ---------------------------------------------------------------------------------
@@ -432,9 +482,9 @@ __global__ void __launch_bounds__(256)
            const int *__restrict__ bedge, const T *__restrict__ bconv, T *__restrict__ fx,
            T *__restrict__ fy, int N, unsigned *status) {
   const long long n = 12LL * N * (N - 1) + 12LL * N;
-  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n) return;
-  flux_item<T, ME>(idx, ep, mx, gwg, bedge, bconv, fx, fy, N, status);
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x)
+    flux_item<T, ME>(idx, ep, mx, gwg, bedge, bconv, fx, fy, N, status);
 }
 
 // ---------------------------------------------------------------------------------
@@ -452,9 +502,18 @@ __device__ __forceinline__ void two_sum(T a, T b, T &s, T &e) {
   e = (a - (s - bp)) + (b - bp);
 }
 
+// Rounding residual of a stage coefficient in precision T (zero in FP64).
 template <typename T>
-__device__ __forceinline__ T combine(T a, T q0, T b, T qs, T c, T L, const T *q0l, const T *qsl, T *outl,
-                                     long long idx) {
+inline T coef_lo(double x) {
+  return (T)(x - (double)(T)x);
+}
+
+// The stage coefficients are split too (a = a + alo with alo the rounding residual of
+// the double coefficient): 1/3 and 2/3 round up in FP32, and without their residuals the
+// third SSP-RK3 stage would scale the state by 1 + 3e-8 every step.
+template <typename T>
+__device__ __forceinline__ T combine(T a, T q0, T b, T qs, T c, T L, T alo, T blo, T clo, const T *q0l,
+                                     const T *qsl, T *outl, long long idx) {
   if (q0l == nullptr) return a * q0 + b * qs + c * L;
   const T p1 = a * q0, e1 = fma(a, q0, -p1);
   const T p2 = b * qs, e2 = fma(b, qs, -p2);
@@ -462,7 +521,7 @@ __device__ __forceinline__ T combine(T a, T q0, T b, T qs, T c, T L, const T *q0
   T s, r1, s2, r2;
   two_sum(p1, p2, s, r1);
   two_sum(s, p3, s2, r2);
-  T lo = ((r1 + r2) + (e1 + e2 + e3)) + (a * q0l[idx] + b * qsl[idx]);
+  T lo = ((r1 + r2) + (e1 + e2 + e3)) + (a * q0l[idx] + b * qsl[idx]) + (alo * q0 + blo * qs + clo * L);
   T hi = s2 + lo;
   outl[idx] = lo - (hi - s2);
   return hi;
@@ -471,8 +530,8 @@ __device__ __forceinline__ T combine(T a, T q0, T b, T qs, T c, T L, const T *q0
 template <typename T>
 __device__ __forceinline__ void update_cell(long long cid, const T *__restrict__ fx, const T *__restrict__ fy,
                                             const T *__restrict__ sb, const T *q0, const T *qs, T *out, int N,
-                                            T inv_dx, int mode, T a, T b, T c, const T *q0l, const T *qsl, T *outl,
-                                            unsigned *status) {
+                                            T inv_dx, int mode, T a, T b, T c, T alo, T blo, T clo, const T *q0l,
+                                            const T *qsl, T *outl, unsigned *status) {
   const long long ncell = 6LL * N * N;
   const int i = (int)(cid % N);
   const long long pj = cid / N;  // p*N + j
@@ -493,7 +552,7 @@ __device__ __forceinline__ void update_cell(long long cid, const T *__restrict__
       r = L;
     } else {
       const long long idx = v * ncell + cid;
-      r = combine(a, q0[idx], b, qs[idx], c, L, q0l, qsl, outl, idx);
+      r = combine(a, q0[idx], b, qs[idx], c, L, alo, blo, clo, q0l, qsl, outl, idx);
     }
     bad |= !isfinite(r);
     out[v * ncell + cid] = r;
@@ -504,11 +563,11 @@ __device__ __forceinline__ void update_cell(long long cid, const T *__restrict__
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_update(const T *__restrict__ fx, const T *__restrict__ fy, const T *__restrict__ sb,
-             const T *q0, const T *qs, T *out, int N, T inv_dx, int mode, T a, T b, T c,
-             const T *q0l, const T *qsl, T *outl, unsigned *status) {
+             const T *q0, const T *qs, T *out, int N, T inv_dx, int mode, T a, T b, T c, T alo, T blo,
+             T clo, const T *q0l, const T *qsl, T *outl, unsigned *status) {
   long long cid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (cid >= 6LL * N * N) return;
-  update_cell(cid, fx, fy, sb, q0, qs, out, N, inv_dx, mode, a, b, c, q0l, qsl, outl, status);
+  update_cell(cid, fx, fy, sb, q0, qs, out, N, inv_dx, mode, a, b, c, alo, blo, clo, q0l, qsl, outl, status);
 }
 
 // ---------------------------------------------------------------------------------

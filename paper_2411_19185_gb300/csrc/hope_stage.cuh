@@ -23,6 +23,48 @@ namespace hope {
     }                                                                                    \
   } while (0)
 
+// Launch shape of a grid-strided kernel over n equal items: every block resident from
+// the start (at most nsm x the kernel's resident blocks per SM at that block size) and
+// every SM given the same number of items, so that an FP64-bound kernel neither ends with
+// some SMs running one block more than the others nor with a partial second wave.  Tries
+// 1, 2, ... items per thread and block sizes that are multiples of 32 up to max_tpb, and
+// keeps the shape that wastes the fewest thread slots.
+template <typename Kern>
+inline void balanced_grid(Kern kern, long long n, int nsm, int max_tpb, int *blocks, int *tpb) {
+  double best = -1.0;
+  *tpb = max_tpb;
+  *blocks = (int)((n + max_tpb - 1) / max_tpb);
+  for (int k = 1; k <= 4 && best < 0.97; ++k) {
+    const long long nt = (n + k - 1) / k;  // threads
+    for (int m = 1; m <= 32; ++m) {
+      const long long t = 32 * ((nt + 32LL * nsm * m - 1) / (32LL * nsm * m));
+      if (t > max_tpb) continue;
+      if (t < 64) break;
+      int resident = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, kern, (int)t, 0) != cudaSuccess) resident = 1;
+      if (m > resident) continue;
+      const long long b = (nt + t - 1) / t;
+      const double eff = (double)n / ((double)nsm * ((b + nsm - 1) / nsm) * t * k);
+      if (eff > best + 1e-3) {
+        best = eff;
+        *tpb = (int)t;
+        *blocks = (int)b;
+      }
+    }
+  }
+}
+
+// Resident-grid size of a row-strided kernel with 256-thread blocks.
+template <typename Kern>
+inline int resident_blocks(Kern kern, const hope_ctx *ctx, long long rows_x32) {
+  int resident = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, kern, 256, 0) != cudaSuccess || resident < 1)
+    resident = 1;
+  const long long need = (rows_x32 + 255) / 256;
+  const long long cap = (long long)resident * ctx->nsm;
+  return (int)(need < cap ? need : cap);
+}
+
 template <typename T>
 inline FCoef<T> fcoef(const hope_ctx *ctx) {
   FCoef<T> f;
@@ -98,6 +140,17 @@ int launch_recon_weno_adj(hope_ctx *ctx, Grid &g, const T *qs, const T *lamL, cu
 // -------------------------------------------------------------------------------
 // One stage on one grid: out = L(qs) (mode 0) or a*q0 + b*qs + c*L(qs) (mode 1).
 // -------------------------------------------------------------------------------
+// TPP reconstruction + sources of one grid with the grid's tile shape.
+template <typename T, int K>
+inline void launch_recon_tpp(hope_ctx *ctx, Grid &g, const T *qs, cudaStream_t st) {
+  const int N = g.N, TX = g.rtx, TY = g.rty;
+  dim3 grid((N + TX - 1) / TX, (N + TY - 1) / TY, 6);
+  const int threads = (TX * TY + 31) / 32 * 32;
+  k_recon_tpp<T, K><<<grid, threads, recon_tile_smem_bytes<T, K>(TX, TY), st>>>(
+      qs, (const T *)g.gext, (const T *)ctx->w1, (const T *)g.Xg, (const T *)g.t1w, (const T *)g.src8, (T *)g.ep,
+      (T *)g.sb, N, g.ne, TX, TY, (T)ctx->omega, fcoef<T>(ctx));
+}
+
 template <typename T, int K>
 inline int stage_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *q0, T *out, int mode, double a,
                       double b, double c, const T *q0l, const T *qsl, T *outl, cudaStream_t st) {
@@ -110,19 +163,14 @@ inline int stage_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *q0, T *out, 
   mark(0);
   // ghost ring
   if (g.rows > 0) {
-    long long threads = g.rows * 32;
-    int blocks = (int)((threads + 255) / 256);
-    k_ghost<T><<<blocks, 256, 0, st>>>(qs, (T *)g.gext, g.grow, g.gcol, (const T *)g.gval, g.gdst,
+    if (!g.ghost_grid) g.ghost_grid = resident_blocks(k_ghost<T>, ctx, g.rows * 32);
+    k_ghost<T><<<g.ghost_grid, 256, 0, st>>>(qs, (T *)g.gext, g.grow, g.gcol, (const T *)g.gval, g.gdst,
                                        g.trow, g.tcol, g.tval, (int)g.rows, N, ne);
   }
   mark(1);
   // reconstruction + sources
-  dim3 grid((N + REC_TX - 1) / REC_TX, (N + REC_TY - 1) / REC_TY, 6);
   if (ctx->scheme == HOPE_TPP) {
-    size_t smem = recon_smem_bytes<T, K>();
-    k_recon_tpp<T, K><<<grid, REC_TX * REC_TY, smem, st>>>(qs, (const T *)g.gext, (const T *)ctx->w1,
-                                                          (const T *)g.Xg, (const T *)g.t1w, (const T *)g.src8, (T *)g.ep,
-                                                          (T *)g.sb, N, ne, (T)ctx->omega, fcoef<T>(ctx));
+    launch_recon_tpp<T, K>(ctx, g, qs, st);
   } else {
     int rc = launch_recon_weno<T, K>(ctx, g, qs, st);
     if (rc) return rc;
@@ -131,8 +179,8 @@ inline int stage_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *q0, T *out, 
   // fluxes
   {
     long long items = 12LL * N * (N - 1) + 12LL * N;
-    int blocks = (int)((items + 255) / 256);
-    k_flux<T, ME><<<blocks, 256, 0, st>>>((const T *)g.ep, (const T *)g.mx, (const T *)ctx->gw, g.bedge,
+    if (!g.flux_tpb) balanced_grid(k_flux<T, ME>, items, ctx->nsm, 256, &g.flux_grid, &g.flux_tpb);
+    k_flux<T, ME><<<g.flux_grid, g.flux_tpb, 0, st>>>((const T *)g.ep, (const T *)g.mx, (const T *)ctx->gw, g.bedge,
                                           (const T *)g.bconv, (T *)g.fx, (T *)g.fy, N, ctx->status);
   }
   mark(3);
@@ -141,8 +189,8 @@ inline int stage_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *q0, T *out, 
     long long cells = 6LL * N * N;
     int blocks = (int)((cells + 255) / 256);
     k_update<T><<<blocks, 256, 0, st>>>((const T *)g.fx, (const T *)g.fy, (const T *)g.sb, q0, qs, out, N,
-                                        (T)(2.0 * N / HOPE_PI), mode, (T)a, (T)b, (T)c, q0l, qsl, outl,
-                                        ctx->status);
+                                        (T)(2.0 * N / HOPE_PI), mode, (T)a, (T)b, (T)c, coef_lo<T>(a),
+                                        coef_lo<T>(b), coef_lo<T>(c), q0l, qsl, outl, ctx->status);
   }
   mark(4);
   HOPE_CUDA_TRY(cudaGetLastError());
@@ -172,8 +220,10 @@ typedef int (*stage_fn)(hope_ctx *, const void *, const void *, void *, int, dou
 
 template <typename T, int K>
 inline int set_smem_attr() {
-  size_t smem = recon_smem_bytes<T, K>();
-  HOPE_CUDA_TRY(cudaFuncSetAttribute(k_recon_tpp<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int optin = 0, dev = 0;
+  HOPE_CUDA_TRY(cudaGetDevice(&dev));
+  HOPE_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  HOPE_CUDA_TRY(cudaFuncSetAttribute(k_recon_tpp<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   HOPE_CUDA_TRY(cudaFuncSetAttribute(k_recon_tpp_adj<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)recon_adj_smem_bytes<T, K>()));
   return weno_set_smem_attr<T, K>();
@@ -193,15 +243,13 @@ inline int stage_vjp_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *lamL, co
   constexpr int ME = (K + 1) / 2;
   const int N = g.N, ne = g.ne;
   if (g.rows > 0) {
-    int blocks = (int)((g.rows * 32 + 255) / 256);
-    k_ghost<T><<<blocks, 256, 0, st>>>(qs, (T *)g.gext, g.grow, g.gcol, (const T *)g.gval, g.gdst, g.trow, g.tcol,
+    if (!g.ghost_grid) g.ghost_grid = resident_blocks(k_ghost<T>, ctx, g.rows * 32);
+    k_ghost<T><<<g.ghost_grid, 256, 0, st>>>(qs, (T *)g.gext, g.grow, g.gcol, (const T *)g.gval, g.gdst, g.trow, g.tcol,
                                        g.tval, (int)g.rows, N, ne);
   }
   dim3 grid((N + REC_TX - 1) / REC_TX, (N + REC_TY - 1) / REC_TY, 6);
   if (ctx->scheme == HOPE_TPP) {
-    k_recon_tpp<T, K><<<grid, REC_TX * REC_TY, recon_smem_bytes<T, K>(), st>>>(
-        qs, (const T *)g.gext, (const T *)ctx->w1, (const T *)g.Xg, (const T *)g.t1w, (const T *)g.src8, (T *)g.ep, (T *)g.sb, N, ne,
-        (T)ctx->omega, fcoef<T>(ctx));
+    launch_recon_tpp<T, K>(ctx, g, qs, st);
   } else {
     int rc = launch_recon_weno<T, K>(ctx, g, qs, st);
     if (rc) return rc;

@@ -185,6 +185,15 @@ class Sphere:
         L.check(L.load().hope_autotune(self._h, reps, ms, ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(grid)))
         return list(ms), (tx.value, ty.value), grid.value
 
+    def recon_tile(self):
+        """(tx, ty): cells per block of the per-kernel TPP reconstruction."""
+        tx, ty = ctypes.c_int(), ctypes.c_int()
+        L.check(L.load().hope_recon_tile(self._h, ctypes.byref(tx), ctypes.byref(ty)))
+        return tx.value, ty.value
+
+    def set_recon_tile(self, tx, ty):
+        L.check(L.load().hope_set_recon_tile(self._h, int(tx), int(ty)))
+
     def launches_per_stage(self):
         n = ctypes.c_int()
         L.check(L.load().hope_launches_per_stage(self._h, ctypes.byref(n)))

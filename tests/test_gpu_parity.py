@@ -238,7 +238,8 @@ def test_c90_weno9_dam_break_fp32_vs_fp64_one_day(hp):
         schemes in nearly flat regions (tiny indicators meet a larger epsilon and the
         weights stay linear): FP64 with 1e-40 against FP64 with 1e-12 differs by about
         8e-5, and FP32 (1e-12) against FP64 (1e-40) by the same amount; both bounded by 2e-4;
-      * mass: FP64 conserved to round-off, FP32 to FP32 round-off of the state."""
+      * mass: FP64 conserved to round-off, FP32 to FP32 round-off of the state (1e-6 over
+        the day; without the stage coefficients' residuals it would drift by ~9e-6)."""
     N, k, dt, steps = 90, 9, 300.0, 288
     s64a = hp.Sphere(N, k, scheme=hp.HOPE_WENO2D, precision=hp.HOPE_FP64, omega=0.0, weno_eps=1e-40)
     s64b = hp.Sphere(N, k, scheme=hp.HOPE_WENO2D, precision=hp.HOPE_FP64, omega=0.0, weno_eps=1e-12)
@@ -258,7 +259,7 @@ def test_c90_weno9_dam_break_fp32_vs_fp64_one_day(hp):
     assert arith < 1e-5, (arith, scheme, total)
     assert scheme < 2e-4 and total < 2e-4, (arith, scheme, total)
     assert abs(s64a.mass(q64a) - m64) / m64 < 1e-13
-    assert abs(s32.mass(q32) - m32) / m32 < 1e-5
+    assert abs(s32.mass(q32) - m32) / m32 < 1e-6
     assert s64a.status() == 0 and s64b.status() == 0 and s32.status() == 0
 
 
@@ -275,3 +276,62 @@ def test_ten_to_one_dam_break_is_reported_nonphysical(hp):
     o = O.Oracle(N, k, scheme=O.WENO, omega=0.0)
     ext, _ = o.fill_ghosts(o.dam_break(h_in=10.0, h_out=1.0))
     assert o.reconstruct_all(ext)[0].min() < 0.0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("k,N", [(11, 29), (5, 21), (7, 40)])
+def test_recon_tile_shape_leaves_results_bitwise_equal(hp, prec, k, N):
+    """The per-kernel TPP reconstruction's tile shape (chosen at set-up, overridable) only
+    regroups cells: every point value and source sum is the same sequence of operations,
+    so tendencies and a step are bitwise equal across shapes, ragged tiles included
+    (tiles wider or taller than the panel, tails of 1 cell, non-multiple-of-32 blocks)."""
+    P = hp.HOPE_FP64 if prec == "fp64" else hp.HOPE_FP32
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    s = hp.Sphere(N, k, precision=P)
+    tx0, ty0 = s.recon_tile()
+    if prec == "fp32":
+        assert (tx0, ty0) == (16, 8)
+    q = to_dev(rh_perturbed(O.Oracle(N, k), 5), dt)
+    ref_t = s.tendency(q).clone()
+    ref_s = q.clone()
+    s.step(ref_s, 600.0, 2)
+    for tx, ty in [(16, 8), (7, 9), (N - 1, 3), (32, 16), (9, 32), (N + 3, 2)]:
+        if tx * ty > 512:
+            continue
+        s.set_recon_tile(tx, ty)
+        assert s.recon_tile() == (tx, ty)
+        t = s.tendency(q)
+        qs = q.clone()
+        s.step(qs, 600.0, 2)
+        assert torch.equal(t, ref_t), (tx, ty)
+        assert torch.equal(qs, ref_s), (tx, ty)
+    assert s.status() == 0
+
+
+def test_recon_tile_model_pick_for_c90_tpp11(hp):
+    """At C90 TPP11 FP64 the set-up picks a tile larger than 16 x 8 (the modelled FP64-pipe
+    time favours ~330-cell tiles, one per SM); invalid overrides are refused."""
+    s = hp.Sphere(90, 11)
+    tx, ty = s.recon_tile()
+    assert 64 <= tx * ty <= 512 and tx * ty > 128, (tx, ty)
+    with pytest.raises(hp.HopeError):
+        s.set_recon_tile(32, 32)
+    with pytest.raises(hp.HopeError):
+        s.set_recon_tile(0, 8)
+    assert s.recon_tile() == (tx, ty)
+
+
+def test_fp32_mass_drift_stays_at_roundoff(hp):
+    """FP32 bulk path, 300 SSP-RK3 steps of a noisy Rossby-Haurwitz state at C32 TPP5: the
+    flux form conserves mass exactly in exact arithmetic and the compensated stage
+    combination (error-free products and sums, split stage coefficients) keeps the FP32
+    state's drift at round-off.  With 1/3 and 2/3 rounded to FP32 and no residual the
+    third stage scales the state by 1 + 3e-8 per step: ~9e-6 after 300 steps of 300 s."""
+    N, k = 32, 5
+    s = hp.Sphere(N, k, precision=hp.HOPE_FP32)
+    q = to_dev(rh_perturbed(O.Oracle(N, k), 11), torch.float32)
+    m0 = s.mass(q)
+    s.step(q, 300.0, 300)
+    drift = abs(s.mass(q) - m0) / m0
+    assert drift < 3e-7, drift
+    assert s.status() == 0
