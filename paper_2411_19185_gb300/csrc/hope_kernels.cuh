@@ -70,6 +70,7 @@ __device__ __forceinline__ float f64_to_f32_trunc(double x) {
 
 // One ghost row: FP64/FP32 head sum in the context precision, plus (FP64 contexts) the
 // FP32 tail of negligible weights.
+constexpr int GHOST_UNROLL = 4;
 template <typename T>
 __device__ __forceinline__ void ghost_row(int row, int lane, const T *__restrict__ q, T *__restrict__ gext,
                                           const int *__restrict__ grow, const int *__restrict__ gcol,
@@ -77,31 +78,65 @@ __device__ __forceinline__ void ghost_row(int row, int lane, const T *__restrict
                                           const int *__restrict__ trow, const int *__restrict__ tcol,
                                           const float *__restrict__ tval, int N, int ne) {
   size_t pn = (size_t)6 * N * N, pe = (size_t)6 * ne * ne;
+  // GHOST_UNROLL nonzeros per lane in flight: all their loads are issued before the FMAs,
+  // so a lane waits for one round of (index, gather) latencies per GHOST_UNROLL entries.
+  // Each lane still adds its entries in increasing order.
+  constexpr int U = GHOST_UNROLL;
   int b = grow[row], e = grow[row + 1];
   T s0 = 0, s1 = 0, s2 = 0;
-  for (int t = b + lane; t < e; t += 32) {
-    int c = gcol[t];
-    const T *w = gval + (size_t)t * 5;
-    T a0 = q[c], a1 = q[pn + c], a2 = q[2 * pn + c];
-    s0 = fma(w[0], a0, s0);
-    s1 = fma(w[1], a1, fma(w[2], a2, s1));
-    s2 = fma(w[3], a1, fma(w[4], a2, s2));
+  for (int t0 = b + lane; t0 < e; t0 += 32 * U) {
+    int c[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) c[u] = t0 + 32 * u < e ? gcol[t0 + 32 * u] : -1;
+    T a[U][3], w[U][5];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool ok = c[u] >= 0;
+      const int cc = ok ? c[u] : 0;
+      const T *wp = gval + (size_t)(ok ? t0 + 32 * u : b) * 5;
+      a[u][0] = q[cc];
+      a[u][1] = q[pn + cc];
+      a[u][2] = q[2 * pn + cc];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) w[u][k] = ok ? wp[k] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      s0 = fma(w[u][0], a[u][0], s0);
+      s1 = fma(w[u][1], a[u][1], fma(w[u][2], a[u][2], s1));
+      s2 = fma(w[u][3], a[u][1], fma(w[u][4], a[u][2], s2));
+    }
   }
   if constexpr (sizeof(T) == 8) {
     if (trow) {
-    float f0 = 0.f, f1 = 0.f, f2 = 0.f;
-    const int tb = trow[row], te = trow[row + 1];
-    for (int t = tb + lane; t < te; t += 32) {
-      int c = tcol[t];
-      const float *w = tval + (size_t)t * 5;
-      float a0 = f64_to_f32_trunc(q[c]), a1 = f64_to_f32_trunc(q[pn + c]), a2 = f64_to_f32_trunc(q[2 * pn + c]);
-      f0 = fmaf(w[0], a0, f0);
-      f1 = fmaf(w[1], a1, fmaf(w[2], a2, f1));
-      f2 = fmaf(w[3], a1, fmaf(w[4], a2, f2));
-    }
-    s0 += (T)f0;
-    s1 += (T)f1;
-    s2 += (T)f2;
+      float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+      const int tb = trow[row], te = trow[row + 1];
+      for (int t0 = tb + lane; t0 < te; t0 += 32 * U) {
+        int c[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) c[u] = t0 + 32 * u < te ? tcol[t0 + 32 * u] : -1;
+        float a[U][3], w[U][5];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const bool ok = c[u] >= 0;
+          const int cc = ok ? c[u] : 0;
+          const float *wp = tval + (size_t)(ok ? t0 + 32 * u : tb) * 5;
+          a[u][0] = f64_to_f32_trunc(q[cc]);
+          a[u][1] = f64_to_f32_trunc(q[pn + cc]);
+          a[u][2] = f64_to_f32_trunc(q[2 * pn + cc]);
+#pragma unroll
+          for (int k = 0; k < 5; ++k) w[u][k] = ok ? wp[k] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          f0 = fmaf(w[u][0], a[u][0], f0);
+          f1 = fmaf(w[u][1], a[u][1], fmaf(w[u][2], a[u][2], f1));
+          f2 = fmaf(w[u][3], a[u][1], fmaf(w[u][4], a[u][2], f2));
+        }
+      }
+      s0 += (T)f0;
+      s1 += (T)f1;
+      s2 += (T)f2;
     }
   }
 #pragma unroll
