@@ -196,9 +196,10 @@ int hope_total_mass(hope_t ctx, const void *q_dev, double *mass_host, hope_strea
  * counterpart: this is an interface for callers that cannot allocate.)
  *
  * Who needs it: code that must not call cudaMalloc when it wants the diagnostic -- for
- * example code running while a CUDA graph is being captured on its stream (allocation is
- * not a capturable operation), a host framework that fixes its device-memory budget after
- * start-up, or a monitoring thread that must not change the device's allocation state.
+ * example a host framework that fixes its device-memory budget after start-up and owns
+ * every allocation, a monitoring thread that must not change the device's allocation
+ * state, or a time-stepping loop that cannot afford the device-wide synchronisation an
+ * allocation may cause.
  * Creating a context allocates its tables, so these callers cannot use hope_total_mass.
  *
  *   q_dev      state (3, 6, N, N) of one sphere on the current device, element type

@@ -2,10 +2,10 @@
 // that must not allocate device memory.
 //
 // Some callers cannot call cudaMalloc at the point where they need the diagnostic:
-// code running while a CUDA graph is being captured on its stream (cudaMalloc is not
-// a capturable operation), host code embedded in a framework whose device-memory
-// budget is fixed after start-up, or a monitor thread that must never change the
-// device's allocation state.  This entry point needs no context (creating one
+// host code embedded in a framework whose device-memory budget is fixed after start-up
+// and which owns every allocation, a monitor thread that must never change the
+// device's allocation state, or a time-stepping loop that cannot afford the
+// device-wide synchronisation an allocation may cause.  This entry point needs no context (creating one
 // allocates tables) and no per-call allocation: the per-block partial sums live in the
 // file-scope device array below, which every GPU that loads the library holds
 // (32 KiB) until the process exits.

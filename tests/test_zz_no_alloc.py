@@ -1,6 +1,6 @@
 """hope_total_mass_noalloc: the mass diagnostic for callers that cannot allocate device
-memory (for example code running during CUDA-graph capture, or a host framework whose
-device-memory budget is fixed after start-up).  It is called through the C ABI and must
+memory (for example a host framework whose device-memory budget is fixed after start-up,
+or a loop that cannot afford the synchronisation an allocation may cause).  It is called through the C ABI and must
 agree with hope_total_mass, the context-based entry point, on two calls in a row (the
 second call reuses the static scratch left by the first).
 
