@@ -37,7 +37,7 @@ L2_FLUSH_BYTES = 512 << 20
 
 # DRAM bytes per launch of the dominant kernel from the ncu capture summarised in
 # profiles/recon_tpp11_c90_fp64.md (None until captured for the current kernel).
-RECON_TRAFFIC_BYTES = 20410112  # 20.388096 MB read + 22 KB written
+RECON_TRAFFIC_BYTES = 20398336  # 20.390144 MB read + 8 KB written
 
 
 def recon_flops_per_launch(N, K):
@@ -49,6 +49,41 @@ def recon_flops_per_launch(N, K):
     npoc = 4 * me + me * me
     per_panel = 3 * 2 * K * ((me + 2) * N * (N + 2 * H) + npoc * N * N) + 28 * me * me * N * N
     return 6 * per_panel
+
+
+LMARS_FLOPS = 53  # per edge point: LMARS of eqs. 3.30-3.38 (sqrt, division = 1) + quadrature
+
+
+def weno_recon_flops_per_launch(N, K):
+    """Algorithmic FLOPs of one genuine-2D WENO reconstruction + sources launch, counted
+    from the method's steps as the library evaluates them (FMA = 2): indicators of the
+    L^2 sub-stencils through the factorised forms, tau and the weights f, the sub-stencil
+    values at the n_poc points (x-pass per sub-stencil column, y-pass per row), the split
+    combination, and 28 flops of sources per cell point."""
+    L = (K + 1) // 2
+    S, me = L * L, L
+    npos, npoc = me + 2, 4 * me + me * me
+    beta = L * L * (K * (L + 1) + L * L * (L + 2))
+    tau = S * (S - 1) // 2 + 3 * S / 2
+    points = npos * L * K * L + L * npoc * L * (L + 3)
+    comb = npoc * (2 * S + 5) / 2
+    per_cell = 3 * 2 * (beta + tau + points + comb) + 28 * me * me
+    return 6 * N * N * per_cell
+
+
+def stage_flops(N, K, ghost_nnz, weno=False):
+    """Algorithmic FLOPs of one RK stage on one sphere: ghost fill (10 per nonzero of G),
+    reconstruction + sources, LMARS + quadrature at the 12 N^2 me edge points, tendency +
+    stage combination (30 per cell)."""
+    me = (K + 1) // 2
+    rec = weno_recon_flops_per_launch(N, K) if weno else recon_flops_per_launch(N, K)
+    return 10 * ghost_nnz + rec + 12 * N * N * me * LMARS_FLOPS + 6 * N * N * 30
+
+
+def roofline(flops_per_stage, stages_per_s, peak):
+    a = flops_per_stage * stages_per_s
+    return {"bound": "alu", "flops_per_stage": flops_per_stage, "achieved_tflops": a / 1e12,
+            "peak_tflops": peak / 1e12, "frac": a / peak}
 
 
 class ClockSampler:
@@ -155,7 +190,7 @@ def _rel(a, b):
     return float(torch.linalg.norm((a - b).double()) / torch.linalg.norm(b.double()))
 
 
-def measure_forms(hp, stream):
+def measure_forms(hp, stream, fp64_peak):
     """The precision, differentiation and batching forms on the same box, each at the length
     its workload states, with its error (throughput in cell-stage updates/s)."""
     import torch
@@ -194,15 +229,18 @@ def measure_forms(hp, stream):
                              "rel_l2_h_vs_analytic": _rel(q32[0], qa[0]),
                              "fp64_rel_l2_h_vs_analytic": _rel(q64[0], qa[0]),
                              "mass_drift": (s.mass(q32) - m0) / m0,
-                             "status": s.status() | s64.status()}
+                             "status": s.status() | s64.status(),
+                             "roofline": roofline(stage_flops(N_CELLS, ORDER, s.ghost_nnz()[0]),
+                                                  3e3 / ms, fp32_peak)}
     del s64, s, q64, q32, q, qa
     # precision form, discontinuous flow: WENO9 dam break (2:1), C90, two days; FP64 with
     # epsilon 1e-40 and with 1e-12 (the FP32 epsilon: same scheme, arithmetic error alone)
     nd = 2 * day
-    runs = {}
+    runs, nnz = {}, {}
     for name, P, eps in (("fp64", hp.HOPE_FP64, 1e-40), ("fp64_eps12", hp.HOPE_FP64, 1e-12),
                          ("fp32", hp.HOPE_FP32, 1e-12)):
         sw = hp.Sphere(N_CELLS, 9, hp.HOPE_WENO2D, P, omega=0.0, weno_eps=eps)
+        nnz[name] = sw.ghost_nnz()[0]
         qw = sw.dam_break(h_in=10.0, h_out=5.0)
         m0 = sw.mass(qw)
         warm = qw.clone()
@@ -215,7 +253,10 @@ def measure_forms(hp, stream):
     for name in ("fp64", "fp32"):
         qw, msr, drift, st = runs[name]
         out["weno9_c90_dam_" + name] = {"value": cells * 3 / (msr * 1e-3), "ms_per_step": msr,
-                                        "days": nd * 300.0 / 86400.0, "mass_drift": drift, "status": st}
+                                        "days": nd * 300.0 / 86400.0, "mass_drift": drift, "status": st,
+                                        "roofline": roofline(stage_flops(N_CELLS, 9, nnz[name], weno=True),
+                                                             3e3 / msr,
+                                                             fp64_peak if name == "fp64" else fp32_peak)}
     out["weno9_c90_dam_fp32"].update({"rel_l2_h_vs_fp64": _rel(h32, h64),
                                       "rel_l2_h_vs_fp64_same_eps": _rel(h32, h64b),
                                       "rel_l2_h_fp64_eps_1e-12_vs_1e-40": _rel(h64b, h64)})
@@ -246,9 +287,12 @@ def measure_forms(hp, stream):
         fwd, bwd = times[-1]
         grads[name] = x.grad.double()
         c180 = 6 * 180 * 180 * 3 * nsteps
+        fl = stage_flops(180, 5, s.ghost_nnz()[0], weno=True)
         out[name] = {"forward": c180 / (fwd * 1e-3), "forward_plus_adjoint": c180 / ((fwd + bwd) * 1e-3),
                      "steps": nsteps, "checkpoint_every": every, "fwd_ms": fwd, "adjoint_ms": bwd,
-                     "status": s.status()}
+                     "adjoint_over_forward": bwd / fwd, "status": s.status(),
+                     "roofline_forward": roofline(fl, 3 * nsteps / (fwd * 1e-3),
+                                                  fp64_peak if P == hp.HOPE_FP64 else fp32_peak)}
         del s
     out["adjoint_c180_weno5_fp32"]["rel_l2_grad_vs_fp64"] = _rel(grads["adjoint_c180_weno5_fp32"],
                                                                  grads["adjoint_c180_weno5_fp64"])
@@ -291,7 +335,9 @@ def measure_forms(hp, stream):
                                    "adjoint_steps": nadj, "adjoint_ms": adj20,
                                    "forward_plus_adjoint": total * 3 * nadj / ((fwd20 + adj20) * 1e-3),
                                    "max_member_mass_drift": max(abs(b - a) / a for a, b in zip(m0, m1)),
-                                   "status": ens.status()}
+                                   "status": ens.status(),
+                                   "roofline": roofline(sum(stage_flops(n, 7, 0) for n in members) +
+                                                        10 * ens.ghost_nnz()[0], 3e3 / ms, fp32_peak)}
     return out
 
 
@@ -412,7 +458,7 @@ def main():
     # cell averages it started from (steps taken: warm-up + profiled capture + timed)
     steps_run = args.warmup + 1 + args.steps
     err_h = float(torch.linalg.norm(q[0] - q_analytic[0]) / torch.linalg.norm(q_analytic[0]))
-    forms = measure_forms(hp, stream) if not args.no_forms else None
+    forms = measure_forms(hp, stream, fp64_peak) if not args.no_forms else None
     total_ms = reduce_max(total_ms, world)
     e2e_s = reduce_max(e2e_s, world)
     value = world * cells * 3 * args.steps / (total_ms * 1e-3)

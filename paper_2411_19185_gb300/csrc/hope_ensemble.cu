@@ -14,6 +14,7 @@
 
 #include "hope_ensemble.h"
 #include "hope_kernels.cuh"
+#include "hope_setup_math.cuh"
 
 namespace hope {
 
@@ -31,6 +32,7 @@ struct MemberDev {
   T *ep, *sb, *fx, *fy;
   long long b_ghost, b_tile, b_flux, b_cell;  // first global item of each phase
   int tiles_x, tiles_y;
+  T inv_dx;  // 2N / pi, computed on the host (no FP64 division per cell)
 };
 
 template <typename T>
@@ -142,7 +144,7 @@ __global__ void __launch_bounds__(TX *TY)
     const MemberDev<T> &m = mem[find_member(mem, nmem, it, 3)];
     auto off = [&](const T *p) -> const T * { return p ? p + m.off : nullptr; };
     update_cell(it - m.b_cell, m.fx, m.fy, m.sb, off(sa.q0), sa.qs + m.off, sa.out + m.off, m.N,
-                (T)(2.0 * m.N / 3.14159265358979323846), sa.mode, sa.a, sa.b, sa.c, sa.alo, sa.blo, sa.clo, off(sa.q0l), off(sa.qsl),
+                m.inv_dx, sa.mode, sa.a, sa.b, sa.c, sa.alo, sa.blo, sa.clo, off(sa.q0l), off(sa.qsl),
                 sa.outl ? sa.outl + m.off : nullptr, status);
   }
 }
@@ -157,6 +159,7 @@ static int build_members(hope_ctx *ctx, int TX, int TY, std::vector<MemberDev<T>
   for (auto &g : ctx->grids) {
     MemberDev<T> m{};
     m.N = g.N;
+    m.inv_dx = (T)(2.0 * g.N / HOPE_PI);
     m.ne = g.ne;
     m.off = (long long)g.off;
     m.grow = g.grow;
