@@ -228,7 +228,8 @@ template <typename T, int K>
 struct WenoAdjShape {
   static constexpr size_t smem_elems() {
     using W = WenoShape<T, K>;
-    return W::smem_elems() + 3 * W::ME * W::ME * W::NT;  // + adjoint at the cell points
+    // + adjoint at the cell points + each thread's k x k stencil gradient
+    return W::smem_elems() + 3 * W::ME * W::ME * W::NT + K * K * W::NT;
   }
 };
 
@@ -286,6 +287,7 @@ __global__ void __launch_bounds__(REC_TX *REC_TY)
   T *bcoef = bform + L * (L * L + L);
   T *cq = bcoef + S * S;       // [3][ME*ME][NT] forward values at the cell points
   T *lcq = cq + 3 * ME * ME * NT;  // [3][ME*ME][NT] adjoint at the cell points
+  T *gsm = lcq + 3 * ME * ME * NT;  // [K*K][NT] stencil gradient of the current variable
   const int p = blockIdx.z;
   const int i0 = blockIdx.x * REC_TX, j0 = blockIdx.y * REC_TY;
   for (int t = threadIdx.x; t < NPOS * L * L; t += blockDim.x) wsub[t] = wsub_g[t];
@@ -389,12 +391,14 @@ __global__ void __launch_bounds__(REC_TX *REC_TY)
     }
   }
   // ---------------- phase C: per variable, back through WENO into the stencil gradient
+  // (accumulated in the thread's shared-memory slice gs[t * NT], written out once)
+  T *gs = gsm + tid;
 #pragma unroll 1
   for (int v = 0; v < 3; ++v) {
     const T *Qv = raw + (v * SH::RH + ty) * SH::RW + tx;
     T *gv = grad + (size_t)v * K * K * pn + cell;  // gv[(b*K + a) * pn]
 #pragma unroll 1
-    for (int t = 0; t < K * K; ++t) gv[(size_t)t * pn] = T(0);
+    for (int t = 0; t < K * K; ++t) gs[t * NT] = T(0);
     T beta[S], f[S], lf[S];
     weno_indicators<T, K>(Qv, bform, bcoef, beta);
     T tsum = 0;
@@ -412,72 +416,36 @@ __global__ void __launch_bounds__(REC_TX *REC_TY)
     for (int t = 0; t < NPOS; ++t) {
       const int npt = t < 2 ? ME : ME + 2;
       const int g = t - 2;
-      // pass 1: forward sums of the points at x-position t
-      T Ap[ME + 2], Am[ME + 2];
-#pragma unroll
-      for (int jj = 0; jj < ME + 2; ++jj) Ap[jj] = Am[jj] = T(0);
-#pragma unroll
-      for (int sx = 0; sx < L; ++sx) {
-        T Xc[K];
-        const T *wx = wsub + (t * L + sx) * L;
-#pragma unroll
-        for (int r = 0; r < K; ++r) {
-          T s = 0;
-#pragma unroll
-          for (int a = 0; a < L; ++a) s = fma(wx[a], Qv[r * RW + sx + a], s);
-          Xc[r] = s;
-        }
-#pragma unroll
-        for (int jj = 0; jj < ME + 2; ++jj) {
-          if (jj < npt) {
-            const int tyi = t < 2 ? 2 + jj : jj;
-            const T *gp = gpm + ptidx(t, jj) * 2 * S;
-#pragma unroll
-            for (int sy = 0; sy < L; ++sy) {
-              const T *wy = wsub + (tyi * L + sy) * L;
-              T pv = 0;
-#pragma unroll
-              for (int b = 0; b < L; ++b) pv = fma(wy[b], Xc[sy + b], pv);
-              const int ii = sy * L + sx;
-              const T fp = f[ii] * pv;
-              Ap[jj] = fma(gp[ii], fp, Ap[jj]);
-              Am[jj] = fma(gp[S + ii], fp, Am[jj]);
-            }
-          }
-        }
-      }
-      // adjoints of A+-, D+- at each point
-      T lAp[ME + 2], lAm[ME + 2], lDp[ME + 2], lDm[ME + 2];
+      // per point: denominators D+-, the point's adjoint lv and those of A+- (which need
+      // no forward sums); A+- themselves are summed in the same sweep as their adjoints
+      T Ap[ME + 2], Am[ME + 2], Dp[ME + 2], Dm[ME + 2], lAp[ME + 2], lAm[ME + 2], lv[ME + 2];
 #pragma unroll
       for (int jj = 0; jj < ME + 2; ++jj) {
-        lAp[jj] = lAm[jj] = lDp[jj] = lDm[jj] = T(0);
+        Ap[jj] = Am[jj] = lAp[jj] = lAm[jj] = lv[jj] = T(0);
+        Dp[jj] = Dm[jj] = T(1);
         if (jj < npt) {
           const int pt = ptidx(t, jj);
           const T *gp = gpm + pt * 2 * S;
-          T Dp = 0, Dm = 0;
+          T dp = 0, dm = 0;
 #pragma unroll
           for (int ii = 0; ii < S; ++ii) {
-            Dp = fma(gp[ii], f[ii], Dp);
-            Dm = fma(gp[S + ii], f[ii], Dm);
+            dp = fma(gp[ii], f[ii], dp);
+            dm = fma(gp[S + ii], f[ii], dm);
           }
-          T lv;
+          Dp[jj] = dp;
+          Dm[jj] = dm;
           if (t < 2)
-            lv = lep[((size_t)(t * 3 + v) * ME + jj) * pn + cell];
+            lv[jj] = lep[((size_t)(t * 3 + v) * ME + jj) * pn + cell];
           else if (jj < 2)
-            lv = lep[((size_t)((2 + jj) * 3 + v) * ME + g) * pn + cell];
+            lv[jj] = lep[((size_t)((2 + jj) * 3 + v) * ME + g) * pn + cell];
           else
-            lv = lcq[(v * ME * ME + (jj - 2) * ME + g) * NT + tid];
-          const T sp = sig[2 * pt], sm = sig[2 * pt + 1];
-          lAp[jj] = sp / Dp * lv;
-          lAm[jj] = -sm / Dm * lv;
-          lDp[jj] = -sp * Ap[jj] / (Dp * Dp) * lv;
-          lDm[jj] = sm * Am[jj] / (Dm * Dm) * lv;
-          // dD+-/df_i = gamma+-_i
-#pragma unroll
-          for (int ii = 0; ii < S; ++ii) lf[ii] = fma(gp[ii], lDp[jj], fma(gp[S + ii], lDm[jj], lf[ii]));
+            lv[jj] = lcq[(v * ME * ME + (jj - 2) * ME + g) * NT + tid];
+          lAp[jj] = sig[2 * pt] / dp * lv[jj];
+          lAm[jj] = -sig[2 * pt + 1] / dm * lv[jj];
         }
       }
-      // pass 2: p-dependent parts -> lf and the stencil gradient
+      // one sweep over the sub-stencil values p_i(pt): forward sums A+- and the
+      // p-dependent adjoints (-> lf and the stencil gradient)
 #pragma unroll
       for (int sx = 0; sx < L; ++sx) {
         T Xc[K], lXc[K];
@@ -502,6 +470,9 @@ __global__ void __launch_bounds__(REC_TX *REC_TY)
 #pragma unroll
               for (int b = 0; b < L; ++b) pv = fma(wy[b], Xc[sy + b], pv);
               const int ii = sy * L + sx;
+              const T fp = f[ii] * pv;
+              Ap[jj] = fma(gp[ii], fp, Ap[jj]);
+              Am[jj] = fma(gp[S + ii], fp, Am[jj]);
               const T gl = gp[ii] * lAp[jj] + gp[S + ii] * lAm[jj];
               lf[ii] = fma(gl, pv, lf[ii]);
               const T lp = gl * f[ii];
@@ -513,7 +484,19 @@ __global__ void __launch_bounds__(REC_TX *REC_TY)
 #pragma unroll
         for (int r = 0; r < K; ++r)
 #pragma unroll
-          for (int a = 0; a < L; ++a) gv[(size_t)(r * K + sx + a) * pn] += wx[a] * lXc[r];
+          for (int a = 0; a < L; ++a) gs[(r * K + sx + a) * NT] += wx[a] * lXc[r];
+      }
+      // adjoints of D+- (they need A+-), through dD+-/df_i = gamma+-_i
+#pragma unroll
+      for (int jj = 0; jj < ME + 2; ++jj) {
+        if (jj < npt) {
+          const int pt = ptidx(t, jj);
+          const T *gp = gpm + pt * 2 * S;
+          const T lDp = -sig[2 * pt] * Ap[jj] / (Dp[jj] * Dp[jj]) * lv[jj];
+          const T lDm = sig[2 * pt + 1] * Am[jj] / (Dm[jj] * Dm[jj]) * lv[jj];
+#pragma unroll
+          for (int ii = 0; ii < S; ++ii) lf[ii] = fma(gp[ii], lDp, fma(gp[S + ii], lDm, lf[ii]));
+        }
       }
     }
     // f_i = 1 + tau / (beta_i + eps)
@@ -570,11 +553,13 @@ __global__ void __launch_bounds__(REC_TX *REC_TY)
         for (int r = 0; r < K; ++r) {
           lqc -= rs * lZx[r];
 #pragma unroll
-          for (int a = 0; a < L; ++a) gv[(size_t)(r * K + sx + a) * pn] += Wx[kp * L + a] * lZx[r];
+          for (int a = 0; a < L; ++a) gs[(r * K + sx + a) * NT] += Wx[kp * L + a] * lZx[r];
         }
       }
     }
-    gv[(size_t)(SH::H * K + SH::H) * pn] += lqc;
+    gs[(SH::H * K + SH::H) * NT] += lqc;
+#pragma unroll 1
+    for (int t = 0; t < K * K; ++t) gv[(size_t)t * pn] = gs[t * NT];
   }
 }
 
