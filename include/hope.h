@@ -184,6 +184,26 @@ int hope_step_vjp(hope_t ctx, const void *qn_dev, const void *lam_np1_dev, void 
                   double dt, hope_stream_t stream);
 
 /*
+ * Step tapes for reverse sweeps over recomputed steps (the checkpointed recompute of the
+ * differentiation form, section 4's autograd replaced by hand-written adjoints).
+ *   hope_tape_bytes:    bytes of one step's tape: the stage states q1, q2 and, per sphere
+ *                       and stage, the ghost ring and the edge-point reconstructions
+ *                       (C180 WENO5 FP64: 188 MB).
+ *   hope_step_record:   one RK step of q_dev in place (plain stage combinations, also in
+ *                       FP32), writing its tape to tape_dev (caller-owned device memory of
+ *                       hope_tape_bytes() bytes, alignment 256 B).
+ *   hope_step_vjp_tape: hope_step_vjp for the step recorded in tape_dev from qn_dev: the
+ *                       stage states, ghost rings and edge points come from the tape, so
+ *                       only the adjoint kernels run.  Results equal hope_step_vjp's up to
+ *                       rounding.  Output may not overlap an input.
+ * Errors: HOPE_EINVAL for null or overlapping arguments, HOPE_ECUDA for failed copies.
+ */
+int hope_tape_bytes(hope_t ctx, size_t *bytes);
+int hope_step_record(hope_t ctx, void *q_dev, double dt, void *tape_dev, hope_stream_t stream);
+int hope_step_vjp_tape(hope_t ctx, const void *qn_dev, const void *tape_dev, const void *lam_np1_dev,
+                       void *lam_n_dev, double dt, hope_stream_t stream);
+
+/*
  * Total mass M = dx*dy*sum(q[0]) (the I() sum of eq. 5.7 times the cell area) of q_dev,
  * accumulated in FP64 in a fixed order on the device (bitwise reproducible).  For an
  * ensemble, mass_host receives one value per member.  Synchronises the stream.

@@ -22,6 +22,7 @@ EXPORTED = [
     "hope_total_mass", "hope_status", "hope_ghost_nnz", "hope_launches_per_stage", "hope_strerror",
     "hope_last_error_message", "hope_measure_fma_peak", "hope_set_profiling", "hope_kernel_times",
     "hope_total_mass_noalloc", "hope_autotune", "hope_inject_fault", "hope_set_recon_tile", "hope_recon_tile",
+    "hope_tape_bytes", "hope_step_record", "hope_step_vjp_tape",
 ]
 
 
@@ -82,6 +83,9 @@ def load():
         "hope_kernel_times": (i, [vp, P(ctypes.c_float), i, P(i)]),
         "hope_set_recon_tile": (i, [vp, i, i]),
         "hope_recon_tile": (i, [vp, P(i), P(i)]),
+        "hope_tape_bytes": (i, [vp, P(sz)]),
+        "hope_step_record": (i, [vp, vp, d, vp, vp]),
+        "hope_step_vjp_tape": (i, [vp, vp, vp, vp, vp, d, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -816,6 +816,126 @@ int hope_step_vjp(hope_t ctx, const void *qn_dev, const void *lam_np1_dev, void 
   return v(ctx, qn_dev, ctx->lam_a, lam_n_dev, c1, st);
 }
 
+// ---------------------------------------------------------------------------------
+// Step tapes: one RK step's stage states and each stage's ghost ring and edge points,
+// so that a reverse sweep over recomputed steps needs no further forward work.
+// Layout (bytes): q1, q2 (one state each), then per grid and stage s = 0, 1, 2: the
+// ghost ring, then the edge points, of the stage whose input is q^n, q1, q2.
+// ---------------------------------------------------------------------------------
+static size_t gext_bytes(const hope_ctx *ctx, const Grid &g) { return ctx->esize * 3 * 6 * (size_t)g.ne * g.ne; }
+static size_t ep_bytes(const hope_ctx *ctx, const Grid &g) {
+  return ctx->esize * 4 * 3 * (size_t)ctx->me * 6 * g.N * g.N;
+}
+
+static size_t tape_size(const hope_ctx *ctx) {
+  size_t b = 2 * ctx->esize * ctx->total;
+  for (auto &g : ctx->grids) b += 3 * (gext_bytes(ctx, g) + ep_bytes(ctx, g));
+  return b;
+}
+
+// copy the grids' ghost rings and edge points to (save) or from (!save) a tape's stage s
+static int tape_io(hope_ctx *ctx, unsigned char *tape, int s, bool save, cudaStream_t st) {
+  size_t off = 2 * ctx->esize * ctx->total;
+  for (auto &g : ctx->grids) {
+    const size_t gb = gext_bytes(ctx, g), eb = ep_bytes(ctx, g);
+    unsigned char *t = tape + off + (size_t)s * (gb + eb);
+    cudaError_t e1 = save ? cudaMemcpyAsync(t, g.gext, gb, cudaMemcpyDeviceToDevice, st)
+                          : cudaMemcpyAsync(g.gext, t, gb, cudaMemcpyDeviceToDevice, st);
+    cudaError_t e2 = save ? cudaMemcpyAsync(t + gb, g.ep, eb, cudaMemcpyDeviceToDevice, st)
+                          : cudaMemcpyAsync(g.ep, t + gb, eb, cudaMemcpyDeviceToDevice, st);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      set_error("step tape copy failed");
+      return HOPE_ECUDA;
+    }
+    off += 3 * (gb + eb);
+  }
+  return HOPE_OK;
+}
+
+int hope_tape_bytes(hope_t ctx, size_t *bytes) {
+  if (!ctx || !bytes) return HOPE_EINVAL;
+  *bytes = tape_size(ctx);
+  return HOPE_OK;
+}
+
+int hope_step_record(hope_t ctx, void *q_dev, double dt, void *tape_dev, hope_stream_t stream) {
+  if (!ctx || !q_dev || !tape_dev || !(dt == dt)) {
+    set_error("hope_step_record: invalid argument");
+    return HOPE_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  stage_fn f = pick_stage(ctx);
+  unsigned char *tape = (unsigned char *)tape_dev;
+  void *q1 = tape, *q2 = tape + ctx->esize * ctx->total;
+  int rc;
+  if (ctx->rk == HOPE_WSRK3) {
+    if ((rc = f(ctx, q_dev, q_dev, q1, 1, 1.0, 0.0, dt / 3.0, LoWords(), st)) || (rc = tape_io(ctx, tape, 0, true, st)))
+      return rc;
+    if ((rc = f(ctx, q1, q_dev, q2, 1, 1.0, 0.0, dt / 2.0, LoWords(), st)) || (rc = tape_io(ctx, tape, 1, true, st)))
+      return rc;
+    if ((rc = f(ctx, q2, q_dev, q_dev, 1, 1.0, 0.0, dt, LoWords(), st))) return rc;
+    return tape_io(ctx, tape, 2, true, st);
+  }
+  if ((rc = f(ctx, q_dev, q_dev, q1, 1, 0.0, 1.0, dt, LoWords(), st)) || (rc = tape_io(ctx, tape, 0, true, st)))
+    return rc;
+  if ((rc = f(ctx, q1, q_dev, q2, 1, 0.75, 0.25, 0.25 * dt, LoWords(), st)) ||
+      (rc = tape_io(ctx, tape, 1, true, st)))
+    return rc;
+  if ((rc = f(ctx, q2, q_dev, q_dev, 1, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * dt, LoWords(), st))) return rc;
+  return tape_io(ctx, tape, 2, true, st);
+}
+
+int hope_step_vjp_tape(hope_t ctx, const void *qn_dev, const void *tape_dev, const void *lam_np1_dev,
+                       void *lam_n_dev, double dt, hope_stream_t stream) {
+  if (!ctx || !qn_dev || !tape_dev || !lam_np1_dev || !lam_n_dev || lam_n_dev == qn_dev ||
+      lam_n_dev == lam_np1_dev || !(dt == dt)) {
+    set_error("hope_step_vjp_tape: invalid or overlapping arguments");
+    return HOPE_EINVAL;
+  }
+  int rc = ensure_adjoint_scratch(ctx);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  vjp_fn v = pick_vjp(ctx);
+  unsigned char *tape = (unsigned char *)tape_dev;
+  const void *q1 = tape, *q2 = tape + ctx->esize * ctx->total;
+  if (ctx->rk == HOPE_WSRK3) {
+    VjpComb c3;
+    c3.c = dt;
+    c3.have_fwd = 1;
+    if ((rc = tape_io(ctx, tape, 2, false, st)) || (rc = v(ctx, q2, lam_np1_dev, ctx->lam_b, c3, st))) return rc;
+    VjpComb c2;
+    c2.c = dt / 2.0;
+    c2.have_fwd = 1;
+    if ((rc = tape_io(ctx, tape, 1, false, st)) || (rc = v(ctx, q1, ctx->lam_b, ctx->lam_a, c2, st))) return rc;
+    VjpComb c1;
+    c1.x = lam_np1_dev; c1.a = 1.0;
+    c1.y = ctx->lam_b; c1.b = 1.0;
+    c1.z = ctx->lam_a; c1.d = 1.0;
+    c1.c = dt / 3.0;
+    c1.have_fwd = 1;
+    if ((rc = tape_io(ctx, tape, 0, false, st))) return rc;
+    return v(ctx, qn_dev, ctx->lam_a, lam_n_dev, c1, st);
+  }
+  VjpComb c3;  // lam2 = 2/3 lam + 2/3 dt L^T(q2) lam
+  c3.x = lam_np1_dev; c3.a = 2.0 / 3.0;
+  c3.c = 2.0 / 3.0 * dt;
+  c3.have_fwd = 1;
+  if ((rc = tape_io(ctx, tape, 2, false, st)) || (rc = v(ctx, q2, lam_np1_dev, ctx->lam_b, c3, st))) return rc;
+  VjpComb c2;  // lam1 = 1/4 lam2 + 1/4 dt L^T(q1) lam2
+  c2.x = ctx->lam_b; c2.a = 0.25;
+  c2.c = 0.25 * dt;
+  c2.have_fwd = 1;
+  if ((rc = tape_io(ctx, tape, 1, false, st)) || (rc = v(ctx, q1, ctx->lam_b, ctx->lam_a, c2, st))) return rc;
+  VjpComb c1;  // lam_n = 1/3 lam + 3/4 lam2 + lam1 + dt L^T(q) lam1
+  c1.x = lam_np1_dev; c1.a = 1.0 / 3.0;
+  c1.y = ctx->lam_b; c1.b = 0.75;
+  c1.z = ctx->lam_a; c1.d = 1.0;
+  c1.c = dt;
+  c1.have_fwd = 1;
+  if ((rc = tape_io(ctx, tape, 0, false, st))) return rc;
+  return v(ctx, qn_dev, ctx->lam_a, lam_n_dev, c1, st);
+}
+
 static void drop_graphs(hope_ctx *ctx) {
   for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
   ctx->graphs.clear();

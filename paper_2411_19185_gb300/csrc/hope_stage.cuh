@@ -235,6 +235,7 @@ inline int set_smem_attr() {
 struct VjpComb {
   const void *x = nullptr, *y = nullptr, *z = nullptr;
   double a = 0, b = 0, d = 0, c = 1;
+  int have_fwd = 0;  // the grids' ghost rings and edge points already hold the forward at qs
 };
 
 template <typename T, int K>
@@ -242,13 +243,15 @@ inline int stage_vjp_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *lamL, co
                           T *out, const VjpComb &cb, cudaStream_t st) {
   constexpr int ME = (K + 1) / 2;
   const int N = g.N, ne = g.ne;
-  if (g.rows > 0) {
+  if (g.rows > 0 && !cb.have_fwd) {
     if (!g.ghost_grid) g.ghost_grid = resident_blocks(k_ghost<T>, ctx, g.rows * 32);
     k_ghost<T><<<g.ghost_grid, 256, 0, st>>>(qs, (T *)g.gext, g.grow, g.gcol, (const T *)g.gval, g.gdst, g.trow, g.tcol,
                                        g.tval, (int)g.rows, N, ne);
   }
   dim3 grid((N + REC_TX - 1) / REC_TX, (N + REC_TY - 1) / REC_TY, 6);
-  if (ctx->scheme == HOPE_TPP) {
+  if (cb.have_fwd) {
+    // ghost ring and edge points restored from a step tape
+  } else if (ctx->scheme == HOPE_TPP) {
     launch_recon_tpp<T, K>(ctx, g, qs, st);
   } else {
     int rc = launch_recon_weno<T, K>(ctx, g, qs, st);

@@ -144,11 +144,39 @@ class Sphere:
                                        _stream()))
         return out
 
-    def rollout(self, q0, dt, nsteps, checkpoint_every=10):
+    def tape_bytes(self):
+        """Bytes of one step's tape (stage states, ghost rings, edge points)."""
+        n = ctypes.c_size_t()
+        L.check(L.load().hope_tape_bytes(self._h, ctypes.byref(n)))
+        return n.value
+
+    def _tape_ptr(self, tape):
+        if not tape.is_cuda or not tape.is_contiguous() or tape.dtype != torch.uint8 or \
+                tape.numel() < self.tape_bytes():
+            raise ValueError("expected a contiguous CUDA uint8 tensor of %d bytes" % self.tape_bytes())
+        return ctypes.c_void_p(tape.data_ptr())
+
+    def step_record(self, q, dt, tape):
+        """One RK step of q in place, recording its tape (uint8 CUDA tensor)."""
+        L.check(L.load().hope_step_record(self._h, _ptr(q, self), float(dt), self._tape_ptr(tape), _stream()))
+        return q
+
+    def step_vjp_tape(self, qn, tape, lam_np1, dt, out=None):
+        """step_vjp for the step recorded in `tape` from qn, without forward recomputation."""
+        if out is None:
+            out = torch.empty_like(qn)
+        L.check(L.load().hope_step_vjp_tape(self._h, _ptr(qn, self), self._tape_ptr(tape), _ptr(lam_np1, self),
+                                            _ptr(out, self), float(dt), _stream()))
+        return out
+
+    def rollout(self, q0, dt, nsteps, checkpoint_every=10, tapes=True):
         """Differentiable nsteps-step integration: returns q(T) with a backward pass that
-        recomputes from checkpoints every `checkpoint_every` steps and applies the
-        hand-written step adjoints in reverse."""
-        return _Rollout.apply(q0, self, float(dt), int(nsteps), int(checkpoint_every))
+        recomputes each segment of `checkpoint_every` steps once from its checkpoint and
+        applies the hand-written step adjoints in reverse.  With tapes=True the recompute
+        records every step's tape (checkpoint_every x tape_bytes() of device memory) so
+        the step adjoints run no forward work; with tapes=False each step adjoint
+        recomputes its stages."""
+        return _Rollout.apply(q0, self, float(dt), int(nsteps), int(checkpoint_every), bool(tapes))
 
     def mass(self, q):
         m = (ctypes.c_double * len(self.members))()
@@ -210,14 +238,14 @@ class _Rollout(torch.autograd.Function):
     """q(T) = S^n(q0) with checkpointed recompute and hand-written step adjoints."""
 
     @staticmethod
-    def forward(ctx, q0, sphere, dt, nsteps, every):
+    def forward(ctx, q0, sphere, dt, nsteps, every, tapes):
         work = q0.detach().clone().contiguous()
         ckpts = [work.clone()]
         for s in range(nsteps):
             sphere.step(work, dt)
             if (s + 1) % every == 0 and s + 1 < nsteps:
                 ckpts.append(work.clone())
-        ctx.sphere, ctx.dt, ctx.nsteps, ctx.every, ctx.ckpts = sphere, dt, nsteps, every, ckpts
+        ctx.sphere, ctx.dt, ctx.nsteps, ctx.every, ctx.ckpts, ctx.tapes = sphere, dt, nsteps, every, ckpts, tapes
         return work
 
     @staticmethod
@@ -226,16 +254,25 @@ class _Rollout(torch.autograd.Function):
         lam = lam.detach().contiguous().clone()
         work = torch.empty_like(lam)
         buf = torch.empty_like(lam)
+        tb = (sphere.tape_bytes() + 255) // 256 * 256 if ctx.tapes else 0  # rows 256-B aligned
+        tape = torch.empty((min(every, nsteps), tb), dtype=torch.uint8, device=lam.device) if ctx.tapes else None
         for seg in reversed(range(len(ctx.ckpts))):
             start = seg * every
             n = min(every, nsteps - start)
             work.copy_(ctx.ckpts[seg])
             states = [work.clone()]
-            for _ in range(n - 1):
-                sphere.step(work, dt)
-                states.append(work.clone())
+            for k in range(n - 1 if tape is None else n):
+                if tape is None:
+                    sphere.step(work, dt)
+                else:
+                    sphere.step_record(work, dt, tape[k])
+                if k < n - 1:
+                    states.append(work.clone())
             for s in reversed(range(n)):
-                sphere.step_vjp(states[s], lam, dt, out=buf)
+                if tape is None:
+                    sphere.step_vjp(states[s], lam, dt, out=buf)
+                else:
+                    sphere.step_vjp_tape(states[s], tape[s], lam, dt, out=buf)
                 lam, buf = buf, lam
         ctx.ckpts = None
-        return lam, None, None, None, None
+        return lam, None, None, None, None, None

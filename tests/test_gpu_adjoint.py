@@ -187,3 +187,44 @@ def test_weno_rollout_gradient_matches_torch_autograd_reference(hp):
     got = xg.grad.cpu().numpy()
     err = [np.linalg.norm(got[v] - ref[v]) / np.linalg.norm(ref[v]) for v in range(3)]
     assert max(err) < 1e-10, err
+
+
+@pytest.mark.parametrize("scheme,k,N,rk,prec", [("tpp", 5, 12, "ssp", "fp64"), ("weno", 5, 11, "ssp", "fp64"),
+                                                ("tpp", 3, 10, "ws", "fp64"), ("weno", 3, 9, "ssp", "fp32")])
+def test_step_vjp_from_tape_equals_recomputing_step_vjp(hp, scheme, k, N, rk, prec):
+    """A step recorded with its tape (stage states, ghost rings, edge points) gives the same
+    state as hope_step and the same step adjoint as hope_step_vjp, which recomputes the
+    stages: the tape only removes forward work (FP64 to 1e-13 relative, FP32 to 1e-5)."""
+    P = hp.HOPE_FP64 if prec == "fp64" else hp.HOPE_FP32
+    dt_ = torch.float64 if prec == "fp64" else torch.float32
+    s = hp.Sphere(N, k, scheme=hp.HOPE_TPP if scheme == "tpp" else hp.HOPE_WENO2D, precision=P,
+                  rk=hp.HOPE_SSPRK3 if rk == "ssp" else hp.HOPE_WSRK3)
+    q = state(N, 4).to(dt_)
+    lam = torch.from_numpy(fd_direction(q.shape, 5)).cuda().to(dt_)
+    tape = torch.empty(s.tape_bytes(), dtype=torch.uint8, device="cuda")
+    a = s.step_vjp(q, lam, 600.0)
+    qr = q.clone()
+    s.step_record(qr, 600.0, tape)
+    b = s.step_vjp_tape(q, tape, lam, 600.0)
+    qs = q.clone()
+    s.step(qs, 600.0)
+    tol = 1e-13 if prec == "fp64" else 1e-5
+    assert (torch.linalg.norm((a - b).double()) / torch.linalg.norm(a.double())).item() < tol
+    assert (torch.linalg.norm((qr - qs).double()) / torch.linalg.norm(qs.double())).item() < tol
+    assert s.status() == 0
+
+
+def test_rollout_with_tapes_equals_rollout_with_recompute(hp):
+    """The taped backward (each segment recomputed once, step adjoints from tapes) and the
+    recomputing backward give the same gradient (FP64, WENO5, 7 steps, checkpoints every 3)."""
+    N, k = 10, 5
+    s = hp.Sphere(N, k, scheme=hp.HOPE_WENO2D)
+    q0 = state(N, 6)
+    w = torch.from_numpy(fd_direction(q0.shape, 7)).cuda()
+    grads = []
+    for tapes in (True, False):
+        x = q0.clone().requires_grad_(True)
+        qT = s.rollout(x, 600.0, 7, checkpoint_every=3, tapes=tapes)
+        (w * qT).sum().backward()
+        grads.append(x.grad.clone())
+    assert (torch.linalg.norm(grads[0] - grads[1]) / torch.linalg.norm(grads[1])).item() < 1e-13
