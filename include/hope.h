@@ -297,7 +297,10 @@ int hope_launches_per_stage(hope_t ctx, int *launches);
  * the first sphere's stages; hope_kernel_times() then returns, for the most recent step,
  * the elapsed milliseconds of each kernel in launch order: stage-major, and within a
  * stage [ghost fill, reconstruction, flux, update] (HOPE_KERNELS_PER_STAGE entries).
- * It synchronises on the last event.  n_entries receives the number written.
+ * It synchronises on the last event.  n_entries receives the number written.  For TPP
+ * ensembles (one persistent launch per stage over all members) the four entries are the
+ * launch's phases, from GPU global-timer stamps that block 0 takes at the grid barriers
+ * (the last entry ends when the last block finishes); the call synchronises the device.
  */
 #define HOPE_KERNELS_PER_STAGE 4
 int hope_set_profiling(hope_t ctx, int enable);

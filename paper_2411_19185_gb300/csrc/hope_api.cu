@@ -1008,6 +1008,18 @@ int hope_set_profiling(hope_t ctx, int enable) {
 
 int hope_kernel_times(hope_t ctx, float *ms_out, int max_entries, int *n_entries) {
   if (!ctx || !ms_out || !n_entries || !ctx->prof_ev[0][0]) return HOPE_EINVAL;
+  if (ctx->ens) {
+    // persistent stage: the phases' global-timer stamps (block 0 after each grid barrier)
+    unsigned long long t[5 * PROF_STAGES];
+    HOPE_CUDA_TRY(cudaDeviceSynchronize());
+    HOPE_CUDA_TRY(cudaMemcpy(t, ctx->ens->stamps, sizeof(t), cudaMemcpyDeviceToHost));
+    int n = 0;
+    for (int s = 0; s < PROF_STAGES; ++s)
+      for (int k = 0; k < PROF_KERNELS && n < max_entries; ++k)
+        ms_out[n++] = (float)((double)(t[5 * s + k + 1] - t[5 * s + k]) * 1e-6);
+    *n_entries = n;
+    return HOPE_OK;
+  }
   HOPE_CUDA_TRY(cudaEventSynchronize(ctx->prof_ev[PROF_STAGES - 1][PROF_KERNELS]));
   int n = 0;
   for (int s = 0; s < PROF_STAGES; ++s)

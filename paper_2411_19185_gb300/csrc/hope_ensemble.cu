@@ -46,7 +46,14 @@ struct StageArgs {
   T omega;
   FCoef<T> fc;
   const T *gw, *w1;
+  unsigned long long *stamp;  // profiling: [start, 3 phase ends, end] or null
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 constexpr long long BARRIER_WAIT_CYCLES = 2000000000ll;  // about one second of SM clock
 
@@ -112,6 +119,8 @@ __global__ void __launch_bounds__(TX *TY)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int ME = (K + 1) / 2;
   constexpr int NT = TX * TY, WPB = NT / 32;
+  const bool stamper = sa.stamp && blockIdx.x == 0 && threadIdx.x == 0;
+  if (stamper) sa.stamp[0] = global_ns();
   // phase 1: ghost rows, one warp each
   {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -122,6 +131,7 @@ __global__ void __launch_bounds__(TX *TY)
     }
   }
   if (!grid_sync(bar, status, inject)) return;
+  if (stamper) sa.stamp[1] = global_ns();
   // phase 2: reconstruction tiles, one block each
   for (long long it = blockIdx.x; it < n_tile; it += gridDim.x) {
     const MemberDev<T> &m = mem[find_member(mem, nmem, it, 1)];
@@ -133,12 +143,14 @@ __global__ void __launch_bounds__(TX *TY)
                                  m.sb, m.N, m.ne, sa.omega, sa.fc);
   }
   if (!grid_sync(bar, status, inject)) return;
+  if (stamper) sa.stamp[2] = global_ns();
   // phase 3: edge fluxes, one thread per edge
   for (long long it = (long long)blockIdx.x * NT + threadIdx.x; it < n_flux; it += (long long)gridDim.x * NT) {
     const MemberDev<T> &m = mem[find_member(mem, nmem, it, 2)];
     flux_item<T, ME>(it - m.b_flux, m.ep, m.mx, sa.gw, m.bedge, m.bconv, m.fx, m.fy, m.N, status);
   }
   if (!grid_sync(bar, status, inject)) return;
+  if (stamper) sa.stamp[3] = global_ns();
   // phase 4: tendency and stage combination, one thread per cell
   for (long long it = (long long)blockIdx.x * NT + threadIdx.x; it < n_cell; it += (long long)gridDim.x * NT) {
     const MemberDev<T> &m = mem[find_member(mem, nmem, it, 3)];
@@ -146,6 +158,10 @@ __global__ void __launch_bounds__(TX *TY)
     update_cell(it - m.b_cell, m.fx, m.fy, m.sb, off(sa.q0), sa.qs + m.off, sa.out + m.off, m.N,
                 m.inv_dx, sa.mode, sa.a, sa.b, sa.c, sa.alo, sa.blo, sa.clo, off(sa.q0l), off(sa.qsl),
                 sa.outl ? sa.outl + m.off : nullptr, status);
+  }
+  if (sa.stamp) {
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax(sa.stamp + 4, global_ns());
   }
 }
 
@@ -277,6 +293,8 @@ static int stage_persistent_t(hope_ctx *ctx, const void *qs, const void *q0, voi
   for (int t = 0; t < 18; ++t) sa.fc.c[t] = (T)ctx->fcoef[t];
   sa.gw = (const T *)ctx->gw;
   sa.w1 = (const T *)ctx->w1;
+  sa.stamp = ctx->profiling && ctx->prof_stage >= 0 ? es.stamps + 5 * ctx->prof_stage : nullptr;
+  if (sa.stamp && cudaMemsetAsync(sa.stamp + 4, 0, sizeof(unsigned long long), st) != cudaSuccess) return HOPE_ECUDA;
   switch (ctx->k) {
     case 3: return launch_any<T, 3>(ctx, es, sa, st);
     case 5: return launch_any<T, 5>(ctx, es, sa, st);
@@ -305,6 +323,8 @@ static int ensemble_init_t(hope_ctx *ctx) {
     cudaMemcpy(es->members[s], mv.data(), sizeof(MemberDev<T>) * mv.size(), cudaMemcpyHostToDevice);
   }
   if (cudaMalloc(&es->barrier, 2 * sizeof(unsigned)) != cudaSuccess) return HOPE_ENOMEM;
+  if (cudaMalloc(&es->stamps, 5 * PROF_STAGES * sizeof(unsigned long long)) != cudaSuccess) return HOPE_ENOMEM;
+  cudaMemset(es->stamps, 0, 5 * PROF_STAGES * sizeof(unsigned long long));
   cudaMemset(es->barrier, 0, 2 * sizeof(unsigned));
   return HOPE_OK;
 }
@@ -318,6 +338,7 @@ void ensemble_free(hope_ctx *ctx) {
   for (int s = 0; s < kNumShapes; ++s)
     if (ctx->ens->members[s]) cudaFree(ctx->ens->members[s]);
   if (ctx->ens->barrier) cudaFree(ctx->ens->barrier);
+  if (ctx->ens->stamps) cudaFree(ctx->ens->stamps);
   delete ctx->ens;
   ctx->ens = nullptr;
 }

@@ -14,6 +14,7 @@ struct EnsembleState {
   int tuned = 0;
   int inject_timeout = 0;  // the next launch's barriers expect one block more (test hook)
   unsigned *barrier = nullptr;  // [count, generation]
+  unsigned long long *stamps = nullptr;  // profiling: per stage [start, 3 phase ends, end] (ns)
 };
 
 int ensemble_init(hope_ctx *ctx);

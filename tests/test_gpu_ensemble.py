@@ -110,3 +110,20 @@ def test_grid_barrier_timeout_is_reported_and_recoverable(hp):
     again = ens.tendency(q)
     assert ens.status() == 0
     assert torch.equal(again, good)
+
+
+def test_persistent_phase_times_are_reported(hp):
+    """Profiling of the persistent stage: four positive phase times per stage, and the same
+    state as an unprofiled step (the stamps only time the phases)."""
+    members = [12, 16, 12]
+    ens = hp.Sphere(members, 5, precision=hp.HOPE_FP32)
+    states = member_states(members, 9)
+    q = torch.cat([torch.from_numpy(s).reshape(-1) for s in states]).to("cuda", torch.float32)
+    q2 = q.clone()
+    ens.step(q2, 600.0)
+    ens.set_profiling(True)
+    ens.step(q, 600.0)
+    kt = ens.kernel_times()
+    ens.set_profiling(False)
+    assert len(kt) == 3 and all(len(st) == 4 and all(t > 0 for t in st) for st in kt), kt
+    assert torch.equal(q, q2)
