@@ -112,7 +112,7 @@ __device__ __forceinline__ int find_member(const MemberDev<T> *mem, int nmem, lo
 }
 
 template <typename T, int K, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY)
+__global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 1024 / (TX * TY) : 1)
     k_stage_persistent(const MemberDev<T> *__restrict__ mem, int nmem, long long n_ghost, long long n_tile,
                        long long n_flux, long long n_cell, StageArgs<T> sa, unsigned *bar, unsigned *status,
                        unsigned inject) {
