@@ -511,27 +511,15 @@ __device__ __forceinline__ void flux_item(long long idx, const T *__restrict__ e
   }
 }
 
-// Launch order of the flux items: the 12 N cube-edge items (about twice the work of an
-// interior edge) are interleaved, one every k = n / (12 N) launch slots, instead of
-// ending the index range, so no block collects them all.  Returns the item of slot t.
-__device__ __forceinline__ long long flux_slot_item(long long t, int N) {
-  const long long ni = 12LL * N * (N - 1), nb = 12LL * N;
-  const long long k = (ni + nb) / nb;
-  if (t < nb * k) {
-    if (t % k == k - 1) return ni + t / k;
-    return t - (t + 1) / k;
-  }
-  return t - nb;
-}
-
 template <typename T, int ME>
 __global__ void __launch_bounds__(256)
     k_flux(const T *__restrict__ ep, const T *__restrict__ mx, const T *__restrict__ gwg,
            const int *__restrict__ bedge, const T *__restrict__ bconv, T *__restrict__ fx,
            T *__restrict__ fy, int N, unsigned *status) {
   const long long n = 12LL * N * (N - 1) + 12LL * N;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
-    flux_item<T, ME>(flux_slot_item(t, N), ep, mx, gwg, bedge, bconv, fx, fy, N, status);
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x)
+    flux_item<T, ME>(idx, ep, mx, gwg, bedge, bconv, fx, fy, N, status);
 }
 
 // ---------------------------------------------------------------------------------
