@@ -194,7 +194,7 @@ def measure_forms(hp, stream, fp64_peak):
     """The precision, differentiation and batching forms on the same box, each at the length
     its workload states, with its error (throughput in cell-stage updates/s)."""
     import torch
-    from synth import bump_centres, noise_field
+    from synth import bump_centres
     out = {}
     fp32_peak = hp.measure_fma_peak(hp.HOPE_FP32)
     out["fp32_fma_peak_tflops"] = fp32_peak / 1e12
@@ -299,15 +299,7 @@ def measure_forms(hp, stream, fp64_peak):
     del grads
     # batching form: 64 members (32 x C48, 24 x C96, 8 x C192), TPP7, FP32, RH + 1% noise;
     # one simulated day of 45 s steps, then the adjoint of the last 20 steps
-    members = [48] * 32 + [96] * 24 + [192] * 8
-    ens = hp.Sphere(members, 7, hp.HOPE_TPP, hp.HOPE_FP32)
-    q = ens.empty()
-    for N in (48, 96, 192):
-        base = hp.Sphere(N, 7, hp.HOPE_TPP, hp.HOPE_FP32).rossby_haurwitz()
-        for m, Nm in enumerate(members):
-            if Nm == N:
-                xi = torch.from_numpy(noise_field((6, N, N), 0, member=m)).to("cuda", torch.float32)
-                ens.member(q, m).copy_(base * (1 + 0.01 * xi)[None])
+    members, ens, q = ensemble_members(hp, hp.HOPE_FP32)
     dte, nday, nadj = 45.0, int(round(86400.0 / 45.0)), 20
     m0 = ens.mass(q)
     warm = q.clone()
@@ -382,6 +374,63 @@ def run_reference(args, world, rank):
     print(json.dumps(line))
 
 
+def ensemble_members(hp, precision):
+    """The batching-form ensemble: 32 x C48, 24 x C96, 8 x C192, TPP7, Rossby-Haurwitz
+    wave 4 with seeded 1 % h noise per member."""
+    import torch
+    from synth import noise_field
+    members = [48] * 32 + [96] * 24 + [192] * 8
+    ens = hp.Sphere(members, 7, hp.HOPE_TPP, precision)
+    q = ens.empty()
+    for N in (48, 96, 192):
+        base = hp.Sphere(N, 7, hp.HOPE_TPP, precision).rossby_haurwitz()
+        for m, Nm in enumerate(members):
+            if Nm == N:
+                xi = torch.from_numpy(noise_field((6, N, N), 0, member=m)).to("cuda", base.dtype)
+                ens.member(q, m).copy_(base * (1 + 0.01 * xi)[None])
+    return members, ens, q
+
+
+def run_case(args):
+    """Short single-form runs for profiling (`--case`): not the benchmark line."""
+    import torch
+    import paper_2411_19185_gb300 as hp
+    if args.case == "ensemble64":
+        members, ens, q = ensemble_members(hp, hp.HOPE_FP32)
+        ens.step(q, 45.0, 3)
+        ens.set_profiling(True)
+        ens.step(q, 45.0)
+        acc = np.zeros(4)
+        for _ in range(10):
+            ens.step(q, 45.0)
+            acc += np.sum(np.array(ens.kernel_times()), axis=0)
+        ens.set_profiling(False)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.case, "phase_ms_per_stage": dict(zip(["ghost", "recon", "flux", "update"],
+                                                                        (acc / 30).tolist())),
+                          "status": ens.status()}))
+        return
+    from synth import bump_centres
+    P = hp.HOPE_FP32 if args.case.endswith("fp32") else hp.HOPE_FP64
+    s = hp.Sphere(180, 5, hp.HOPE_WENO2D, P)
+    q0 = s.bumps(bump_centres(16, 0))
+    target = s.bumps(bump_centres(16, 1))[0].clone()
+    n = args.steps
+    for rep in range(2):
+        x = q0.clone().requires_grad_(True)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        e[0].record()
+        qT = s.rollout(x, 150.0, n, checkpoint_every=10)
+        e[1].record()
+        loss = 0.5 * ((qT[0] - target) ** 2).sum()
+        loss.backward()
+        e[2].record()
+        torch.cuda.synchronize()
+    print(json.dumps({"case": args.case, "steps": n, "fwd_ms": e[0].elapsed_time(e[1]),
+                      "adjoint_ms": e[1].elapsed_time(e[2]), "status": s.status()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -391,7 +440,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-stages", type=int, default=150)
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--case", choices=["ensemble64", "adjoint_c180_fp64", "adjoint_c180_fp32"],
+                    help="run one form briefly for profiling instead of the benchmark")
     args = ap.parse_args()
+    if args.case:
+        run_case(args)
+        return
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
