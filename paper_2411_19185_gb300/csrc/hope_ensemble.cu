@@ -35,6 +35,16 @@ struct MemberDev {
   T inv_dx;  // 2N / pi, computed on the host (no FP64 division per cell)
 };
 
+// Ghost-fill work of the members that share one ghost operator (equal N): one item per
+// (operator row, chunk of up to GHOST_GROUP_CHUNK members), chunks fastest, so the warps
+// that apply one row to the members of a group run back to back on one SM and find the
+// row's weights in L1 instead of streaming them once per member.
+constexpr int GHOST_GROUP_CHUNK = 8;
+struct GhostGroup {
+  long long b_item;  // first item
+  int rows, nchunk, first, nmem;  // operator rows; member chunks; members gmem[first ...]
+};
+
 template <typename T>
 struct StageArgs {
   const T *qs, *q0;
@@ -47,6 +57,9 @@ struct StageArgs {
   FCoef<T> fc;
   const T *gw, *w1;
   unsigned long long *stamp;  // profiling: [start, 3 phase ends, end] or null
+  const GhostGroup *ggrp;     // ghost-fill groups
+  const int *gmem;            // member indices of the groups
+  int ngrp;
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -121,13 +134,27 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 1024 / (TX * TY) : 1)
   constexpr int NT = TX * TY, WPB = NT / 32;
   const bool stamper = sa.stamp && blockIdx.x == 0 && threadIdx.x == 0;
   if (stamper) sa.stamp[0] = global_ns();
-  // phase 1: ghost rows, one warp each
+  // phase 1: ghost rows, one warp per (row, member chunk) item
   {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (long long it = (long long)blockIdx.x * WPB + warp; it < n_ghost; it += (long long)gridDim.x * WPB) {
-      const MemberDev<T> &m = mem[find_member(mem, nmem, it, 0)];
-      ghost_row(int(it - m.b_ghost), lane, sa.qs + m.off, m.gext, m.grow, m.gcol, m.gval, m.gdst, m.trow, m.tcol,
-                m.tval, m.N, m.ne);
+      int lo = 0, hi = sa.ngrp - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sa.ggrp[mid].b_item <= it)
+          lo = mid;
+        else
+          hi = mid - 1;
+      }
+      const GhostGroup &G = sa.ggrp[lo];
+      const long long local = it - G.b_item;
+      const int r = (int)(local / G.nchunk), c = (int)(local - (long long)r * G.nchunk);
+      const int k1 = min(G.nmem, (c + 1) * GHOST_GROUP_CHUNK);
+      for (int k = c * GHOST_GROUP_CHUNK; k < k1; ++k) {
+        const MemberDev<T> &m = mem[sa.gmem[G.first + k]];
+        ghost_row(r, lane, sa.qs + m.off, m.gext, m.grow, m.gcol, m.gval, m.gdst, m.trow, m.tcol, m.tval, m.N,
+                  m.ne);
+      }
     }
   }
   if (!grid_sync(bar, status, inject)) return;
@@ -294,6 +321,9 @@ static int stage_persistent_t(hope_ctx *ctx, const void *qs, const void *q0, voi
   sa.gw = (const T *)ctx->gw;
   sa.w1 = (const T *)ctx->w1;
   sa.stamp = ctx->profiling && ctx->prof_stage >= 0 ? es.stamps + 5 * ctx->prof_stage : nullptr;
+  sa.ggrp = (const GhostGroup *)es.ggrp;
+  sa.gmem = es.gmem;
+  sa.ngrp = es.ngrp;
   if (sa.stamp && cudaMemsetAsync(sa.stamp + 4, 0, sizeof(unsigned long long), st) != cudaSuccess) return HOPE_ECUDA;
   switch (ctx->k) {
     case 3: return launch_any<T, 3>(ctx, es, sa, st);
@@ -322,6 +352,42 @@ static int ensemble_init_t(hope_ctx *ctx) {
     if (cudaMalloc(&es->members[s], sizeof(MemberDev<T>) * mv.size()) != cudaSuccess) return HOPE_ENOMEM;
     cudaMemcpy(es->members[s], mv.data(), sizeof(MemberDev<T>) * mv.size(), cudaMemcpyHostToDevice);
   }
+  {
+    // ghost-fill groups: members that share an operator (the same table pointers)
+    std::vector<const int *> tables;
+    std::vector<std::vector<int>> members;
+    for (int i = 0; i < (int)ctx->grids.size(); ++i) {
+      const int *t = ctx->grids[i].grow;
+      size_t g = 0;
+      while (g < tables.size() && tables[g] != t) ++g;
+      if (g == tables.size()) {
+        tables.push_back(t);
+        members.emplace_back();
+      }
+      members[g].push_back(i);
+    }
+    std::vector<GhostGroup> groups;
+    std::vector<int> gm;
+    long long b = 0;
+    for (size_t g = 0; g < tables.size(); ++g) {
+      GhostGroup G;
+      G.b_item = b;
+      G.rows = (int)ctx->grids[members[g][0]].rows;
+      G.nmem = (int)members[g].size();
+      G.nchunk = (G.nmem + GHOST_GROUP_CHUNK - 1) / GHOST_GROUP_CHUNK;
+      G.first = (int)gm.size();
+      gm.insert(gm.end(), members[g].begin(), members[g].end());
+      b += (long long)G.rows * G.nchunk;
+      groups.push_back(G);
+    }
+    for (int s = 0; s < kNumShapes; ++s) es->items[s][0] = b;
+    es->ngrp = (int)groups.size();
+    if (cudaMalloc(&es->ggrp, sizeof(GhostGroup) * groups.size()) != cudaSuccess ||
+        cudaMalloc(&es->gmem, sizeof(int) * gm.size()) != cudaSuccess)
+      return HOPE_ENOMEM;
+    cudaMemcpy(es->ggrp, groups.data(), sizeof(GhostGroup) * groups.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(es->gmem, gm.data(), sizeof(int) * gm.size(), cudaMemcpyHostToDevice);
+  }
   if (cudaMalloc(&es->barrier, 2 * sizeof(unsigned)) != cudaSuccess) return HOPE_ENOMEM;
   if (cudaMalloc(&es->stamps, 5 * PROF_STAGES * sizeof(unsigned long long)) != cudaSuccess) return HOPE_ENOMEM;
   cudaMemset(es->stamps, 0, 5 * PROF_STAGES * sizeof(unsigned long long));
@@ -339,6 +405,8 @@ void ensemble_free(hope_ctx *ctx) {
     if (ctx->ens->members[s]) cudaFree(ctx->ens->members[s]);
   if (ctx->ens->barrier) cudaFree(ctx->ens->barrier);
   if (ctx->ens->stamps) cudaFree(ctx->ens->stamps);
+  if (ctx->ens->ggrp) cudaFree(ctx->ens->ggrp);
+  if (ctx->ens->gmem) cudaFree(ctx->ens->gmem);
   delete ctx->ens;
   ctx->ens = nullptr;
 }

@@ -15,6 +15,9 @@ struct EnsembleState {
   int inject_timeout = 0;  // the next launch's barriers expect one block more (test hook)
   unsigned *barrier = nullptr;  // [count, generation]
   unsigned long long *stamps = nullptr;  // profiling: per stage [start, 3 phase ends, end] (ns)
+  void *ggrp = nullptr;  // GhostGroup[ngrp]: ghost-fill work grouped by shared operator
+  int *gmem = nullptr;   // member indices of the groups
+  int ngrp = 0;
 };
 
 int ensemble_init(hope_ctx *ctx);
