@@ -324,8 +324,23 @@ void orc_xyz(int p, double X, double Y, double *xyz) {
   for (int c = 0; c < 3; ++c) xyz[c] = (FR_N[p][c] + X * FR_E1[p][c] + Y * FR_E2[p][c]) / d;
 }
 
+/* Panels owning a point: largest projection on the panel normal.  Returns the */
+/* number of owners, 1, or 2 for a point on a cube edge (projections within    */
+/* 1e-12), and the owners in B[0], B[1] (lower panel first).                   */
+static int owner_panels(const double *xyz, int exclude, int *B) {
+  double d[6], bv = -2.0;
+  for (int p = 0; p < 6; ++p) {
+    d[p] = xyz[0] * FR_N[p][0] + xyz[1] * FR_N[p][1] + xyz[2] * FR_N[p][2];
+    if (p != exclude && d[p] > bv) bv = d[p];
+  }
+  int n = 0;
+  for (int p = 0; p < 6 && n < 2; ++p)
+    if (p != exclude && d[p] > bv - 1e-12) B[n++] = p;
+  return n;
+}
+
 /* Panel owning a point: largest projection on the panel normal; a tie (point */
-/* on a cube edge, up to 1e-12) goes to the lower panel number (reading c11).  */
+/* on a cube edge, up to 1e-12) goes to the lower panel number.                 */
 static int owner_panel(const double *xyz, int exclude) {
   int best = -1;
   double bv = -2.0;
@@ -439,6 +454,7 @@ typedef struct {
   int B, ic, jc;  /* source panel and containing cell */
   double wx[MAXK], wy[MAXK];
   double ratio, C[4];
+  double w;       /* share of the point's value: 1, or 1/2 for each panel of a tie */
 } gqp_t;
 
 typedef struct {
@@ -458,7 +474,7 @@ struct orc {
   double *sigp, *sigm;
   int nring;       /* ghost cells per panel */
   int *ring;       /* [nring] jj*ne + ii */
-  gqp_t *gq;       /* [6][nring][me*me] */
+  gqp_t *gq;       /* [6][nring][me*me][2]: two owner slots per ghost Gauss point */
   nbr_t *nb;       /* [6][4][N][me] */
 };
 
@@ -564,33 +580,40 @@ orc *orc_new(int N, int k, int scheme, double radius, double gravity, double ome
   /* ghost quadrature-point tables (section 3.3.1): each ghost cell's me x me  */
   /* Gauss points, located on the sphere, assigned to the owning panel, and    */
   /* given that panel's central k x k TPP stencil around the containing cell.  */
-  o->gq = (gqp_t *)malloc(sizeof(gqp_t) * 6 * o->nring * me * me);
+  o->gq = (gqp_t *)malloc(sizeof(gqp_t) * 6 * o->nring * me * me * 2);
   for (int p = 0; p < 6; ++p)
     for (int c = 0; c < o->nring; ++c) {
       int ii = o->ring[c] % ne, jj = o->ring[c] / ne;
       int i = ii - H, j = jj - H;
       for (int h = 0; h < me; ++h)
         for (int g = 0; g < me; ++g) {
-          gqp_t *q = &o->gq[((size_t)p * o->nring + c) * me * me + h * me + g];
+          gqp_t *q2 = &o->gq[(((size_t)p * o->nring + c) * me * me + h * me + g) * 2];
           double x = cell_centre(o, i) + o->gx[g] * o->dx;
           double y = cell_centre(o, j) + o->gx[h] * o->dx;
           double X = tan(x), Y = tan(y), xyz[3], XB[2];
+          int own[2];
           orc_xyz(p, X, Y, xyz);
-          int B = owner_panel(xyz, -1);
-          to_panel(B, xyz, XB);
-          double xb = atan(XB[0]), yb = atan(XB[1]);
-          int ic = (int)floor((xb + QPI) / o->dx), jc = (int)floor((yb + QPI) / o->dx);
-          if (ic < 0) ic = 0;
-          if (ic > N - 1) ic = N - 1;
-          if (jc < 0) jc = 0;
-          if (jc > N - 1) jc = N - 1;
-          double xi = (xb - cell_centre(o, ic)) / o->dx, eta = (yb - cell_centre(o, jc)) / o->dx;
-          q->B = B;
-          q->ic = ic;
-          q->jc = jc;
-          orc_weights_1d(k, -H, xi, q->wx);
-          orc_weights_1d(k, -H, eta, q->wy);
-          conversion(p, X, Y, B, XB[0], XB[1], &q->ratio, q->C);
+          /* reading c11: a point on a cube edge takes the mean of both panels' values */
+          int nown = owner_panels(xyz, -1, own);
+          for (int sl = 0; sl < 2; ++sl) {
+            gqp_t *q = &q2[sl];
+            int B = own[sl < nown ? sl : 0];
+            to_panel(B, xyz, XB);
+            double xb = atan(XB[0]), yb = atan(XB[1]);
+            int ic = (int)floor((xb + QPI) / o->dx), jc = (int)floor((yb + QPI) / o->dx);
+            if (ic < 0) ic = 0;
+            if (ic > N - 1) ic = N - 1;
+            if (jc < 0) jc = 0;
+            if (jc > N - 1) jc = N - 1;
+            double xi = (xb - cell_centre(o, ic)) / o->dx, eta = (yb - cell_centre(o, jc)) / o->dx;
+            q->B = B;
+            q->ic = ic;
+            q->jc = jc;
+            q->w = nown == 2 ? 0.5 : (sl == 0 ? 1.0 : 0.0);
+            orc_weights_1d(k, -H, xi, q->wx);
+            orc_weights_1d(k, -H, eta, q->wy);
+            conversion(p, X, Y, B, XB[0], XB[1], &q->ratio, q->C);
+          }
         }
     }
   /* panel-edge neighbours of every edge Gauss point (for reading c10) */
@@ -658,9 +681,11 @@ void orc_fill_ghosts(orc *o, const double *q, double *ext, double *resid) {
     for (int pc = 0; pc < 6 * o->nring; ++pc) {
       int p = pc / o->nring, c = pc % o->nring;
       double acc[3] = {0, 0, 0};
-      for (int r = 0; r < me * me; ++r) {
-        const gqp_t *g = &o->gq[(size_t)pc * me * me + r];
-        double wq = o->gw[r % me] * o->gw[r / me];
+      for (int r2 = 0; r2 < me * me * 2; ++r2) {
+        const int r = r2 / 2;
+        const gqp_t *g = &o->gq[(size_t)pc * me * me * 2 + r2];
+        if (g->w == 0.0) continue;
+        double wq = o->gw[r % me] * o->gw[r / me] * g->w;
         double val[3];
         for (int v = 0; v < 3; ++v) {
           const double *src = ext + (v * 6 + g->B) * pe;
@@ -1136,11 +1161,12 @@ void orc_norms(const orc *o, const double *q, const double *qr, double *out) {
 int orc_ghost_count(const orc *o) { return o->nring; }
 
 void orc_ghost_tables(const orc *o, int *ring, int *B, int *ic, int *jc, double *wx, double *wy,
-                      double *ratio, double *C) {
+                      double *ratio, double *C, double *w) {
   int me = o->me, k = o->k;
   for (int c = 0; c < o->nring; ++c) ring[c] = o->ring[c];
-  for (size_t r = 0; r < (size_t)6 * o->nring * me * me; ++r) {
+  for (size_t r = 0; r < (size_t)6 * o->nring * me * me * 2; ++r) {
     const gqp_t *g = &o->gq[r];
+    w[r] = g->w;
     B[r] = g->B;
     ic[r] = g->ic;
     jc[r] = g->jc;

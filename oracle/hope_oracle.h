@@ -92,8 +92,9 @@ void orc_sources(const orc *o, int panel, double X, double Y, const double *qv, 
 
 /* ---- table exports for the PyTorch reference composition ---- */
 int orc_ghost_count(const orc *o);
+/* per ghost Gauss point two owner slots (w = 1 and 0, or 1/2 and 1/2 on a cube edge) */
 void orc_ghost_tables(const orc *o, int *ring, int *B, int *ic, int *jc, double *wx, double *wy,
-                      double *ratio, double *C);
+                      double *ratio, double *C, double *w);
 void orc_edge_tables(const orc *o, int *B, int *sideB, int *tB, int *gB, double *ratio, double *C);
 double orc_coriolis(const orc *o, int panel, double X, double Y);
 

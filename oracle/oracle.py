@@ -82,7 +82,7 @@ def lib():
         Pi = ctypes.POINTER(ctypes.c_int)
         L.orc_ghost_count.restype = ctypes.c_int
         L.orc_ghost_count.argtypes = [vp]
-        L.orc_ghost_tables.argtypes = [vp, Pi, Pi, Pi, Pi, P, P, P, P]
+        L.orc_ghost_tables.argtypes = [vp, Pi, Pi, Pi, Pi, P, P, P, P, P]
         L.orc_edge_tables.argtypes = [vp, Pi, Pi, Pi, Pi, P, P]
         L.orc_coriolis.restype = ctypes.c_double
         L.orc_coriolis.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
@@ -203,17 +203,18 @@ class Oracle:
         return S
 
     def ghost_tables(self):
-        """Per ghost Gauss point (panel, ring cell, h, g): owning panel, containing cell,
-        1-D weights, mass ratio and momentum matrix; plus the ring cell list."""
+        """Per ghost Gauss point (panel, ring cell, h, g) two owner slots (owning panel,
+        containing cell, 1-D weights, mass ratio, momentum matrix, share w: 1 and 0, or
+        1/2 and 1/2 for a point on a cube edge); plus the ring cell list."""
         nr = lib().orc_ghost_count(self._h)
-        n = 6 * nr * self.me * self.me
+        n = 6 * nr * self.me * self.me * 2
         ring = np.empty(nr, np.int32)
         B, ic, jc = (np.empty(n, np.int32) for _ in range(3))
         wx, wy = np.empty((n, self.k)), np.empty((n, self.k))
-        ratio, C = np.empty(n), np.empty((n, 4))
+        ratio, C, w = np.empty(n), np.empty((n, 4)), np.empty(n)
         ip = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
-        lib().orc_ghost_tables(self._h, ip(ring), ip(B), ip(ic), ip(jc), _p(wx), _p(wy), _p(ratio), _p(C))
-        return dict(ring=ring, B=B, ic=ic, jc=jc, wx=wx, wy=wy, ratio=ratio, C=C)
+        lib().orc_ghost_tables(self._h, ip(ring), ip(B), ip(ic), ip(jc), _p(wx), _p(wy), _p(ratio), _p(C), _p(w))
+        return dict(ring=ring, B=B, ic=ic, jc=jc, wx=wx, wy=wy, ratio=ratio, C=C, w=w)
 
     def edge_tables(self):
         """Per (panel, side, cell, node): neighbour panel, side, cell, node and the B->A

@@ -80,13 +80,13 @@ class TorchReference:
         nr = len(ring)
         self.ring_idx = torch.tensor(np.concatenate([p * ne * ne + ring for p in range(6)]))
         src = []
-        for r in range(6 * nr * me * me):
+        for r in range(len(gt["B"])):
             B, ic, jc = gt["B"][r], gt["ic"][r], gt["jc"][r]
             src.append(B * ne * ne + ((jc + bb) * ne + (ic + aa)).ravel())
         self.g_src = torch.tensor(np.array(src))
         self.g_w = torch.tensor(np.einsum("rb,ra->rba", gt["wy"], gt["wx"]).reshape(-1, K * K))
-        self.g_ratio = torch.tensor(gt["ratio"])
-        self.g_C = torch.tensor(gt["C"])
+        self.g_ratio = torch.tensor(gt["ratio"] * gt["w"])  # two owner slots per point, shares w
+        self.g_C = torch.tensor(gt["C"] * gt["w"][:, None])
         W = np.outer(gw, gw).ravel()  # [h*me + g]
         self.g_W = torch.tensor(W)
         # metric terms at the edge points: x-edges (X_e, Y_jg) as m7x[e, j, g], y-edges
@@ -123,7 +123,7 @@ class TorchReference:
             m = self.g_ratio * vals[0]
             u = self.g_C[:, 0] * vals[1] + self.g_C[:, 1] * vals[2]
             v = self.g_C[:, 2] * vals[1] + self.g_C[:, 3] * vals[2]
-            gq = torch.stack([m, u, v]).reshape(3, -1, me * me)
+            gq = torch.stack([m, u, v]).reshape(3, -1, me * me, 2).sum(-1)
             ghost = (gq * self.g_W).sum(-1)  # (3, 6*nring)
             flat = flat.clone()
             flat[:, self.ring_idx] = ghost

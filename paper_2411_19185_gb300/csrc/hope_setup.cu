@@ -199,7 +199,22 @@ int build_ghost_operator(const hope_ctx *ctx, int N, const std::vector<double> &
         double y = -HOPE_QPI + (j + 0.5 + nodes[h]) * dx;
         double X = tan(x), Y = tan(y), P[3], XB, YB;
         panel_point(p, X, Y, P);
-        int B = face_of(P, -1);
+        // owners: the face(s) with the largest projection; a point on a cube edge (two
+        // projections within 1e-12) takes the mean of both panels' interpolations
+        int own[2], nown = 0;
+        {
+          double d[6], bv = -2.0;
+          for (int f = 0; f < 6; ++f) {
+            double n[3], e1[3], e2[3];
+            panel_frame(f, n, e1, e2);
+            d[f] = dot3(P, n);
+            bv = fmax(bv, d[f]);
+          }
+          for (int f = 0; f < 6 && nown < 2; ++f)
+            if (d[f] > bv - 1e-12) own[nown++] = f;
+        }
+        for (int o = 0; o < nown; ++o) {
+        const int B = own[o];
         if (B == p) {
 #pragma omp atomic
           ++bad;
@@ -216,7 +231,7 @@ int build_ghost_operator(const hope_ctx *ctx, int N, const std::vector<double> &
         cell_avg_weights(K, -H, xi, wx);
         cell_avg_weights(K, -H, eta, wy);
         panel_conversion(p, X, Y, B, XB, YB, &ratio, C);
-        double W = weights[g] * weights[h];
+        double W = weights[g] * weights[h] / nown;
         for (int b = 0; b < K; ++b)
           for (int a = 0; a < K; ++a) {
             int ci = ic + a - H, cj = jc + b - H;
@@ -241,6 +256,7 @@ int build_ghost_operator(const hope_ctx *ctx, int N, const std::vector<double> &
               }
             if (!merged) acc.push_back(le);
           }
+        }
       }
     loc[r] = std::move(acc);
   }
