@@ -303,7 +303,7 @@ const char *hope_last_error_message(void) { return g_err.c_str(); }
 
 static void free_grid(Grid &g) {
   if (g.owns_tables) {
-    void *tables[] = {g.Xg, g.t1w, g.mx, g.src8, g.gval, g.grow, g.gcol, g.gdst, g.bedge, g.bconv, g.gtp, g.gtr, g.gtv,
+    void *tables[] = {g.Xg, g.t1w, g.mx, g.src8, g.gval, g.grow, g.gcol, g.gdst, g.gsym, g.bedge, g.bconv, g.gtp, g.gtr, g.gtv,
                       g.trow, g.tcol, g.tval};
     for (void *p : tables)
       if (p) cudaFree(p);
@@ -443,7 +443,8 @@ static int init_impl(int n_members, const int *Ns, int order, int scheme, const 
     if (it != first_of_N.end()) {
       const Grid &src = ctx->grids[it->second];
       g.Xg = src.Xg; g.t1w = src.t1w; g.mx = src.mx; g.src8 = src.src8;
-      g.gval = src.gval; g.grow = src.grow; g.gcol = src.gcol; g.gdst = src.gdst;
+      g.gval = src.gval; g.grow = src.grow; g.gcol = src.gcol; g.gdst = src.gdst; g.gsym = src.gsym;
+      g.ghost_symmetric = src.ghost_symmetric;
       g.trow = src.trow; g.tcol = src.tcol; g.tval = src.tval; g.tnnz = src.tnnz;
       g.rows = src.rows; g.nnz = src.nnz;
       g.bedge = src.bedge; g.bconv = src.bconv;
@@ -459,11 +460,14 @@ static int init_impl(int n_members, const int *Ns, int order, int scheme, const 
       std::vector<int> rowptr, cols, dst;
       std::vector<double> vals;
       GhostSplit split;
+      GhostSym sym;
       TRY(build_ghost_operator(ctx, gr.N, nodes, weights, rowptr, cols, vals, dst,
-                               ctx->prec == HOPE_FP64 ? &split : nullptr));
+                               ctx->prec == HOPE_FP64 ? &split : nullptr, &sym));
       gr.rows = (long long)dst.size();
       gr.nnz = rowptr.back();
+      gr.ghost_symmetric = sym.symmetric;
       TRY(upload_int(&gr.gdst, dst));
+      TRY(upload_int(&gr.gsym, sym.finfo));
       if (ctx->prec == HOPE_FP64) {
         TRY(upload_int(&gr.grow, split.head_ptr));
         TRY(upload_int(&gr.gcol, split.head_col));
@@ -475,8 +479,10 @@ static int init_impl(int n_members, const int *Ns, int order, int scheme, const 
         if (!split.tail_val.empty())
           cudaMemcpy(gr.tval, split.tail_val.data(), sizeof(float) * split.tail_val.size(), cudaMemcpyHostToDevice);
       } else {
+        std::vector<int> tagged(cols.size());
+        for (size_t e = 0; e < cols.size(); ++e) tagged[e] = cols[e] | (sym.ccode[e] << 28);
         TRY(upload_int(&gr.grow, rowptr));
-        TRY(upload_int(&gr.gcol, cols));
+        TRY(upload_int(&gr.gcol, tagged));
         TRY(upload(&gr.gval, vals, ctx->esize));
       }
       {

@@ -22,7 +22,7 @@ template <typename T>
 struct MemberDev {
   int N, ne;
   long long off;  // element offset of the member in ensemble states
-  const int *grow, *gcol, *gdst;
+  const int *grow, *gcol, *gdst, *gsym;
   const T *gval;
   const int *trow, *tcol;
   const float *tval;
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 1024 / (TX * TY) : 1)
       const int k1 = min(G.nmem, (c + 1) * GHOST_GROUP_CHUNK);
       for (int k = c * GHOST_GROUP_CHUNK; k < k1; ++k) {
         const MemberDev<T> &m = mem[sa.gmem[G.first + k]];
-        ghost_row(r, lane, sa.qs + m.off, m.gext, m.grow, m.gcol, m.gval, m.gdst, m.trow, m.tcol, m.tval, m.N,
+        ghost_row(r, lane, sa.qs + m.off, m.gext, m.grow, m.gcol, m.gval, m.gdst, m.gsym, m.trow, m.tcol, m.tval, m.N,
                   m.ne);
       }
     }
@@ -207,6 +207,7 @@ static int build_members(hope_ctx *ctx, int TX, int TY, std::vector<MemberDev<T>
     m.off = (long long)g.off;
     m.grow = g.grow;
     m.gcol = g.gcol;
+    m.gsym = g.gsym;
     m.gdst = g.gdst;
     m.gval = (const T *)g.gval;
     m.trow = g.trow;

@@ -39,6 +39,10 @@ struct Grid {
   int *grow = nullptr;   // [rows+1]
   int *gcol = nullptr;   // [nnz]  source cell p*N*N + j*N + i
   int *gdst = nullptr;   // [rows] destination p*ne*ne + jj*ne + ii
+  // [rows] cube symmetry: row whose weights this row uses | output transform code << 28
+  // (gcol/tcol carry each nonzero's input transform code in bits 28-30)
+  int *gsym = nullptr;
+  bool ghost_symmetric = false;
   long long rows = 0, nnz = 0;
   // FP64 contexts: grow/gcol/gval hold the FP64 head of each row, these the FP32 tail
   int *trow = nullptr, *tcol = nullptr;

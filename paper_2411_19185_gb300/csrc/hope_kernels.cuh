@@ -68,6 +68,18 @@ __device__ __forceinline__ float f64_to_f32_trunc(double x) {
   return __uint_as_float(sign | ((unsigned)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
 }
 
+// Cube symmetry of the ghost operator (eq. 7.12 with the mean-at-tie reading): row r is
+// the image of a panel-0 row under a rotation of the cube, so it reuses that row's weights
+// (gsym[r] low bits) with its own columns.  Momentum components go through 2x2 signed
+// permutations: each column carries the code of v = M^T u (bits 28-30: swap, negate the
+// first, negate the second), the row the code of g = M s (gsym[r] bits 28-30).
+template <typename V>
+__device__ __forceinline__ void sym_apply(int code, V &x, V &y) {
+  V a = (code & 1) ? y : x, b = (code & 1) ? x : y;
+  x = (code & 2) ? -a : a;
+  y = (code & 4) ? -b : b;
+}
+
 // One ghost row: FP64/FP32 head sum in the context precision, plus (FP64 contexts) the
 // FP32 tail of negligible weights.
 constexpr int GHOST_UNROLL = 4;
@@ -75,14 +87,18 @@ template <typename T>
 __device__ __forceinline__ void ghost_row(int row, int lane, const T *__restrict__ q, T *__restrict__ gext,
                                           const int *__restrict__ grow, const int *__restrict__ gcol,
                                           const T *__restrict__ gval, const int *__restrict__ gdst,
-                                          const int *__restrict__ trow, const int *__restrict__ tcol,
-                                          const float *__restrict__ tval, int N, int ne) {
+                                          const int *__restrict__ gsym, const int *__restrict__ trow,
+                                          const int *__restrict__ tcol, const float *__restrict__ tval, int N,
+                                          int ne) {
   size_t pn = (size_t)6 * N * N, pe = (size_t)6 * ne * ne;
+  const int info = gsym[row];
+  const int wrow = info & 0x0FFFFFFF, ocode = info >> 28;
   // GHOST_UNROLL nonzeros per lane in flight: all their loads are issued before the FMAs,
   // so a lane waits for one round of (index, gather) latencies per GHOST_UNROLL entries.
   // Each lane still adds its entries in increasing order.
   constexpr int U = GHOST_UNROLL;
-  int b = grow[row], e = grow[row + 1];
+  const int b = grow[row], e = grow[row + 1];
+  const int wb = grow[wrow];  // entry t of this row uses the weights of entry wb + (t - b)
   T s0 = 0, s1 = 0, s2 = 0;
   for (int t0 = b + lane; t0 < e; t0 += 32 * U) {
     int c[U];
@@ -92,11 +108,12 @@ __device__ __forceinline__ void ghost_row(int row, int lane, const T *__restrict
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const bool ok = c[u] >= 0;
-      const int cc = ok ? c[u] : 0;
-      const T *wp = gval + (size_t)(ok ? t0 + 32 * u : b) * 5;
+      const int cc = ok ? (c[u] & 0x0FFFFFFF) : 0;
+      const T *wp = gval + (size_t)(wb + (ok ? t0 + 32 * u - b : 0)) * 5;
       a[u][0] = q[cc];
       a[u][1] = q[pn + cc];
       a[u][2] = q[2 * pn + cc];
+      sym_apply(ok ? c[u] >> 28 : 0, a[u][1], a[u][2]);
 #pragma unroll
       for (int k = 0; k < 5; ++k) w[u][k] = ok ? wp[k] : T(0);
     }
@@ -111,6 +128,7 @@ __device__ __forceinline__ void ghost_row(int row, int lane, const T *__restrict
     if (trow) {
       float f0 = 0.f, f1 = 0.f, f2 = 0.f;
       const int tb = trow[row], te = trow[row + 1];
+      const int twb = trow[wrow];
       for (int t0 = tb + lane; t0 < te; t0 += 32 * U) {
         int c[U];
 #pragma unroll
@@ -119,11 +137,12 @@ __device__ __forceinline__ void ghost_row(int row, int lane, const T *__restrict
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const bool ok = c[u] >= 0;
-          const int cc = ok ? c[u] : 0;
-          const float *wp = tval + (size_t)(ok ? t0 + 32 * u : tb) * 5;
+          const int cc = ok ? (c[u] & 0x0FFFFFFF) : 0;
+          const float *wp = tval + (size_t)(twb + (ok ? t0 + 32 * u - tb : 0)) * 5;
           a[u][0] = f64_to_f32_trunc(q[cc]);
           a[u][1] = f64_to_f32_trunc(q[pn + cc]);
           a[u][2] = f64_to_f32_trunc(q[2 * pn + cc]);
+          sym_apply(ok ? c[u] >> 28 : 0, a[u][1], a[u][2]);
 #pragma unroll
           for (int k = 0; k < 5; ++k) w[u][k] = ok ? wp[k] : 0.f;
         }
@@ -145,6 +164,7 @@ __device__ __forceinline__ void ghost_row(int row, int lane, const T *__restrict
     s1 += __shfl_xor_sync(0xffffffffu, s1, o);
     s2 += __shfl_xor_sync(0xffffffffu, s2, o);
   }
+  sym_apply(ocode, s1, s2);
   if (lane == 0) {
     int d = gdst[row];
     gext[d] = s0;
@@ -157,12 +177,13 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_ghost(const T *__restrict__ q, T *__restrict__ gext,
                                                const int *__restrict__ grow, const int *__restrict__ gcol,
                                                const T *__restrict__ gval, const int *__restrict__ gdst,
-                                               const int *__restrict__ trow, const int *__restrict__ tcol,
-                                               const float *__restrict__ tval, int rows, int N, int ne) {
+                                               const int *__restrict__ gsym, const int *__restrict__ trow,
+                                               const int *__restrict__ tcol, const float *__restrict__ tval,
+                                               int rows, int N, int ne) {
   // grid of resident blocks; warps stride over the rows so every SM gets an equal share
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows; row += nwarps)
-    ghost_row(row, threadIdx.x & 31, q, gext, grow, gcol, gval, gdst, trow, tcol, tval, N, ne);
+    ghost_row(row, threadIdx.x & 31, q, gext, grow, gcol, gval, gdst, gsym, trow, tcol, tval, N, ne);
 }
 
 // ---------------------------------------------------------------------------------

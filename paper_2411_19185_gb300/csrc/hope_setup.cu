@@ -166,10 +166,78 @@ struct LocalEnt {
 };
 }  // namespace
 
+// The 24 rotations of the cube and, per rotation t and panel p, the image panel and the
+// induced map of panel coordinates X' = a X + c Y, Y' = b X + d Y (A = {a, b, c, d}).
+struct CubeRotations {
+  int img[24][6];
+  int A[24][6][4];
+  int identity = -1;
+};
+
+static void cube_rotations(CubeRotations &cr) {
+  static const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  int t = 0;
+  for (int pi = 0; pi < 6; ++pi)
+    for (int sg = 0; sg < 8; ++sg) {
+      int m[3][3] = {};
+      for (int i = 0; i < 3; ++i) m[i][perm[pi][i]] = (sg >> i & 1) ? -1 : 1;
+      const int det = m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) -
+                      m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+                      m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+      if (det != 1) continue;
+      if (pi == 0 && sg == 0) cr.identity = t;
+      for (int p = 0; p < 6; ++p) {
+        double n[3], e1[3], e2[3], Rn[3], R1[3], R2[3];
+        panel_frame(p, n, e1, e2);
+        for (int i = 0; i < 3; ++i) {
+          Rn[i] = R1[i] = R2[i] = 0.0;
+          for (int j = 0; j < 3; ++j) {
+            Rn[i] += m[i][j] * n[j];
+            R1[i] += m[i][j] * e1[j];
+            R2[i] += m[i][j] * e2[j];
+          }
+        }
+        int q = 0;
+        for (int f = 0; f < 6; ++f) {
+          double fn[3], f1[3], f2[3];
+          panel_frame(f, fn, f1, f2);
+          if (dot3(fn, Rn) > 0.5) q = f;
+        }
+        double fn[3], f1[3], f2[3];
+        panel_frame(q, fn, f1, f2);
+        cr.img[t][p] = q;
+        cr.A[t][p][0] = (int)lround(dot3(R1, f1));
+        cr.A[t][p][1] = (int)lround(dot3(R1, f2));
+        cr.A[t][p][2] = (int)lround(dot3(R2, f1));
+        cr.A[t][p][3] = (int)lround(dot3(R2, f2));
+      }
+      ++t;
+    }
+}
+
+// index (i, j) of an n x n array centred on the panel centre, mapped by rotation t from panel p
+static inline void rot_index(const CubeRotations &cr, int t, int p, int i, int j, int n, int *p2, int *i2,
+                             int *j2) {
+  const int *A = cr.A[t][p];
+  const int u = 2 * i - (n - 1), v = 2 * j - (n - 1);
+  *p2 = cr.img[t][p];
+  *i2 = (A[0] * u + A[2] * v + (n - 1)) / 2;
+  *j2 = (A[1] * u + A[3] * v + (n - 1)) / 2;
+}
+
+// transform code of a 2x2 signed permutation: bit 0 swap, bit 1 negate the first output,
+// bit 2 negate the second.  in: v = M^T u (M = [[a, c], [b, d]]); out: g = M s.
+static inline int code_in(const int *A) {
+  return A[0] != 0 ? ((A[0] < 0) << 1) | ((A[3] < 0) << 2) : 1 | ((A[1] < 0) << 1) | ((A[2] < 0) << 2);
+}
+static inline int code_out(const int *A) {
+  return A[0] != 0 ? ((A[0] < 0) << 1) | ((A[3] < 0) << 2) : 1 | ((A[2] < 0) << 1) | ((A[1] < 0) << 2);
+}
+
 int build_ghost_operator(const hope_ctx *ctx, int N, const std::vector<double> &nodes,
                          const std::vector<double> &weights, std::vector<int> &rowptr,
                          std::vector<int> &cols, std::vector<double> &vals, std::vector<int> &dst,
-                         GhostSplit *split) {
+                         GhostSplit *split, GhostSym *sym) {
   const int K = ctx->k, H = ctx->H, me = ctx->me, ne = N + 2 * H;
   const double dx = HOPE_PI / (2.0 * N);
   // ring enumeration
@@ -314,6 +382,94 @@ int build_ghost_operator(const hope_ctx *ctx, int N, const std::vector<double> &
     }
     std::swap(G, Gn);
   }
+  // Cube symmetry: every row as the rotated copy of its panel-0 representative (rows on
+  // panel 0 with ii < H, jj < ne - H; one per orbit of the 24 rotations), in the
+  // representative's entry order, so equivalent rows share one set of weights.
+  std::vector<int> rep(rows, -1), rot(rows, -1);
+  bool symmetric = sym != nullptr;
+  CubeRotations cr;
+  if (symmetric) {
+    cube_rotations(cr);
+    std::vector<int> rowid((size_t)6 * ne * ne, -1);
+    for (int r = 0; r < rows; ++r) rowid[dst[r]] = r;
+    for (int jj = 0; jj < ne - H && symmetric; ++jj)
+      for (int ii = 0; ii < H && symmetric; ++ii) {
+        const int r0 = rowid[(size_t)jj * ne + ii];
+        if (r0 < 0) { symmetric = false; break; }
+        for (int t = 0; t < 24; ++t) {
+          int p2, i2, j2;
+          rot_index(cr, t, 0, ii, jj, ne, &p2, &i2, &j2);
+          const int r = rowid[((size_t)p2 * ne + j2) * ne + i2];
+          if (r < 0 || rep[r] >= 0) { symmetric = false; break; }
+          rep[r] = r0;
+          rot[r] = t;
+        }
+      }
+    for (int r = 0; r < rows && symmetric; ++r)
+      if (rep[r] < 0) symmetric = false;
+  }
+  if (symmetric) {
+    std::vector<std::vector<Ent>> S(rows);
+    double worst = 0.0;
+#pragma omp parallel for schedule(dynamic, 8) reduction(max : worst)
+    for (int r = 0; r < rows; ++r) {
+      const int t = rot[r];
+      const int *Ap = cr.A[t][0];
+      const double Mp[4] = {(double)Ap[0], (double)Ap[2], (double)Ap[1], (double)Ap[3]};  // [[a, c], [b, d]]
+      std::vector<Ent> &out = S[r];
+      out.reserve(G[rep[r]].size());
+      double mx = 0.0, dev = 0.0;
+      for (const auto &e : G[r]) {
+        mx = fmax(mx, fabs(e.m));
+        for (int u = 0; u < 4; ++u) mx = fmax(mx, fabs(e.c[u]));
+      }
+      for (const auto &e : G[rep[r]]) {
+        const int q = e.col / (N * N), rem = e.col % (N * N);
+        int q2, i2, j2;
+        rot_index(cr, t, q, rem % N, rem / N, N, &q2, &i2, &j2);
+        const int *Aq = cr.A[t][q];
+        const double Mq[4] = {(double)Aq[0], (double)Aq[2], (double)Aq[1], (double)Aq[3]};
+        // C' = Mp C Mq^T (signed permutations: exact)
+        const double T0 = e.c[0] * Mq[0] + e.c[1] * Mq[1], T1 = e.c[0] * Mq[2] + e.c[1] * Mq[3];
+        const double T2 = e.c[2] * Mq[0] + e.c[3] * Mq[1], T3 = e.c[2] * Mq[2] + e.c[3] * Mq[3];
+        Ent n;
+        n.col = (q2 * N + j2) * N + i2;
+        n.m = e.m;
+        n.c[0] = Mp[0] * T0 + Mp[1] * T2;
+        n.c[1] = Mp[0] * T1 + Mp[1] * T3;
+        n.c[2] = Mp[2] * T0 + Mp[3] * T2;
+        n.c[3] = Mp[2] * T1 + Mp[3] * T3;
+        out.push_back(n);
+      }
+      // deviation from the directly composed row (entries matched by column)
+      std::vector<Ent> a = G[r], b = out;
+      auto bycol = [](const Ent &x, const Ent &y) { return x.col < y.col; };
+      std::sort(a.begin(), a.end(), bycol);
+      std::sort(b.begin(), b.end(), bycol);
+      size_t ia = 0, ib = 0;
+      while (ia < a.size() || ib < b.size()) {
+        const Ent *x = ia < a.size() ? &a[ia] : nullptr, *y = ib < b.size() ? &b[ib] : nullptr;
+        double d = 0.0;
+        if (x && y && x->col == y->col) {
+          d = fabs(x->m - y->m);
+          for (int u = 0; u < 4; ++u) d = fmax(d, fabs(x->c[u] - y->c[u]));
+          ++ia;
+          ++ib;
+        } else if (x && (!y || x->col < y->col)) {
+          d = fmax(fabs(x->m), fmax(fmax(fabs(x->c[0]), fabs(x->c[1])), fmax(fabs(x->c[2]), fabs(x->c[3]))));
+          ++ia;
+        } else {
+          d = fmax(fabs(y->m), fmax(fmax(fabs(y->c[0]), fabs(y->c[1])), fmax(fabs(y->c[2]), fabs(y->c[3]))));
+          ++ib;
+        }
+        dev = fmax(dev, d);
+      }
+      worst = fmax(worst, mx > 0.0 ? dev / mx : dev);
+    }
+    sym->max_dev = worst;
+    if (worst < 1e-12) G = std::move(S);
+    else symmetric = false;
+  }
   // Drop the negligible tail of every row: entries whose largest weight is below
   // drop_rel times the row's largest weight (contributions of deep sweeps, which decay
   // geometrically).  The dropped weights sum to well under the precision's rounding
@@ -336,6 +492,11 @@ int build_ghost_operator(const hope_ctx *ctx, int N, const std::vector<double> &
   }
   rowptr.assign(rows + 1, 0);
   for (int r = 0; r < rows; ++r) rowptr[r + 1] = rowptr[r] + (int)G[r].size();
+  // input transform code of entry k of row r (0 without symmetry)
+  auto ecode = [&](int r, int k) -> int {
+    if (!symmetric) return 0;
+    return code_in(cr.A[rot[r]][G[rep[r]][k].col / (N * N)]);
+  };
   if (split) {
     // Head/tail split for FP64 contexts: entries whose largest weight is at least
     // split_rel of the row's largest stay in FP64; the rest (at most ~2e-8 of a row's
@@ -354,21 +515,35 @@ int build_ghost_operator(const hope_ctx *ctx, int N, const std::vector<double> &
         for (int t = 0; t < 4; ++t) m = fmax(m, fabs(e.c[t]));
         mx = fmax(mx, m);
       }
-      for (const auto &e : G[r]) {
+      for (size_t k = 0; k < G[r].size(); ++k) {
+        const Ent &e = G[r][k];
         double m = fabs(e.m);
         for (int t = 0; t < 4; ++t) m = fmax(m, fabs(e.c[t]));
         if (m >= split_rel * mx) {
-          split->head_col.push_back(e.col);
+          split->head_col.push_back(e.col | (ecode(r, (int)k) << 28));
           split->head_val.push_back(e.m);
           for (int t = 0; t < 4; ++t) split->head_val.push_back(e.c[t]);
         } else {
-          split->tail_col.push_back(e.col);
+          split->tail_col.push_back(e.col | (ecode(r, (int)k) << 28));
           split->tail_val.push_back((float)e.m);
           for (int t = 0; t < 4; ++t) split->tail_val.push_back((float)e.c[t]);
         }
       }
       split->head_ptr[r + 1] = (int)split->head_col.size();
       split->tail_ptr[r + 1] = (int)split->tail_col.size();
+    }
+  }
+  if (sym) {
+    sym->symmetric = symmetric;
+    sym->finfo.assign(rows, 0);
+    sym->ccode.assign(rowptr[rows], 0);
+    for (int r = 0; r < rows; ++r) {
+      if (!symmetric) {
+        sym->finfo[r] = r;
+        continue;
+      }
+      sym->finfo[r] = rep[r] | (code_out(cr.A[rot[r]][0]) << 28);
+      for (int e = rowptr[r], k = 0; e < rowptr[r + 1]; ++e, ++k) sym->ccode[e] = ecode(r, k);
     }
   }
   cols.resize(rowptr[rows]);

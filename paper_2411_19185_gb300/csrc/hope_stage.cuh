@@ -164,7 +164,7 @@ inline int stage_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *q0, T *out, 
   // ghost ring
   if (g.rows > 0) {
     if (!g.ghost_grid) g.ghost_grid = resident_blocks(k_ghost<T>, ctx, g.rows * 32);
-    k_ghost<T><<<g.ghost_grid, 256, 0, st>>>(qs, (T *)g.gext, g.grow, g.gcol, (const T *)g.gval, g.gdst,
+    k_ghost<T><<<g.ghost_grid, 256, 0, st>>>(qs, (T *)g.gext, g.grow, g.gcol, (const T *)g.gval, g.gdst, g.gsym,
                                        g.trow, g.tcol, g.tval, (int)g.rows, N, ne);
   }
   mark(1);
@@ -245,7 +245,7 @@ inline int stage_vjp_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *lamL, co
   const int N = g.N, ne = g.ne;
   if (g.rows > 0 && !cb.have_fwd) {
     if (!g.ghost_grid) g.ghost_grid = resident_blocks(k_ghost<T>, ctx, g.rows * 32);
-    k_ghost<T><<<g.ghost_grid, 256, 0, st>>>(qs, (T *)g.gext, g.grow, g.gcol, (const T *)g.gval, g.gdst, g.trow, g.tcol,
+    k_ghost<T><<<g.ghost_grid, 256, 0, st>>>(qs, (T *)g.gext, g.grow, g.gcol, (const T *)g.gval, g.gdst, g.gsym, g.trow, g.tcol,
                                        g.tval, (int)g.rows, N, ne);
   }
   dim3 grid((N + REC_TX - 1) / REC_TX, (N + REC_TY - 1) / REC_TY, 6);
