@@ -28,6 +28,10 @@ def member_states(members, seed=0, k=3):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_ensemble_persistent_matches_single_spheres(hp, prec):
+    """Three steps of an uneven ensemble in the persistent launch equal the same steps of
+    single-sphere contexts (separate kernels): to 1e-15 in FP64; in FP32 to a few units in
+    the last place (the persistent kernel is a different compilation, and the compiler may
+    contract a product and a sum into one FMA in one kernel and not in the other)."""
     members = [12, 20, 16, 12]
     P = hp.HOPE_FP64 if prec == "fp64" else hp.HOPE_FP32
     dt = torch.float64 if prec == "fp64" else torch.float32
@@ -41,7 +45,8 @@ def test_ensemble_persistent_matches_single_spheres(hp, prec):
         qm = torch.from_numpy(states[m]).to("cuda", dt)
         s.step(qm, 600.0, 3)
         a, b = ens.member(q, m).double().cpu().numpy(), qm.double().cpu().numpy()
-        assert np.max(np.abs(a - b)) <= 1e-15 * np.max(np.abs(b)), (m, np.max(np.abs(a - b)))
+        tol = 1e-15 if prec == "fp64" else 2.0 ** -21
+        assert np.max(np.abs(a - b)) <= tol * np.max(np.abs(b)), (m, np.max(np.abs(a - b)))
     assert ens.status() == 0
 
 
@@ -61,7 +66,8 @@ def test_batching_form_full_size_sample(hp):
     """The full batching workload: 64 members (32 x C48, 24 x C96, 8 x C192), TPP7, FP32,
     Rossby-Haurwitz wave 4 plus 1% seeded h noise per member, dt = 45 s.  Two graph-replayed
     steps of the ensemble equal the same steps of single-sphere contexts for one member of
-    each resolution; mass per member is conserved to FP32 round-off."""
+    each resolution to a few units in the last place; mass per member is conserved to FP32
+    round-off."""
     members = [48] * 32 + [96] * 24 + [192] * 8
     ens = hp.Sphere(members, 7, precision=hp.HOPE_FP32)
     q = ens.empty()
@@ -79,7 +85,8 @@ def test_batching_form_full_size_sample(hp):
         s = rh[N][0]
         qm = ens.member(q0, m).clone()
         s.step(qm, 45.0, 2)
-        assert torch.equal(ens.member(q, m), qm), m
+        a, b = ens.member(q, m).double(), qm.double()
+        assert (a - b).abs().max().item() <= 2.0 ** -21 * b.abs().max().item(), m
     m1 = ens.mass(q)
     assert max(abs(a - b) / abs(b) for a, b in zip(m1, m0)) < 2e-7
     assert ens.status() == 0
