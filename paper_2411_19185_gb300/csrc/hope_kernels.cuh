@@ -73,11 +73,18 @@ __device__ __forceinline__ float f64_to_f32_trunc(double x) {
 // (gsym[r] low bits) with its own columns.  Momentum components go through 2x2 signed
 // permutations: each column carries the code of v = M^T u (bits 28-30: swap, negate the
 // first, negate the second), the row the code of g = M s (gsym[r] bits 28-30).
-template <typename V>
-__device__ __forceinline__ void sym_apply(int code, V &x, V &y) {
-  V a = (code & 1) ? y : x, b = (code & 1) ? x : y;
-  x = (code & 2) ? -a : a;
-  y = (code & 4) ? -b : b;
+// (integer selects and sign-bit flips: no FP64-pipe instruction)
+__device__ __forceinline__ void sym_apply(int code, double &x, double &y) {
+  const long long a = __double_as_longlong(x), b = __double_as_longlong(y);
+  const long long s1 = (code & 1) ? b : a, s2 = (code & 1) ? a : b;
+  x = __longlong_as_double(s1 ^ ((long long)((code >> 1) & 1) << 63));
+  y = __longlong_as_double(s2 ^ ((long long)((code >> 2) & 1) << 63));
+}
+__device__ __forceinline__ void sym_apply(int code, float &x, float &y) {
+  const int a = __float_as_int(x), b = __float_as_int(y);
+  const int s1 = (code & 1) ? b : a, s2 = (code & 1) ? a : b;
+  x = __int_as_float(s1 ^ (int)((unsigned)((code >> 1) & 1) << 31));
+  y = __int_as_float(s2 ^ (int)((unsigned)((code >> 2) & 1) << 31));
 }
 
 // One ghost row: FP64/FP32 head sum in the context precision, plus (FP64 contexts) the
@@ -174,7 +181,7 @@ __device__ __forceinline__ void ghost_row(int row, int lane, const T *__restrict
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_ghost(const T *__restrict__ q, T *__restrict__ gext,
+__global__ void __launch_bounds__(256, 4) k_ghost(const T *__restrict__ q, T *__restrict__ gext,
                                                const int *__restrict__ grow, const int *__restrict__ gcol,
                                                const T *__restrict__ gval, const int *__restrict__ gdst,
                                                const int *__restrict__ gsym, const int *__restrict__ trow,
