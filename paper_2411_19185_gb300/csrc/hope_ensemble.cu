@@ -38,7 +38,8 @@ struct MemberDev {
 // Ghost-fill work of the members that share one ghost operator (equal N): one item per
 // (operator row, chunk of up to GHOST_GROUP_CHUNK members), chunks fastest, so the warps
 // that apply one row to the members of a group run back to back on one SM and find the
-// row's weights in L1 instead of streaming them once per member.
+// row's weights in L1 instead of streaming them once per member.  The rows use their own
+// weights (no cube-symmetry transforms: this reuse already keeps the weights on chip).
 constexpr int GHOST_GROUP_CHUNK = 8;
 struct GhostGroup {
   long long b_item;  // first item
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 1024 / (TX * TY) : 1)
       const int k1 = min(G.nmem, (c + 1) * GHOST_GROUP_CHUNK);
       for (int k = c * GHOST_GROUP_CHUNK; k < k1; ++k) {
         const MemberDev<T> &m = mem[sa.gmem[G.first + k]];
-        ghost_row(r, lane, sa.qs + m.off, m.gext, m.grow, m.gcol, m.gval, m.gdst, m.gsym, m.trow, m.tcol, m.tval, m.N,
+        ghost_row<T, false>(r, lane, sa.qs + m.off, m.gext, m.grow, m.gcol, m.gval, m.gdst, m.gsym, m.trow, m.tcol, m.tval, m.N,
                   m.ne);
       }
     }

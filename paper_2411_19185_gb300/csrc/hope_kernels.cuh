@@ -88,9 +88,11 @@ __device__ __forceinline__ void sym_apply(int code, float &x, float &y) {
 }
 
 // One ghost row: FP64/FP32 head sum in the context precision, plus (FP64 contexts) the
-// FP32 tail of negligible weights.
+// FP32 tail of negligible weights.  SYM: weights of the row's representative with the
+// symmetry transforms (the weights stay in L2); otherwise the row's own weights (every
+// row holds the same values in its own order) and no transforms.
 constexpr int GHOST_UNROLL = 4;
-template <typename T>
+template <typename T, bool SYM = true>
 __device__ __forceinline__ void ghost_row(int row, int lane, const T *__restrict__ q, T *__restrict__ gext,
                                           const int *__restrict__ grow, const int *__restrict__ gcol,
                                           const T *__restrict__ gval, const int *__restrict__ gdst,
@@ -98,7 +100,7 @@ __device__ __forceinline__ void ghost_row(int row, int lane, const T *__restrict
                                           const int *__restrict__ tcol, const float *__restrict__ tval, int N,
                                           int ne) {
   size_t pn = (size_t)6 * N * N, pe = (size_t)6 * ne * ne;
-  const int info = gsym[row];
+  const int info = SYM ? gsym[row] : row;
   const int wrow = info & 0x0FFFFFFF, ocode = info >> 28;
   // GHOST_UNROLL nonzeros per lane in flight: all their loads are issued before the FMAs,
   // so a lane waits for one round of (index, gather) latencies per GHOST_UNROLL entries.
@@ -120,7 +122,7 @@ __device__ __forceinline__ void ghost_row(int row, int lane, const T *__restrict
       a[u][0] = q[cc];
       a[u][1] = q[pn + cc];
       a[u][2] = q[2 * pn + cc];
-      sym_apply(ok ? c[u] >> 28 : 0, a[u][1], a[u][2]);
+      if (SYM) sym_apply(ok ? c[u] >> 28 : 0, a[u][1], a[u][2]);
 #pragma unroll
       for (int k = 0; k < 5; ++k) w[u][k] = ok ? wp[k] : T(0);
     }
@@ -149,7 +151,7 @@ __device__ __forceinline__ void ghost_row(int row, int lane, const T *__restrict
           a[u][0] = f64_to_f32_trunc(q[cc]);
           a[u][1] = f64_to_f32_trunc(q[pn + cc]);
           a[u][2] = f64_to_f32_trunc(q[2 * pn + cc]);
-          sym_apply(ok ? c[u] >> 28 : 0, a[u][1], a[u][2]);
+          if (SYM) sym_apply(ok ? c[u] >> 28 : 0, a[u][1], a[u][2]);
 #pragma unroll
           for (int k = 0; k < 5; ++k) w[u][k] = ok ? wp[k] : 0.f;
         }
@@ -171,7 +173,7 @@ __device__ __forceinline__ void ghost_row(int row, int lane, const T *__restrict
     s1 += __shfl_xor_sync(0xffffffffu, s1, o);
     s2 += __shfl_xor_sync(0xffffffffu, s2, o);
   }
-  sym_apply(ocode, s1, s2);
+  if (SYM) sym_apply(ocode, s1, s2);
   if (lane == 0) {
     int d = gdst[row];
     gext[d] = s0;
