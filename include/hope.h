@@ -253,8 +253,11 @@ int hope_status(hope_t ctx, unsigned *device_status);
  * all members' work lists.  hope_autotune times the compiled tile shapes (TX x TY cells per
  * work item: 16x8, 16x4, 32x4) for reps stages on the context's scratch buffers and keeps
  * the fastest; it runs once at hope_init_ensemble.  ms_out (3 floats, may be NULL) gets the
- * per-shape stage times, tx/ty/grid the chosen shape and resident grid size.  Returns
- * HOPE_EUNSUPPORTED for contexts without the persistent path (one sphere, WENO2D).
+ * per-shape stage times, tx/ty/grid the chosen shape and resident grid size.  For a single
+ * TPP sphere it times the reconstruction tile candidates 16 x 8, the model's shape and
+ * 12 x 12 (-1 for a repeated candidate), keeps the fastest (as hope_set_recon_tile) and
+ * returns the tile count in grid; it runs at hope_init_grid for FP32.  Returns
+ * HOPE_EUNSUPPORTED for WENO2D contexts.
  */
 int hope_autotune(hope_t ctx, int reps, float *ms_out, int *tx, int *ty, int *grid);
 
@@ -264,7 +267,8 @@ int hope_autotune(hope_t ctx, int reps, float *ms_out, int *tx, int *ty, int *gr
  * one panel: it stages the tile with its (k-1)/2 halo in shared memory, runs the x-pass
  * over the tile's extended rows and one thread per cell runs the y-pass and the sources.
  * hope_init_grid picks the shape: for FP64 the one that minimises a model of the FP64-pipe
- * time of the most loaded SM (tiles of 64..512 cells), for FP32 16 x 8.  The results do
+ * time of the most loaded SM (tiles of 64..512 cells); for FP32 (latency-bound) the fastest
+ * of 16 x 8, the model's shape and 12 x 12, timed at set-up (hope_autotune).  The results do
  * not depend on the shape (every point value is the same sum in the same order).
  * hope_set_recon_tile overrides it (1 <= tx*ty <= 512 and the tile's shared memory,
  * 8 (FP64) or 4 (FP32) bytes x (3 (ty+k-1)(tx+k-1) + 3 ((k+1)/2+2)(ty+k-1) tx + ((k+1)/2+2) k),

@@ -68,32 +68,41 @@ static double recon_tile_cost(int N, int K, int TX, int TY, int nsm) {
   return worst;
 }
 
-// Tile shape of the per-kernel TPP reconstruction.  The FP64 kernel is bound by the FP64
-// pipe, so its shape minimises recon_tile_cost over tiles of 64..512 cells that fit the
-// shared memory; the FP32 kernel is latency-bound at these sizes and keeps 16 x 8.
-static void choose_recon_tile(const hope_ctx *ctx, Grid &g) {
-  g.rtx = REC_TX;
-  g.rty = REC_TY;
-  if (ctx->scheme != HOPE_TPP || ctx->prec != HOPE_FP64) return;
+// Tile shape of the per-kernel TPP reconstruction that minimises recon_tile_cost over
+// tiles of 64..512 cells that fit the shared memory.
+static void model_recon_tile(const hope_ctx *ctx, int N, int *tx, int *ty) {
+  *tx = REC_TX;
+  *ty = REC_TY;
   int nsm = 0, optin = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
   if (nsm < 1) return;
   const int K = ctx->k;
   const int me = (K + 1) / 2, npos = me + 2;
-  double best = recon_tile_cost(g.N, K, g.rtx, g.rty, nsm);
+  double best = recon_tile_cost(N, K, *tx, *ty, nsm);
   for (int TY = 4; TY <= 32; ++TY)
     for (int TX = 8; TX <= 32; ++TX) {
       if (TX * TY < 64 || TX * TY > REC_MAX_THREADS) continue;
-      const size_t smem = sizeof(double) * (3 * (TY + K - 1) * (TX + K - 1) + 3 * npos * (TY + K - 1) * TX + npos * K);
+      const size_t smem =
+          (size_t)ctx->esize * (3 * (TY + K - 1) * (TX + K - 1) + 3 * npos * (TY + K - 1) * TX + npos * K);
       if (smem > (size_t)optin) continue;
-      const double c = recon_tile_cost(g.N, K, TX, TY, nsm);
+      const double c = recon_tile_cost(N, K, TX, TY, nsm);
       if (c < best * 0.999) {
         best = c;
-        g.rtx = TX;
-        g.rty = TY;
+        *tx = TX;
+        *ty = TY;
       }
     }
+}
+
+// Set-up choice: the FP64 kernel is bound by the FP64 pipe, so it takes the model's shape;
+// the FP32 kernel is latency-bound and starts from 16 x 8 (hope_init_grid then times the
+// candidates, tune_recon_tile).
+static void choose_recon_tile(const hope_ctx *ctx, Grid &g) {
+  g.rtx = REC_TX;
+  g.rty = REC_TY;
+  if (ctx->scheme != HOPE_TPP || ctx->prec != HOPE_FP64) return;
+  model_recon_tile(ctx, g.N, &g.rtx, &g.rty);
 }
 
 static int ensure_adjoint_scratch(hope_ctx *ctx) {
@@ -362,6 +371,8 @@ static int upload_int(int **dst, const std::vector<int> &v) {
   return cudaMemcpy(*dst, v.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess ? HOPE_OK : HOPE_ECUDA;
 }
 
+static int tune_recon_tile(hope_ctx *ctx, int reps, float *ms_out, cudaStream_t st);
+
 static int init_impl(int n_members, const int *Ns, int order, int scheme, const hope_params *params,
                      hope_t *out) {
   if (!out) {
@@ -566,6 +577,7 @@ static int init_impl(int n_members, const int *Ns, int order, int scheme, const 
     }
     cudaMemset(ctx->status, 0, sizeof(unsigned));
   }
+  if (n_members == 1 && scheme == HOPE_TPP && ctx->prec == HOPE_FP32) TRY(tune_recon_tile(ctx, 3, nullptr, nullptr));
 #undef TRY
   *out = ctx;
   return HOPE_OK;
@@ -947,6 +959,58 @@ static void drop_graphs(hope_ctx *ctx) {
   ctx->graphs.clear();
 }
 
+// Times `reps` tendency stages of a single TPP sphere with each candidate tile shape --
+// 16 x 8, the model's shape, 12 x 12 -- on a benign state in the context's scratch
+// buffers and keeps the fastest.  ms_out (3 floats, may be null) gets the times (-1 for a
+// candidate equal to an earlier one).
+static int tune_recon_tile(hope_ctx *ctx, int reps, float *ms_out, cudaStream_t st) {
+  Grid &g = ctx->grids[0];
+  int cand[3][2] = {{REC_TX, REC_TY}, {0, 0}, {12, 12}};
+  model_recon_tile(ctx, g.N, &cand[1][0], &cand[1][1]);
+  const double u0 = 2.0 * HOPE_PI * ctx->radius / (12.0 * 86400.0);
+  const double prm[3] = {0.0, u0, 2.94e4};
+  int rc = hope_initial_state(ctx, 2, prm, 3, nullptr, 0, ctx->q1, st);
+  if (rc) return rc;
+  stage_fn f = pick_stage(ctx);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int bx = g.rtx, by = g.rty;
+  for (int c = 0; c < 3; ++c) {
+    bool dup = false;
+    for (int d = 0; d < c; ++d) dup |= cand[d][0] == cand[c][0] && cand[d][1] == cand[c][1];
+    if (dup) {
+      if (ms_out) ms_out[c] = -1.0f;
+      continue;
+    }
+    g.rtx = cand[c][0];
+    g.rty = cand[c][1];
+    if ((rc = f(ctx, ctx->q1, nullptr, ctx->lbuf, 0, 0, 0, 0, LoWords(), st))) break;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && !rc; ++r) rc = f(ctx, ctx->q1, nullptr, ctx->lbuf, 0, 0, 0, 0, LoWords(), st);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    if (ms_out) ms_out[c] = ms;
+    if (ms < best) {
+      best = ms;
+      bx = cand[c][0];
+      by = cand[c][1];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g.rtx = bx;
+  g.rty = by;
+  drop_graphs(ctx);
+  cudaMemsetAsync(ctx->status, 0, sizeof(unsigned), st);
+  if (rc) return rc;
+  return cudaStreamSynchronize(st) == cudaSuccess ? HOPE_OK : HOPE_ECUDA;
+}
+
 int hope_set_recon_tile(hope_t ctx, int tx, int ty) {
   if (!ctx || ctx->scheme != HOPE_TPP || tx < 1 || ty < 1 || tx * ty > REC_MAX_THREADS) {
     set_error("hope_set_recon_tile: needs a TPP context and 1 <= tx*ty <= 512");
@@ -978,8 +1042,17 @@ int hope_recon_tile(hope_t ctx, int *tx, int *ty) {
 int hope_autotune(hope_t ctx, int reps, float *ms_out, int *tx, int *ty, int *grid) {
   if (!ctx || reps < 1) return HOPE_EINVAL;
   if (!ctx->ens) {
-    set_error("hope_autotune: only ensembles of TPP spheres use the persistent stage");
-    return HOPE_EUNSUPPORTED;
+    if (ctx->scheme != HOPE_TPP || ctx->grids.size() != 1) {
+      set_error("hope_autotune: needs a TPP sphere or a TPP ensemble");
+      return HOPE_EUNSUPPORTED;
+    }
+    int rc = tune_recon_tile(ctx, reps, ms_out, nullptr);
+    if (rc) return rc;
+    const Grid &g = ctx->grids[0];
+    if (tx) *tx = g.rtx;
+    if (ty) *ty = g.rty;
+    if (grid) *grid = 6 * ((g.N + g.rtx - 1) / g.rtx) * ((g.N + g.rty - 1) / g.rty);
+    return HOPE_OK;
   }
   int rc = ensemble_autotune(ctx, ctx->q1, ctx->lbuf, reps, ms_out, nullptr);
   if (rc) return rc;

@@ -206,8 +206,9 @@ class Sphere:
         return [v[i:i + 4] for i in range(0, len(v), 4)]
 
     def autotune(self, reps=5):
-        """Re-time the persistent stage's tile shapes (ensembles); returns
-        (per-shape ms, (tx, ty), grid)."""
+        """Re-time the tile shapes -- of the persistent stage (ensembles) or of the TPP
+        reconstruction (one sphere) -- and keep the fastest; returns (per-candidate ms,
+        (tx, ty), resident grid or tile count)."""
         ms = (ctypes.c_float * 3)()
         tx, ty, grid = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         L.check(L.load().hope_autotune(self._h, reps, ms, ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(grid)))

@@ -289,8 +289,7 @@ def test_recon_tile_shape_leaves_results_bitwise_equal(hp, prec, k, N):
     dt = torch.float64 if prec == "fp64" else torch.float32
     s = hp.Sphere(N, k, precision=P)
     tx0, ty0 = s.recon_tile()
-    if prec == "fp32":
-        assert (tx0, ty0) == (16, 8)
+    assert 1 <= tx0 * ty0 <= 512
     q = to_dev(rh_perturbed(O.Oracle(N, k), 5), dt)
     ref_t = s.tendency(q).clone()
     ref_s = q.clone()
@@ -334,4 +333,19 @@ def test_fp32_mass_drift_stays_at_roundoff(hp):
     s.step(q, 300.0, 300)
     drift = abs(s.mass(q) - m0) / m0
     assert drift < 3e-7, drift
+    assert s.status() == 0
+
+
+def test_single_sphere_autotune_keeps_a_candidate_and_the_results(hp):
+    """hope_autotune on a single TPP sphere times the reconstruction tile candidates and
+    keeps the fastest; the tendency is bitwise unchanged."""
+    N, k = 33, 7
+    s = hp.Sphere(N, k, precision=hp.HOPE_FP32)
+    q = to_dev(rh_perturbed(O.Oracle(N, k), 2), torch.float32)
+    ref = s.tendency(q).clone()
+    ms, shape, tiles = s.autotune(reps=2)
+    assert len(ms) == 3 and ms[0] > 0 and ms[2] > 0 and (ms[1] > 0 or ms[1] == -1.0)
+    assert s.recon_tile() == shape
+    assert tiles == 6 * ((N + shape[0] - 1) // shape[0]) * ((N + shape[1] - 1) // shape[1])
+    assert torch.equal(s.tendency(q), ref)
     assert s.status() == 0
