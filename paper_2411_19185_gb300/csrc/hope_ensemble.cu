@@ -169,52 +169,13 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 1024 / (TX * TY) : 1)
     const int ty = rem / m.tiles_x, tx = rem - ty * m.tiles_x;
     recon_tpp_tile<T, K>(smem_raw, p, tx * TX, ty * TY, TX, TY, sa.qs + m.off, m.gext, sa.w1, m.Xg, m.t1w, m.src8, m.ep,
                                  m.sb, m.N, m.ne, sa.omega, sa.fc);
-    // fluxes of the edges between two cells of this tile, while its edge points are in
-    // L2 (the tile's final barrier makes the block's edge-point writes visible to it);
-    // the edges on tile boundaries and cube edges follow in phase 3
-    const int N = m.N, i0 = tx * TX, j0 = ty * TY;
-    const int vx = min(TX, N - i0), vy = min(TY, N - j0);
-    const int nxe = vy * (vx - 1), nye = (vy - 1) * vx;
-    const long long nx = 6LL * N * (N - 1);
-    for (int k = threadIdx.x; k < nxe + nye; k += NT) {
-      long long idx;
-      if (k < nxe) {
-        const int a = j0 + k / (vx - 1), e = i0 + 1 + k % (vx - 1);
-        idx = ((long long)p * N + a) * (N - 1) + (e - 1);
-      } else {
-        const int kk = k - nxe;
-        const int a = i0 + kk % vx, e = j0 + 1 + kk / vx;
-        idx = nx + ((long long)p * (N - 1) + (e - 1)) * N + a;
-      }
-      flux_item<T, ME>(idx, m.ep, m.mx, sa.gw, m.bedge, m.bconv, m.fx, m.fy, N, status);
-    }
   }
   if (!grid_sync(bar, status, inject)) return;
   if (stamper) sa.stamp[2] = global_ns();
-  // phase 3: the remaining edge fluxes, one thread per edge: x-edges on tile columns
-  // (e = TX, 2 TX, ...), y-edges on tile rows (e = TY, 2 TY, ...), then the cube edges
+  // phase 3: edge fluxes, one thread per edge
   for (long long it = (long long)blockIdx.x * NT + threadIdx.x; it < n_flux; it += (long long)gridDim.x * NT) {
     const MemberDev<T> &m = mem[find_member(mem, nmem, it, 2)];
-    const int N = m.N;
-    const long long nx = 6LL * N * (N - 1);
-    const int nbx = (N - 1) / TX, nby = (N - 1) / TY;
-    const long long cx = 6LL * N * nbx, cy = 6LL * N * nby;
-    const long long k = it - m.b_flux;
-    long long idx;
-    if (k < cx) {
-      const long long pa = k / nbx;  // p * N + a
-      const int e = (int)(k - pa * nbx + 1) * TX;
-      idx = pa * (N - 1) + (e - 1);
-    } else if (k < cx + cy) {
-      const long long kk = k - cx;
-      const int a = (int)(kk % N);
-      const long long pm = kk / N;  // p * nby + m
-      const int p = (int)(pm / nby), e = (int)(pm % nby + 1) * TY;
-      idx = nx + ((long long)p * (N - 1) + (e - 1)) * N + a;
-    } else {
-      idx = 2 * nx + (k - cx - cy);
-    }
-    flux_item<T, ME>(idx, m.ep, m.mx, sa.gw, m.bedge, m.bconv, m.fx, m.fy, N, status);
+    flux_item<T, ME>(it - m.b_flux, m.ep, m.mx, sa.gw, m.bedge, m.bconv, m.fx, m.fy, m.N, status);
   }
   if (!grid_sync(bar, status, inject)) return;
   if (stamper) sa.stamp[3] = global_ns();
@@ -272,7 +233,7 @@ static int build_members(hope_ctx *ctx, int TX, int TY, std::vector<MemberDev<T>
     m.b_cell = bc;
     bg += g.rows;
     bt += 6LL * m.tiles_x * m.tiles_y;
-    bf += 6LL * g.N * ((g.N - 1) / TX + (g.N - 1) / TY) + 12LL * g.N;  // edges left for phase 3
+    bf += 12LL * g.N * (g.N - 1) + 12LL * g.N;
     bc += 6LL * g.N * g.N;
     out.push_back(m);
   }
