@@ -28,7 +28,7 @@ __device__ __forceinline__ void lmars_vjp(const T qL[3], const T qR[3], const T 
   const T rLR = rcp(qL[0] * qR[0]);
   const T rL = qR[0] * rLR, rR = qL[0] * rLR;
   const T uL = qnL * rL * is11, uR = qnR * rR * is11;
-  const T sL = sqrt(phL), sR = sqrt(phR);
+  const T sL = sqrt_pos(phL), sR = sqrt_pos(phR);
   const T c = T(0.5) * (sL + sR);
   const T ms = T(0.5) * (uL + uR) - (sR - sL);
   const T ph = T(0.5) * (phL + phR - c * (uR - uL));

@@ -43,6 +43,23 @@ struct Acc<float> {
 
 template <typename T>
 __device__ __forceinline__ T rcp(T x) { return T(1) / x; }
+// FP32 path: the PTX approximate reciprocal and square root (about 1 ulp) instead of the
+// correctly rounded multi-instruction sequences; their error is of the order of the FP32
+// rounding already in every value (inputs are normal, positive geopotentials and masses).
+template <>
+__device__ __forceinline__ float rcp<float>(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ T sqrt_pos(T x) { return sqrt(x); }
+template <>
+__device__ __forceinline__ float sqrt_pos<float>(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 
 // Coriolis coefficients per panel: sin(latitude about the rotation axis) * delta
 // = c0 + c1 X + c2 Y (eq. 2.5 for an untilted axis: Y, 1 or -1).
@@ -409,7 +426,7 @@ __device__ __forceinline__ void lmars(const T qL[3], const T qR[3], const T *m5,
   const T qnL = dir ? qL[2] : qL[1], qnR = dir ? qR[2] : qR[1];
   const T rLR = rcp(qL[0] * qR[0]);  // one reciprocal for both states
   const T uL = qnL * (qR[0] * rLR) * is11, uR = qnR * (qL[0] * rLR) * is11;
-  const T sL = sqrt(phL), sR = sqrt(phR);
+  const T sL = sqrt_pos(phL), sR = sqrt_pos(phR);
   const T c = T(0.5) * (sL + sR);
   // (phR - phL) / (2 c) = sR - sL exactly, so the interface velocity needs no division
   const T ms = T(0.5) * (uL + uR) - (sR - sL);
