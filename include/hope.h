@@ -182,6 +182,10 @@ int hope_tendency_vjp(hope_t ctx, const void *q_dev, const void *lam_dqdt_dev, v
                       hope_stream_t stream);
 int hope_step_vjp(hope_t ctx, const void *qn_dev, const void *lam_np1_dev, void *lam_n_dev,
                   double dt, hope_stream_t stream);
+/* hope_step_vjp of an SSP-RK3 step regardless of the context's default stepper (the
+   adjoint of hope_step_ssprk3). */
+int hope_step_ssprk3_vjp(hope_t ctx, const void *qn_dev, const void *lam_np1_dev, void *lam_n_dev,
+                         double dt, hope_stream_t stream);
 
 /*
  * Step tapes for reverse sweeps over recomputed steps (the checkpointed recompute of the

@@ -22,7 +22,7 @@ EXPORTED = [
     "hope_total_mass", "hope_status", "hope_ghost_nnz", "hope_launches_per_stage", "hope_strerror",
     "hope_last_error_message", "hope_measure_fma_peak", "hope_set_profiling", "hope_kernel_times",
     "hope_total_mass_noalloc", "hope_autotune", "hope_inject_fault", "hope_set_recon_tile", "hope_recon_tile",
-    "hope_tape_bytes", "hope_step_record", "hope_step_vjp_tape",
+    "hope_tape_bytes", "hope_step_record", "hope_step_vjp_tape", "hope_step_ssprk3_vjp",
 ]
 
 
@@ -86,6 +86,7 @@ def load():
         "hope_tape_bytes": (i, [vp, P(sz)]),
         "hope_step_record": (i, [vp, vp, d, vp, vp]),
         "hope_step_vjp_tape": (i, [vp, vp, vp, vp, vp, d, vp]),
+        "hope_step_ssprk3_vjp": (i, [vp, vp, vp, vp, d, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

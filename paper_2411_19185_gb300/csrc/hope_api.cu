@@ -787,8 +787,21 @@ int hope_tendency_vjp(hope_t ctx, const void *q_dev, const void *lam_dqdt_dev, v
   return pick_vjp(ctx)(ctx, q_dev, lam_dqdt_dev, lam_q_dev, cb, (cudaStream_t)stream);
 }
 
+static int step_vjp_impl(hope_t ctx, int rk, const void *qn_dev, const void *lam_np1_dev, void *lam_n_dev,
+                         double dt, hope_stream_t stream);
+
 int hope_step_vjp(hope_t ctx, const void *qn_dev, const void *lam_np1_dev, void *lam_n_dev, double dt,
                   hope_stream_t stream) {
+  return ctx ? step_vjp_impl(ctx, ctx->rk, qn_dev, lam_np1_dev, lam_n_dev, dt, stream) : HOPE_EINVAL;
+}
+
+int hope_step_ssprk3_vjp(hope_t ctx, const void *qn_dev, const void *lam_np1_dev, void *lam_n_dev, double dt,
+                         hope_stream_t stream) {
+  return step_vjp_impl(ctx, HOPE_SSPRK3, qn_dev, lam_np1_dev, lam_n_dev, dt, stream);
+}
+
+static int step_vjp_impl(hope_t ctx, int rk, const void *qn_dev, const void *lam_np1_dev, void *lam_n_dev,
+                         double dt, hope_stream_t stream) {
   if (!ctx || !qn_dev || !lam_np1_dev || !lam_n_dev || lam_n_dev == qn_dev || lam_n_dev == lam_np1_dev ||
       !(dt == dt)) {
     set_error("hope_step_vjp: invalid or overlapping arguments");
@@ -800,7 +813,7 @@ int hope_step_vjp(hope_t ctx, const void *qn_dev, const void *lam_np1_dev, void 
   stage_fn f = pick_stage(ctx);
   vjp_fn v = pick_vjp(ctx);
   // recompute the stage states q1, q2 from q^n
-  if (ctx->rk == HOPE_WSRK3) {
+  if (rk == HOPE_WSRK3) {
     if ((rc = f(ctx, qn_dev, qn_dev, ctx->q1, 1, 1.0, 0.0, dt / 3.0, LoWords(), st))) return rc;
     if ((rc = f(ctx, ctx->q1, qn_dev, ctx->q2, 1, 1.0, 0.0, dt / 2.0, LoWords(), st))) return rc;
     VjpComb c3;  // lam** = dt L^T(q**) lam

@@ -144,6 +144,14 @@ class Sphere:
                                        _stream()))
         return out
 
+    def step_ssprk3_vjp(self, qn, lam_np1, dt, out=None):
+        """step_vjp of an SSP-RK3 step whatever the context's default stepper."""
+        if out is None:
+            out = torch.empty_like(qn)
+        L.check(L.load().hope_step_ssprk3_vjp(self._h, _ptr(qn, self), _ptr(lam_np1, self), _ptr(out, self),
+                                              float(dt), _stream()))
+        return out
+
     def tape_bytes(self):
         """Bytes of one step's tape (stage states, ghost rings, edge points)."""
         n = ctypes.c_size_t()

@@ -228,3 +228,14 @@ def test_rollout_with_tapes_equals_rollout_with_recompute(hp):
         (w * qT).sum().backward()
         grads.append(x.grad.clone())
     assert (torch.linalg.norm(grads[0] - grads[1]) / torch.linalg.norm(grads[1])).item() < 1e-13
+
+
+def test_ssprk3_step_vjp_ignores_the_default_stepper(hp):
+    """hope_step_ssprk3_vjp on a Wicker-Skamarock context equals hope_step_vjp on an
+    SSP-RK3 context (the same adjoint, bitwise)."""
+    N, k = 10, 5
+    s_ws = hp.Sphere(N, k, rk=hp.HOPE_WSRK3)
+    s_ssp = hp.Sphere(N, k, rk=hp.HOPE_SSPRK3)
+    q = state(N, 8)
+    lam = torch.from_numpy(fd_direction(q.shape, 9)).cuda()
+    assert torch.equal(s_ws.step_ssprk3_vjp(q, lam, 600.0), s_ssp.step_vjp(q, lam, 600.0))
