@@ -95,6 +95,51 @@ static void model_recon_tile(const hope_ctx *ctx, int N, int *tx, int *ty) {
     }
 }
 
+// Tile of the forward WENO2D kernel (one thread per cell, ~1e5 FP64 flops per cell at
+// k = 9): FP64 contexts deal tiles of 96..256 cells (whole warps of work each) to the least
+// loaded SM and keep the shape with the smallest most-loaded SM that fits the shared
+// memory; FP32 keeps 16 x 8.
+static void choose_weno_tile(const hope_ctx *ctx, Grid &g) {
+  g.wtx = REC_TX;
+  g.wty = REC_TY;
+  if (ctx->scheme != HOPE_WENO2D || ctx->prec != HOPE_FP64) return;
+  int nsm = 0, optin = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+  if (nsm < 1) return;
+  const int N = g.N, K = ctx->k, L = (K + 1) / 2, S = L * L, npos = L + 2, npoc = 4 * L + L * L;
+  auto cost = [&](int TX, int TY) {
+    std::priority_queue<double, std::vector<double>, std::greater<double>> heap;
+    for (int s = 0; s < nsm; ++s) heap.push(0.0);
+    double worst = 0.0;
+    for (int p = 0; p < 6; ++p)
+      for (int by = 0; by < (N + TY - 1) / TY; ++by)
+        for (int bx = 0; bx < (N + TX - 1) / TX; ++bx) {
+          const int cells = std::min(TX, N - bx * TX) * std::min(TY, N - by * TY);
+          double l = heap.top() + (cells + 31) / 32;
+          heap.pop();
+          heap.push(l);
+          worst = std::max(worst, l);
+        }
+    return worst;
+  };
+  double best = cost(g.wtx, g.wty);
+  for (int TY = 2; TY <= 32; ++TY)
+    for (int TX = 4; TX <= 32; ++TX) {
+      const int T = TX * TY, threads = (T + 31) / 32 * 32;
+      if (T < 96 || threads > 256) continue;  // at least three warps per block
+      const size_t smem = sizeof(double) * (3 * (TY + K - 1) * (TX + K - 1) + npos * L * L + npoc * 2 * S +
+                                            npoc * 2 + L * (L * L + L) + S * S + 3 * L * L * threads);
+      if (smem > (size_t)optin) continue;
+      const double c = cost(TX, TY);
+      if (c < best * 0.999) {
+        best = c;
+        g.wtx = TX;
+        g.wty = TY;
+      }
+    }
+}
+
 // Set-up choice: the FP64 kernel is bound by the FP64 pipe, so it takes the model's shape;
 // the FP32 kernel is latency-bound and starts from 16 x 8 (hope_init_grid then times the
 // candidates, tune_recon_tile).
@@ -536,6 +581,7 @@ static int init_impl(int n_members, const int *Ns, int order, int scheme, const 
     TRY(alloc(&gr.fy, es * 3 * 6 * (N + 1) * N));
     TRY(alloc(&gr.sb, es * 2 * 6 * N * N));
     choose_recon_tile(ctx, gr);
+    choose_weno_tile(ctx, gr);
   }
   ctx->total = off;
   const size_t es = ctx->esize;

@@ -27,6 +27,7 @@ struct CubeEdge {
 struct Grid {
   int N = 0, ne = 0;
   int rtx = 16, rty = 8;  // TPP reconstruction tile (cells) of the per-kernel path
+  int wtx = 16, wty = 8;  // forward WENO2D tile (cells)
   int ghost_grid = 0, flux_grid = 0, flux_tpb = 0;  // launch shapes, set on first use
   size_t off = 0;   // element offset of this member in ensemble states
   bool owns_tables = true;  // false: tables shared with an earlier member of equal N

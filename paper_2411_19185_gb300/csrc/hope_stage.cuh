@@ -79,14 +79,13 @@ int launch_recon_weno(hope_ctx *ctx, Grid &g, const T *qs, cudaStream_t st) {
     set_error("WENO2D supports orders up to 9");
     return HOPE_EUNSUPPORTED;
   } else {
-  using W = WenoShape<T, K>;
-  const int N = g.N;
-  dim3 grid((N + REC_TX - 1) / REC_TX, (N + REC_TY - 1) / REC_TY, 6);
-  size_t smem = sizeof(T) * W::smem_elems();
-  k_recon_weno<T, K><<<grid, REC_TX * REC_TY, smem, st>>>(
+  const int N = g.N, TX = g.wtx, TY = g.wty;
+  dim3 grid((N + TX - 1) / TX, (N + TY - 1) / TY, 6);
+  const int threads = (TX * TY + 31) / 32 * 32;
+  k_recon_weno<T, K><<<grid, threads, weno_tile_smem_bytes<T, K>(TX, TY, threads), st>>>(
       qs, (const T *)g.gext, (const T *)ctx->wsub, (const T *)ctx->gpm, (const T *)ctx->sig,
-      (const T *)ctx->bform, (const T *)ctx->bcoef, (const T *)g.Xg, (const T *)g.t1w, (T *)g.ep, (T *)g.sb, N, g.ne, (T)ctx->omega,
-      fcoef<T>(ctx), (T)ctx->eps);
+      (const T *)ctx->bform, (const T *)ctx->bcoef, (const T *)g.Xg, (const T *)g.t1w, (T *)g.ep, (T *)g.sb, N, g.ne,
+      TX, TY, (T)ctx->omega, fcoef<T>(ctx), (T)ctx->eps);
   return HOPE_OK;
   }
 }
@@ -106,7 +105,11 @@ int weno_set_smem_attr() {
       return HOPE_ECUDA;
     }
   }
-  cudaError_t e = cudaFuncSetAttribute(k_recon_weno<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int optin = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  (void)smem;
+  cudaError_t e = cudaFuncSetAttribute(k_recon_weno<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   if (e != cudaSuccess) {
     set_error(std::string("WENO shared memory attribute: ") + cudaGetErrorString(e));
     return HOPE_ECUDA;

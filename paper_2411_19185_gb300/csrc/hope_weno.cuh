@@ -34,46 +34,76 @@ struct WenoShape {
   }
 };
 
+// Shared memory of the forward WENO kernel for a TX x TY tile and NT threads.
 template <typename T, int K>
-__global__ void __launch_bounds__(REC_TX *REC_TY)
+__host__ __device__ constexpr size_t weno_tile_smem_bytes(int TX, int TY, int NT) {
+  using W = WenoShape<T, K>;
+  return sizeof(T) * (3 * (TY + K - 1) * (TX + K - 1) + W::NPOS * W::L * W::L + W::NPOC * 2 * W::S + W::NPOC * 2 +
+                      W::L * (W::L * W::L + W::L) + W::S * W::S + 3 * W::ME * W::ME * NT);
+}
+
+// Largest thread count of a forward WENO block (one thread per cell of the tile).
+constexpr int WENO_MAX_THREADS = 256;
+
+// One block per tile of TX x TY cells (runtime shape; blockIdx.z: panel); cells of a tile
+// cut by the panel's edge are packed onto the first vx * vy threads.
+template <typename T, int K>
+__global__ void __launch_bounds__(WENO_MAX_THREADS)
     k_recon_weno(const T *__restrict__ q, const T *__restrict__ gext, const T *__restrict__ wsub_g,
                  const T *__restrict__ gpm_g, const T *__restrict__ sig_g, const T *__restrict__ bform_g,
                  const T *__restrict__ bcoef_g, const T *__restrict__ Xg, const T *__restrict__ t1w, T *__restrict__ ep, T *__restrict__ sb,
-                 int N, int ne, T omega, FCoef<T> fc, T eps) {
+                 int N, int ne, int TX, int TY, T omega, FCoef<T> fc, T eps) {
   using W = WenoShape<T, K>;
-  using SH = Shape<K>;
-  constexpr int L = W::L, S = W::S, ME = W::ME, NPOS = W::NPOS, NPOC = W::NPOC, NT = W::NT;
+  constexpr int L = W::L, S = W::S, ME = W::ME, NPOS = W::NPOS, NPOC = W::NPOC, H = (K - 1) / 2;
+  const int NT = blockDim.x, RW = TX + 2 * H, RH = TY + 2 * H;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *raw = reinterpret_cast<T *>(smem_raw);        // [3][RH][RW]
-  T *wsub = raw + 3 * SH::RH * SH::RW;             // [NPOS][L][L]
+  T *wsub = raw + 3 * RH * RW;                     // [NPOS][L][L]
   T *gpm = wsub + NPOS * L * L;                    // [NPOC][2][S]
   T *sig = gpm + NPOC * 2 * S;                     // [NPOC][2]
   T *bform = sig + NPOC * 2;                       // [L][L*L + L] Winv, row sums
   T *bcoef = bform + L * (L * L + L);              // [L][L][L][L]
   T *cq = bcoef + S * S;                           // [3][ME*ME][NT]
   const int p = blockIdx.z;
-  const int i0 = blockIdx.x * REC_TX, j0 = blockIdx.y * REC_TY;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int vx = min(TX, N - i0), vy = min(TY, N - j0);
   for (int t = threadIdx.x; t < NPOS * L * L; t += blockDim.x) wsub[t] = wsub_g[t];
   for (int t = threadIdx.x; t < NPOC * 2 * S; t += blockDim.x) gpm[t] = gpm_g[t];
   for (int t = threadIdx.x; t < NPOC * 2; t += blockDim.x) sig[t] = sig_g[t];
   for (int t = threadIdx.x; t < L * (L * L + L); t += blockDim.x) bform[t] = bform_g[t];
   for (int t = threadIdx.x; t < S * S; t += blockDim.x) bcoef[t] = bcoef_g[t];
-  load_tile<T, K>(raw, q, gext, p, i0, j0, N, ne);
+  {
+    // the valid part of the extended tile: interior cells from q, ring cells from gext
+    const int vw = vx + 2 * H, vh = vy + 2 * H;
+    const size_t pn = (size_t)6 * N * N, pe = (size_t)6 * ne * ne;
+    for (int idx = threadIdx.x; idx < 3 * vh * vw; idx += blockDim.x) {
+      const int v = idx / (vh * vw);
+      const int rem = idx - v * vh * vw;
+      const int r = rem / vw, c = rem - r * vw;
+      const int ii = i0 + c - H, jj = j0 + r - H;
+      T val = T(0);
+      if (ii >= 0 && ii < N && jj >= 0 && jj < N)
+        val = q[v * pn + ((size_t)p * N + jj) * N + ii];
+      else if (ii >= -H && ii < N + H && jj >= -H && jj < N + H)
+        val = gext[v * pe + ((size_t)p * ne + (jj + H)) * ne + (ii + H)];
+      raw[(v * RH + r) * RW + c] = val;
+    }
+  }
   __syncthreads();
   const int tid = threadIdx.x;
-  const int tx = tid % REC_TX, ty = tid / REC_TX;
+  if (tid >= vx * vy) return;
+  const int ty = tid / vx, tx = tid - ty * vx;
   const int i = i0 + tx, j = j0 + ty;
-  if (i >= N || j >= N) return;
   const size_t pn = (size_t)6 * N * N;
   const size_t cell = ((size_t)p * N + j) * N + i;
   const T tau_scale = T(2) / (T(S + 1) * T(S));
 
 #pragma unroll 1
   for (int v = 0; v < 3; ++v) {
-    const T *Qv = raw + (v * SH::RH + ty) * SH::RW + tx;  // Q(r, c) = Qv[r * RW + c]
+    const T *Qv = raw + (v * RH + ty) * RW + tx;  // Q(r, c) = Qv[r * RW + c]
     // ---------------------------------------------------------------- beta (eq. 3.25)
     // on Q - q_c (beta ignores constants): Zx = Winv_x (Q - q_c) row-wise, then Winv_y.
-    const T qc = Qv[SH::H * SH::RW + SH::H];
+    const T qc = Qv[H * RW + H];
     T f[S];
 #pragma unroll
     for (int t = 0; t < S; ++t) f[t] = T(0);
@@ -88,7 +118,7 @@ __global__ void __launch_bounds__(REC_TX *REC_TY)
         for (int r = 0; r < K; ++r) {
           T s = -qc * rs;
 #pragma unroll
-          for (int a = 0; a < L; ++a) s = fma(Wx[kp * L + a], Qv[r * SH::RW + sx + a], s);
+          for (int a = 0; a < L; ++a) s = fma(Wx[kp * L + a], Qv[r * RW + sx + a], s);
           Zx[r] = s;
         }
 #pragma unroll
@@ -130,7 +160,7 @@ __global__ void __launch_bounds__(REC_TX *REC_TY)
         for (int r = 0; r < K; ++r) {
           T s = 0;
 #pragma unroll
-          for (int a = 0; a < L; ++a) s = fma(wx[a], Qv[r * SH::RW + sx + a], s);
+          for (int a = 0; a < L; ++a) s = fma(wx[a], Qv[r * RW + sx + a], s);
           Xc[r] = s;
         }
 #pragma unroll
