@@ -82,10 +82,20 @@ int launch_recon_weno(hope_ctx *ctx, Grid &g, const T *qs, cudaStream_t st) {
   const int N = g.N, TX = g.wtx, TY = g.wty;
   dim3 grid((N + TX - 1) / TX, (N + TY - 1) / TY, 6);
   const int threads = (TX * TY + 31) / 32 * 32;
-  k_recon_weno<T, K><<<grid, threads, weno_tile_smem_bytes<T, K>(TX, TY, threads), st>>>(
-      qs, (const T *)g.gext, (const T *)ctx->wsub, (const T *)ctx->gpm, (const T *)ctx->sig,
-      (const T *)ctx->bform, (const T *)ctx->bcoef, (const T *)g.Xg, (const T *)g.t1w, (T *)g.ep, (T *)g.sb, N, g.ne,
-      TX, TY, (T)ctx->omega, fcoef<T>(ctx), (T)ctx->eps);
+  const size_t smem = weno_tile_smem_bytes<T, K>(TX, TY, threads);
+  auto args = [&](auto kern) {
+    kern<<<grid, threads, smem, st>>>(qs, (const T *)g.gext, (const T *)ctx->wsub, (const T *)ctx->gpm,
+                                      (const T *)ctx->sig, (const T *)ctx->bform, (const T *)ctx->bcoef,
+                                      (const T *)g.Xg, (const T *)g.t1w, (T *)g.ep, (T *)g.sb, N, g.ne, TX, TY,
+                                      (T)ctx->omega, fcoef<T>(ctx), (T)ctx->eps);
+  };
+  if constexpr (sizeof(T) == 8) {
+    if (TX != REC_TX || TY != REC_TY) {
+      args(k_recon_weno<T, K, true>);
+      return HOPE_OK;
+    }
+  }
+  args(k_recon_weno<T, K, false>);
   return HOPE_OK;
   }
 }
@@ -109,7 +119,11 @@ int weno_set_smem_attr() {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   (void)smem;
-  cudaError_t e = cudaFuncSetAttribute(k_recon_weno<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  cudaError_t e = cudaFuncSetAttribute(k_recon_weno<T, K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if constexpr (sizeof(T) == 8) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_recon_weno<T, K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  }
   if (e != cudaSuccess) {
     set_error(std::string("WENO shared memory attribute: ") + cudaGetErrorString(e));
     return HOPE_ECUDA;

@@ -45,17 +45,21 @@ __host__ __device__ constexpr size_t weno_tile_smem_bytes(int TX, int TY, int NT
 // Largest thread count of a forward WENO block (one thread per cell of the tile).
 constexpr int WENO_MAX_THREADS = 256;
 
-// One block per tile of TX x TY cells (runtime shape; blockIdx.z: panel); cells of a tile
-// cut by the panel's edge are packed onto the first vx * vy threads.
-template <typename T, int K>
-__global__ void __launch_bounds__(WENO_MAX_THREADS)
+// One block per tile of TX x TY cells (blockIdx.z: panel); cells of a tile cut by the
+// panel's edge are packed onto the first vx * vy threads.  RT = false compiles the
+// default 16 x 8 tile with 128 threads as constants (the FP32 kernel is bound by its
+// instruction count, and constant strides save the address arithmetic); RT = true takes
+// the shape at run time (FP64 tiles chosen for balance).
+template <typename T, int K, bool RT = false>
+__global__ void __launch_bounds__(RT ? WENO_MAX_THREADS : REC_TX * REC_TY)
     k_recon_weno(const T *__restrict__ q, const T *__restrict__ gext, const T *__restrict__ wsub_g,
                  const T *__restrict__ gpm_g, const T *__restrict__ sig_g, const T *__restrict__ bform_g,
                  const T *__restrict__ bcoef_g, const T *__restrict__ Xg, const T *__restrict__ t1w, T *__restrict__ ep, T *__restrict__ sb,
-                 int N, int ne, int TX, int TY, T omega, FCoef<T> fc, T eps) {
+                 int N, int ne, int TXr, int TYr, T omega, FCoef<T> fc, T eps) {
   using W = WenoShape<T, K>;
   constexpr int L = W::L, S = W::S, ME = W::ME, NPOS = W::NPOS, NPOC = W::NPOC, H = (K - 1) / 2;
-  const int NT = blockDim.x, RW = TX + 2 * H, RH = TY + 2 * H;
+  const int TX = RT ? TXr : REC_TX, TY = RT ? TYr : REC_TY;
+  const int NT = RT ? (int)blockDim.x : REC_TX * REC_TY, RW = TX + 2 * H, RH = TY + 2 * H;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *raw = reinterpret_cast<T *>(smem_raw);        // [3][RH][RW]
   T *wsub = raw + 3 * RH * RW;                     // [NPOS][L][L]
