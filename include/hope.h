@@ -295,6 +295,20 @@ int hope_inject_fault(hope_t ctx, int what);
 /* Total nonzeros of the ghost operator G (eq. 7.12) and its row count. */
 int hope_ghost_nnz(hope_t ctx, long long *nnz, long long *rows);
 
+/*
+ * Host-only check of the ghost operator's storage (eq. 7.12; needs no GPU): builds the
+ * operator for (N, order, precision) on the host as hope_init_grid does and reports
+ * whether every row is stored as the rotated copy of a panel-0 representative
+ * (symmetric), the largest relative deviation of a directly composed row from its
+ * representative's image (max_dev_sym), and the largest relative difference between the
+ * stored form as the ghost kernel applies it (the row's columns with their symmetry codes,
+ * the representative's weights) and the full operator on a seeded state
+ * (max_dev_apply).  HOPE_EINVAL for N < 1, an unsupported order or precision, or null
+ * outputs.
+ */
+int hope_ghost_selfcheck(int N, int order, int precision, int *symmetric, double *max_dev_sym,
+                         double *max_dev_apply);
+
 /* Launch configuration introspection for profiling: number of kernel launches one
    tendency enqueues. */
 int hope_launches_per_stage(hope_t ctx, int *launches);

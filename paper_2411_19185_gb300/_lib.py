@@ -23,6 +23,7 @@ EXPORTED = [
     "hope_last_error_message", "hope_measure_fma_peak", "hope_set_profiling", "hope_kernel_times",
     "hope_total_mass_noalloc", "hope_autotune", "hope_inject_fault", "hope_set_recon_tile", "hope_recon_tile",
     "hope_tape_bytes", "hope_step_record", "hope_step_vjp_tape", "hope_step_ssprk3_vjp",
+    "hope_ghost_selfcheck",
 ]
 
 
@@ -87,6 +88,7 @@ def load():
         "hope_step_record": (i, [vp, vp, d, vp, vp]),
         "hope_step_vjp_tape": (i, [vp, vp, vp, vp, vp, d, vp]),
         "hope_step_ssprk3_vjp": (i, [vp, vp, vp, vp, d, vp]),
+        "hope_ghost_selfcheck": (i, [i, i, i, P(i), P(d), P(d)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -804,6 +804,86 @@ int hope_status(hope_t ctx, unsigned *device_status) {
   return HOPE_OK;
 }
 
+int hope_ghost_selfcheck(int N, int order, int precision, int *symmetric, double *max_dev_sym,
+                         double *max_dev_apply) {
+  if (N < 1 || order < 3 || order > HOPE_MAXK || order % 2 == 0 ||
+      (precision != HOPE_FP64 && precision != HOPE_FP32) || !symmetric || !max_dev_sym || !max_dev_apply) {
+    set_error("hope_ghost_selfcheck: invalid argument");
+    return HOPE_EINVAL;
+  }
+  hope_ctx ctx;
+  ctx.k = order;
+  ctx.H = (order - 1) / 2;
+  ctx.me = (order + 1) / 2;
+  ctx.prec = precision;
+  ctx.scheme = HOPE_TPP;
+  ctx.ghost_iters = 10;
+  std::vector<double> nodes(ctx.me), weights(ctx.me);
+  gauss_legendre(ctx.me, nodes.data(), weights.data());
+  std::vector<int> rowptr, cols, dst;
+  std::vector<double> vals;
+  GhostSplit split;
+  GhostSym sym;
+  const bool fp64 = precision == HOPE_FP64;
+  int rc = build_ghost_operator(&ctx, N, nodes, weights, rowptr, cols, vals, dst, fp64 ? &split : nullptr, &sym);
+  if (rc) return rc;
+  *symmetric = sym.symmetric ? 1 : 0;
+  *max_dev_sym = sym.max_dev;
+  // the stored form as the ghost kernel reads it (row's columns with their input codes,
+  // the representative's weights, the row's output code) against the full operator, on a
+  // seeded state
+  const size_t pn = (size_t)6 * N * N;
+  std::vector<double> q(3 * pn);
+  unsigned long long st = 0x9E3779B97F4A7C15ull;
+  for (auto &v : q) {
+    st = st * 6364136223846793005ull + 1442695040888963407ull;
+    v = (double)(st >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+  }
+  auto apply_code = [](int code, double &x, double &y) {
+    const double a = (code & 1) ? y : x, b = (code & 1) ? x : y;
+    x = (code & 2) ? -a : a;
+    y = (code & 4) ? -b : b;
+  };
+  const int rows = (int)dst.size();
+  std::vector<int> tagged(cols.size());
+  for (size_t e = 0; e < cols.size(); ++e) tagged[e] = cols[e] | (sym.ccode[e] << 28);
+  double worst = 0.0, scale = 0.0;
+  for (int r = 0; r < rows; ++r) {
+    double f[3] = {0, 0, 0}, g3[3] = {0, 0, 0};
+    for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+      const int c = cols[e];
+      const double *v = &vals[(size_t)5 * e];
+      f[0] += v[0] * q[c];
+      f[1] += v[1] * q[pn + c] + v[2] * q[2 * pn + c];
+      f[2] += v[3] * q[pn + c] + v[4] * q[2 * pn + c];
+    }
+    const int info = sym.finfo[r], wrow = info & 0x0FFFFFFF, oc = info >> 28;
+    for (int part = 0; part < (fp64 ? 2 : 1); ++part) {
+      const std::vector<int> &ptr = !fp64 ? rowptr : (part ? split.tail_ptr : split.head_ptr);
+      const std::vector<int> &col = !fp64 ? tagged : (part ? split.tail_col : split.head_col);
+      for (int t = ptr[r]; t < ptr[r + 1]; ++t) {
+        const int c = col[t] & 0x0FFFFFFF, code = col[t] >> 28, wi = ptr[wrow] + (t - ptr[r]);
+        double w[5];
+        for (int k = 0; k < 5; ++k)
+          w[k] = !fp64 ? vals[(size_t)5 * wi + k]
+                       : (part ? (double)split.tail_val[(size_t)5 * wi + k] : split.head_val[(size_t)5 * wi + k]);
+        double a1 = q[pn + c], a2 = q[2 * pn + c];
+        apply_code(code, a1, a2);
+        g3[0] += w[0] * q[c];
+        g3[1] += w[1] * a1 + w[2] * a2;
+        g3[2] += w[3] * a1 + w[4] * a2;
+      }
+    }
+    apply_code(oc, g3[1], g3[2]);
+    for (int v = 0; v < 3; ++v) {
+      worst = fmax(worst, fabs(g3[v] - f[v]));
+      scale = fmax(scale, fabs(f[v]));
+    }
+  }
+  *max_dev_apply = scale > 0.0 ? worst / scale : worst;
+  return HOPE_OK;
+}
+
 int hope_ghost_nnz(hope_t ctx, long long *nnz, long long *rows) {
   if (!ctx || !nnz || !rows) return HOPE_EINVAL;
   *nnz = 0;

@@ -64,3 +64,33 @@ def test_product_path_has_no_oracle_import():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 txt = open(os.path.join(dp, f)).read()
                 assert "oracle" not in txt.lower(), os.path.join(dp, f)
+
+
+@pytest.mark.parametrize("N,k,prec", [(8, 3, 0), (10, 5, 0), (9, 7, 0), (10, 5, 1), (12, 11, 0), (9, 9, 1)])
+def test_ghost_operator_storage_selfcheck_on_host(lib, N, k, prec):
+    """The ghost operator built on the host (no GPU) is stored as rotated copies of panel-0
+    representatives: every composed row equals its representative's image to 1e-12, and
+    the stored form, applied as the ghost kernel applies it (columns with symmetry codes,
+    representative weights; FP64 head and FP32 tail), equals the full operator on a seeded
+    state to 1e-13 (FP64 contexts: the tail's FP32 weights) or exactly (FP32 contexts)."""
+    s, a, b = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+    rc = lib.hope_ghost_selfcheck(N, k, prec, ctypes.byref(s), ctypes.byref(a), ctypes.byref(b))
+    assert rc == 0
+    assert s.value == 1
+    assert a.value < 1e-12
+    assert b.value < (1e-13 if prec == 0 else 1e-15)
+
+
+def test_ghost_selfcheck_rejects_invalid_arguments(lib):
+    s, a, b = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+    for args in [(0, 5, 0), (10, 4, 0), (10, 13, 0), (10, 5, 2)]:
+        assert lib.hope_ghost_selfcheck(*args, ctypes.byref(s), ctypes.byref(a), ctypes.byref(b)) == -1  # EINVAL
+
+
+def test_ghost_storage_falls_back_when_rows_are_not_images(lib):
+    """A stencil wider than the panel (N = 7, k = 9) amplifies round-off in the composed
+    rows beyond the 1e-12 acceptance, so every row keeps its own weights (identity codes)
+    and the stored form is the full operator exactly."""
+    s, a, b = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+    assert lib.hope_ghost_selfcheck(7, 9, 0, ctypes.byref(s), ctypes.byref(a), ctypes.byref(b)) == 0
+    assert s.value == 0 and a.value > 1e-12 and b.value == 0.0
