@@ -38,7 +38,7 @@ def _rank(rank, world, port, out):
 
 def test_two_gloo_ranks_take_the_slowest_rank_and_sum_the_work():
     world, port = 2, _free_port()
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
     for r in range(world):
         w, rr, local, job_s, value = out[r]
