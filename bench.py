@@ -86,6 +86,58 @@ def roofline(flops_per_stage, stages_per_s, peak):
             "peak_tflops": peak / 1e12, "frac": a / peak}
 
 
+def measured_hbm_bps(default_gbs=6800.0):
+    """Copy bandwidth of the GB300s (MEASURED_PEAKS.json beside this file), else the
+    fallback figure; returns (bytes/s, source)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]) * 1e9, "measured"
+    except (OSError, KeyError, ValueError):
+        return default_gbs * 1e9, "fallback"
+
+
+def step_roofline(flops_per_stage, state_bytes, g_bytes, stage_s, alu_peak, hbm_bps):
+    """Whole-stage roofline, two ways: the state alone (q_stage and q^n read, q_next written)
+    and the state plus one pass over the ghost operator streamed as a sparse matrix
+    (nnz x (weight + index) bytes).  Roofline time = max(FLOPs / ALU peak, bytes / HBM);
+    frac = roofline time / measured stage time."""
+    out = {"flops_per_stage": flops_per_stage, "alu_peak_tflops": alu_peak / 1e12, "hbm_gbs": hbm_bps / 1e9}
+    for name, b in (("state", state_bytes), ("state_plus_G", state_bytes + g_bytes)):
+        t_alu, t_hbm = flops_per_stage / alu_peak, b / hbm_bps
+        out[name] = {"bytes_per_stage": b, "bound": "alu" if t_alu >= t_hbm else "hbm",
+                     "roofline_ms": 1e3 * max(t_alu, t_hbm), "frac": max(t_alu, t_hbm) / stage_s}
+    return out
+
+
+def cpu_model():
+    """The host CPU's model line from /proc/cpuinfo (x86 'model name', Arm implementer/part)."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return None
+    for line in info:
+        if line.lower().startswith("model name"):
+            return line.split(":", 1)[1].strip()
+    fields = {}
+    for line in info:
+        if ":" in line:
+            k, v = (x.strip() for x in line.split(":", 1))
+            fields.setdefault(k, v)
+    if "CPU implementer" in fields or "CPU part" in fields:
+        return "arm implementer %s part %s" % (fields.get("CPU implementer", "?"), fields.get("CPU part", "?"))
+    return None
+
+
+def set_host_threads(n):
+    """Thread count of the OpenMP runtime the oracle uses (libgomp); False if unavailable."""
+    import ctypes
+    try:
+        ctypes.CDLL("libgomp.so.1").omp_set_num_threads(int(n))
+        return True
+    except OSError:
+        return False
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -559,11 +611,26 @@ def main():
         "device_status": status,
         "forms": forms,
     }
+    g_nnz = s.ghost_nnz()[0]
+    hbm_bps, hbm_src = measured_hbm_bps()
+    line["step_roofline"] = step_roofline(stage_flops(N_CELLS, ORDER, g_nnz), 72 * cells, 12 * g_nnz,
+                                          total_ms * 1e-3 / args.steps / 3, fp64_peak, hbm_bps)
+    line["step_roofline"]["hbm_source"] = hbm_src
+    if forms:
+        for name, f in forms.items():
+            if isinstance(f, dict) and ("value" in f or "forward" in f):
+                f["vs_fp64_path"] = f.get("value", f.get("forward")) / value
     if world == 1 and not args.no_cpu_baseline:
         v, el = cpu_baseline(args.cpu_stages)
         line["cpu_baseline"] = {"value": v, "unit": "cell-stage/s", "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": "%d tendency evaluations (stages) of the full workload, %.1f s" %
-                                          (args.cpu_stages, el)}
+                                          (args.cpu_stages, el),
+                                "cpu_model": cpu_model()}
+        if set_host_threads(1):
+            v1, el1 = cpu_baseline(max(1, args.cpu_stages // 30))
+            set_host_threads(os.cpu_count())
+            line["cpu_baseline"]["single_core"] = {"value": v1, "sample": "%d stages, %.1f s" %
+                                                   (max(1, args.cpu_stages // 30), el1)}
     print(json.dumps(line))
 
 
