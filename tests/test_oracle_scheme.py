@@ -23,7 +23,7 @@ def _table51():
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("k", [3, 5])
+@pytest.mark.parametrize("k", [3, 5, 7])
 def test_table_5_1_geostrophic_12_days(k):
     """Table 5.1 (section 5.1): steady geostrophic flow, C30, Wicker-Skamarock RK3,
     dt = 600 s, 12 days.  The FP64 oracle reproduces the printed L1/L2/Linf errors
