@@ -291,3 +291,30 @@ def test_lmars_upwind_and_rest_state():
     assert F[0] > 0
     F0 = o.lmars(0, 0.0, 0.0, qL, qL)
     assert F0[0] == 0.0
+
+
+def test_lmars_interface_velocity_identity_of_reading_c24():
+    """Reading c24: eq. 3.32's (phi_R - phi_L) / (2 c) with c = (sqrt(phi_L) + sqrt(phi_R)) / 2
+    (eqs. 3.34-3.35) equals sqrt(phi_R) - sqrt(phi_L), the form the library evaluates.  The
+    oracle's mass flux (printed form) is reproduced from the identity form to round-off over
+    random states, jumps of both signs included."""
+    o = O.Oracle(8, 3)
+    rng = np.random.default_rng(24)
+    r2 = o.radius ** 2
+    for _ in range(50):
+        X, Y = np.tan(rng.uniform(-0.78, 0.78, 2))
+        m = O.metric(X, Y)
+        phiL, phiR = rng.uniform(1e3, 6e4, 2)
+        uL, uR = rng.uniform(-3e-5, 3e-5, 2)
+        vL, vR = rng.uniform(-3e-5, 3e-5, 2)
+        qL = m[0] * phiL * np.array([1.0, uL, vL])
+        qR = m[0] * phiR * np.array([1.0, uR, vR])
+        for d in (0, 1):
+            g = (m[1], m[3])[d] / r2  # G^ii
+            sL, sR = np.sqrt(phiL), np.sqrt(phiR)
+            upL, upR = (uL, vL)[d] / np.sqrt(g), (uR, vR)[d] / np.sqrt(g)
+            ms = 0.5 * (upL + upR) - (sR - sL)
+            mm = ms * np.sqrt(g)
+            mass = 0.5 * (mm * (qL[0] + qR[0]) - abs(mm) * (qR[0] - qL[0]))
+            F = o.lmars(d, X, Y, qL, qR)
+            assert abs(F[0] - mass) <= 1e-12 * (abs(mm) * (qL[0] + qR[0]) + 1e-300)
