@@ -216,3 +216,43 @@ def test_ghost_fill_is_equivariant_under_cube_rotations(k, N):
         ext_r, _ = o.fill_ghosts(_rotate_field(q, R, N))
         want = _rotate_field(ext, R, ne)
         assert np.max(np.abs(ext_r - want)) < 1e-13 * np.max(np.abs(want))
+
+
+def test_ssp_rk3_local_error_is_fourth_order():
+    """SSP-RK3 (Shu-Osher form, section 3.4) is third order for nonlinear systems: on a
+    Rossby-Haurwitz state (C8, TPP3) the one-step error against 64 steps of dt/64 falls by
+    close to 2^4 = 16 when dt halves.  A misplaced stage weight (0.75/0.25 swapped, or the
+    last stage taken from q^n) drops the ratio to about 4."""
+    o = O.Oracle(8, 3)
+    q0 = o.rossby_haurwitz()
+    s = np.max(np.abs(q0), axis=(1, 2, 3), keepdims=True)
+    errs = []
+    for dt in (600.0, 300.0, 150.0):
+        ref = o.step(q0, dt / 64, 64, O.SSPRK3)
+        errs.append(np.max(np.abs(o.step(q0, dt, 1, O.SSPRK3) - ref) / s))
+    ratios = np.array(errs[:-1]) / np.array(errs[1:])
+    assert np.all((ratios > 14.0) & (ratios < 18.0)), (errs, ratios)
+
+
+def test_ws_rk3_nonlinear_defect_is_f2_over_24():
+    """Eqs. 3.39-3.41 (reading c8: every stage starts from q^n) have the Butcher weights
+    b = (0, 0, 1), c = (0, 1/3, 1/2).  They satisfy sum b = 1, b.c = 1/2 and b.A.c = 1/6 but
+    b.c^2 = 1/4 instead of 1/3: third order for linear problems, and for nonlinear ones a
+    one-step defect of -dt^3/24 f''(f, f) against any third-order step.  The oracle's
+    WS-RK3 minus its SSP-RK3, divided by dt^3 and Richardson-extrapolated in dt, equals
+    -f''(f, f)/24, with f'' a centred second difference of the tendency along f, to 5e-3
+    relative (C8, TPP3, Rossby-Haurwitz).  Starting the second stage from the first
+    stage's result instead misses it by a factor of ~1e5."""
+    o = O.Oracle(8, 3)
+    y = o.rossby_haurwitz()
+    f = o.tendency(y)
+    eps = 100.0
+    f2 = (o.tendency(y + eps * f) - 2.0 * f + o.tendency(y - eps * f)) / eps**2
+    target = -f2 / 24.0
+
+    def defect(dt):
+        return (o.step(y, dt, 1, O.WSRK3) - o.step(y, dt, 1, O.SSPRK3)) / dt**3
+
+    extrap = 2.0 * defect(150.0) - defect(300.0)
+    rel = np.linalg.norm(extrap - target) / np.linalg.norm(target)
+    assert rel < 5e-3, rel
