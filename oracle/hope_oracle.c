@@ -109,7 +109,7 @@ void orc_gauss(int m, double *x, double *w) {
 /* out[j] is the weight of cell j in the value at xi:  r = A^{-T} c(xi).      */
 /* Monomials are scaled by s = max|offset|+1/2 for conditioning only.         */
 /* ------------------------------------------------------------------------- */
-static void weights_1d_ld(int n, int o0, long double xi, long double *out) {
+static void weights_1d_any(int n, int o0, long double xi, int deriv, long double *out) {
   long double A[MAXK * MAXK], b[MAXK];
   long double s = 0.5L;
   for (int j = 0; j < n; ++j) {
@@ -128,12 +128,24 @@ static void weights_1d_ld(int n, int o0, long double xi, long double *out) {
     }
   }
   long double c = 1.0L;
-  for (int a = 0; a < n; ++a) {
-    b[a] = c;
-    c *= xi / s;
+  if (!deriv) {
+    for (int a = 0; a < n; ++a) {
+      b[a] = c;
+      c *= xi / s;
+    }
+  } else { /* d/dxi (xi/s)^a = a (xi/s)^(a-1) / s */
+    b[0] = 0.0L;
+    for (int a = 1; a < n; ++a) {
+      b[a] = (long double)a * c / s;
+      c *= xi / s;
+    }
   }
   solve_ld(n, A, b);
   for (int j = 0; j < n; ++j) out[j] = b[j];
+}
+
+static void weights_1d_ld(int n, int o0, long double xi, long double *out) {
+  weights_1d_any(n, o0, xi, 0, out);
 }
 
 void orc_weights_1d(int n, int o0, double xi, double *out) {
@@ -150,6 +162,18 @@ void orc_tpp_weights_2d(int k, double xi, double eta, double *out) {
   long double rx[MAXK], ry[MAXK];
   weights_1d_ld(k, -H, xi, rx);
   weights_1d_ld(k, -H, eta, ry);
+  for (int b = 0; b < k; ++b)
+    for (int a = 0; a < k; ++a) out[b * k + a] = (double)(rx[a] * ry[b]);
+}
+
+/* Weights of the x- (dir 0) or y-derivative (dir 1), with respect to the      */
+/* cell-unit coordinate, of the same tensor-product polynomial at (xi, eta):    */
+/* r_x' (x) r_y or r_x (x) r_y'.  Used for the gradient of phi_t in eq. 2.14.   */
+void orc_tpp_dweights_2d(int k, double xi, double eta, int dir, double *out) {
+  int H = (k - 1) / 2;
+  long double rx[MAXK], ry[MAXK];
+  weights_1d_any(k, -H, xi, dir == 0, rx);
+  weights_1d_any(k, -H, eta, dir == 1, ry);
   for (int b = 0; b < k; ++b)
     for (int a = 0; a < k; ++a) out[b * k + a] = (double)(rx[a] * ry[b]);
 }
@@ -380,6 +404,16 @@ void orc_metric(double X, double Y, double *o) {
   o[6] = cl * ay;
 }
 
+/* Gradient of the unit-sphere sqrtG of eq. 2.8 with respect to (x, y):        */
+/* with A = (1+X^2)(1+Y^2) and delta^2 = 1+X^2+Y^2, d(A delta^-3)/dX =          */
+/* X (1+Y^2)(2Y^2 - X^2 - 1) / delta^5, and dX/dx = 1 + X^2 (symmetric in y).   */
+void orc_sqrtg_grad(double X, double Y, double *out2) {
+  double d2 = 1.0 + X * X + Y * Y, d5 = d2 * d2 * sqrt(d2);
+  double ax = 1.0 + X * X, ay = 1.0 + Y * Y;
+  out2[0] = X * ay * (2.0 * Y * Y - X * X - 1.0) / d5 * ax;
+  out2[1] = Y * ax * (2.0 * X * X - Y * Y - 1.0) / d5 * ay;
+}
+
 static void lonlat(const double *xyz, double *lam, double *th) {
   *lam = atan2(xyz[1], xyz[0]);
   *th = atan2(xyz[2], sqrt(xyz[0] * xyz[0] + xyz[1] * xyz[1]));
@@ -476,6 +510,11 @@ struct orc {
   int *ring;       /* [nring] jj*ne + ii */
   gqp_t *gq;       /* [6][nring][me*me][2]: two owner slots per ghost Gauss point */
   nbr_t *nb;       /* [6][4][N][me] */
+  /* bottom topography (eqs. 2.13-2.14); sbar == NULL: none */
+  double *sbar;    /* [6][N][N] cell averages of sqrtG phi_s */
+  int tcase;       /* analytic surface behind sbar (ORC_TOPO_*), 0 if set from averages */
+  double tpar[4];
+  double *Rd;      /* [me*me][2][k*k] x- and y-derivative weights at the cell points */
 };
 
 int orc_npoc(const orc *o) { return o->npoc; }
@@ -654,6 +693,7 @@ void orc_free(orc *o) {
   if (!o) return;
   free(o->px); free(o->py); free(o->R); free(o->Rsub); free(o->gp); free(o->gm);
   free(o->sigp); free(o->sigm); free(o->ring); free(o->gq); free(o->nb);
+  free(o->sbar); free(o->Rd);
   free(o);
 }
 
@@ -809,25 +849,41 @@ void orc_reconstruct_all(orc *o, const double *ext, double *pts) {
 /* scaling: q = sqrtG_u (phi, phi u, phi v), true metric G^ij = G_u^ij / r^2.   */
 /* reading c1: |m| (q_R - q_L), i.e. m*sign(m); reading c9: P uses the         */
 /* interface value phi of eq. 3.33.                                            */
+/* With topography (eqs. 2.13, 3.38) sL, sR are sqrtG phi_s at the point on    */
+/* each side; reading c26: the depth phi = q0/sqrtG gives the wave speed c     */
+/* (eq. 3.35) and the upwinded q, the total phi_t = phi + phi_s enters the      */
+/* pressure jump of eq. 3.32 and the interface value of eq. 3.33 that P uses.  */
+/* Without topography sL = sR = 0 and phi_t = phi exactly.                      */
 /* ------------------------------------------------------------------------- */
-void orc_lmars(const orc *o, int dir, double X, double Y, const double *qL, const double *qR,
-               double *F) {
+static void lmars_core(const orc *o, int dir, double X, double Y, const double *qL, const double *qR,
+                       double sL, double sR, double *F) {
   double m7[7];
   orc_metric(X, Y, m7);
   double sG = m7[0], r2 = o->r * o->r;
   double Gii = (dir == 0 ? m7[1] : m7[3]) / r2; /* true G^ii */
   double G1i = (dir == 0 ? m7[1] : m7[2]) / r2, G2i = (dir == 0 ? m7[2] : m7[3]) / r2;
   double phL = qL[0] / sG, phR = qR[0] / sG;
+  double ptL = phL + sL / sG, ptR = phR + sR / sG;              /* phi_t */
   double uL = qL[1 + dir] / qL[0], uR = qR[1 + dir] / qR[0];
   double upL = uL / sqrt(Gii), upR = uR / sqrt(Gii);          /* eq. 3.31 */
   double c = 0.5 * (sqrt(phL) + sqrt(phR));                     /* eqs. 3.34-3.35 */
-  double ms = 0.5 * (upL + upR - (phR - phL) / c);              /* eq. 3.32 */
-  double ph = 0.5 * (phL + phR - c * (upR - upL));              /* eq. 3.33 */
+  double ms = 0.5 * (upL + upR - (ptR - ptL) / c);              /* eq. 3.32 */
+  double ph = 0.5 * (ptL + ptR - c * (upR - upL));              /* eq. 3.33 */
   double m = ms * sqrt(Gii);                                    /* eq. 3.36 */
   double am = fabs(m);
   for (int v = 0; v < 3; ++v) F[v] = 0.5 * (m * (qL[v] + qR[v]) - am * (qR[v] - qL[v])); /* eq. 3.37 */
   F[1] += 0.5 * sG * G1i * ph * ph;                             /* eq. 3.38 */
   F[2] += 0.5 * sG * G2i * ph * ph;
+}
+
+void orc_lmars(const orc *o, int dir, double X, double Y, const double *qL, const double *qR,
+               double *F) {
+  lmars_core(o, dir, X, Y, qL, qR, 0.0, 0.0, F);
+}
+
+void orc_lmars_topo(const orc *o, int dir, double X, double Y, const double *qL, const double *qR,
+                    double sL, double sR, double *F) {
+  lmars_core(o, dir, X, Y, qL, qR, sL, sR, F);
 }
 
 /* Coriolis parameter.  With alpha_c = 0 it is 2 Omega sin(theta) with sin(theta)   */
@@ -863,6 +919,158 @@ void orc_sources(const orc *o, int p, double X, double Y, const double *q, doubl
 }
 
 /* ------------------------------------------------------------------------- */
+/* Bottom topography (section 2, eqs. 2.13-2.14; section 5.2, eq. 5.8).        */
+/* The state keeps the depth, q0 = sqrtG phi; the mass variable is             */
+/* reconstructed as sqrtG phi_t = q0 + sqrtG phi_s (the cell averages of        */
+/* sqrtG phi_s are added before the ghost fill), and phi_s at the points is     */
+/* the linear reconstruction of its own cell averages (reading c26).            */
+/* ------------------------------------------------------------------------- */
+static double gc_dist(double l1, double t1, double l2, double t2);
+
+static double topo_lonlat(const orc *o, double lam, double th) {
+  const double *P = o->tpar;
+  if (o->tcase == ORC_TOPO_MOUNTAIN) {
+    /* eq. 5.8: hs = hs0 (1 - r/R), r = sqrt(min(R^2, dlam^2 + dtheta^2));     */
+    /* reading c27: the longitude difference is taken modulo 2 pi.             */
+    double dl = remainder(lam - P[2], 2.0 * M_PI), dt = th - P[3];
+    double r = sqrt(fmin(P[1] * P[1], dl * dl + dt * dt));
+    return o->g * P[0] * (1.0 - r / P[1]);
+  }
+  if (o->tcase == ORC_TOPO_ZONAL) {
+    /* hs = hs0 cos^2(theta'), theta' the latitude about the axis tilted by    */
+    /* alpha (the same rotated latitude as eq. 5.1)                             */
+    double t = -cos(lam) * cos(th) * sin(P[1]) + sin(th) * cos(P[1]);
+    return o->g * P[0] * (1.0 - t * t);
+  }
+  if (o->tcase == ORC_TOPO_HILL) {
+    double d = gc_dist(lam, th, P[2], P[3]) / P[1];
+    return o->g * P[0] * exp(-d * d);
+  }
+  return 0.0;
+}
+
+double orc_topography_point(const orc *o, int p, double X, double Y) {
+  double xyz[3], lam, th;
+  orc_xyz(p, X, Y, xyz);
+  lonlat(xyz, &lam, &th);
+  return topo_lonlat(o, lam, th);
+}
+
+static void topo_prepare(orc *o) {
+  int k = o->k, me = o->me, kk = k * k;
+  if (!o->Rd) o->Rd = (double *)malloc(sizeof(double) * me * me * 2 * kk);
+  for (int h = 0; h < me; ++h)
+    for (int g = 0; g < me; ++g)
+      for (int d = 0; d < 2; ++d)
+        orc_tpp_dweights_2d(k, o->gx[g], o->gx[h], d, o->Rd + ((size_t)(h * me + g) * 2 + d) * kk);
+}
+
+void orc_set_topography(orc *o, const double *sbar) {
+  size_t n = (size_t)6 * o->N * o->N;
+  free(o->sbar);
+  o->sbar = NULL;
+  o->tcase = 0;
+  if (!sbar) return;
+  o->sbar = (double *)malloc(sizeof(double) * n);
+  memcpy(o->sbar, sbar, sizeof(double) * n);
+  topo_prepare(o);
+}
+
+/* Analytic surface: cell averages of sqrtG phi_s by the me x me Gauss rule    */
+/* (reading c15); initial conditions then read their phi as phi_t (c28).       */
+void orc_set_topography_case(orc *o, int tcase, const double *P) {
+  int N = o->N, me = o->me;
+  double *sb = (double *)malloc(sizeof(double) * 6 * N * N);
+  o->tcase = tcase;
+  for (int i = 0; i < 4; ++i) o->tpar[i] = P[i];
+  for (int p = 0; p < 6; ++p)
+    for (int j = 0; j < N; ++j)
+      for (int i = 0; i < N; ++i) {
+        double acc = 0.0;
+        for (int h = 0; h < me; ++h)
+          for (int g = 0; g < me; ++g) {
+            double X = tan(cell_centre(o, i) + o->gx[g] * o->dx);
+            double Y = tan(cell_centre(o, j) + o->gx[h] * o->dx);
+            double m7[7];
+            orc_metric(X, Y, m7);
+            acc += o->gw[g] * o->gw[h] * m7[0] * orc_topography_point(o, p, X, Y);
+          }
+        sb[((size_t)p * N + j) * N + i] = acc;
+      }
+  orc_set_topography(o, sb);
+  o->tcase = tcase;
+  free(sb);
+}
+
+void orc_get_topography(const orc *o, double *out) {
+  size_t n = (size_t)6 * o->N * o->N;
+  for (size_t c = 0; c < n; ++c) out[c] = o->sbar ? o->sbar[c] : 0.0;
+}
+
+/* Point values for the topography terms of one tendency evaluation.          */
+/* ext holds the extended sqrtG phi_t (and momentum); pts its reconstruction.  */
+/* On return spt[p][j][i][pt] = sqrtG phi_s (TPP of its averages), pts' mass    */
+/* variable is the depth sqrtG phi_t - sqrtG phi_s, and dpt[p][j][i][c][2] is    */
+/* the gradient of phi_t at cell point c, reading c29: phi_t = P / sqrtG with P  */
+/* the TPP polynomial of sqrtG phi_t, so d phi_t = (dP - phi_t d sqrtG) / sqrtG. */
+static void topo_points(orc *o, const double *ext, double *pts, double *spt, double *dpt) {
+  int N = o->N, k = o->k, ne = o->ne, np = o->npoc, me = o->me, kk = k * k;
+  size_t pe = (size_t)ne * ne, pi = (size_t)N * N;
+  double *s3 = (double *)calloc(3 * 6 * pi, sizeof(double));
+  double *exs = (double *)malloc(sizeof(double) * 3 * 6 * pe);
+  memcpy(s3, o->sbar, sizeof(double) * 6 * pi);
+  orc_fill_ghosts(o, s3, exs, NULL);
+#pragma omp parallel for schedule(static)
+  for (int pj = 0; pj < 6 * N; ++pj) {
+    int p = pj / N, j = pj % N;
+    double st[MAXK * MAXK], tt[MAXK * MAXK];
+    for (int i = 0; i < N; ++i) {
+      for (int b = 0; b < k; ++b)
+        for (int a = 0; a < k; ++a) {
+          st[b * k + a] = exs[p * pe + (size_t)(j + b) * ne + (i + a)];
+          tt[b * k + a] = ext[p * pe + (size_t)(j + b) * ne + (i + a)];
+        }
+      size_t cell = ((size_t)p * N + j) * N + i;
+      for (int pt = 0; pt < np; ++pt) {
+        double sv = tpp_point(o, st, pt);
+        spt[cell * np + pt] = sv;
+        pts[cell * np + pt] -= sv; /* the v = 0 block of pts */
+      }
+      for (int h = 0; h < me; ++h)
+        for (int g = 0; g < me; ++g) {
+          int c = h * me + g;
+          double X = tan(cell_centre(o, i) + o->gx[g] * o->dx);
+          double Y = tan(cell_centre(o, j) + o->gx[h] * o->dx);
+          double m7[7], gs[2];
+          orc_metric(X, Y, m7);
+          orc_sqrtg_grad(X, Y, gs);
+          double P = tpp_point(o, tt, 4 * me + c);
+          double dP[2] = {0.0, 0.0};
+          for (int d = 0; d < 2; ++d) {
+            const double *w = o->Rd + ((size_t)c * 2 + d) * kk;
+            for (int q = 0; q < kk; ++q) dP[d] += w[q] * tt[q];
+            dP[d] /= o->dx;
+          }
+          double pt_t = P / m7[0];
+          for (int d = 0; d < 2; ++d) dpt[(cell * me * me + c) * 2 + d] = (dP[d] - pt_t * gs[d]) / m7[0];
+        }
+    }
+  }
+  free(s3);
+  free(exs);
+}
+
+/* psi_B of eq. 2.14 at a cell point, unit-sphere scaling like the pressure    */
+/* term: sqrtG phi_s G^ij d phi_t / dx^j with the true G^ij = G_unit^ij / r^2.  */
+static void topo_source(const orc *o, double X, double Y, double s, const double *dphit, double *S) {
+  double m7[7];
+  orc_metric(X, Y, m7);
+  double sG = m7[0], r2 = o->r * o->r, fs = s / sG;
+  S[1] += sG * fs * (m7[1] * dphit[0] + m7[2] * dphit[1]) / r2;
+  S[2] += sG * fs * (m7[2] * dphit[0] + m7[3] * dphit[1]) / r2;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Tendency (eq. 3.1, reading c6: F_{i+1/2} - F_{i-1/2} over dx = pi/(2N)).    */
 /* ------------------------------------------------------------------------- */
 #define PTS(v, p, j, i, pt) pts[((((size_t)(v) * 6 + (p)) * N + (j)) * N + (i)) * np + (pt)]
@@ -874,8 +1082,19 @@ void orc_tendency(orc *o, const double *q, double *dqdt) {
   double dx = o->dx;
   double *ext = (double *)malloc(sizeof(double) * 3 * 6 * ne * ne);
   double *pts = (double *)malloc(sizeof(double) * 3 * 6 * (size_t)N * N * np);
-  orc_fill_ghosts(o, q, ext, NULL);
+  double *qt = NULL, *spt = NULL, *dpt = NULL;
+  if (o->sbar) { /* eq. 2.13: reconstruct sqrtG phi_t = q0 + sqrtG phi_s */
+    size_t nq = (size_t)3 * 6 * N * N;
+    qt = (double *)malloc(sizeof(double) * nq);
+    memcpy(qt, q, sizeof(double) * nq);
+    for (size_t c = 0; c < (size_t)6 * N * N; ++c) qt[c] += o->sbar[c];
+    spt = (double *)malloc(sizeof(double) * 6 * (size_t)N * N * np);
+    dpt = (double *)malloc(sizeof(double) * 6 * (size_t)N * N * me * me * 2);
+  }
+  orc_fill_ghosts(o, qt ? qt : q, ext, NULL);
   orc_reconstruct_all(o, ext, pts);
+  if (o->sbar) topo_points(o, ext, pts, spt, dpt);
+#define SPT(p, j, i, pt) (spt ? spt[((((size_t)(p)) * N + (j)) * N + (i)) * np + (pt)] : 0.0)
   /* edge-averaged fluxes: Fx[v][p][j][i'] i' = 0..N, Fy[v][p][j'][i] j' = 0..N */
   size_t fe = (size_t)N * (N + 1);
   double *Fx = (double *)calloc(3 * 6 * fe, sizeof(double));
@@ -892,7 +1111,8 @@ void orc_tendency(orc *o, const double *q, double *dqdt) {
           qR[v] = PTS(v, p, j, e, side_point(me, 0, g));
         }
         double x = -QPI + e * dx, y = cell_centre(o, j) + o->gx[g] * dx;
-        orc_lmars(o, 0, tan(x), tan(y), qL, qR, F);
+        lmars_core(o, 0, tan(x), tan(y), qL, qR, SPT(p, j, e - 1, side_point(me, 1, g)),
+                   SPT(p, j, e, side_point(me, 0, g)), F);
         for (int v = 0; v < 3; ++v) acc[v] += o->gw[g] * F[v];
       }
       for (int v = 0; v < 3; ++v) Fx[(v * 6 + p) * fe + (size_t)j * (N + 1) + e] = acc[v];
@@ -907,7 +1127,8 @@ void orc_tendency(orc *o, const double *q, double *dqdt) {
           qR[v] = PTS(v, p, e, i, side_point(me, 2, g));
         }
         double x = cell_centre(o, i) + o->gx[g] * dx, y = -QPI + e * dx;
-        orc_lmars(o, 1, tan(x), tan(y), qL, qR, F);
+        lmars_core(o, 1, tan(x), tan(y), qL, qR, SPT(p, e - 1, i, side_point(me, 3, g)),
+                   SPT(p, e, i, side_point(me, 2, g)), F);
         for (int v = 0; v < 3; ++v) acc[v] += o->gw[g] * F[v];
       }
       for (int v = 0; v < 3; ++v) Fy[(v * 6 + p) * fe + (size_t)e * N + i] = acc[v];
@@ -946,10 +1167,12 @@ void orc_tendency(orc *o, const double *q, double *dqdt) {
           qo[0] = nb->ratio * qb[0];
           qo[1] = nb->C[0] * qb[1] + nb->C[1] * qb[2];
           qo[2] = nb->C[2] * qb[1] + nb->C[3] * qb[2];
+          double sin_ = SPT(A, cj, ci, side_point(me, side, g));
+          double so = nb->ratio * SPT(B, bj, bi, side_point(me, nb->sideB, nb->gB));
           double x, y, F[3];
           edge_point(o, side, t, g, &x, &y);
-          if (sA > 0) orc_lmars(o, dirA, tan(x), tan(y), qin, qo, F);
-          else orc_lmars(o, dirA, tan(x), tan(y), qo, qin, F);
+          if (sA > 0) lmars_core(o, dirA, tan(x), tan(y), qin, qo, sin_, so, F);
+          else lmars_core(o, dirA, tan(x), tan(y), qo, qin, so, sin_, F);
           for (int v = 0; v < 3; ++v) accA[v] += o->gw[g] * F[v];
           /* back to B: C_{A->B} is the inverse of C_{B->A} at the same point */
           double Ci[4];
@@ -988,6 +1211,9 @@ void orc_tendency(orc *o, const double *q, double *dqdt) {
           for (int v = 0; v < 3; ++v) qv[v] = PTS(v, p, j, i, pt);
           double x = cell_centre(o, i) + o->gx[g] * dx, y = cell_centre(o, j) + o->gx[h] * dx;
           orc_sources(o, p, tan(x), tan(y), qv, S);
+          if (spt)
+            topo_source(o, tan(x), tan(y), SPT(p, j, i, pt),
+                        dpt + ((((size_t)p * N + j) * N + i) * me * me + h * me + g) * 2, S);
           for (int v = 0; v < 3; ++v) sb[v] += o->gw[g] * o->gw[h] * S[v];
         }
       for (int v = 0; v < 3; ++v) {
@@ -998,10 +1224,14 @@ void orc_tendency(orc *o, const double *q, double *dqdt) {
       }
     }
   }
+#undef SPT
   free(ext);
   free(pts);
   free(Fx);
   free(Fy);
+  free(qt);
+  free(spt);
+  free(dpt);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -1102,6 +1332,7 @@ void orc_ic(const orc *o, int cs, const double *P, int n_extra, const double *ex
           orc_xyz(p, X, Y, xyz);
           lonlat(xyz, &lam, &th);
           ic_point(o, cs, P, n_extra, ex, lam, th, &phi, &us, &vs);
+          if (o->tcase) phi -= topo_lonlat(o, lam, th); /* reading c28: depth = phi_t - phi_s */
           orc_metric(X, Y, m7);
           orc_jacobian(p, X, Y, J);
           inv2(J, Ji);

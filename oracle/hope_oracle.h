@@ -44,6 +44,14 @@ extern "C" {
 #define ORC_IC_BUMPS 8         /* geostrophic + n Gaussian bumps; params: alpha,u0,phi0,amp_m,
                                   radius_rad; extra = n pairs (lon, lat)          */
 
+/* analytic bottom surfaces for orc_set_topography_case; params (4 doubles):
+   MOUNTAIN  hs0_m, R_rad, lon_c, lat_c   isolated cone of eq. 5.8
+   ZONAL     hs0_m, alpha                  hs0 cos^2 of the latitude about the tilted axis
+   HILL      hs0_m, R_rad, lon_c, lat_c   Gaussian hs0 exp(-(d/R)^2), d great-circle */
+#define ORC_TOPO_MOUNTAIN 1
+#define ORC_TOPO_ZONAL 2
+#define ORC_TOPO_HILL 3
+
 typedef struct orc orc;
 
 orc *orc_new(int N, int k, int scheme, double radius, double gravity, double omega,
@@ -69,6 +77,13 @@ void orc_reconstruct_all(orc *o, const double *ext, double *pts);
 /* Cell averages of an analytic initial condition by me x me Gauss quadrature. */
 void orc_ic(const orc *o, int ic_case, const double *params, int n_extra, const double *extra,
             double *q);
+/* Bottom topography (eqs. 2.13-2.14): cell averages of sqrtG phi_s [p][j][i] (copied;
+   NULL removes it), or an analytic surface averaged by the me x me Gauss rule.  With an
+   analytic surface set, orc_ic reads its phi as phi_t and stores the depth phi_t - phi_s. */
+void orc_set_topography(orc *o, const double *sbar);
+void orc_set_topography_case(orc *o, int tcase, const double *params4);
+void orc_get_topography(const orc *o, double *sbar);
+double orc_topography_point(const orc *o, int panel, double X, double Y);
 /* Cell-averaged sqrtG (unit sphere) per cell, [p][j][i]. */
 void orc_cell_sqrtg(const orc *o, double *out);
 /* L1, L2, Linf error norms of phi (eqs. 5.4-5.7). */
@@ -79,6 +94,8 @@ void orc_gauss(int m, double *x, double *w);
 void orc_weights_1d(int n, int o0, double xi, double *out);
 void orc_tpp_weights_2d(int k, double xi, double eta, double *out);
 void orc_tpp_weights_2d_literal(int k, double xi, double eta, double *out);
+void orc_tpp_dweights_2d(int k, double xi, double eta, int dir, double *out);
+void orc_sqrtg_grad(double X, double Y, double *out2);
 int orc_weno_gamma(int k, double xi, double eta, double *gam, double *resid);
 double orc_weno_beta(int l, int o0x, int o0y, const double *Qsub);
 double orc_weno_point(const orc *o, const double *stencil, int pt);
@@ -89,6 +106,9 @@ int orc_locate(const double *xyz, double *XY);
 void orc_lmars(const orc *o, int dir, double X, double Y, const double *qL, const double *qR,
                double *F);
 void orc_sources(const orc *o, int panel, double X, double Y, const double *qv, double *S);
+/* LMARS with topography: sL, sR = sqrtG phi_s at the point on each side. */
+void orc_lmars_topo(const orc *o, int dir, double X, double Y, const double *qL, const double *qR,
+                    double sL, double sR, double *F);
 
 /* ---- table exports for the PyTorch reference composition ---- */
 int orc_ghost_count(const orc *o);

@@ -18,6 +18,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 TPP, WENO = 0, 1
 SSPRK3, WSRK3 = 0, 1
 IC_GEOSTROPHIC, IC_ROSSBY, IC_DAMBREAK, IC_BUMPS = 2, 6, 7, 8
+TOPO_MOUNTAIN, TOPO_ZONAL, TOPO_HILL = 1, 2, 3
 
 RADIUS = 6.37122e6
 GRAVITY = 9.80616
@@ -79,6 +80,15 @@ def lib():
         L.orc_locate.argtypes = [P, P]
         L.orc_lmars.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, P, P, P]
         L.orc_sources.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, P, P]
+        L.orc_lmars_topo.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, P, P,
+                                     ctypes.c_double, ctypes.c_double, P]
+        L.orc_set_topography.argtypes = [vp, P]
+        L.orc_set_topography_case.argtypes = [vp, ctypes.c_int, P]
+        L.orc_get_topography.argtypes = [vp, P]
+        L.orc_topography_point.restype = ctypes.c_double
+        L.orc_topography_point.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+        L.orc_tpp_dweights_2d.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, P]
+        L.orc_sqrtg_grad.argtypes = [ctypes.c_double, ctypes.c_double, P]
         Pi = ctypes.POINTER(ctypes.c_int)
         L.orc_ghost_count.restype = ctypes.c_int
         L.orc_ghost_count.argtypes = [vp]
@@ -229,6 +239,38 @@ class Oracle:
     def coriolis(self, panel, X, Y):
         return lib().orc_coriolis(self._h, int(panel), float(X), float(Y))
 
+    def set_topography(self, sbar):
+        """Bottom topography from cell averages of sqrtG phi_s, shape (6, N, N); None removes it."""
+        if sbar is None:
+            lib().orc_set_topography(self._h, None)
+        else:
+            sbar = _f64(sbar)
+            assert sbar.shape == (6, self.N, self.N)
+            lib().orc_set_topography(self._h, _p(sbar))
+
+    def set_topography_case(self, case, params):
+        """Analytic bottom surface (TOPO_*); initial conditions then read phi as phi_t."""
+        P = _f64(list(params) + [0.0] * (4 - len(params)))
+        lib().orc_set_topography_case(self._h, int(case), _p(P))
+
+    def set_mountain(self, hs0=2000.0, R=np.pi / 9, lon_c=1.5 * np.pi, lat_c=np.pi / 6):
+        """The isolated mountain of section 5.2 (eq. 5.8)."""
+        self.set_topography_case(TOPO_MOUNTAIN, [hs0, R, lon_c, lat_c])
+
+    def topography(self):
+        out = np.empty((6, self.N, self.N))
+        lib().orc_get_topography(self._h, _p(out))
+        return out
+
+    def topography_point(self, panel, X, Y):
+        return lib().orc_topography_point(self._h, int(panel), float(X), float(Y))
+
+    def lmars_topo(self, direction, X, Y, qL, qR, sL, sR):
+        F = np.empty(3)
+        lib().orc_lmars_topo(self._h, int(direction), float(X), float(Y), _p(_f64(qL)), _p(_f64(qR)),
+                             float(sL), float(sR), _p(F))
+        return F
+
     def points(self):
         """Local unit-cell coordinates (xi, eta) of the n_poc reconstruction points."""
         g, _ = gauss(self.me)
@@ -243,6 +285,18 @@ def gauss(m):
     w = np.empty(m)
     lib().orc_gauss(int(m), _p(x), _p(w))
     return x, w
+
+
+def tpp_dweights_2d(k, xi, eta, direction):
+    out = np.empty(k * k)
+    lib().orc_tpp_dweights_2d(int(k), float(xi), float(eta), int(direction), _p(out))
+    return out.reshape(k, k)
+
+
+def sqrtg_grad(X, Y):
+    out = np.empty(2)
+    lib().orc_sqrtg_grad(float(X), float(Y), _p(out))
+    return out
 
 
 def weights_1d(n, o0, xi):
