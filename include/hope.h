@@ -135,6 +135,24 @@ int hope_elem_size(hope_t ctx);
 int hope_initial_state(hope_t ctx, int ic_case, const double *params, int n_params,
                        const double *extra_host, int n_extra, void *q_dev, hope_stream_t stream);
 
+/*
+ * Bottom topography (section 2, eqs. 2.13-2.14; the mountain of section 5.2 is one such
+ * surface).  phis_avg_host: HOST array (6, N, N), i fastest, of the cell averages of
+ * sqrtG * phi_s (unit-sphere sqrtG as for the state, phi_s = g h_s in m^2/s^2), FP64
+ * whatever the context's precision; copied, so the caller keeps ownership.  NULL removes
+ * the surface.  The state keeps the fluid depth (q0 = sqrtG phi); the reconstruction acts
+ * on sqrtG phi_t = sqrtG (phi + phi_s), LMARS takes its wave speed and upwinded state from
+ * the depth and its pressure jump and interface value (eqs. 3.32, 3.33, 3.38) from phi_t,
+ * and psi_B = sqrtG phi_s G^ij d phi_t/dx^j (eq. 2.14) joins the cell sources, with the
+ * gradient taken from the TPP polynomial of sqrtG phi_t at the cell Gauss points.
+ * Builds the surface's tables in FP64 on the host (its ghost ring, its edge-point values
+ * and psi_B's weights: 2 k^2 + 4 me + 2 values per cell) after synchronising the device;
+ * captured step graphs are dropped.  Single TPP spheres only (HOPE_EUNSUPPORTED for
+ * ensembles and WENO2D); while a surface is set the VJP and tape-adjoint calls return
+ * HOPE_EUNSUPPORTED.  HOPE_EINVAL for a null context or a non-finite value.
+ */
+int hope_set_topography(hope_t ctx, const double *phis_avg_host);
+
 /* Copy a caller state into / out of the context's own state buffer (device to device). */
 int hope_set_state(hope_t ctx, const void *q_dev, hope_stream_t stream);
 int hope_get_state(hope_t ctx, void *q_dev, hope_stream_t stream);

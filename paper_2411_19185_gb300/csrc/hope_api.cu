@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <queue>
 #include <string>
@@ -362,7 +363,7 @@ static void free_grid(Grid &g) {
     for (void *p : tables)
       if (p) cudaFree(p);
   }
-  void *scratch[] = {g.gext, g.ep, g.fx, g.fy, g.sb, g.lep, g.grad, g.lring, g.ldir};
+  void *scratch[] = {g.gext, g.ep, g.fx, g.fy, g.sb, g.lep, g.grad, g.lring, g.ldir, g.tsep, g.ttw, g.ttb};
   for (void *p : scratch)
     if (p) cudaFree(p);
   g = Grid();
@@ -898,7 +899,20 @@ int hope_ghost_nnz(hope_t ctx, long long *nnz, long long *rows) {
 int hope_launches_per_stage(hope_t ctx, int *launches) {
   if (!ctx || !launches) return HOPE_EINVAL;
   *launches = ctx->ens ? 1 : 4 * (int)ctx->grids.size();
+  if (!ctx->ens)
+    for (auto &g : ctx->grids) *launches += g.tsep ? 1 : 0;
   return HOPE_OK;
+}
+
+static bool has_topography(const hope_ctx *ctx) {
+  for (auto &g : ctx->grids)
+    if (g.tsep) return true;
+  return false;
+}
+
+static int no_topography_adjoint() {
+  set_error("the adjoint of the topography terms is not built: remove the surface first");
+  return HOPE_EUNSUPPORTED;
 }
 
 int hope_tendency_vjp(hope_t ctx, const void *q_dev, const void *lam_dqdt_dev, void *lam_q_dev,
@@ -907,6 +921,7 @@ int hope_tendency_vjp(hope_t ctx, const void *q_dev, const void *lam_dqdt_dev, v
     set_error("hope_tendency_vjp: invalid or overlapping arguments");
     return HOPE_EINVAL;
   }
+  if (has_topography(ctx)) return no_topography_adjoint();
   int rc = ensure_adjoint_scratch(ctx);
   if (rc) return rc;
   VjpComb cb;
@@ -933,6 +948,7 @@ static int step_vjp_impl(hope_t ctx, int rk, const void *qn_dev, const void *lam
     set_error("hope_step_vjp: invalid or overlapping arguments");
     return HOPE_EINVAL;
   }
+  if (has_topography(ctx)) return no_topography_adjoint();
   int rc = ensure_adjoint_scratch(ctx);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
@@ -1049,6 +1065,7 @@ int hope_step_vjp_tape(hope_t ctx, const void *qn_dev, const void *tape_dev, con
     set_error("hope_step_vjp_tape: invalid or overlapping arguments");
     return HOPE_EINVAL;
   }
+  if (has_topography(ctx)) return no_topography_adjoint();
   int rc = ensure_adjoint_scratch(ctx);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
@@ -1248,6 +1265,55 @@ int hope_kernel_times(hope_t ctx, float *ms_out, int max_entries, int *n_entries
       ms_out[n++] = ms;
     }
   *n_entries = n;
+  return HOPE_OK;
+}
+
+// -------------------------------------------------------------------------------
+// Bottom topography (eqs. 2.13-2.14).  The state keeps the depth sqrtG phi; the library
+// reconstructs it as it is and adds the surface's part of phi_t from static tables built
+// here in FP64 from the cell averages of sqrtG phi_s: its ghost ring (the composed ghost
+// operator of eq. 7.12 applied on the host), its TPP values at the edge points (for
+// LMARS's phi_t), and psi_B's cell average as an affine map of the depth stencil.  For
+// the linear TPP reconstruction this is the same operator as reconstructing
+// sqrtG phi_t = sqrtG phi + sqrtG phi_s and subtracting the surface's reconstruction.
+// -------------------------------------------------------------------------------
+static void free_topography(Grid &g) {
+  void *ptrs[] = {g.tsep, g.ttw, g.ttb};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  g.tsep = g.ttw = g.ttb = nullptr;
+}
+
+int hope_set_topography(hope_t ctx, const double *phis_avg_host) {
+  if (!ctx) {
+    set_error("hope_set_topography: null context");
+    return HOPE_EINVAL;
+  }
+  if (ctx->grids.size() != 1 || ctx->ens || ctx->scheme != HOPE_TPP) {
+    set_error("hope_set_topography: bottom topography is built for single TPP spheres");
+    return HOPE_EUNSUPPORTED;
+  }
+  Grid &g = ctx->grids[0];
+  const int N = g.N;
+  const size_t pn = (size_t)6 * N * N;
+  if (phis_avg_host)
+    for (size_t c = 0; c < pn; ++c)
+      if (!std::isfinite(phis_avg_host[c])) {
+        set_error("hope_set_topography: non-finite surface value");
+        return HOPE_EINVAL;
+      }
+  HOPE_CUDA_TRY(cudaDeviceSynchronize());  // queued stages may still read the old tables
+  drop_graphs(ctx);
+  free_topography(g);
+  if (!phis_avg_host) return HOPE_OK;
+  std::vector<double> sep, tw, tb;
+  int rc = build_topography_tables(ctx, N, phis_avg_host, sep, tw, tb);
+  if (rc) return rc;
+  if ((rc = upload(&g.tsep, sep, ctx->esize)) || (rc = upload(&g.ttw, tw, ctx->esize)) ||
+      (rc = upload(&g.ttb, tb, ctx->esize))) {
+    free_topography(g);
+    return rc;
+  }
   return HOPE_OK;
 }
 

@@ -57,6 +57,10 @@ struct Grid {
   void *fx = nullptr;    // [3][6][N][N+1]
   void *fy = nullptr;    // [3][6][N+1][N]
   void *sb = nullptr;    // [2][6][N][N] cell-averaged sources
+  // bottom topography (eqs. 2.13-2.14), null without: sqrtG phi_s at the edge points
+  // [4][me][6][N][N], and psi_B's cell average as an affine map of the depth stencil,
+  // weights [2][k*k][6][N][N] and constants [2][6][N][N]
+  void *tsep = nullptr, *ttw = nullptr, *ttb = nullptr;
   CubeEdge edges[12];
   // transposed ghost operator (adjoint): CSR over interior cells
   int *gtp = nullptr;    // [6*N*N + 1]

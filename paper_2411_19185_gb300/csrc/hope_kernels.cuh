@@ -440,14 +440,44 @@ __device__ __forceinline__ void lmars(const T qL[3], const T qR[3], const T *m5,
   F[2] += (dir ? pn : pc) * p2;
 }
 
+// LMARS over bottom topography (eqs. 2.13, 3.32-3.38): q holds the depth sqrtG phi, and
+// sL, sR are sqrtG phi_s at the point.  The wave speed and the upwinded q come from the
+// depth; the pressure jump and the interface value used by P from phi_t = phi + phi_s:
+// (phi_t,R - phi_t,L)/(2c) = (cR - cL) + (phi_s,R - phi_s,L)/(2c).  With sL = sR = 0 the
+// result is lmars()'s exactly.
+template <typename T>
+__device__ __forceinline__ void lmars_topo(const T qL[3], const T qR[3], T sL, T sR, const T *m5, int dir, T F[3],
+                                           unsigned *status) {
+  const T isg = m5[0], s11 = m5[1], is11 = m5[2], pn = m5[3], pc = m5[4];
+  const T phL = qL[0] * isg, phR = qR[0] * isg;
+  if (!(phL > T(0)) || !(phR > T(0))) atomicOr(status, HOPE_STATUS_NONPHYS_PHI);
+  const T fsL = sL * isg, fsR = sR * isg;
+  const T qnL = dir ? qL[2] : qL[1], qnR = dir ? qR[2] : qR[1];
+  const T rLR = rcp(qL[0] * qR[0]);
+  const T uL = qnL * (qR[0] * rLR) * is11, uR = qnR * (qL[0] * rLR) * is11;
+  const T cL = sqrt_pos(phL), cR = sqrt_pos(phR);
+  const T c = T(0.5) * (cL + cR);
+  const T ms = T(0.5) * (uL + uR) - (cR - cL) - (fsR - fsL) * rcp(c + c);
+  const T ph = T(0.5) * ((phL + fsL) + (phR + fsR) - c * (uR - uL));
+  const T m = ms * s11;
+  const T am = fabs(m);
+#pragma unroll
+  for (int v = 0; v < 3; ++v) F[v] = T(0.5) * (m * (qL[v] + qR[v]) - am * (qR[v] - qL[v]));
+  const T p2 = ph * ph;
+  F[1] += (dir ? pc : pn) * p2;
+  F[2] += (dir ? pn : pc) * p2;
+}
+
 // ---------------------------------------------------------------------------------
 // Edge fluxes: interior x-edges, interior y-edges, then the 12 cube edges x N cells.
+// TOPO: bottom topography, with sep[4][me][6][N][N] = sqrtG phi_s at the edge points
+// (same side and node order as ep).
 // ---------------------------------------------------------------------------------
-template <typename T, int ME>
+template <typename T, int ME, bool TOPO = false>
 __device__ __forceinline__ void flux_item(long long idx, const T *__restrict__ ep, const T *__restrict__ mx,
                                           const T *__restrict__ gwg, const int *__restrict__ bedge,
                                           const T *__restrict__ bconv, T *__restrict__ fx, T *__restrict__ fy,
-                                          int N, unsigned *status) {
+                                          int N, unsigned *status, const T *__restrict__ sep = nullptr) {
   const long long nx = 6LL * N * (N - 1), ny = nx;
   const size_t pn = (size_t)6 * N * N;
   const size_t fe = (size_t)6 * N * (N + 1);
@@ -488,7 +518,11 @@ __device__ __forceinline__ void flux_item(long long idx, const T *__restrict__ e
         qL[v] = ep[((size_t)(sl * 3 + v) * ME + g) * pn + cl];
         qR[v] = ep[((size_t)(sr * 3 + v) * ME + g) * pn + cr];
       }
-      lmars(qL, qR, mx + (((size_t)e * N + a) * ME + g) * 5, dir, F, status);
+      if constexpr (TOPO)
+        lmars_topo(qL, qR, sep[((size_t)sl * ME + g) * pn + cl], sep[((size_t)sr * ME + g) * pn + cr],
+                   mx + (((size_t)e * N + a) * ME + g) * 5, dir, F, status);
+      else
+        lmars(qL, qR, mx + (((size_t)e * N + a) * ME + g) * 5, dir, F, status);
 #pragma unroll
       for (int v = 0; v < 3; ++v) acc[v].add(gw[g] * F[v]);
     }
@@ -532,10 +566,19 @@ __device__ __forceinline__ void flux_item(long long idx, const T *__restrict__ e
     qo[1] = cv[1] * qb[1] + cv[2] * qb[2];
     qo[2] = cv[3] * qb[1] + cv[4] * qb[2];
     const T *m5 = mx + (((size_t)eA * N + t) * ME + g) * 5;
-    if (sA & 1)
-      lmars(qin, qo, m5, dirA, F, status);
-    else
-      lmars(qo, qin, m5, dirA, F, status);
+    if constexpr (TOPO) {
+      const T sin_ = sep[((size_t)sA * ME + g) * pn + cA];
+      const T so = cv[0] * sep[((size_t)sB * ME + gB) * pn + cB];
+      if (sA & 1)
+        lmars_topo(qin, qo, sin_, so, m5, dirA, F, status);
+      else
+        lmars_topo(qo, qin, so, sin_, m5, dirA, F, status);
+    } else {
+      if (sA & 1)
+        lmars(qin, qo, m5, dirA, F, status);
+      else
+        lmars(qo, qin, m5, dirA, F, status);
+    }
 #pragma unroll
     for (int v = 0; v < 3; ++v) accA[v].add(gw[g] * F[v]);
     accB[1].add(gw[gB] * sg * (cv[5] * F[1] + cv[6] * F[2]));
@@ -567,6 +610,53 @@ __global__ void __launch_bounds__(256)
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
        idx += (long long)gridDim.x * blockDim.x)
     flux_item<T, ME>(idx, ep, mx, gwg, bedge, bconv, fx, fy, N, status);
+}
+
+template <typename T, int ME>
+__global__ void __launch_bounds__(256)
+    k_flux_topo(const T *__restrict__ ep, const T *__restrict__ mx, const T *__restrict__ gwg,
+                const int *__restrict__ bedge, const T *__restrict__ bconv, T *__restrict__ fx,
+                T *__restrict__ fy, int N, unsigned *status, const T *__restrict__ sep) {
+  const long long n = 12LL * N * (N - 1) + 12LL * N;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x)
+    flux_item<T, ME, true>(idx, ep, mx, gwg, bedge, bconv, fx, fy, N, status, sep);
+}
+
+// ---------------------------------------------------------------------------------
+// psi_B of eq. 2.14, cell-averaged, added to the sources.  For a fixed surface the
+// gradient of phi_t = (P_depth + P_s)/sqrtG at the cell Gauss points is affine in the
+// cell's k x k depth stencil (P the TPP polynomials of section 3.1), so the cell average
+// of sqrtG phi_s G^ij d_j phi_t is sum_c w[v][c] * stencil_c + b[v], with the weights
+// w[2][k*k][6][N][N] and constants b[2][6][N][N] built in FP64 at set-up.  One thread
+// per cell; the stencil's ring cells come from the ghost ring of the mass variable.
+// ---------------------------------------------------------------------------------
+template <typename T, int K>
+__global__ void __launch_bounds__(256)
+    k_topo_src(const T *__restrict__ q, const T *__restrict__ gext, const T *__restrict__ tw,
+               const T *__restrict__ tb, T *__restrict__ sb, int N, int ne) {
+  constexpr int H = (K - 1) / 2;
+  const long long n = 6LL * N * N;
+  const long long cid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cid >= n) return;
+  const int i = (int)(cid % N), j = (int)((cid / N) % N), p = (int)(cid / ((long long)N * N));
+  T s1 = tb[cid], s2 = tb[n + cid];
+#pragma unroll 1
+  for (int b = 0; b < K; ++b) {
+    const int jj = j + b - H;
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+      const int ii = i + a - H;
+      const T v = (ii >= 0 && ii < N && jj >= 0 && jj < N)
+                      ? q[((size_t)p * N + jj) * N + ii]
+                      : gext[((size_t)p * ne + (jj + H)) * ne + (ii + H)];
+      const size_t c = (size_t)(b * K + a);
+      s1 = fma(tw[c * n + cid], v, s1);
+      s2 = fma(tw[((size_t)K * K + c) * n + cid], v, s2);
+    }
+  }
+  sb[cid] += s1;
+  sb[n + cid] += s2;
 }
 
 // ---------------------------------------------------------------------------------

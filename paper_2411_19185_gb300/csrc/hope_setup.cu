@@ -657,6 +657,101 @@ namespace hope {
 //   bform [l][l*l + l] per sub-stencil offset: Winv (l x l) of the simultaneous
 //                      diagonalisation of the smoothness forms (eq. 3.25), its row sums
 //   bcoef [l][l][l][l] mode weights lam_y lam_x - 1 of the indicator
+// Static tables of a bottom surface (eqs. 2.13-2.14) from the cell averages of sqrtG phi_s,
+// all in FP64: the surface's ghost ring by the composed ghost operator (eq. 7.12), its TPP
+// values at the edge points, sep[4][me][6][N][N] (west, east at the y-nodes; south, north
+// at the x-nodes), and psi_B's cell average (the me x me Gauss rule of eq. 2.14 at the
+// cell points) as an affine map of the k x k depth stencil, weights tw[2][k*k][6][N][N]
+// and constants tb[2][6][N][N].  The gradient of phi_t = (P_depth + P_s)/sqrtG uses the
+// derivative weights of the TPP polynomials and the closed-form gradient of sqrtG.
+int build_topography_tables(const hope_ctx *ctx, int N, const double *phis_avg_host, std::vector<double> &sep,
+                            std::vector<double> &tw, std::vector<double> &tb) {
+  const int K = ctx->k, H = ctx->H, ME = ctx->me, KK = K * K, ne = N + 2 * H;
+  const size_t pn = (size_t)6 * N * N;
+  std::vector<double> nodes(ME), weights(ME);
+  gauss_legendre(ME, nodes.data(), weights.data());
+  std::vector<int> rowptr, cols, dst;
+  std::vector<double> vals;
+  int rc = build_ghost_operator(ctx, N, nodes, weights, rowptr, cols, vals, dst);
+  if (rc) return rc;
+  // extended array of sqrtG phi_s: interior cells and the ghost ring
+  std::vector<double> ext((size_t)6 * ne * ne, 0.0);
+  for (int p = 0; p < 6; ++p)
+    for (int j = 0; j < N; ++j)
+      for (int i = 0; i < N; ++i)
+        ext[((size_t)p * ne + j + H) * ne + i + H] = phis_avg_host[((size_t)p * N + j) * N + i];
+  for (size_t r = 0; r + 1 < rowptr.size(); ++r) {
+    double v = 0.0;
+    for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) v += vals[(size_t)5 * e] * phis_avg_host[cols[e]];
+    ext[dst[r]] = v;
+  }
+  // 1-D weights: values at xi = -1/2, +1/2 and the Gauss nodes; derivatives at the nodes
+  std::vector<double> wv((size_t)(ME + 2) * K), wd((size_t)ME * K);
+  cell_avg_weights(K, -H, -0.5, &wv[0]);
+  cell_avg_weights(K, -H, 0.5, &wv[K]);
+  for (int t = 0; t < ME; ++t) {
+    cell_avg_weights(K, -H, nodes[t], &wv[(size_t)(2 + t) * K]);
+    cell_avg_dweights(K, -H, nodes[t], &wd[(size_t)t * K]);
+  }
+  const double dx = HOPE_PI / (2.0 * N), r2 = ctx->radius * ctx->radius;
+  sep.assign((size_t)4 * ME * pn, 0.0);
+  tw.assign((size_t)2 * KK * pn, 0.0);
+  tb.assign(2 * pn, 0.0);
+  std::vector<double> st(KK), Dx(KK), Dy(KK);
+  for (int p = 0; p < 6; ++p)
+    for (int j = 0; j < N; ++j)
+      for (int i = 0; i < N; ++i) {
+        const size_t cell = ((size_t)p * N + j) * N + i;
+        for (int b = 0; b < K; ++b)
+          for (int a = 0; a < K; ++a) st[b * K + a] = ext[((size_t)p * ne + j + b) * ne + i + a];
+        auto tpp = [&](const double *wx, const double *wy) {
+          double v = 0.0;
+          for (int b = 0; b < K; ++b) {
+            double row = 0.0;
+            for (int a = 0; a < K; ++a) row += wx[a] * st[b * K + a];
+            v += wy[b] * row;
+          }
+          return v;
+        };
+        for (int r = 0; r < ME; ++r) {
+          const double *wn = &wv[(size_t)(2 + r) * K];
+          sep[((size_t)0 * ME + r) * pn + cell] = tpp(&wv[0], wn);  // west
+          sep[((size_t)1 * ME + r) * pn + cell] = tpp(&wv[K], wn);  // east
+          sep[((size_t)2 * ME + r) * pn + cell] = tpp(wn, &wv[0]);  // south
+          sep[((size_t)3 * ME + r) * pn + cell] = tpp(wn, &wv[K]);  // north
+        }
+        for (int h = 0; h < ME; ++h)
+          for (int gg = 0; gg < ME; ++gg) {
+            const double X = tan(-HOPE_QPI + (i + 0.5 + nodes[gg]) * dx);
+            const double Y = tan(-HOPE_QPI + (j + 0.5 + nodes[h]) * dx);
+            const double sG = sqrtg_unit(X, Y), d2 = 1.0 + X * X + Y * Y;
+            double gx, gy;
+            sqrtg_unit_grad(X, Y, &gx, &gy);
+            const double G11 = d2 / (1.0 + X * X), G22 = d2 / (1.0 + Y * Y);
+            const double G12 = d2 * X * Y / ((1.0 + X * X) * (1.0 + Y * Y));
+            const double *vx = &wv[(size_t)(2 + gg) * K], *vy = &wv[(size_t)(2 + h) * K];
+            const double *dxw = &wd[(size_t)gg * K], *dyw = &wd[(size_t)h * K];
+            const double Ps = tpp(vx, vy);
+            const double fs = Ps / sG;  // phi_s at the point
+            const double dsx = (tpp(dxw, vy) / dx - fs * gx) / sG, dsy = (tpp(vx, dyw) / dx - fs * gy) / sG;
+            // quadrature weight times sqrtG phi_s G^ij (true metric) of eq. 2.14
+            const double W = weights[gg] * weights[h] * Ps / r2;
+            const double A11 = W * G11, A12 = W * G12, A22 = W * G22;
+            tb[cell] += A11 * dsx + A12 * dsy;
+            tb[pn + cell] += A12 * dsx + A22 * dsy;
+            for (int b = 0; b < K; ++b)
+              for (int a = 0; a < K; ++a) {
+                const double R = vy[b] * vx[a], Rx = vy[b] * dxw[a] / dx, Ry = dyw[b] * vx[a] / dx;
+                const double ex = (Rx - R * gx / sG) / sG, ey = (Ry - R * gy / sG) / sG;
+                const size_t c = (size_t)b * K + a;
+                tw[c * pn + cell] += A11 * ex + A12 * ey;
+                tw[((size_t)KK + c) * pn + cell] += A12 * ex + A22 * ey;
+              }
+          }
+      }
+  return HOPE_OK;
+}
+
 static int upload_t(hope_ctx *ctx, void **dst, const std::vector<double> &v) {
   size_t bytes = (size_t)ctx->esize * v.size();
   if (cudaMalloc(dst, bytes) != cudaSuccess) return HOPE_ENOMEM;

@@ -32,4 +32,7 @@ int build_ghost_operator(const hope_ctx *ctx, int N, const std::vector<double> &
 int build_cube_edges(const hope_ctx *ctx, int N, const std::vector<double> &nodes, CubeEdge edges[12],
                      std::vector<double> &conv);
 int setup_weno_tables(hope_ctx *ctx, const std::vector<double> &nodes);
+// Static tables of a bottom surface from the cell averages of sqrtG phi_s (FP64).
+int build_topography_tables(const hope_ctx *ctx, int N, const double *phis_avg_host, std::vector<double> &sep,
+                            std::vector<double> &tw, std::vector<double> &tb);
 }  // namespace hope

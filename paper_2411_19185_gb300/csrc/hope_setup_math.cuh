@@ -175,6 +175,47 @@ HOPE_HD void cell_avg_weights(int n, int o0, double xi, double *w) {
   }
 }
 
+// Weights of the first derivative (in target-cell units) of the same polynomial at xi:
+// p'(xi) = sum_m P(z_m) L_m''(xi), so w'_j = sum_{m>j} L_m''(xi), with
+// L_m'' = sum over ordered pairs a != b (both != m) of prod_{c != m, a, b} (xi - z_c)
+// over prod_{c != m} (z_m - z_c).
+HOPE_HD void cell_avg_dweights(int n, int o0, double xi, double *w) {
+  double z[HOPE_MAXK + 2];
+  for (int m = 0; m <= n; ++m) z[m] = o0 - 0.5 + m;
+  double d2[HOPE_MAXK + 2];
+  for (int m = 0; m <= n; ++m) {
+    double den = 1.0;
+    for (int c = 0; c <= n; ++c)
+      if (c != m) den *= z[m] - z[c];
+    double s = 0.0;
+    for (int a = 0; a <= n; ++a) {
+      if (a == m) continue;
+      for (int b = 0; b <= n; ++b) {
+        if (b == m || b == a) continue;
+        double t = 1.0;
+        for (int c = 0; c <= n; ++c)
+          if (c != m && c != a && c != b) t *= xi - z[c];
+        s += t;
+      }
+    }
+    d2[m] = s / den;
+  }
+  for (int j = 0; j < n; ++j) {
+    double s = 0.0;
+    for (int m = j + 1; m <= n; ++m) s += d2[m];
+    w[j] = s;
+  }
+}
+
+// Gradient of the unit-sphere sqrtG = (1+X^2)(1+Y^2)/delta^3 with respect to the panel
+// angles: d/dX = X (1+Y^2)(2Y^2 - X^2 - 1)/delta^5 and dX/dx = 1+X^2 (symmetric in y).
+HOPE_HD void sqrtg_unit_grad(double X, double Y, double *gx, double *gy) {
+  const double d2 = 1.0 + X * X + Y * Y, d5 = d2 * d2 * sqrt(d2);
+  const double ax = 1.0 + X * X, ay = 1.0 + Y * Y;
+  *gx = X * ay * (2.0 * Y * Y - X * X - 1.0) / d5 * ax;
+  *gy = Y * ax * (2.0 * X * X - Y * Y - 1.0) / d5 * ay;
+}
+
 // 1-D WENO linear weights: the l sub-stencils of width l inside the central stencil of
 // width k = 2l-1 (sub-stencil s covers offsets s-H .. s-H+l-1), gamma minimising
 // |R_L gamma - R_H| (normal equations, partial pivoting).  Returns the max residual.

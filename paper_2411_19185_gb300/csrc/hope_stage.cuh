@@ -192,13 +192,26 @@ inline int stage_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *q0, T *out, 
     int rc = launch_recon_weno<T, K>(ctx, g, qs, st);
     if (rc) return rc;
   }
+  // bottom topography: psi_B (eq. 2.14) added to the sources
+  if (g.tsep) {
+    const long long cells = 6LL * N * N;
+    k_topo_src<T, K><<<(int)((cells + 255) / 256), 256, 0, st>>>(qs, (const T *)g.gext, (const T *)g.ttw,
+                                                                 (const T *)g.ttb, (T *)g.sb, N, ne);
+  }
   mark(2);
   // fluxes
   {
     long long items = 12LL * N * (N - 1) + 12LL * N;
-    if (!g.flux_tpb) balanced_grid(k_flux<T, ME>, items, ctx->nsm, 256, &g.flux_grid, &g.flux_tpb);
-    k_flux<T, ME><<<g.flux_grid, g.flux_tpb, 0, st>>>((const T *)g.ep, (const T *)g.mx, (const T *)ctx->gw, g.bedge,
-                                          (const T *)g.bconv, (T *)g.fx, (T *)g.fy, N, ctx->status);
+    if (g.tsep) {
+      k_flux_topo<T, ME><<<(int)((items + 255) / 256), 256, 0, st>>>(
+          (const T *)g.ep, (const T *)g.mx, (const T *)ctx->gw, g.bedge, (const T *)g.bconv, (T *)g.fx, (T *)g.fy, N,
+          ctx->status, (const T *)g.tsep);
+    } else {
+      if (!g.flux_tpb) balanced_grid(k_flux<T, ME>, items, ctx->nsm, 256, &g.flux_grid, &g.flux_tpb);
+      k_flux<T, ME><<<g.flux_grid, g.flux_tpb, 0, st>>>((const T *)g.ep, (const T *)g.mx, (const T *)ctx->gw,
+                                                        g.bedge, (const T *)g.bconv, (T *)g.fx, (T *)g.fy, N,
+                                                        ctx->status);
+    }
   }
   mark(3);
   // tendency + stage combination

@@ -6,6 +6,7 @@ with hope_state_elems() elements (shape (3, 6, N, N) for one sphere).
 """
 import ctypes
 
+import numpy as np
 import torch
 
 from . import _lib as L
@@ -230,6 +231,19 @@ class Sphere:
 
     def set_recon_tile(self, tx, ty):
         L.check(L.load().hope_set_recon_tile(self._h, int(tx), int(ty)))
+
+    def set_topography(self, phis_avg):
+        """Bottom topography: cell averages of sqrtG * phi_s, shape (6, N, N) (any array
+        convertible to FP64 on the host); None removes it."""
+        if phis_avg is None:
+            L.check(L.load().hope_set_topography(self._h, None))
+            return
+        if hasattr(phis_avg, "detach"):
+            phis_avg = phis_avg.detach().cpu().numpy()
+        a = np.ascontiguousarray(np.asarray(phis_avg, dtype=np.float64))
+        if a.shape != (6, self.N, self.N):
+            raise ValueError("topography must have shape (6, N, N)")
+        L.check(L.load().hope_set_topography(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
 
     def launches_per_stage(self):
         n = ctypes.c_int()

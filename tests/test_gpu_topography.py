@@ -1,0 +1,136 @@
+"""GPU-vs-oracle parity of the bottom-topography path (eqs. 2.13-2.14, section 5.2's
+mountain), called through the C ABI.
+
+FP64 bar: relative L2 per variable 1e-11 on tendencies and 1e-12 on states.  The other
+FP64 parity tests hold tendencies to 1e-12; here psi_B's per-cell weights are assembled
+on the host as sums of k^2 products whose terms exceed the sum by up to ~1e3 (the
+derivative weights of a k-point stencil alternate in sign), so the assembly's rounding
+reaches ~1e-13 relative and 1e-11 keeps a factor 100.  FP32: 1e-4 on tendencies, the
+flat FP32 path's bound.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as O  # noqa: E402
+from synth import noise_field, perturb_h  # noqa: E402
+
+G = O.GRAVITY
+H0, U0 = 5960.0, 20.0  # section 5.2
+
+
+@pytest.fixture(scope="module")
+def hp():
+    import paper_2411_19185_gb300 as hp
+    hp.load()
+    return hp
+
+
+def rel_l2(a, b):
+    return [float(np.linalg.norm(a[v] - b[v]) / np.linalg.norm(b[v])) for v in range(3)]
+
+
+def to_dev(q, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(q)).to("cuda", dtype)
+
+
+def mountain_case(N, k, noise_seed=None):
+    """Oracle with the mountain of eq. 5.8, the flow of section 5.2 (optionally with seeded
+    1% depth noise for large tendencies everywhere) and the surface's cell averages."""
+    o = O.Oracle(N, k)
+    o.set_mountain()
+    q = o.geostrophic(u0=U0, phi0=H0 * G)
+    if noise_seed is not None:
+        q = np.ascontiguousarray(perturb_h(q, noise_field((6, N, N), noise_seed)))
+    return o, q, o.topography()
+
+
+@pytest.mark.parametrize("k,N", [(3, 13), (5, 20), (7, 17), (11, 23)])
+def test_tendency_over_mountain_fp64(hp, k, N):
+    """L(q) with the surface (eq. 3.1 with eqs. 2.13-2.14), TPP, FP64, ragged tiles."""
+    o, q, sbar = mountain_case(N, k, noise_seed=3)
+    s = hp.Sphere(N, k)
+    s.set_topography(sbar)
+    d = s.tendency(to_dev(q)).cpu().numpy()
+    ref = o.tendency(q)
+    assert max(rel_l2(d, ref)) < 1e-11, rel_l2(d, ref)
+    assert s.status() == 0
+    assert s.launches_per_stage() == 5
+
+
+def test_steps_over_mountain_fp64(hp):
+    """SSP-RK3 steps of section 5.2's flow (C16, TPP5, dt = 600 s): a step graph captured
+    before the surface is set is not replayed after it; states against the oracle and the
+    depth's mass conserved."""
+    N, k = 16, 5
+    o, q0, sbar = mountain_case(N, k)
+    s = hp.Sphere(N, k)
+    q = to_dev(q0)
+    s.step(q, 600.0, 1)  # captures a flat step graph for (q, dt)
+    q.copy_(to_dev(q0))
+    s.set_topography(sbar)
+    m0 = s.mass(q)
+    s.step(q, 600.0, 5)
+    ref = o.step(q0, 600.0, 5)
+    got = q.cpu().numpy()
+    assert max(rel_l2(got, ref)) < 1e-12, rel_l2(got, ref)
+    # the surface really acts: the flat run differs at the 1e-4 level
+    flat = O.Oracle(N, k).step(q0, 600.0, 5)
+    assert max(rel_l2(got, flat)) > 1e-6
+    assert abs(s.mass(q) - m0) / abs(m0) < 1e-14
+    assert s.status() == 0
+
+
+def test_zero_surface_and_removal(hp):
+    """A zero surface adds exact zeros (psi_B weights and edge values all 0), so the
+    tendency equals the flat one to the last bits; removing the surface restores the flat
+    kernels and their result bit for bit."""
+    N, k = 12, 5
+    o = O.Oracle(N, k)
+    q = to_dev(perturb_h(o.rossby_haurwitz(), noise_field((6, N, N), 1)))
+    s = hp.Sphere(N, k)
+    flat = s.tendency(q).cpu().numpy()
+    s.set_topography(np.zeros((6, N, N)))
+    zero = s.tendency(q).cpu().numpy()
+    assert np.max(np.abs(zero - flat)) <= 1e-15 * np.max(np.abs(flat))
+    s.set_topography(None)
+    assert s.launches_per_stage() == 4
+    assert np.array_equal(s.tendency(q).cpu().numpy(), flat)
+
+
+def test_fp32_tendency_over_mountain(hp):
+    """FP32 context (tables built in FP64, stored in FP32) against the FP64 oracle."""
+    N, k = 17, 5
+    o, q, sbar = mountain_case(N, k, noise_seed=5)
+    s = hp.Sphere(N, k, precision=hp.HOPE_FP32)
+    s.set_topography(sbar)
+    d = s.tendency(to_dev(q, torch.float32)).double().cpu().numpy()
+    err = rel_l2(d, o.tendency(q))
+    assert max(err) < 1e-4, err
+
+
+def test_topography_limits(hp):
+    """WENO2D contexts and ensembles refuse a surface, the adjoints refuse while one is
+    set, and a non-finite value is an invalid argument."""
+    import paper_2411_19185_gb300._lib as L
+    N, k = 8, 3
+    sbar = np.full((6, N, N), 100.0)
+    with pytest.raises(L.HopeError) as e:
+        hp.Sphere(N, k, scheme=hp.HOPE_WENO2D).set_topography(sbar)
+    assert e.value.code == -6
+    with pytest.raises(L.HopeError) as e:
+        hp.Sphere([N, N], k).set_topography(sbar)
+    assert e.value.code == -6
+    s = hp.Sphere(N, k)
+    bad = sbar.copy()
+    bad[0, 0, 0] = np.nan
+    with pytest.raises(L.HopeError) as e:
+        s.set_topography(bad)
+    assert e.value.code == -1
+    s.set_topography(sbar)
+    q = to_dev(O.Oracle(N, k).geostrophic(u0=U0, phi0=H0 * G))
+    with pytest.raises(L.HopeError) as e:
+        s.tendency_vjp(q, torch.ones_like(q))
+    assert e.value.code == -6
