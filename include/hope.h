@@ -130,6 +130,14 @@ int hope_elem_size(hope_t ctx);
  *   case 7  dam break: h_in inside a great-circle cap  params: lon, lat, radius, h_in, h_out
  *   case 8  case 2 plus Gaussian bumps of phi          params: alpha, u0, phi0, amp_m, radius;
  *           extra_host: n_extra/2 (lon, lat) centres
+ *   case 5  the isolated mountain of eq. 5.8 as a surface: sqrtG phi_s in variable 0,
+ *           zero momentum (the input of hope_set_topography)
+ *                                                      params: hs0_m, R_rad, lon_c, lat_c
+ *   case 10 section 5.2's flow over that mountain: case 2 with its phi read as the free
+ *           surface phi_t, stored as the depth phi_t - phi_s
+ *                                                      params: alpha, u0, phi0, hs0_m, R_rad,
+ *                                                              lon_c, lat_c
+ *           (the mountain's longitude difference is taken modulo 2 pi)
  * For an ensemble every member gets the same case.
  */
 int hope_initial_state(hope_t ctx, int ic_case, const double *params, int n_params,

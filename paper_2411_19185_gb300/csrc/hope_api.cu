@@ -216,10 +216,22 @@ struct ICParams {
   double v[8];
 };
 
+// phi_s = g hs0 (1 - r/R) of eq. 5.8, M = (hs0, R, lon_c, lat_c); the longitude
+// difference is taken modulo 2 pi.
+__device__ inline double mountain_phis(const double *M, double g, double lam, double th) {
+  const double dl = remainder(lam - M[2], 2.0 * HOPE_PI), dt = th - M[3];
+  const double r = sqrt(fmin(M[1] * M[1], dl * dl + dt * dt));
+  return g * M[0] * (1.0 - r / M[1]);
+}
+
 __device__ inline void ic_field(int cs, const ICParams &P, const double *ex, int nex, double a, double g,
                                 double Om, double lam, double th, double *phi, double *us, double *vs) {
   double ct = cos(th), st = sin(th);
-  if (cs == 2 || cs == 8) {
+  if (cs == 5) {
+    *phi = mountain_phis(P.v, g, lam, th);
+    *us = 0.0;
+    *vs = 0.0;
+  } else if (cs == 2 || cs == 8 || cs == 10) {
     double al = P.v[0], u0 = P.v[1], phi0 = P.v[2];
     double t = -cos(lam) * ct * sin(al) + st * cos(al);
     *phi = phi0 - (a * Om * u0 + 0.5 * u0 * u0) * t * t;
@@ -234,6 +246,7 @@ __device__ inline void ic_field(int cs, const ICParams &P, const double *ex, int
         *phi += g * P.v[3] * exp(-d * d);
       }
     }
+    if (cs == 10) *phi -= mountain_phis(P.v + 3, g, lam, th);  // phi of eq. 5.1 is the free surface
   } else if (cs == 6) {
     double w = P.v[0], K = P.v[1], R = P.v[2], h0 = P.v[3];
     double c2 = ct * ct;
@@ -644,7 +657,9 @@ int hope_elem_size(hope_t ctx) { return ctx ? ctx->esize : 0; }
 
 int hope_initial_state(hope_t ctx, int ic_case, const double *params, int n_params, const double *extra_host,
                        int n_extra, void *q_dev, hope_stream_t stream) {
-  if (!ctx || !q_dev || (ic_case != 2 && ic_case != 6 && ic_case != 7 && ic_case != 8) || n_params < 0 ||
+  if (!ctx || !q_dev ||
+      (ic_case != 2 && ic_case != 5 && ic_case != 6 && ic_case != 7 && ic_case != 8 && ic_case != 10) ||
+      n_params < 0 ||
       n_params > 8 || (n_params > 0 && !params) || n_extra < 0 || (n_extra > 0 && !extra_host)) {
     set_error("hope_initial_state: invalid argument");
     return HOPE_EINVAL;

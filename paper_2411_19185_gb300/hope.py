@@ -12,6 +12,8 @@ import torch
 from . import _lib as L
 
 IC_GEOSTROPHIC, IC_ROSSBY, IC_DAMBREAK, IC_BUMPS = 2, 6, 7, 8
+IC_MOUNTAIN_SURFACE, IC_MOUNTAIN_FLOW = 5, 10
+MOUNTAIN = (2000.0, 3.141592653589793 / 9, 1.5 * 3.141592653589793, 3.141592653589793 / 6)  # section 5.2
 RADIUS, GRAVITY, OMEGA = 6.37122e6, 9.80616, 7.292e-5
 
 
@@ -95,6 +97,16 @@ class Sphere:
         if u0 is None:
             u0 = 2 * 3.141592653589793 * self.radius / (12 * 86400.0)
         return self.initial_state(IC_GEOSTROPHIC, [alpha, u0, phi0])
+
+    def mountain_surface(self, hs0=MOUNTAIN[0], R=MOUNTAIN[1], lon_c=MOUNTAIN[2], lat_c=MOUNTAIN[3]):
+        """Cell averages of sqrtG phi_s of the mountain of eq. 5.8, shape (6, N, N) on the
+        device (pass to set_topography)."""
+        return self.initial_state(IC_MOUNTAIN_SURFACE, [hs0, R, lon_c, lat_c])[0]
+
+    def mountain_flow(self, alpha=0.0, u0=20.0, h0=5960.0, hs0=MOUNTAIN[0], R=MOUNTAIN[1],
+                      lon_c=MOUNTAIN[2], lat_c=MOUNTAIN[3]):
+        """Section 5.2's zonal flow over the mountain (depth state; h0 the free surface)."""
+        return self.initial_state(IC_MOUNTAIN_FLOW, [alpha, u0, h0 * self.gravity, hs0, R, lon_c, lat_c])
 
     def rossby_haurwitz(self, w=7.848e-6, K=7.848e-6, R=4.0, h0=8000.0):
         return self.initial_state(IC_ROSSBY, [w, K, R, h0])
