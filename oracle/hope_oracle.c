@@ -1282,9 +1282,57 @@ static double gc_dist(double l1, double t1, double l2, double t2) {
   return acos(c);
 }
 
+/* Perturbed jet of section 5.4 (Galewsky et al. 2004), P = (umax, theta0, theta1,     */
+/* theta2, alpha, beta, hhat, phi0).  u(theta) of eq. 5.16, zero outside (theta0,       */
+/* theta1).                                                                            */
+static double jet_u(const double *P, double th) {
+  if (th <= P[1] || th >= P[2]) return 0.0;
+  double en = exp(-4.0 / ((P[2] - P[1]) * (P[2] - P[1])));
+  return P[0] / en * exp(1.0 / ((th - P[1]) * (th - P[2])));
+}
+
+/* The balance integral of eq. 5.17, int_{-pi/2}^{theta} a u (f + tan(t) u / a) dt,     */
+/* f = 2 Omega sin(t), by composite Gauss-Legendre (16 panels of 8 nodes) over          */
+/* (theta0, min(theta, theta1)); u vanishes elsewhere.                                  */
+static double jet_integral(const orc *o, const double *P, double th) {
+  double hi = th < P[2] ? th : P[2];
+  if (hi <= P[1]) return 0.0;
+  double x[8], w[8], s = 0.0, h = (hi - P[1]) / 16.0;
+  orc_gauss(8, x, w);
+  for (int pnl = 0; pnl < 16; ++pnl)
+    for (int q = 0; q < 8; ++q) {
+      double t = P[1] + (pnl + 0.5 + x[q]) * h, u = jet_u(P, t);
+      s += w[q] * h * o->r * u * (2.0 * o->omega * sin(t) + tan(t) * u / o->r);
+    }
+  return s;
+}
+
+/* reading c30: phi0 = 0 in the parameters means Galewsky's choice, the constant that   */
+/* makes the area mean of the balanced phi (without phi') equal g * 10 km:              */
+/* phi0 = g 1e4 + (1/2) int_{-pi/2}^{pi/2} I(theta) cos(theta) d theta.                 */
+static double jet_phi0(const orc *o, const double *P) {
+  double x[8], w[8], s = 0.0, h = (P[2] - P[1]) / 16.0;
+  orc_gauss(8, x, w);
+  for (int pnl = 0; pnl < 16; ++pnl)
+    for (int q = 0; q < 8; ++q) {
+      double t = P[1] + (pnl + 0.5 + x[q]) * h;
+      s += w[q] * h * jet_integral(o, P, t) * cos(t);
+    }
+  s += jet_integral(o, P, P[2]) * (1.0 - sin(P[2]));
+  return o->g * 1.0e4 + 0.5 * s;
+}
+
 static void ic_point(const orc *o, int cs, const double *P, int n_extra, const double *ex, double lam,
                      double th, double *phi, double *us, double *vs) {
   double a = o->r, Om = o->omega, g = o->g;
+  if (cs == ORC_IC_GALEWSKY) {
+    /* eqs. 5.16-5.18, lambda in (-pi, pi] */
+    double d2 = (lam / P[4]) * (lam / P[4]) + ((P[3] - th) / P[5]) * ((P[3] - th) / P[5]);
+    *phi = P[7] + g * P[6] * cos(th) * exp(-d2) - jet_integral(o, P, th);
+    *us = jet_u(P, th);
+    *vs = 0.0;
+    return;
+  }
   if (cs == ORC_IC_GEOSTROPHIC || cs == ORC_IC_BUMPS) {
     double al = P[0], u0 = P[1], phi0 = P[2];
     double t = -cos(lam) * cos(th) * sin(al) + sin(th) * cos(al);
@@ -1316,9 +1364,12 @@ static void ic_point(const orc *o, int cs, const double *P, int n_extra, const d
   }
 }
 
-void orc_ic(const orc *o, int cs, const double *P, int n_extra, const double *ex, double *q) {
+void orc_ic(const orc *o, int cs, const double *P_in, int n_extra, const double *ex, double *q) {
   int N = o->N, me = o->me;
   size_t pi = (size_t)N * N;
+  double P[8];
+  for (int t = 0; t < 8; ++t) P[t] = P_in[t];
+  if (cs == ORC_IC_GALEWSKY && P[7] == 0.0) P[7] = jet_phi0(o, P);
 #pragma omp parallel for schedule(static)
   for (int pj = 0; pj < 6 * N; ++pj) {
     int p = pj / N, j = pj % N;
@@ -1345,6 +1396,13 @@ void orc_ic(const orc *o, int cs, const double *P, int n_extra, const double *ex
       for (int v = 0; v < 3; ++v) q[(size_t)(v * 6 + p) * pi + (size_t)j * N + i] = acc[v];
     }
   }
+}
+
+void orc_ic_point(const orc *o, int cs, const double *P_in, double lam, double th, double *out3) {
+  double P[8];
+  for (int t = 0; t < 8; ++t) P[t] = P_in[t];
+  if (cs == ORC_IC_GALEWSKY && P[7] == 0.0) P[7] = jet_phi0(o, P);
+  ic_point(o, cs, P, 0, NULL, lam, th, out3, out3 + 1, out3 + 2);
 }
 
 void orc_cell_sqrtg(const orc *o, double *out) {

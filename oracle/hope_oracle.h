@@ -43,6 +43,8 @@ extern "C" {
 #define ORC_IC_DAMBREAK 7      /* params: lon_c, lat_c, radius_rad, h_in, h_out   */
 #define ORC_IC_BUMPS 8         /* geostrophic + n Gaussian bumps; params: alpha,u0,phi0,amp_m,
                                   radius_rad; extra = n pairs (lon, lat)          */
+#define ORC_IC_GALEWSKY 11     /* perturbed jet, eqs. 5.16-5.18; params: umax, theta0, theta1,
+                                  theta2, alpha, beta, hhat_m, phi0 (0: mean depth 10 km) */
 
 /* analytic bottom surfaces for orc_set_topography_case; params (4 doubles):
    MOUNTAIN  hs0_m, R_rad, lon_c, lat_c   isolated cone of eq. 5.8
@@ -84,6 +86,9 @@ void orc_set_topography(orc *o, const double *sbar);
 void orc_set_topography_case(orc *o, int tcase, const double *params4);
 void orc_get_topography(const orc *o, double *sbar);
 double orc_topography_point(const orc *o, int panel, double X, double Y);
+/* phi, u_s, v_s of an initial condition at one (lambda, theta) (params as orc_ic,
+   8 doubles; no topography, no extra). */
+void orc_ic_point(const orc *o, int ic_case, const double *params8, double lam, double th, double *out3);
 /* Cell-averaged sqrtG (unit sphere) per cell, [p][j][i]. */
 void orc_cell_sqrtg(const orc *o, double *out);
 /* L1, L2, Linf error norms of phi (eqs. 5.4-5.7). */

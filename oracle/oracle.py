@@ -17,7 +17,9 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 TPP, WENO = 0, 1
 SSPRK3, WSRK3 = 0, 1
-IC_GEOSTROPHIC, IC_ROSSBY, IC_DAMBREAK, IC_BUMPS = 2, 6, 7, 8
+IC_GEOSTROPHIC, IC_ROSSBY, IC_DAMBREAK, IC_BUMPS, IC_GALEWSKY = 2, 6, 7, 8, 11
+# section 5.4: umax, theta0, theta1, theta2, alpha, beta, hhat; phi0 = 0: mean depth 10 km
+GALEWSKY = (80.0, np.pi / 7, 5 * np.pi / 14, np.pi / 4, 1.0 / 3, 1.0 / 15, 120.0)
 TOPO_MOUNTAIN, TOPO_ZONAL, TOPO_HILL = 1, 2, 3
 
 RADIUS = 6.37122e6
@@ -62,6 +64,7 @@ def lib():
         L.orc_reconstruct_all.argtypes = [vp, P, P]
         L.orc_ic.argtypes = [vp, ctypes.c_int, P, ctypes.c_int, P, P]
         L.orc_cell_sqrtg.argtypes = [vp, P]
+        L.orc_ic_point.argtypes = [vp, ctypes.c_int, P, ctypes.c_double, ctypes.c_double, P]
         L.orc_norms.argtypes = [vp, P, P, P]
         L.orc_gauss.argtypes = [ctypes.c_int, P, P]
         L.orc_weights_1d.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, P]
@@ -165,7 +168,7 @@ class Oracle:
         return pts
 
     def ic(self, case, params, extra=None):
-        params = _f64(params)
+        params = _f64(list(np.ravel(params)) + [0.0] * max(0, 8 - np.size(params)))
         extra = _f64(np.zeros(1) if extra is None else np.ravel(extra))
         n_extra = extra.size if case == IC_BUMPS else 0
         out = np.empty(self.shape)
@@ -182,6 +185,19 @@ class Oracle:
 
     def dam_break(self, lon=0.0, lat=0.0, radius=np.deg2rad(20.0), h_in=10.0, h_out=1.0):
         return self.ic(IC_DAMBREAK, [lon, lat, radius, h_in, h_out])
+
+    def galewsky(self, perturbed=True, phi0=0.0):
+        """The perturbed jet of section 5.4 (eqs. 5.16-5.18); perturbed=False drops phi'."""
+        P = list(GALEWSKY)
+        if not perturbed:
+            P[6] = 0.0
+        return self.ic(IC_GALEWSKY, P + [phi0])
+
+    def ic_point(self, case, params, lam, th):
+        P = _f64(list(params) + [0.0] * (8 - len(params)))
+        out = np.empty(3)
+        lib().orc_ic_point(self._h, int(case), _p(P), float(lam), float(th), _p(out))
+        return out
 
     def bumps(self, centres, alpha=0.0, amp=50.0, radius=np.deg2rad(5.0), u0=None, phi0=2.94e4):
         if u0 is None:
