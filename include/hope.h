@@ -138,6 +138,11 @@ int hope_elem_size(hope_t ctx);
  *                                                      params: alpha, u0, phi0, hs0_m, R_rad,
  *                                                              lon_c, lat_c
  *           (the mountain's longitude difference is taken modulo 2 pi)
+ *   case 11 perturbed jet of section 5.4, eqs. 5.16-5.18 (balance integral by composite
+ *           Gauss-Legendre)                            params: umax, theta0, theta1, theta2,
+ *                                                              alpha, beta, hhat_m, phi0
+ *           (phi0 = 0: the constant giving a mean depth of 10 km without the bump);
+ *           extra_host is not used
  * For an ensemble every member gets the same case.
  */
 int hope_initial_state(hope_t ctx, int ic_case, const double *params, int n_params,

@@ -224,10 +224,41 @@ __device__ inline double mountain_phis(const double *M, double g, double lam, do
   return g * M[0] * (1.0 - r / M[1]);
 }
 
+// Perturbed jet of section 5.4 (Galewsky et al. 2004), P = (umax, theta0, theta1, theta2,
+// alpha, beta, hhat, phi0): u(theta) of eq. 5.16, zero outside (theta0, theta1).
+__host__ __device__ inline double jet_u(const double *P, double th) {
+  if (th <= P[1] || th >= P[2]) return 0.0;
+  const double en = exp(-4.0 / ((P[2] - P[1]) * (P[2] - P[1])));
+  return P[0] / en * exp(1.0 / ((th - P[1]) * (th - P[2])));
+}
+
+// The balance integral of eq. 5.17 from the south pole to theta, a u (2 Omega sin t +
+// tan(t) u / a) over (theta0, min(theta, theta1)) by composite Gauss-Legendre: 16 panels of
+// the 8-point rule xw = (nodes on [-1/2, 1/2], weights summing to 1).
+__host__ __device__ inline double jet_balance(const double *P, const double *xw, double a, double Om, double th) {
+  const double hi = th < P[2] ? th : P[2];
+  if (hi <= P[1]) return 0.0;
+  const double h = (hi - P[1]) / 16.0;
+  double s = 0.0;
+  for (int pnl = 0; pnl < 16; ++pnl)
+    for (int q = 0; q < 8; ++q) {
+      const double t = P[1] + (pnl + 0.5 + xw[q]) * h, u = jet_u(P, t);
+      s += xw[8 + q] * h * a * u * (2.0 * Om * sin(t) + tan(t) * u / a);
+    }
+  return s;
+}
+
 __device__ inline void ic_field(int cs, const ICParams &P, const double *ex, int nex, double a, double g,
                                 double Om, double lam, double th, double *phi, double *us, double *vs) {
   double ct = cos(th), st = sin(th);
-  if (cs == 5) {
+  if (cs == 11) {
+    // eqs. 5.16-5.18, lambda in (-pi, pi]; ex holds the 8-point rule of jet_balance
+    const double d2 = (lam / P.v[4]) * (lam / P.v[4]) + ((P.v[3] - th) / P.v[5]) * ((P.v[3] - th) / P.v[5]);
+    *phi = P.v[7] + g * P.v[6] * ct * exp(-d2) - jet_balance(P.v, ex, a, Om, th);
+    *us = jet_u(P.v, th);
+    *vs = 0.0;
+    (void)nex;
+  } else if (cs == 5) {
     *phi = mountain_phis(P.v, g, lam, th);
     *us = 0.0;
     *vs = 0.0;
@@ -658,7 +689,8 @@ int hope_elem_size(hope_t ctx) { return ctx ? ctx->esize : 0; }
 int hope_initial_state(hope_t ctx, int ic_case, const double *params, int n_params, const double *extra_host,
                        int n_extra, void *q_dev, hope_stream_t stream) {
   if (!ctx || !q_dev ||
-      (ic_case != 2 && ic_case != 5 && ic_case != 6 && ic_case != 7 && ic_case != 8 && ic_case != 10) ||
+      (ic_case != 2 && ic_case != 5 && ic_case != 6 && ic_case != 7 && ic_case != 8 && ic_case != 10 &&
+       ic_case != 11) ||
       n_params < 0 ||
       n_params > 8 || (n_params > 0 && !params) || n_extra < 0 || (n_extra > 0 && !extra_host)) {
     set_error("hope_initial_state: invalid argument");
@@ -667,6 +699,27 @@ int hope_initial_state(hope_t ctx, int ic_case, const double *params, int n_para
   cudaStream_t st = (cudaStream_t)stream;
   ICParams P;
   for (int t = 0; t < 8; ++t) P.v[t] = t < n_params ? params[t] : 0.0;
+  std::vector<double> jet_rule;
+  if (ic_case == 11) {
+    // the quadrature rule of the jet's balance integral travels in the extra array
+    jet_rule.resize(16);
+    gauss_legendre(8, jet_rule.data(), jet_rule.data() + 8);
+    if (P.v[7] == 0.0) {
+      // phi0 = 0 asks for Galewsky's constant: the area mean of the balanced phi (without
+      // the bump) is g x 10 km, phi0 = g 1e4 + 1/2 int I(theta) cos(theta) d theta
+      const double h = (P.v[2] - P.v[1]) / 16.0;
+      double s = 0.0;
+      for (int pnl = 0; pnl < 16; ++pnl)
+        for (int q = 0; q < 8; ++q) {
+          const double t = P.v[1] + (pnl + 0.5 + jet_rule[q]) * h;
+          s += jet_rule[8 + q] * h * jet_balance(P.v, jet_rule.data(), ctx->radius, ctx->omega, t) * cos(t);
+        }
+      s += jet_balance(P.v, jet_rule.data(), ctx->radius, ctx->omega, P.v[2]) * (1.0 - sin(P.v[2]));
+      P.v[7] = ctx->gravity * 1.0e4 + 0.5 * s;
+    }
+    extra_host = jet_rule.data();
+    n_extra = 16;
+  }
   double *d_ex = nullptr, *d_nw = nullptr;
   HOPE_CUDA_TRY(cudaMalloc(&d_ex, sizeof(double) * (n_extra > 0 ? n_extra : 1)));
   if (n_extra > 0) HOPE_CUDA_TRY(cudaMemcpy(d_ex, extra_host, sizeof(double) * n_extra, cudaMemcpyHostToDevice));

@@ -12,7 +12,9 @@ import torch
 from . import _lib as L
 
 IC_GEOSTROPHIC, IC_ROSSBY, IC_DAMBREAK, IC_BUMPS = 2, 6, 7, 8
-IC_MOUNTAIN_SURFACE, IC_MOUNTAIN_FLOW = 5, 10
+IC_MOUNTAIN_SURFACE, IC_MOUNTAIN_FLOW, IC_JET = 5, 10, 11
+# section 5.4: umax, theta0, theta1, theta2, alpha, beta, hhat
+JET = (80.0, 3.141592653589793 / 7, 5 * 3.141592653589793 / 14, 3.141592653589793 / 4, 1.0 / 3, 1.0 / 15, 120.0)
 MOUNTAIN = (2000.0, 3.141592653589793 / 9, 1.5 * 3.141592653589793, 3.141592653589793 / 6)  # section 5.2
 RADIUS, GRAVITY, OMEGA = 6.37122e6, 9.80616, 7.292e-5
 
@@ -107,6 +109,14 @@ class Sphere:
                       lon_c=MOUNTAIN[2], lat_c=MOUNTAIN[3]):
         """Section 5.2's zonal flow over the mountain (depth state; h0 the free surface)."""
         return self.initial_state(IC_MOUNTAIN_FLOW, [alpha, u0, h0 * self.gravity, hs0, R, lon_c, lat_c])
+
+    def galewsky(self, perturbed=True, phi0=0.0):
+        """The perturbed jet of section 5.4; perturbed=False drops the bump of eq. 5.18;
+        phi0 = 0 gives a mean depth of 10 km."""
+        P = list(JET)
+        if not perturbed:
+            P[6] = 0.0
+        return self.initial_state(IC_JET, P + [phi0])
 
     def rossby_haurwitz(self, w=7.848e-6, K=7.848e-6, R=4.0, h0=8000.0):
         return self.initial_state(IC_ROSSBY, [w, K, R, h0])

@@ -35,7 +35,7 @@ def to_dev(q, dtype=torch.float64):
     return torch.from_numpy(np.ascontiguousarray(q)).to("cuda", dtype)
 
 
-@pytest.mark.parametrize("case", ["geo", "rh", "dam", "bumps"])
+@pytest.mark.parametrize("case", ["geo", "rh", "dam", "bumps", "jet"])
 def test_initial_conditions_match(hp, case):
     """Cell averages of the analytic cases (section 5): device kernel vs oracle."""
     N, k = 20, 5
@@ -48,6 +48,8 @@ def test_initial_conditions_match(hp, case):
         a, b = s.rossby_haurwitz(), o.rossby_haurwitz()
     elif case == "dam":
         a, b = s.dam_break(), o.dam_break()
+    elif case == "jet":
+        a, b = s.galewsky(), o.galewsky()
     else:
         a, b = s.bumps(cent), o.bumps(cent)
     torch.cuda.synchronize()
