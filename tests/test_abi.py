@@ -47,6 +47,9 @@ def test_invalid_arguments_rejected_without_device(lib):
     assert b"invalid" in lib.hope_last_error_message()
     assert lib.hope_tendency(None, None, None, None) == -1
     assert lib.hope_step(None, None, 1.0, 1, None) == -1
+    assert lib.hope_set_topography(None, None) == -1
+    assert b"null context" in lib.hope_last_error_message()
+    assert lib.hope_initial_state(None, 11, None, 0, None, 0, None, None) == -1
 
 
 def test_default_params(lib):
