@@ -329,6 +329,121 @@ double orc_weno_beta(int l, int o0x, int o0y, const double *Qsub) {
   return (double)beta;
 }
 
+
+/* ------------------------------------------------------------------------- */
+/* Dimension-by-dimension WENO-Z, the 1-D comparator of section 5.5 (fifth     */
+/* order): the 1-D WENO-Z of Borges et al. (2008) on the k cell averages of a  */
+/* line, at xi.  Sub-stencil s (s = 0..l-1) covers offsets [s-H, s-H+l-1];     */
+/* the linear weights solve sum_s gamma_s r_s = r_k (the 1-D form of eqs.      */
+/* 3.16-3.19, least squares in long double), split with theta = 3 as in eq.    */
+/* 3.20 (reading c2); beta_s is the Jiang-Shu indicator sum_{m=1}^{l-1} of the  */
+/* integral of (p_s^(m))^2 over the unit target cell; tau = |beta_0 -          */
+/* beta_{l-1}|; alpha = gamma (1 + tau / (beta + eps)) (reading c31).          */
+/* ------------------------------------------------------------------------- */
+int orc_weno1d_gamma(int k, double xi, double *gam, double *resid) {
+  int H = (k - 1) / 2, l = (k + 1) / 2;
+  long double RH[MAXK], RL[MAXK * MAXK], sub[MAXK], NE[MAXK * MAXK], rhs[MAXK];
+  weights_1d_ld(k, -H, xi, RH);
+  for (int r = 0; r < k * l; ++r) RL[r] = 0.0L;
+  for (int sb = 0; sb < l; ++sb) {
+    weights_1d_ld(l, sb - H, xi, sub);
+    for (int a = 0; a < l; ++a) RL[(sb + a) * l + sb] = sub[a];
+  }
+  for (int i = 0; i < l; ++i) {
+    long double t = 0.0L;
+    for (int r = 0; r < k; ++r) t += RL[r * l + i] * RH[r];
+    rhs[i] = t;
+    for (int j = 0; j < l; ++j) {
+      long double u = 0.0L;
+      for (int r = 0; r < k; ++r) u += RL[r * l + i] * RL[r * l + j];
+      NE[i * l + j] = u;
+    }
+  }
+  solve_ld(l, NE, rhs);
+  long double mx = 0.0L;
+  for (int r = 0; r < k; ++r) {
+    long double t = -RH[r];
+    for (int i = 0; i < l; ++i) t += RL[r * l + i] * rhs[i];
+    if (fabsl(t) > mx) mx = fabsl(t);
+  }
+  for (int i = 0; i < l; ++i) gam[i] = (double)rhs[i];
+  if (resid) *resid = (double)mx;
+  return l;
+}
+
+static double beta_1d(int l, int o0, const double *v) {
+  long double C[MAXK * MAXK], c[MAXK];
+  coeffs_1d(l, o0, C);
+  for (int a = 0; a < l; ++a) {
+    long double t = 0.0L;
+    for (int j = 0; j < l; ++j) t += C[a * l + j] * v[j];
+    c[a] = t;
+  }
+  double gx[MAXK], gw[MAXK];
+  orc_gauss(l, gx, gw);
+  long double b = 0.0L;
+  for (int m = 1; m < l; ++m)
+    for (int q = 0; q < l; ++q) {
+      long double d = 0.0L;
+      for (int a = 0; a < l; ++a) d += c[a] * dmono(a, m, gx[q]);
+      b += (long double)gw[q] * d * d;
+    }
+  return (double)b;
+}
+
+/* 1-D tables at one position: sub-stencil weights r[l][l] and the split weights */
+typedef struct {
+  double r[MAXK * MAXK], gp[MAXK], gm[MAXK], sp, sm;
+} w1d_t;
+
+static void w1d_tables(int k, double xi, w1d_t *t) {
+  int H = (k - 1) / 2, l = (k + 1) / 2;
+  long double sub[MAXK];
+  for (int sb = 0; sb < l; ++sb) {
+    weights_1d_ld(l, sb - H, xi, sub);
+    for (int a = 0; a < l; ++a) t->r[sb * l + a] = (double)sub[a];
+  }
+  double gam[MAXK];
+  orc_weno1d_gamma(k, xi, gam, NULL);
+  t->sp = t->sm = 0.0;
+  for (int i = 0; i < l; ++i) {
+    t->gp[i] = 0.5 * (3.0 * fabs(gam[i]) + gam[i]);
+    t->gm[i] = 0.5 * (3.0 * fabs(gam[i]) - gam[i]);
+    t->sp += t->gp[i];
+    t->sm += t->gm[i];
+  }
+}
+
+static double w1d_value(int k, const w1d_t *t, const double *v, double eps) {
+  int H = (k - 1) / 2, l = (k + 1) / 2;
+  double beta[MAXK], p[MAXK], ap[MAXK], am[MAXK], sap = 0.0, sam = 0.0;
+  for (int sb = 0; sb < l; ++sb) {
+    double u = 0.0;
+    for (int a = 0; a < l; ++a) u += t->r[sb * l + a] * v[sb + a];
+    p[sb] = u;
+    beta[sb] = beta_1d(l, sb - H, v + sb);
+  }
+  double tau = fabs(beta[0] - beta[l - 1]);
+  for (int sb = 0; sb < l; ++sb) {
+    double f = 1.0 + tau / (beta[sb] + eps);
+    ap[sb] = t->gp[sb] / t->sp * f;
+    am[sb] = t->gm[sb] / t->sm * f;
+    sap += ap[sb];
+    sam += am[sb];
+  }
+  double qp = 0.0, qm = 0.0;
+  for (int sb = 0; sb < l; ++sb) {
+    qp += ap[sb] / sap * p[sb];
+    qm += am[sb] / sam * p[sb];
+  }
+  return t->sp * qp - t->sm * qm;
+}
+
+double orc_weno1d_point(int k, const double *v, double xi, double eps) {
+  w1d_t t;
+  w1d_tables(k, xi, &t);
+  return w1d_value(k, &t, v, eps);
+}
 /* ------------------------------------------------------------------------- */
 /* Geometry (section 2): gnomonic equiangular cube, unit sphere.               */
 /* Panel p (0-based, paper's panel p+1) maps (X, Y) = (tan x, tan y) to        */
@@ -515,6 +630,7 @@ struct orc {
   int tcase;       /* analytic surface behind sbar (ORC_TOPO_*), 0 if set from averages */
   double tpar[4];
   double *Rd;      /* [me*me][2][k*k] x- and y-derivative weights at the cell points */
+  void *w1d;       /* [me+2] 1-D WENO-Z tables at xi = -1/2, +1/2, g_0.. (ORC_WENO1D) */
 };
 
 int orc_npoc(const orc *o) { return o->npoc; }
@@ -571,6 +687,14 @@ orc *orc_new(int N, int k, int scheme, double radius, double gravity, double ome
   o->R = (double *)malloc(sizeof(double) * np * kk);
   for (int pt = 0; pt < np; ++pt) orc_tpp_weights_2d(k, o->px[pt], o->py[pt], o->R + (size_t)pt * kk);
 
+  if (scheme == ORC_WENO1D) {
+    if (k != 5) { orc_free(o); return NULL; } /* the comparator of section 5.5 is fifth order */
+    w1d_t *t = (w1d_t *)malloc(sizeof(w1d_t) * (me + 2));
+    w1d_tables(k, -0.5, &t[0]);
+    w1d_tables(k, 0.5, &t[1]);
+    for (int g = 0; g < me; ++g) w1d_tables(k, o->gx[g], &t[2 + g]);
+    o->w1d = t;
+  }
   if (scheme == ORC_WENO) {
     int l = o->l, s = o->s;
     o->Rsub = (double *)malloc(sizeof(double) * np * s * l * l);
@@ -693,7 +817,7 @@ void orc_free(orc *o) {
   if (!o) return;
   free(o->px); free(o->py); free(o->R); free(o->Rsub); free(o->gp); free(o->gm);
   free(o->sigp); free(o->sigm); free(o->ring); free(o->gq); free(o->nb);
-  free(o->sbar); free(o->Rd);
+  free(o->sbar); free(o->Rd); free(o->w1d);
   free(o);
 }
 
@@ -836,6 +960,24 @@ void orc_reconstruct_all(orc *o, const double *ext, double *pts) {
         weno_betas(o, st, beta);
         double tau = weno_tau(o->s, beta);
         for (int pt = 0; pt < np; ++pt) out[pt] = weno_value(o, st, pt, beta, tau);
+      } else if (o->scheme == ORC_WENO1D) {
+        /* x on every stencil row at the point's xi, then y on the row values */
+        const w1d_t *t = (const w1d_t *)o->w1d;
+        int me = o->me;
+        for (int pt = 0; pt < np; ++pt) {
+          int ix, iy;
+          if (pt < 4 * me) {
+            int side = pt / me, r = pt % me;
+            ix = side == 0 ? 0 : (side == 1 ? 1 : 2 + r);
+            iy = side == 2 ? 0 : (side == 3 ? 1 : 2 + r);
+          } else {
+            ix = 2 + (pt - 4 * me) % me;
+            iy = 2 + (pt - 4 * me) / me;
+          }
+          double L[MAXK];
+          for (int b = 0; b < k; ++b) L[b] = w1d_value(k, &t[ix], st + b * k, o->eps);
+          out[pt] = w1d_value(k, &t[iy], L, o->eps);
+        }
       } else {
         for (int pt = 0; pt < np; ++pt) out[pt] = tpp_point(o, st, pt);
       }

@@ -34,6 +34,7 @@ extern "C" {
 
 #define ORC_TPP 0
 #define ORC_WENO 1
+#define ORC_WENO1D 2   /* dimension-by-dimension WENO-Z (fifth order only), section 5.5 */
 #define ORC_SSPRK3 0
 #define ORC_WSRK3 1
 
@@ -104,6 +105,10 @@ void orc_sqrtg_grad(double X, double Y, double *out2);
 int orc_weno_gamma(int k, double xi, double eta, double *gam, double *resid);
 double orc_weno_beta(int l, int o0x, int o0y, const double *Qsub);
 double orc_weno_point(const orc *o, const double *stencil, int pt);
+/* 1-D WENO-Z (dimension-by-dimension comparator): linear weights at xi and the value at
+   xi from k cell averages v (offsets -H..H) with the given epsilon. */
+int orc_weno1d_gamma(int k, double xi, double *gam, double *resid);
+double orc_weno1d_point(int k, const double *v, double xi, double eps);
 void orc_metric(double X, double Y, double *out7);
 void orc_jacobian(int panel, double X, double Y, double *J4);
 void orc_xyz(int panel, double X, double Y, double *xyz);

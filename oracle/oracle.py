@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hope_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-TPP, WENO = 0, 1
+TPP, WENO, WENO1D = 0, 1, 2
 SSPRK3, WSRK3 = 0, 1
 IC_GEOSTROPHIC, IC_ROSSBY, IC_DAMBREAK, IC_BUMPS, IC_GALEWSKY = 2, 6, 7, 8, 11
 # section 5.4: umax, theta0, theta1, theta2, alpha, beta, hhat; phi0 = 0: mean depth 10 km
@@ -74,6 +74,10 @@ def lib():
         L.orc_weno_gamma.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, P, P]
         L.orc_weno_beta.restype = ctypes.c_double
         L.orc_weno_beta.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
+        L.orc_weno1d_gamma.restype = ctypes.c_int
+        L.orc_weno1d_gamma.argtypes = [ctypes.c_int, ctypes.c_double, P, P]
+        L.orc_weno1d_point.restype = ctypes.c_double
+        L.orc_weno1d_point.argtypes = [ctypes.c_int, P, ctypes.c_double, ctypes.c_double]
         L.orc_weno_point.restype = ctypes.c_double
         L.orc_weno_point.argtypes = [vp, P, ctypes.c_int]
         L.orc_metric.argtypes = [ctypes.c_double, ctypes.c_double, P]
@@ -339,6 +343,17 @@ def weno_gamma(k, xi, eta):
     r = np.empty(1)
     lib().orc_weno_gamma(int(k), float(xi), float(eta), _p(g), _p(r))
     return g.reshape(l, l), float(r[0])
+
+
+def weno1d_gamma(k, xi):
+    g = np.empty((k + 1) // 2)
+    r = np.empty(1)
+    lib().orc_weno1d_gamma(int(k), float(xi), _p(g), _p(r))
+    return g, float(r[0])
+
+
+def weno1d_point(k, v, xi, eps=1e-40):
+    return lib().orc_weno1d_point(int(k), _p(_f64(v)), float(xi), float(eps))
 
 
 def weno_beta(l, o0x, o0y, Qsub):
