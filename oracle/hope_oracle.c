@@ -961,9 +961,13 @@ void orc_reconstruct_all(orc *o, const double *ext, double *pts) {
         double tau = weno_tau(o->s, beta);
         for (int pt = 0; pt < np; ++pt) out[pt] = weno_value(o, st, pt, beta, tau);
       } else if (o->scheme == ORC_WENO1D) {
-        /* x on every stencil row at the point's xi, then y on the row values */
+        /* x on every stencil row at the point's xi, then y on the row values; the     */
+        /* x pass depends only on (row, xi position), so it is evaluated once for each */
         const w1d_t *t = (const w1d_t *)o->w1d;
         int me = o->me;
+        double Lx[MAXK + 2][MAXK];
+        for (int ix = 0; ix < me + 2; ++ix)
+          for (int b = 0; b < k; ++b) Lx[ix][b] = w1d_value(k, &t[ix], st + b * k, o->eps);
         for (int pt = 0; pt < np; ++pt) {
           int ix, iy;
           if (pt < 4 * me) {
@@ -974,9 +978,7 @@ void orc_reconstruct_all(orc *o, const double *ext, double *pts) {
             ix = 2 + (pt - 4 * me) % me;
             iy = 2 + (pt - 4 * me) / me;
           }
-          double L[MAXK];
-          for (int b = 0; b < k; ++b) L[b] = w1d_value(k, &t[ix], st + b * k, o->eps);
-          out[pt] = w1d_value(k, &t[iy], L, o->eps);
+          out[pt] = w1d_value(k, &t[iy], Lx[ix], o->eps);
         }
       } else {
         for (int pt = 0; pt < np; ++pt) out[pt] = tpp_point(o, st, pt);
