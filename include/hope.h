@@ -340,6 +340,23 @@ int hope_ghost_nnz(hope_t ctx, long long *nnz, long long *rows);
 int hope_ghost_selfcheck(int N, int order, int precision, int *symmetric, double *max_dev_sym,
                          double *max_dev_apply);
 
+/*
+ * Host-only construction, in FP64, of the bottom-surface tables that hope_set_topography
+ * uploads (no device is touched), for checks on machines without a GPU.  N >= order,
+ * order odd in 3..11, radius > 0 (m).  phis_avg_host: (6, N, N) cell averages of
+ * sqrtG phi_s.  Outputs are caller-owned host arrays, each may be NULL:
+ *   sep_out [4][me][6][N][N]  sqrtG phi_s at the edge points (west and east at the
+ *                             y-nodes, south and north at the x-nodes)
+ *   w_out   [2][k*k][6][N][N] weights of psi_B's cell average (eq. 2.14, momentum x and y)
+ *                             on the k x k stencil of the depth (cell (a, b) of the
+ *                             stencil at index b*k + a, offsets -H..H)
+ *   b_out   [2][6][N][N]      its constant part
+ * so that the cell average of psi_B is b + sum_c w[c] * stencil_c.  HOPE_EINVAL on bad
+ * arguments.
+ */
+int hope_topography_tables(int N, int order, double radius, const double *phis_avg_host, double *sep_out,
+                           double *w_out, double *b_out);
+
 /* Launch configuration introspection for profiling: number of kernel launches one
    tendency enqueues. */
 int hope_launches_per_stage(hope_t ctx, int *launches);

@@ -1214,6 +1214,44 @@ static void topo_source(const orc *o, double X, double Y, double s, const double
   S[2] += sG * fs * (m7[2] * dphit[0] + m7[3] * dphit[1]) / r2;
 }
 
+/* The cell average of psi_B (eq. 2.14) alone, out[2][6][N][N] (momentum x, y), */
+/* by the same steps as the tendency's sources: zero without a surface.        */
+void orc_topo_psib(orc *o, const double *q, double *out) {
+  int N = o->N, ne = o->ne, np = o->npoc, me = o->me;
+  size_t pn = (size_t)6 * N * N, nq = 3 * pn;
+  memset(out, 0, sizeof(double) * 2 * pn);
+  if (!o->sbar) return;
+  double *qt = (double *)malloc(sizeof(double) * nq);
+  double *ext = (double *)malloc(sizeof(double) * 3 * 6 * ne * ne);
+  double *pts = (double *)malloc(sizeof(double) * nq * np);
+  double *spt = (double *)malloc(sizeof(double) * pn * np);
+  double *dpt = (double *)malloc(sizeof(double) * pn * me * me * 2);
+  memcpy(qt, q, sizeof(double) * nq);
+  for (size_t c = 0; c < pn; ++c) qt[c] += o->sbar[c];
+  orc_fill_ghosts(o, qt, ext, NULL);
+  orc_reconstruct_all(o, ext, pts);
+  topo_points(o, ext, pts, spt, dpt);
+  for (int p = 0; p < 6; ++p)
+    for (int j = 0; j < N; ++j)
+      for (int i = 0; i < N; ++i) {
+        size_t cell = ((size_t)p * N + j) * N + i;
+        for (int h = 0; h < me; ++h)
+          for (int g = 0; g < me; ++g) {
+            double x = cell_centre(o, i) + o->gx[g] * o->dx, y = cell_centre(o, j) + o->gx[h] * o->dx;
+            double S[3] = {0.0, 0.0, 0.0};
+            topo_source(o, tan(x), tan(y), spt[cell * np + 4 * me + h * me + g],
+                        dpt + (cell * me * me + h * me + g) * 2, S);
+            out[cell] += o->gw[g] * o->gw[h] * S[1];
+            out[pn + cell] += o->gw[g] * o->gw[h] * S[2];
+          }
+      }
+  free(qt);
+  free(ext);
+  free(pts);
+  free(spt);
+  free(dpt);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Tendency (eq. 3.1, reading c6: F_{i+1/2} - F_{i-1/2} over dx = pi/(2N)).    */
 /* ------------------------------------------------------------------------- */

@@ -87,6 +87,8 @@ void orc_set_topography(orc *o, const double *sbar);
 void orc_set_topography_case(orc *o, int tcase, const double *params4);
 void orc_get_topography(const orc *o, double *sbar);
 double orc_topography_point(const orc *o, int panel, double X, double Y);
+/* The cell average of psi_B (eq. 2.14) alone for state q: out[2][6][N][N]. */
+void orc_topo_psib(orc *o, const double *q, double *out);
 /* phi, u_s, v_s of an initial condition at one (lambda, theta) (params as orc_ic,
    8 doubles; no topography, no extra). */
 void orc_ic_point(const orc *o, int ic_case, const double *params8, double lam, double th, double *out3);

@@ -94,6 +94,7 @@ def lib():
         L.orc_get_topography.argtypes = [vp, P]
         L.orc_topography_point.restype = ctypes.c_double
         L.orc_topography_point.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+        L.orc_topo_psib.argtypes = [vp, P, P]
         L.orc_tpp_dweights_2d.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, P]
         L.orc_sqrtg_grad.argtypes = [ctypes.c_double, ctypes.c_double, P]
         Pi = ctypes.POINTER(ctypes.c_int)
@@ -280,6 +281,12 @@ class Oracle:
     def topography(self):
         out = np.empty((6, self.N, self.N))
         lib().orc_get_topography(self._h, _p(out))
+        return out
+
+    def topo_psib(self, q):
+        """The cell average of psi_B (eq. 2.14) alone, shape (2, 6, N, N)."""
+        out = np.empty((2, 6, self.N, self.N))
+        lib().orc_topo_psib(self._h, _p(_f64(q)), _p(out))
         return out
 
     def topography_point(self, panel, X, Y):

@@ -23,7 +23,7 @@ EXPORTED = [
     "hope_last_error_message", "hope_measure_fma_peak", "hope_set_profiling", "hope_kernel_times",
     "hope_total_mass_noalloc", "hope_autotune", "hope_inject_fault", "hope_set_recon_tile", "hope_recon_tile",
     "hope_tape_bytes", "hope_step_record", "hope_step_vjp_tape", "hope_step_ssprk3_vjp",
-    "hope_ghost_selfcheck", "hope_set_topography",
+    "hope_ghost_selfcheck", "hope_set_topography", "hope_topography_tables",
 ]
 
 
@@ -90,6 +90,7 @@ def load():
         "hope_step_ssprk3_vjp": (i, [vp, vp, vp, vp, d, vp]),
         "hope_ghost_selfcheck": (i, [i, i, i, P(i), P(d), P(d)]),
         "hope_set_topography": (i, [vp, P(d)]),
+        "hope_topography_tables": (i, [i, i, d, P(d), P(d), P(d), P(d)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -1385,6 +1385,29 @@ int hope_set_topography(hope_t ctx, const double *phis_avg_host) {
   return HOPE_OK;
 }
 
+int hope_topography_tables(int N, int order, double radius, const double *phis_avg_host, double *sep_out,
+                           double *w_out, double *b_out) {
+  if (N < order || order < 3 || order > HOPE_MAXK || order % 2 == 0 || !(radius > 0) || !phis_avg_host) {
+    set_error("hope_topography_tables: invalid argument");
+    return HOPE_EINVAL;
+  }
+  hope_ctx ctx;
+  ctx.k = order;
+  ctx.H = (order - 1) / 2;
+  ctx.me = (order + 1) / 2;
+  ctx.prec = HOPE_FP64;
+  ctx.scheme = HOPE_TPP;
+  ctx.ghost_iters = 10;
+  ctx.radius = radius;
+  std::vector<double> sep, tw, tb;
+  int rc = build_topography_tables(&ctx, N, phis_avg_host, sep, tw, tb);
+  if (rc) return rc;
+  if (sep_out) memcpy(sep_out, sep.data(), sizeof(double) * sep.size());
+  if (w_out) memcpy(w_out, tw.data(), sizeof(double) * tw.size());
+  if (b_out) memcpy(b_out, tb.data(), sizeof(double) * tb.size());
+  return HOPE_OK;
+}
+
 int hope_measure_fma_peak(int precision, double *flops_per_s) {
   if (!flops_per_s || (precision != HOPE_FP64 && precision != HOPE_FP32)) return HOPE_EINVAL;
   int dev, sms;
