@@ -697,10 +697,12 @@ int build_topography_tables(const hope_ctx *ctx, int N, const double *phis_avg_h
   sep.assign((size_t)4 * ME * pn, 0.0);
   tw.assign((size_t)2 * KK * pn, 0.0);
   tb.assign(2 * pn, 0.0);
-  std::vector<double> st(KK), Dx(KK), Dy(KK);
-  for (int p = 0; p < 6; ++p)
-    for (int j = 0; j < N; ++j)
-      for (int i = 0; i < N; ++i) {
+  // every cell writes only its own entries, so the panel rows run in parallel
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int pj = 0; pj < 6 * N; ++pj) {
+    const int p = pj / N, j = pj % N;
+    std::vector<double> st(KK);
+    for (int i = 0; i < N; ++i) {
         const size_t cell = ((size_t)p * N + j) * N + i;
         for (int b = 0; b < K; ++b)
           for (int a = 0; a < K; ++a) st[b * K + a] = ext[((size_t)p * ne + j + b) * ne + i + a];
@@ -749,6 +751,7 @@ int build_topography_tables(const hope_ctx *ctx, int N, const double *phis_avg_h
               }
           }
       }
+  }
   return HOPE_OK;
 }
 
