@@ -631,6 +631,7 @@ struct orc {
   double tpar[4];
   double *Rd;      /* [me*me][2][k*k] x- and y-derivative weights at the cell points */
   void *w1d;       /* [me+2] 1-D WENO-Z tables at xi = -1/2, +1/2, g_0.. (ORC_WENO1D) */
+  int tform;       /* 0: total-geopotential form (eqs. 2.13-2.14); 1: depth form (2.1, 2.4) */
 };
 
 int orc_npoc(const orc *o) { return o->npoc; }
@@ -1146,6 +1147,13 @@ void orc_set_topography_case(orc *o, int tcase, const double *P) {
   free(sb);
 }
 
+/* Which form of the topography terms the tendency uses: 0 (default) the paper's        */
+/* total-geopotential form, eqs. 2.13-2.14 (reconstruct sqrtG phi_t, pressure with     */
+/* phi_t, psi_B = sqrtG phi_s G^ij d_j phi_t); 1 the depth form of eqs. 2.1 and 2.4     */
+/* that section 2 replaces (reconstruct sqrtG phi, pressure with phi, psi_B =           */
+/* -sqrtG phi G^ij d_j phi_s, the gradient of the surface's own TPP polynomial).        */
+void orc_set_topography_form(orc *o, int form) { o->tform = form ? 1 : 0; }
+
 void orc_get_topography(const orc *o, double *out) {
   size_t n = (size_t)6 * o->N * o->N;
   for (size_t c = 0; c < n; ++c) out[c] = o->sbar ? o->sbar[c] : 0.0;
@@ -1157,7 +1165,7 @@ void orc_get_topography(const orc *o, double *out) {
 /* variable is the depth sqrtG phi_t - sqrtG phi_s, and dpt[p][j][i][c][2] is    */
 /* the gradient of phi_t at cell point c, reading c29: phi_t = P / sqrtG with P  */
 /* the TPP polynomial of sqrtG phi_t, so d phi_t = (dP - phi_t d sqrtG) / sqrtG. */
-static void topo_points(orc *o, const double *ext, double *pts, double *spt, double *dpt) {
+static void topo_points(orc *o, const double *ext, double *pts, double *spt, double *dpt, int depth_form) {
   int N = o->N, k = o->k, ne = o->ne, np = o->npoc, me = o->me, kk = k * k;
   size_t pe = (size_t)ne * ne, pi = (size_t)N * N;
   double *s3 = (double *)calloc(3 * 6 * pi, sizeof(double));
@@ -1178,8 +1186,9 @@ static void topo_points(orc *o, const double *ext, double *pts, double *spt, dou
       for (int pt = 0; pt < np; ++pt) {
         double sv = tpp_point(o, st, pt);
         spt[cell * np + pt] = sv;
-        pts[cell * np + pt] -= sv; /* the v = 0 block of pts */
+        if (!depth_form) pts[cell * np + pt] -= sv; /* the v = 0 block of pts */
       }
+      const double *G = depth_form ? st : tt; /* the field whose gradient the source takes */
       for (int h = 0; h < me; ++h)
         for (int g = 0; g < me; ++g) {
           int c = h * me + g;
@@ -1188,11 +1197,11 @@ static void topo_points(orc *o, const double *ext, double *pts, double *spt, dou
           double m7[7], gs[2];
           orc_metric(X, Y, m7);
           orc_sqrtg_grad(X, Y, gs);
-          double P = tpp_point(o, tt, 4 * me + c);
+          double P = tpp_point(o, G, 4 * me + c);
           double dP[2] = {0.0, 0.0};
           for (int d = 0; d < 2; ++d) {
             const double *w = o->Rd + ((size_t)c * 2 + d) * kk;
-            for (int q = 0; q < kk; ++q) dP[d] += w[q] * tt[q];
+            for (int q = 0; q < kk; ++q) dP[d] += w[q] * G[q];
             dP[d] /= o->dx;
           }
           double pt_t = P / m7[0];
@@ -1230,7 +1239,7 @@ void orc_topo_psib(orc *o, const double *q, double *out) {
   for (size_t c = 0; c < pn; ++c) qt[c] += o->sbar[c];
   orc_fill_ghosts(o, qt, ext, NULL);
   orc_reconstruct_all(o, ext, pts);
-  topo_points(o, ext, pts, spt, dpt);
+  topo_points(o, ext, pts, spt, dpt, 0);
   for (int p = 0; p < 6; ++p)
     for (int j = 0; j < N; ++j)
       for (int i = 0; i < N; ++i) {
@@ -1265,18 +1274,21 @@ void orc_tendency(orc *o, const double *q, double *dqdt) {
   double *ext = (double *)malloc(sizeof(double) * 3 * 6 * ne * ne);
   double *pts = (double *)malloc(sizeof(double) * 3 * 6 * (size_t)N * N * np);
   double *qt = NULL, *spt = NULL, *dpt = NULL;
-  if (o->sbar) { /* eq. 2.13: reconstruct sqrtG phi_t = q0 + sqrtG phi_s */
+  if (o->sbar && !o->tform) { /* eq. 2.13: reconstruct sqrtG phi_t = q0 + sqrtG phi_s */
     size_t nq = (size_t)3 * 6 * N * N;
     qt = (double *)malloc(sizeof(double) * nq);
     memcpy(qt, q, sizeof(double) * nq);
     for (size_t c = 0; c < (size_t)6 * N * N; ++c) qt[c] += o->sbar[c];
+  }
+  if (o->sbar) {
     spt = (double *)malloc(sizeof(double) * 6 * (size_t)N * N * np);
     dpt = (double *)malloc(sizeof(double) * 6 * (size_t)N * N * me * me * 2);
   }
   orc_fill_ghosts(o, qt ? qt : q, ext, NULL);
   orc_reconstruct_all(o, ext, pts);
-  if (o->sbar) topo_points(o, ext, pts, spt, dpt);
-#define SPT(p, j, i, pt) (spt ? spt[((((size_t)(p)) * N + (j)) * N + (i)) * np + (pt)] : 0.0)
+  if (o->sbar) topo_points(o, ext, pts, spt, dpt, o->tform);
+  /* the depth form of eqs. 2.1 and 2.4 keeps phi in LMARS: no surface there */
+#define SPT(p, j, i, pt) (spt && !o->tform ? spt[((((size_t)(p)) * N + (j)) * N + (i)) * np + (pt)] : 0.0)
   /* edge-averaged fluxes: Fx[v][p][j][i'] i' = 0..N, Fy[v][p][j'][i] j' = 0..N */
   size_t fe = (size_t)N * (N + 1);
   double *Fx = (double *)calloc(3 * 6 * fe, sizeof(double));
@@ -1393,8 +1405,11 @@ void orc_tendency(orc *o, const double *q, double *dqdt) {
           for (int v = 0; v < 3; ++v) qv[v] = PTS(v, p, j, i, pt);
           double x = cell_centre(o, i) + o->gx[g] * dx, y = cell_centre(o, j) + o->gx[h] * dx;
           orc_sources(o, p, tan(x), tan(y), qv, S);
-          if (spt)
+          if (spt && !o->tform) /* eq. 2.14: sqrtG phi_s G^ij d_j phi_t */
             topo_source(o, tan(x), tan(y), SPT(p, j, i, pt),
+                        dpt + ((((size_t)p * N + j) * N + i) * me * me + h * me + g) * 2, S);
+          else if (spt) /* eq. 2.4: -sqrtG phi G^ij d_j phi_s */
+            topo_source(o, tan(x), tan(y), -PTS(0, p, j, i, pt),
                         dpt + ((((size_t)p * N + j) * N + i) * me * me + h * me + g) * 2, S);
           for (int v = 0; v < 3; ++v) sb[v] += o->gw[g] * o->gw[h] * S[v];
         }

@@ -87,6 +87,9 @@ void orc_set_topography(orc *o, const double *sbar);
 void orc_set_topography_case(orc *o, int tcase, const double *params4);
 void orc_get_topography(const orc *o, double *sbar);
 double orc_topography_point(const orc *o, int panel, double X, double Y);
+/* 0 (default): the total-geopotential form of eqs. 2.13-2.14; 1: the depth form of eqs.
+   2.1 and 2.4 (for comparisons only). */
+void orc_set_topography_form(orc *o, int form);
 /* The cell average of psi_B (eq. 2.14) alone for state q: out[2][6][N][N]. */
 void orc_topo_psib(orc *o, const double *q, double *out);
 /* phi, u_s, v_s of an initial condition at one (lambda, theta) (params as orc_ic,

@@ -95,6 +95,7 @@ def lib():
         L.orc_topography_point.restype = ctypes.c_double
         L.orc_topography_point.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
         L.orc_topo_psib.argtypes = [vp, P, P]
+        L.orc_set_topography_form.argtypes = [vp, ctypes.c_int]
         L.orc_tpp_dweights_2d.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, P]
         L.orc_sqrtg_grad.argtypes = [ctypes.c_double, ctypes.c_double, P]
         Pi = ctypes.POINTER(ctypes.c_int)
@@ -282,6 +283,10 @@ class Oracle:
         out = np.empty((6, self.N, self.N))
         lib().orc_get_topography(self._h, _p(out))
         return out
+
+    def set_topography_form(self, form):
+        """0: total-geopotential form (eqs. 2.13-2.14, default); 1: depth form (2.1, 2.4)."""
+        lib().orc_set_topography_form(self._h, int(form))
 
     def topo_psib(self, q):
         """The cell average of psi_B (eq. 2.14) alone, shape (2, 6, N, N)."""
