@@ -632,6 +632,7 @@ struct orc {
   double *Rd;      /* [me*me][2][k*k] x- and y-derivative weights at the cell points */
   void *w1d;       /* [me+2] 1-D WENO-Z tables at xi = -1/2, +1/2, g_0.. (ORC_WENO1D) */
   int tform;       /* 0: total-geopotential form (eqs. 2.13-2.14); 1: depth form (2.1, 2.4) */
+  const unsigned char *rmask; /* [6][N][N]: cells to reconstruct (NULL: all), orc_tendency_cells */
 };
 
 int orc_npoc(const orc *o) { return o->npoc; }
@@ -957,6 +958,10 @@ void orc_reconstruct_all(orc *o, const double *ext, double *pts) {
       for (int b = 0; b < k; ++b)
         for (int a = 0; a < k; ++a) st[b * k + a] = src[(size_t)(j + b) * ne + (i + a)];
       double *out = pts + ((((size_t)v * 6 + p) * N + j) * N + i) * np;
+      if (o->rmask && !o->rmask[((size_t)p * N + j) * N + i]) { /* not needed by the sample */
+        for (int pt = 0; pt < np; ++pt) out[pt] = NAN;
+        continue;
+      }
       if (o->scheme == ORC_WENO) {
         weno_betas(o, st, beta);
         double tau = weno_tau(o->s, beta);
@@ -1429,6 +1434,41 @@ void orc_tendency(orc *o, const double *q, double *dqdt) {
   free(qt);
   free(spt);
   free(dpt);
+}
+
+/* L(q) at selected cells only: the cells' own reconstructions and those of   */
+/* their four edge neighbours (across panel edges, the neighbour panel's       */
+/* boundary cell) are computed, every other cell's reconstruction is skipped;  */
+/* then orc_tendency runs unchanged.  The ghost fill stays global.  out[3][n]. */
+void orc_tendency_cells(orc *o, const double *q, int n, const int *cells, double *out) {
+  int N = o->N, me = o->me;
+  size_t pn = (size_t)6 * N * N;
+  unsigned char *mask = (unsigned char *)calloc(pn, 1);
+  double *full = (double *)malloc(sizeof(double) * 3 * pn);
+  for (int c = 0; c < n; ++c) {
+    int p = cells[c] / (N * N), j = (cells[c] / N) % N, i = cells[c] % N;
+    mask[cells[c]] = 1;
+    int di[4] = {-1, 1, 0, 0}, dj[4] = {0, 0, -1, 1};
+    for (int side = 0; side < 4; ++side) {
+      int ii = i + di[side], jj = j + dj[side];
+      if (ii >= 0 && ii < N && jj >= 0 && jj < N) {
+        mask[((size_t)p * N + jj) * N + ii] = 1;
+      } else { /* the cell across the cube edge */
+        int t = side < 2 ? j : i;
+        const nbr_t *nb = &o->nb[((p * 4 + side) * N + t) * me];
+        int bi = nb->sideB == 0 ? 0 : (nb->sideB == 1 ? N - 1 : nb->tB);
+        int bj = nb->sideB == 2 ? 0 : (nb->sideB == 3 ? N - 1 : nb->tB);
+        mask[((size_t)nb->B * N + bj) * N + bi] = 1;
+      }
+    }
+  }
+  o->rmask = mask;
+  orc_tendency(o, q, full);
+  o->rmask = NULL;
+  for (int v = 0; v < 3; ++v)
+    for (int c = 0; c < n; ++c) out[(size_t)v * n + c] = full[v * pn + cells[c]];
+  free(full);
+  free(mask);
 }
 
 /* ------------------------------------------------------------------------- */

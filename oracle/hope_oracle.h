@@ -67,6 +67,10 @@ int orc_halo(const orc *o);
 
 /* One evaluation of the spatial operator L(q) = dq/dt (eq. 3.1). */
 void orc_tendency(orc *o, const double *q, double *dqdt);
+/* L(q) at n selected cells (cells[c] = p*N*N + j*N + i): the same computation as
+   orc_tendency with the reconstruction restricted to the cells the selected cells'
+   edge fluxes and sources need; out[3][n]. */
+void orc_tendency_cells(orc *o, const double *q, int n, const int *cells, double *out);
 /* nsteps Runge-Kutta steps in place (rk = ORC_SSPRK3 or ORC_WSRK3). */
 void orc_step(orc *o, double *q, double dt, int nsteps, int rk);
 /* Total mass dx*dy*sum(q0) (the I() weighted sum of eq. 5.7), long-double accumulation. */

@@ -57,6 +57,7 @@ def lib():
         L.orc_npoc.argtypes = [vp]
         L.orc_halo.argtypes = [vp]
         L.orc_tendency.argtypes = [vp, P, P]
+        L.orc_tendency_cells.argtypes = [vp, P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), P]
         L.orc_step.argtypes = [vp, P, ctypes.c_double, ctypes.c_int, ctypes.c_int]
         L.orc_mass.restype = ctypes.c_double
         L.orc_mass.argtypes = [vp, P]
@@ -149,6 +150,17 @@ class Oracle:
         q = _f64(q)
         out = np.empty(self.shape)
         lib().orc_tendency(self._h, _p(q), _p(out))
+        return out
+
+    def tendency_cells(self, q, cells):
+        """L(q) at the flat cell indices p*N*N + j*N + i only, shape (3, len(cells)): the
+        tendency's computation with the reconstruction restricted to what those cells need."""
+        q = _f64(q)
+        cells = np.ascontiguousarray(np.asarray(cells, dtype=np.int32))
+        assert cells.ndim == 1 and cells.size and cells.min() >= 0 and cells.max() < 6 * self.N ** 2
+        out = np.empty((3, cells.size))
+        lib().orc_tendency_cells(self._h, _p(q), int(cells.size),
+                                 cells.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(out))
         return out
 
     def step(self, q, dt, nsteps=1, rk=SSPRK3):

@@ -256,3 +256,28 @@ def test_ws_rk3_nonlinear_defect_is_f2_over_24():
     extrap = 2.0 * defect(150.0) - defect(300.0)
     rel = np.linalg.norm(extrap - target) / np.linalg.norm(target)
     assert rel < 5e-3, rel
+
+
+def sample_cells(N, n, seed):
+    """Flat cell indices p*N*N + j*N + i: the four corners and an edge-midpoint cell of every
+    panel (cube-edge and cube-corner cells), plus n seeded random cells."""
+    rng = np.random.default_rng(seed)
+    fixed = []
+    for p in range(6):
+        for j, i in ((0, 0), (0, N - 1), (N - 1, 0), (N - 1, N - 1), (0, N // 2), (N // 2, N - 1)):
+            fixed.append((p * N + j) * N + i)
+    rand = rng.choice(6 * N * N, size=n, replace=False)
+    return np.unique(np.concatenate([np.array(fixed), rand]))
+
+
+@pytest.mark.parametrize("k,N,scheme", [(5, 9, O.TPP), (5, 8, O.WENO), (5, 7, O.WENO1D)])
+def test_sampled_tendency_equals_full_tendency(k, N, scheme):
+    """orc_tendency_cells only skips reconstructions that the chosen cells' fluxes and
+    sources do not use: at every chosen cell it equals orc_tendency bitwise, corners and
+    cube edges included."""
+    o = O.Oracle(N, k, scheme=scheme)
+    q = o.rossby_haurwitz() * (1 + 0.01 * np.random.default_rng(1).uniform(-1, 1, (6, N, N)))[None]
+    cells = sample_cells(N, 20, 2)
+    full = o.tendency(q).reshape(3, -1)[:, cells]
+    got = o.tendency_cells(q, cells)
+    assert np.array_equal(got, full)
