@@ -64,6 +64,13 @@ typedef void *hope_stream_t; /* a cudaStream_t; NULL = the legacy default stream
 /* schemes, precisions, time steppers */
 #define HOPE_TPP 0     /* tensor-product polynomial reconstruction, section 3.1 */
 #define HOPE_WENO2D 1  /* genuine two-dimensional WENO-Z, section 3.2            */
+#define HOPE_WENO1D 2  /* dimension-by-dimension WENO-Z, the comparator of section 5.5: the 1-D
+                          WENO-Z of Borges et al. (2008) along x on each stencil row at a point's
+                          x position, then along y on the row values; 1-D linear weights by the
+                          least squares of eqs. 3.16-3.19 split as eq. 3.20, Jiang-Shu indicators,
+                          tau5 = |beta_0 - beta_2|; fifth order only (order 5, the paper's;
+                          WENO-Z's tau is order-specific); forward only (the VJP calls return
+                          HOPE_EUNSUPPORTED) */
 #define HOPE_FP64 0
 #define HOPE_FP32 1
 #define HOPE_SSPRK3 0  /* strong-stability-preserving RK3 (Shu-Osher form) */
@@ -96,7 +103,7 @@ void hope_default_params(hope_params *p);
 /*
  * Create a context for one cubed sphere with N cells per panel edge, stencil width
  * `order` (odd; 3..11 for TPP, the design order of section 3.1; 3..9 for WENO2D, whose
- * adjoint is available up to 7) and `scheme`.  All tables
+ * adjoint is available up to 7; 5 for WENO1D) and `scheme`.  All tables
  * (reconstruction weights eqs. 3.14-3.15, WENO linear weights eqs. 3.19-3.20 and
  * smoothness forms eq. 3.25, the ghost operator G of eq. 7.12, per-point metric terms
  * eqs. 2.2-2.8) are built in FP64 and stored on the current CUDA device.  Requires
@@ -160,9 +167,13 @@ int hope_initial_state(hope_t ctx, int ic_case, const double *params, int n_para
  * gradient taken from the TPP polynomial of sqrtG phi_t at the cell Gauss points.
  * Builds the surface's tables in FP64 on the host (its ghost ring, its edge-point values
  * and psi_B's weights: 2 k^2 + 4 me + 2 values per cell) after synchronising the device;
- * captured step graphs are dropped.  Single TPP spheres only (HOPE_EUNSUPPORTED for
- * ensembles and WENO2D); while a surface is set the VJP and tape-adjoint calls return
- * HOPE_EUNSUPPORTED.  HOPE_EINVAL for a null context or a non-finite value.
+ * captured step graphs are dropped.  Single TPP and WENO2D spheres (HOPE_EUNSUPPORTED for
+ * ensembles and WENO1D).  With WENO2D the nonlinear reconstruction acts on sqrtG phi_t
+ * (the surface's extended averages added to the depth's) and the surface's own TPP values
+ * at the points are subtracted, leaving the depth (two more tables: (N+k-1)^2 and me^2 per
+ * cell and panel).  The VJP and tape-adjoint calls include the surface's terms (the
+ * LMARS adjoint with phi_t, psi_B's stencil map transposed; WENO2D's adjoint recomputes
+ * its forward on sqrtG phi_t).  HOPE_EINVAL for a null context or a non-finite value.
  */
 int hope_set_topography(hope_t ctx, const double *phis_avg_host);
 
@@ -375,6 +386,13 @@ int hope_launches_per_stage(hope_t ctx, int *launches);
 #define HOPE_KERNELS_PER_STAGE 4
 int hope_set_profiling(hope_t ctx, int enable);
 int hope_kernel_times(hope_t ctx, float *ms_out, int max_entries, int *n_entries);
+/* Phases of the most recent stage VJP of a TPP ensemble (one persistent launch) while
+ * profiling is enabled: ms_out[6] = forward ghost fill, forward reconstruction (both 0 when
+ * the stage's forward came from a step tape), flux adjoint, reconstruction and source
+ * adjoint, stencil-gradient gather, transposed ghost operator; from global-timer stamps of
+ * block 0 at the grid barriers (the last ends when the last block finishes).  Synchronises
+ * the device.  HOPE_EINVAL for a context that is not a TPP ensemble. */
+int hope_vjp_phase_times(hope_t ctx, float *ms_out);
 
 const char *hope_strerror(int code);
 const char *hope_last_error_message(void);
@@ -385,6 +403,15 @@ const char *hope_last_error_message(void);
  * CUDA events.  *flops_per_s receives the measured rate (2 flops per FMA).
  */
 int hope_measure_fma_peak(int precision, double *flops_per_s);
+/*
+ * hope_measure_fma_peak with the clock it ran at: reps launches (>= 2; the first is a
+ * warm-up), the fastest kept.  sm_mhz (may be NULL) receives the SM clock during that
+ * launch (SM cycle counter over the global timer, summed over blocks), flops_per_sm_clock
+ * (may be NULL) the flops per SM per clock cycle, i.e. the rate independent of the clock
+ * (the FP64 pipe's nominal 2 FMA per SM per cycle give 4).
+ */
+int hope_measure_fma_peak_clock(int precision, int reps, double *flops_per_s, double *sm_mhz,
+                                double *flops_per_sm_clock);
 
 #ifdef __cplusplus
 }

@@ -10,7 +10,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libhope.so")
 
 HOPE_OK = 0
-HOPE_TPP, HOPE_WENO2D = 0, 1
+HOPE_TPP, HOPE_WENO2D, HOPE_WENO1D = 0, 1, 2
 HOPE_FP64, HOPE_FP32 = 0, 1
 HOPE_SSPRK3, HOPE_WSRK3 = 0, 1
 HOPE_STATUS_NONPHYS_PHI, HOPE_STATUS_NAN, HOPE_STATUS_TIMEOUT = 1, 2, 4
@@ -23,7 +23,8 @@ EXPORTED = [
     "hope_last_error_message", "hope_measure_fma_peak", "hope_set_profiling", "hope_kernel_times",
     "hope_total_mass_noalloc", "hope_autotune", "hope_inject_fault", "hope_set_recon_tile", "hope_recon_tile",
     "hope_tape_bytes", "hope_step_record", "hope_step_vjp_tape", "hope_step_ssprk3_vjp",
-    "hope_ghost_selfcheck", "hope_set_topography", "hope_topography_tables",
+    "hope_ghost_selfcheck", "hope_set_topography", "hope_topography_tables", "hope_measure_fma_peak_clock",
+    "hope_vjp_phase_times",
 ]
 
 
@@ -77,6 +78,8 @@ def load():
         "hope_strerror": (ctypes.c_char_p, [i]),
         "hope_last_error_message": (ctypes.c_char_p, []),
         "hope_measure_fma_peak": (i, [i, P(d)]),
+        "hope_measure_fma_peak_clock": (i, [i, i, P(d), P(d), P(d)]),
+        "hope_vjp_phase_times": (i, [vp, P(ctypes.c_float)]),
         "hope_set_profiling": (i, [vp, i]),
         "hope_total_mass_noalloc": (i, [vp, i, i, P(d), vp]),
         "hope_autotune": (i, [vp, i, P(ctypes.c_float), P(i), P(i), P(i)]),

@@ -19,9 +19,12 @@ namespace hope {
 
 // LMARS flux and its vector-Jacobian product at one edge point (same arithmetic as lmars():
 // interface velocity 1/2 (uL + uR) - (sR - sL), s = sqrt(phi)).
-template <typename T>
+// TOPO: LMARS over bottom topography (lmars_topo), zL, zR = sqrtG phi_s at the point; the
+// surface enters the interface velocity through -(phi_s,R - phi_s,L)/(2c), whose derivative
+// with respect to c joins the adjoint of c, and the interface value through constants.
+template <typename T, bool TOPO = false>
 __device__ __forceinline__ void lmars_vjp(const T qL[3], const T qR[3], const T *m5, int dir, const T lF[3],
-                                          T lqL[3], T lqR[3]) {
+                                          T lqL[3], T lqR[3], T zL = T(0), T zR = T(0)) {
   const T isg = m5[0], s11 = m5[1], is11 = m5[2], pn = m5[3], pc = m5[4];
   const T qnL = dir ? qL[2] : qL[1], qnR = dir ? qR[2] : qR[1];
   const T phL = qL[0] * isg, phR = qR[0] * isg;
@@ -30,8 +33,15 @@ __device__ __forceinline__ void lmars_vjp(const T qL[3], const T qR[3], const T 
   const T uL = qnL * rL * is11, uR = qnR * rR * is11;
   const T sL = sqrt_pos(phL), sR = sqrt_pos(phR);
   const T c = T(0.5) * (sL + sR);
-  const T ms = T(0.5) * (uL + uR) - (sR - sL);
-  const T ph = T(0.5) * (phL + phR - c * (uR - uL));
+  T ms = T(0.5) * (uL + uR) - (sR - sL);
+  T ph = T(0.5) * (phL + phR - c * (uR - uL));
+  T dfs = T(0);  // phi_s,R - phi_s,L
+  if constexpr (TOPO) {
+    const T fsL = zL * isg, fsR = zR * isg;
+    dfs = fsR - fsL;
+    ms = T(0.5) * (uL + uR) - (sR - sL) - dfs * rcp(c + c);
+    ph = T(0.5) * ((phL + fsL) + (phR + fsR) - c * (uR - uL));
+  }
   const T m = ms * s11;
   const T am = fabs(m);
   const T sg = m > T(0) ? T(1) : (m < T(0) ? T(-1) : T(0));
@@ -49,7 +59,8 @@ __device__ __forceinline__ void lmars_vjp(const T qL[3], const T qR[3], const T 
   T luL = T(0.5) * lms, luR = T(0.5) * lms;
   T lsL = lms, lsR = -lms;
   T lphL = T(0.5) * lph, lphR = T(0.5) * lph;
-  const T lc = -T(0.5) * (uR - uL) * lph;
+  T lc = -T(0.5) * (uR - uL) * lph;
+  if constexpr (TOPO) lc += lms * dfs * rcp(T(2) * c * c);  // d/dc of -dfs / (2c)
   luR -= T(0.5) * c * lph;
   luL += T(0.5) * c * lph;
   lsL += T(0.5) * lc;
@@ -68,14 +79,15 @@ __device__ __forceinline__ void lmars_vjp(const T qL[3], const T qR[3], const T 
 // ---------------------------------------------------------------------------------
 // Flux adjoint.  lamL: adjoint of the tendency [3][6][N][N]; lep: [4][3][me][6][N][N].
 // ---------------------------------------------------------------------------------
-template <typename T, int ME>
-__global__ void __launch_bounds__(256)
-    k_flux_adj(const T *__restrict__ ep, const T *__restrict__ mx, const T *__restrict__ gwg,
-               const int *__restrict__ bedge, const T *__restrict__ bconv, const T *__restrict__ lamL,
-               T *__restrict__ lep, int N, T inv_dx) {
-  const long long nx = 6LL * N * (N - 1), ny = nx, nb = 12LL * N;
-  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nx + ny + nb) return;
+// One edge item (interior x-edges, interior y-edges, then the 12 cube edges x N cells).
+// TOPO: over a surface, sep[4][me][6][N][N] = sqrtG phi_s at the edge points.
+template <typename T, int ME, bool TOPO = false>
+__device__ __forceinline__ void flux_adj_item(long long idx, const T *__restrict__ ep, const T *__restrict__ mx,
+                                              const T *__restrict__ gwg, const int *__restrict__ bedge,
+                                              const T *__restrict__ bconv, const T *__restrict__ lamL,
+                                              T *__restrict__ lep, int N, T inv_dx,
+                                              const T *__restrict__ sep = nullptr) {
+  const long long nx = 6LL * N * (N - 1), ny = nx;
   const size_t pn = (size_t)6 * N * N;
   T gw[ME];
 #pragma unroll
@@ -116,7 +128,11 @@ __global__ void __launch_bounds__(256)
         qR[v] = ep[((size_t)(sr * 3 + v) * ME + g) * pn + cr];
         lF[v] = gw[g] * lFbar[v];
       }
-      lmars_vjp(qL, qR, mx + (((size_t)e * N + a) * ME + g) * 5, dir, lF, lqL, lqR);
+      if constexpr (TOPO)
+        lmars_vjp<T, true>(qL, qR, mx + (((size_t)e * N + a) * ME + g) * 5, dir, lF, lqL, lqR,
+                           sep[((size_t)sl * ME + g) * pn + cl], sep[((size_t)sr * ME + g) * pn + cr]);
+      else
+        lmars_vjp(qL, qR, mx + (((size_t)e * N + a) * ME + g) * 5, dir, lF, lqL, lqR);
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
         lep[((size_t)(sl * 3 + v) * ME + g) * pn + cl] = lqL[v];
@@ -166,12 +182,17 @@ __global__ void __launch_bounds__(256)
     lF[2] = gw[g] * lFA[2] + gw[gB] * sg * (cv[6] * lFB[1] + cv[8] * lFB[2]);
     const T *m5 = mx + (((size_t)eA * N + t) * ME + g) * 5;
     T lin[3], lo[3];
+    T zin = T(0), zo = T(0);
+    if constexpr (TOPO) {
+      zin = sep[((size_t)sA * ME + g) * pn + cA];
+      zo = cv[0] * sep[((size_t)sB * ME + gB) * pn + cB];
+    }
     if (sA & 1) {
-      lmars_vjp(qin, qo, m5, dirA, lF, l1, l2);
+      lmars_vjp<T, TOPO>(qin, qo, m5, dirA, lF, l1, l2, zin, zo);
 #pragma unroll
       for (int v = 0; v < 3; ++v) { lin[v] = l1[v]; lo[v] = l2[v]; }
     } else {
-      lmars_vjp(qo, qin, m5, dirA, lF, l1, l2);
+      lmars_vjp<T, TOPO>(qo, qin, m5, dirA, lF, l1, l2, zo, zin);
 #pragma unroll
       for (int v = 0; v < 3; ++v) { lo[v] = l1[v]; lin[v] = l2[v]; }
     }
@@ -185,6 +206,34 @@ __global__ void __launch_bounds__(256)
       lep[((size_t)(sB * 3 + v) * ME + gB) * pn + cB] = lb[v];
     }
   }
+}
+
+template <typename T, int ME, bool TOPO = false>
+__global__ void __launch_bounds__(256)
+    k_flux_adj(const T *__restrict__ ep, const T *__restrict__ mx, const T *__restrict__ gwg,
+               const int *__restrict__ bedge, const T *__restrict__ bconv, const T *__restrict__ lamL,
+               T *__restrict__ lep, int N, T inv_dx, const T *__restrict__ sep = nullptr) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 12LL * N * (N - 1) + 12LL * N) return;
+  flux_adj_item<T, ME, TOPO>(idx, ep, mx, gwg, bedge, bconv, lamL, lep, N, inv_dx, sep);
+}
+
+// ---------------------------------------------------------------------------------
+// psi_B (eq. 2.14) adjoint: the forward adds sum_c w[v][c] * stencil_c (the mass
+// variable's k x k stencil) to the momentum sources (k_topo_src), so the mass variable's
+// stencil gradient gains w[0][c] lam_1 + w[1][c] lam_2 at every cell (after the
+// reconstruction adjoint has written it).
+// ---------------------------------------------------------------------------------
+template <typename T, int K>
+__global__ void __launch_bounds__(256)
+    k_topo_src_adj(const T *__restrict__ lamL, const T *__restrict__ tw, T *__restrict__ grad, int N) {
+  const long long n = 6LL * N * N;
+  const long long cid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cid >= n) return;
+  const T l1 = lamL[n + cid], l2 = lamL[2 * n + cid];
+#pragma unroll 1
+  for (int c = 0; c < K * K; ++c)
+    grad[(size_t)c * n + cid] += tw[(size_t)c * n + cid] * l1 + tw[((size_t)K * K + c) * n + cid] * l2;
 }
 
 // Vector-Jacobian product of the cell-point source (same arithmetic as the forward).
@@ -204,121 +253,159 @@ __device__ __forceinline__ void source_vjp(const T q[3], T X, T Y, T os, T tw, T
 // ---------------------------------------------------------------------------------
 // TPP reconstruction + sources adjoint: per cell, the gradient with respect to its
 // K x K stencil, grad[v][b*K + a][cell] (a: x offset + H, b: y offset + H).
+// One tile of at most TX x TY cells of panel p with its first cell at (i0, j0), called by
+// all threads of a block of at least TX*TY threads (the valid cells of a tile cut by the
+// panel's edge are packed onto the first threads); ends with a barrier so the shared
+// memory can be reused.  Shared memory: the forward tile's (raw tile, x-pass, weights)
+// plus the adjoint at the cell points, [3][me^2][blockDim.x].
 // ---------------------------------------------------------------------------------
 template <typename T, int K>
-__global__ void __launch_bounds__(REC_TX *REC_TY)
-    k_recon_tpp_adj(const T *__restrict__ q, const T *__restrict__ gext, const T *__restrict__ w1g,
-                    const T *__restrict__ Xg, const T *__restrict__ t1w, const T *__restrict__ lep,
-                    const T *__restrict__ lamL, T *__restrict__ grad, int N, int ne, T omega, FCoef<T> fc) {
-  using S = Shape<K>;
-  constexpr int ME = S::ME, NPOS = S::NPOS, NT = REC_TX * REC_TY;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *raw = reinterpret_cast<T *>(smem_raw);              // [3][RH][RW]
-  T *xs = raw + 3 * S::RH * S::RW;                        // [3][NPOS][RH][TX]
-  T *w1 = xs + 3 * NPOS * S::RH * REC_TX;                 // [NPOS][K]
-  T *lcq = w1 + NPOS * K;                                 // [3][ME*ME][NT] adjoint at cell points
-  const int p = blockIdx.z;
-  const int i0 = blockIdx.x * REC_TX, j0 = blockIdx.y * REC_TY;
+__device__ __forceinline__ void recon_tpp_adj_tile(unsigned char *smem_raw, int p, int i0, int j0, const int TX,
+                                                   const int TY, const T *__restrict__ q, const T *__restrict__ gext,
+                                                   const T *__restrict__ w1g, const T *__restrict__ Xg,
+                                                   const T *__restrict__ t1w, const T *__restrict__ lep,
+                                                   const T *__restrict__ lamL, T *__restrict__ grad, int N, int ne,
+                                                   T omega, const FCoef<T> &fc) {
+  constexpr int H = (K - 1) / 2, ME = (K + 1) / 2, NPOS = ME + 2;
+  const int RW = TX + 2 * H, RH = TY + 2 * H, NT = blockDim.x;
+  const int vx = min(TX, N - i0), vy = min(TY, N - j0);
+  const int vw = vx + 2 * H, vh = vy + 2 * H;
+  T *raw = reinterpret_cast<T *>(smem_raw);  // [3][RH][RW]
+  T *xs = raw + 3 * RH * RW;                  // [3][NPOS][RH][TX]
+  T *w1 = xs + 3 * NPOS * RH * TX;            // [NPOS][K]
+  T *lcq = w1 + NPOS * K;                     // [3][ME*ME][NT] adjoint at cell points
   for (int t = threadIdx.x; t < NPOS * K; t += blockDim.x) w1[t] = w1g[t];
-  load_tile<T, K>(raw, q, gext, p, i0, j0, N, ne);
+  {
+    const size_t pn = (size_t)6 * N * N, pe = (size_t)6 * ne * ne;
+    for (int idx = threadIdx.x; idx < 3 * vh * vw; idx += blockDim.x) {
+      const int v = idx / (vh * vw);
+      const int rem = idx - v * vh * vw;
+      const int r = rem / vw, c = rem - r * vw;
+      const int i = i0 + c - H, j = j0 + r - H;
+      T val = T(0);
+      if (i >= 0 && i < N && j >= 0 && j < N)
+        val = q[v * pn + ((size_t)p * N + j) * N + i];
+      else if (i >= -H && i < N + H && j >= -H && j < N + H)
+        val = gext[v * pe + ((size_t)p * ne + (j + H)) * ne + (i + H)];
+      raw[(v * RH + r) * RW + c] = val;
+    }
+  }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < 3 * S::RH * REC_TX; idx += blockDim.x) {
-    int v = idx / (S::RH * REC_TX);
-    int rem = idx - v * S::RH * REC_TX;
-    int r = rem / REC_TX, c = rem - r * REC_TX;
-    const T *row = raw + (v * S::RH + r) * S::RW + c;
+  for (int idx = threadIdx.x; idx < 3 * vh * vx; idx += blockDim.x) {
+    const int v = idx / (vh * vx);
+    const int rem = idx - v * vh * vx;
+    const int r = rem / vx, c = rem - r * vx;
+    const T *row = raw + (v * RH + r) * RW + c;
 #pragma unroll
     for (int t = 0; t < NPOS; ++t) {
       T s = 0;
 #pragma unroll
       for (int b = 0; b < K; ++b) s = fma(w1[t * K + b], row[b], s);
-      xs[((v * NPOS + t) * S::RH + r) * REC_TX + c] = s;
+      xs[((v * NPOS + t) * RH + r) * TX + c] = s;
     }
   }
   __syncthreads();
   const int tid = threadIdx.x;
-  const int tx = tid % REC_TX, ty = tid / REC_TX;
-  const int i = i0 + tx, j = j0 + ty;
-  if (i >= N || j >= N) return;
-  const size_t pn = (size_t)6 * N * N;
-  const size_t cell = ((size_t)p * N + j) * N + i;
-  const T fc0 = fc.c[3 * p], fc1 = fc.c[3 * p + 1], fc2 = fc.c[3 * p + 2];
-  const T lS1 = lamL[pn + cell], lS2 = lamL[2 * pn + cell];
-  // phase 1: adjoint at the cell points (recomputed values, source VJP)
+  if (tid < vx * vy) {
+    const int ty = tid / vx, tx = tid - ty * vx;
+    const int i = i0 + tx, j = j0 + ty;
+    const size_t pn = (size_t)6 * N * N;
+    const size_t cell = ((size_t)p * N + j) * N + i;
+    const T fc0 = fc.c[3 * p], fc1 = fc.c[3 * p + 1], fc2 = fc.c[3 * p + 2];
+    const T lS1 = lamL[pn + cell], lS2 = lamL[2 * pn + cell];
+    // phase 1: adjoint at the cell points (recomputed values, source VJP)
 #pragma unroll 1
-  for (int g = 0; g < ME; ++g) {
-    const T X = Xg[i * ME + g];
-    T col[3][K];
+    for (int g = 0; g < ME; ++g) {
+      const T X = Xg[i * ME + g];
+      T col[3][K];
 #pragma unroll
-    for (int v = 0; v < 3; ++v)
+      for (int v = 0; v < 3; ++v)
 #pragma unroll
-      for (int b = 0; b < K; ++b) col[v][b] = xs[((v * NPOS + 2 + g) * S::RH + ty + b) * REC_TX + tx];
+        for (int b = 0; b < K; ++b) col[v][b] = xs[((v * NPOS + 2 + g) * RH + ty + b) * TX + tx];
 #pragma unroll 1
-    for (int h = 0; h < ME; ++h) {
-      T qv[3];
+      for (int h = 0; h < ME; ++h) {
+        T qv[3];
 #pragma unroll
-      for (int v = 0; v < 3; ++v) {
-        T s = 0;
+        for (int v = 0; v < 3; ++v) {
+          T s = 0;
 #pragma unroll
-        for (int b = 0; b < K; ++b) s = fma(w1[(2 + h) * K + b], col[v][b], s);
-        qv[v] = s;
-      }
-      const T Y = Xg[j * ME + h];
-      const T tw = t1w[(((size_t)j * N + i) * ME + h) * ME + g];
-      const T os = omega * (fc0 + fc1 * X + fc2 * Y);
-      T lq[3];
-      source_vjp(qv, X, Y, os, tw, lS1, lS2, lq);
-#pragma unroll
-      for (int v = 0; v < 3; ++v) lcq[(v * ME * ME + h * ME + g) * NT + tid] = lq[v];
-    }
-  }
-  // phase 2: per stencil row b, gt[v][t] = sum over points at x-position t of
-  // w1[ty(pt)][b] lam(pt), then grad[v][b][a] = sum_t w1[t][a] gt[v][t]
-#pragma unroll 1
-  for (int b = 0; b < K; ++b) {
-    T gacc[3][K];
-#pragma unroll
-    for (int v = 0; v < 3; ++v)
-#pragma unroll
-      for (int a = 0; a < K; ++a) gacc[v][a] = T(0);
-#pragma unroll 1
-    for (int t = 0; t < NPOS; ++t) {
-      T gt[3] = {0, 0, 0};
-      if (t < 2) {
-#pragma unroll
-        for (int r = 0; r < ME; ++r) {
-          const T w = w1[(2 + r) * K + b];
-#pragma unroll
-          for (int v = 0; v < 3; ++v) gt[v] = fma(w, lep[((size_t)(t * 3 + v) * ME + r) * pn + cell], gt[v]);
+          for (int b = 0; b < K; ++b) s = fma(w1[(2 + h) * K + b], col[v][b], s);
+          qv[v] = s;
         }
-      } else {
-        const int g = t - 2;
+        const T Y = Xg[j * ME + h];
+        const T tw = t1w[(((size_t)j * N + i) * ME + h) * ME + g];
+        const T os = omega * (fc0 + fc1 * X + fc2 * Y);
+        T lq[3];
+        source_vjp(qv, X, Y, os, tw, lS1, lS2, lq);
 #pragma unroll
-        for (int side = 0; side < 2; ++side) {
-          const T w = w1[side * K + b];
-#pragma unroll
-          for (int v = 0; v < 3; ++v)
-            gt[v] = fma(w, lep[((size_t)((2 + side) * 3 + v) * ME + g) * pn + cell], gt[v]);
-        }
-#pragma unroll
-        for (int h = 0; h < ME; ++h) {
-          const T w = w1[(2 + h) * K + b];
-#pragma unroll
-          for (int v = 0; v < 3; ++v) gt[v] = fma(w, lcq[(v * ME * ME + h * ME + g) * NT + tid], gt[v]);
-        }
-      }
-#pragma unroll
-      for (int a = 0; a < K; ++a) {
-        const T w = w1[t * K + a];
-#pragma unroll
-        for (int v = 0; v < 3; ++v) gacc[v][a] = fma(w, gt[v], gacc[v][a]);
+        for (int v = 0; v < 3; ++v) lcq[(v * ME * ME + h * ME + g) * NT + tid] = lq[v];
       }
     }
+    // phase 2: per stencil row b, gt[v][t] = sum over points at x-position t of
+    // w1[ty(pt)][b] lam(pt), then grad[v][b][a] = sum_t w1[t][a] gt[v][t]
+#pragma unroll 1
+    for (int b = 0; b < K; ++b) {
+      T gacc[3][K];
 #pragma unroll
-    for (int v = 0; v < 3; ++v)
+      for (int v = 0; v < 3; ++v)
 #pragma unroll
-      for (int a = 0; a < K; ++a) grad[((size_t)v * K * K + b * K + a) * pn + cell] = gacc[v][a];
+        for (int a = 0; a < K; ++a) gacc[v][a] = T(0);
+#pragma unroll 1
+      for (int t = 0; t < NPOS; ++t) {
+        T gt[3] = {0, 0, 0};
+        if (t < 2) {
+#pragma unroll
+          for (int r = 0; r < ME; ++r) {
+            const T w = w1[(2 + r) * K + b];
+#pragma unroll
+            for (int v = 0; v < 3; ++v) gt[v] = fma(w, lep[((size_t)(t * 3 + v) * ME + r) * pn + cell], gt[v]);
+          }
+        } else {
+          const int g = t - 2;
+#pragma unroll
+          for (int side = 0; side < 2; ++side) {
+            const T w = w1[side * K + b];
+#pragma unroll
+            for (int v = 0; v < 3; ++v)
+              gt[v] = fma(w, lep[((size_t)((2 + side) * 3 + v) * ME + g) * pn + cell], gt[v]);
+          }
+#pragma unroll
+          for (int h = 0; h < ME; ++h) {
+            const T w = w1[(2 + h) * K + b];
+#pragma unroll
+            for (int v = 0; v < 3; ++v) gt[v] = fma(w, lcq[(v * ME * ME + h * ME + g) * NT + tid], gt[v]);
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+          const T w = w1[t * K + a];
+#pragma unroll
+          for (int v = 0; v < 3; ++v) gacc[v][a] = fma(w, gt[v], gacc[v][a]);
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < 3; ++v)
+#pragma unroll
+        for (int a = 0; a < K; ++a) grad[((size_t)v * K * K + b * K + a) * pn + cell] = gacc[v][a];
+    }
   }
+  __syncthreads();
+}
+
+// Shared memory of one reconstruction-adjoint tile of TX x TY cells with NT threads.
+template <typename T, int K>
+__host__ __device__ constexpr size_t recon_adj_tile_smem_bytes(int TX, int TY, int NT) {
+  return recon_tile_smem_bytes<T, K>(TX, TY) + sizeof(T) * 3 * ((K + 1) / 2) * ((K + 1) / 2) * NT;
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(REC_TX *REC_TY)
+    k_recon_tpp_adj(const T *__restrict__ q, const T *__restrict__ gext, const T *__restrict__ w1g,
+                    const T *__restrict__ Xg, const T *__restrict__ t1w, const T *__restrict__ lep,
+                    const T *__restrict__ lamL, T *__restrict__ grad, int N, int ne, T omega, FCoef<T> fc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  recon_tpp_adj_tile<T, K>(smem_raw, blockIdx.z, blockIdx.x * REC_TX, blockIdx.y * REC_TY, REC_TX, REC_TY, q, gext,
+                           w1g, Xg, t1w, lep, lamL, grad, N, ne, omega, fc);
 }
 
 template <typename T, int K>
@@ -332,13 +419,10 @@ __host__ __device__ constexpr size_t recon_adj_smem_bytes() {
 // lam_direct[3][6][N][N], ring cells to lam_ring[3][6][ne][ne].
 // ---------------------------------------------------------------------------------
 template <typename T, int K>
-__global__ void __launch_bounds__(256)
-    k_gather_adj(const T *__restrict__ grad, T *__restrict__ lam_direct, T *__restrict__ lam_ring, int N) {
+__device__ __forceinline__ void gather_adj_item(long long idx, const T *__restrict__ grad, T *__restrict__ lam_direct,
+                                                T *__restrict__ lam_ring, int N) {
   constexpr int H = (K - 1) / 2;
   const int ne = N + 2 * H;
-  const long long total = 6LL * ne * ne;
-  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
   const int ii = (int)(idx % ne);
   const long long pj = idx / ne;
   const int jj = (int)(pj % ne), p = (int)(pj / ne);
@@ -368,6 +452,15 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+template <typename T, int K>
+__global__ void __launch_bounds__(256)
+    k_gather_adj(const T *__restrict__ grad, T *__restrict__ lam_direct, T *__restrict__ lam_ring, int N) {
+  const long long ne = N + K - 1;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 6LL * ne * ne) return;
+  gather_adj_item<T, K>(idx, grad, lam_direct, lam_ring, N);
+}
+
 // ---------------------------------------------------------------------------------
 // Transposed ghost operator + Runge-Kutta adjoint combination, per interior cell:
 //   Lt = lam_direct + sum_rows G^T lam_ring
@@ -375,13 +468,12 @@ __global__ void __launch_bounds__(256)
 // gtp/gtr/gtv: G^T in CSR over interior cells (row index = ghost row, weights as G).
 // ---------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256)
-    k_ghost_adj(const T *__restrict__ lam_direct, const T *__restrict__ lam_ring, const int *__restrict__ gtp,
-                const int *__restrict__ gtr, const T *__restrict__ gtv, const int *__restrict__ gdst,
-                const T *x, const T *y, const T *z, T *out, T a, T b, T d, T c, int N, int ne) {
+__device__ __forceinline__ void ghost_adj_cell(long long cid, const T *__restrict__ lam_direct,
+                                               const T *__restrict__ lam_ring, const int *__restrict__ gtp,
+                                               const int *__restrict__ gtr, const T *__restrict__ gtv,
+                                               const int *__restrict__ gdst, const T *x, const T *y, const T *z,
+                                               T *out, T a, T b, T d, T c, int N, int ne) {
   const long long ncell = 6LL * N * N;
-  long long cid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (cid >= ncell) return;
   const size_t pe = (size_t)6 * ne * ne;
   T s0 = lam_direct[cid], s1 = lam_direct[ncell + cid], s2 = lam_direct[2 * ncell + cid];
   for (int t = gtp[cid]; t < gtp[cid + 1]; ++t) {
@@ -403,6 +495,16 @@ __global__ void __launch_bounds__(256)
     if (z) o += d * z[k];
     out[k] = o;
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_ghost_adj(const T *__restrict__ lam_direct, const T *__restrict__ lam_ring, const int *__restrict__ gtp,
+                const int *__restrict__ gtr, const T *__restrict__ gtv, const int *__restrict__ gdst,
+                const T *x, const T *y, const T *z, T *out, T a, T b, T d, T c, int N, int ne) {
+  const long long cid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cid >= 6LL * N * N) return;
+  ghost_adj_cell(cid, lam_direct, lam_ring, gtp, gtr, gtv, gdst, x, y, z, out, a, b, d, c, N, ne);
 }
 
 }  // namespace hope

@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "hope_adjoint.cuh"
 #include "hope_ensemble.h"
 #include "hope_kernels.cuh"
 #include "hope_setup_math.cuh"
@@ -33,6 +34,15 @@ struct MemberDev {
   long long b_ghost, b_tile, b_flux, b_cell;  // first global item of each phase
   int tiles_x, tiles_y;
   T inv_dx;  // 2N / pi, computed on the host (no FP64 division per cell)
+  // adjoint (filled once the context's adjoint scratch exists): edge-point adjoints,
+  // stencil gradients, ring and interior adjoints, the transposed ghost operator, the
+  // first item of the gather phase (6 ne^2 per member), and the member's block in a step
+  // tape (element offset; ghost-ring and edge-point elements of one stage)
+  T *lep, *grad, *lring, *ldir;
+  const int *gtp, *gtr;
+  const T *gtv;
+  long long b_gather;
+  long long tape_off, tape_ge, tape_ee;
 };
 
 // Ghost-fill work of the members that share one ghost operator (equal N): one item per
@@ -107,16 +117,45 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned *status, unsig
   return ok != 0;
 }
 
+// Begin offsets of one phase's work lists, staged in shared memory at the start of the
+// phase (ensembles of at most MEMBER_CACHE members; larger ones search the member table
+// in global memory), so that the per-item member lookup reads no global memory.
+constexpr int MEMBER_CACHE = 128;
+
+template <typename T>
+__device__ __forceinline__ long long phase_begin(const MemberDev<T> &m, int phase) {
+  return phase == 0 ? m.b_ghost : phase == 1 ? m.b_tile : phase == 2 ? m.b_flux : phase == 3 ? m.b_cell : m.b_gather;
+}
+
+// Called by every thread of the block between two block-wide barriers.
+template <typename T>
+__device__ __forceinline__ void stage_member_begins(long long *sbeg, const MemberDev<T> *mem, int nmem, int phase) {
+  if (nmem > MEMBER_CACHE) return;
+  __syncthreads();
+  for (int i = threadIdx.x; i < nmem; i += blockDim.x) sbeg[i] = phase_begin(mem[i], phase);
+  __syncthreads();
+}
+
+// member owning global item `it` of a phase: binary search over the staged begin offsets
+__device__ __forceinline__ int find_member_cached(const long long *sbeg, int nmem, long long it) {
+  int lo = 0, hi = nmem - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (sbeg[mid] <= it)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
 // member owning global item `it` of a phase (begin offsets ascending by member)
 template <typename T>
 __device__ __forceinline__ int find_member(const MemberDev<T> *mem, int nmem, long long it, int phase) {
   int lo = 0, hi = nmem - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
-    const long long b = phase == 0 ? mem[mid].b_ghost
-                        : phase == 1 ? mem[mid].b_tile
-                        : phase == 2 ? mem[mid].b_flux
-                                     : mem[mid].b_cell;
+    const long long b = phase_begin(mem[mid], phase);
     if (b <= it)
       lo = mid;
     else
@@ -133,6 +172,10 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 1024 / (TX * TY) : 1)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int ME = (K + 1) / 2;
   constexpr int NT = TX * TY, WPB = NT / 32;
+  __shared__ long long sbeg[MEMBER_CACHE];
+  auto lookup = [&](long long it, int phase) {
+    return nmem <= MEMBER_CACHE ? find_member_cached(sbeg, nmem, it) : find_member(mem, nmem, it, phase);
+  };
   const bool stamper = sa.stamp && blockIdx.x == 0 && threadIdx.x == 0;
   if (stamper) sa.stamp[0] = global_ns();
   // phase 1: ghost rows, one warp per (row, member chunk) item
@@ -161,8 +204,9 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 1024 / (TX * TY) : 1)
   if (!grid_sync(bar, status, inject)) return;
   if (stamper) sa.stamp[1] = global_ns();
   // phase 2: reconstruction tiles, one block each
+  stage_member_begins(sbeg, mem, nmem, 1);
   for (long long it = blockIdx.x; it < n_tile; it += gridDim.x) {
-    const MemberDev<T> &m = mem[find_member(mem, nmem, it, 1)];
+    const MemberDev<T> &m = mem[lookup(it, 1)];
     const int local = int(it - m.b_tile);
     const int p = local / (m.tiles_x * m.tiles_y);
     const int rem = local - p * m.tiles_x * m.tiles_y;
@@ -173,15 +217,17 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 1024 / (TX * TY) : 1)
   if (!grid_sync(bar, status, inject)) return;
   if (stamper) sa.stamp[2] = global_ns();
   // phase 3: edge fluxes, one thread per edge
+  stage_member_begins(sbeg, mem, nmem, 2);
   for (long long it = (long long)blockIdx.x * NT + threadIdx.x; it < n_flux; it += (long long)gridDim.x * NT) {
-    const MemberDev<T> &m = mem[find_member(mem, nmem, it, 2)];
+    const MemberDev<T> &m = mem[lookup(it, 2)];
     flux_item<T, ME>(it - m.b_flux, m.ep, m.mx, sa.gw, m.bedge, m.bconv, m.fx, m.fy, m.N, status);
   }
   if (!grid_sync(bar, status, inject)) return;
   if (stamper) sa.stamp[3] = global_ns();
   // phase 4: tendency and stage combination, one thread per cell
+  stage_member_begins(sbeg, mem, nmem, 3);
   for (long long it = (long long)blockIdx.x * NT + threadIdx.x; it < n_cell; it += (long long)gridDim.x * NT) {
-    const MemberDev<T> &m = mem[find_member(mem, nmem, it, 3)];
+    const MemberDev<T> &m = mem[lookup(it, 3)];
     auto off = [&](const T *p) -> const T * { return p ? p + m.off : nullptr; };
     update_cell(it - m.b_cell, m.fx, m.fy, m.sb, off(sa.q0), sa.qs + m.off, sa.out + m.off, m.N,
                 m.inv_dx, sa.mode, sa.a, sa.b, sa.c, sa.alo, sa.blo, sa.clo, off(sa.q0l), off(sa.qsl),
@@ -194,12 +240,141 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 1024 / (TX * TY) : 1)
 }
 
 // -------------------------------------------------------------------------------------
+// One stage VJP of the whole ensemble (the reverse of a stage, section 4's autograd
+// replaced by hand-written adjoints): out = a x + b y + d z + c (dL/dq at qs)^T lamL for
+// every member, as one cooperative launch whose phases walk all members' work lists:
+//   [forward recompute of the ghost rings and edge points, unless a step tape holds them]
+//   flux adjoint per edge | reconstruction + source adjoint per tile | stencil-gradient
+//   gather per extended cell | transposed ghost operator + combination per cell,
+// separated by the same bounded grid barriers as the forward stage.
+// -------------------------------------------------------------------------------------
+template <typename T>
+struct VjpArgs {
+  const T *qs, *lamL;
+  const T *x, *y, *z;
+  T *out;
+  T a, b, d, c;
+  int have_fwd;
+  const T *tape;   // step tape holding the stage's ghost rings and edge points, or null
+  int tape_stage;  // its stage slot
+  T omega;
+  FCoef<T> fc;
+  const T *gw, *w1;
+  const GhostGroup *ggrp;
+  const int *gmem;
+  int ngrp;
+  unsigned long long *stamp;  // profiling: 7 phase stamps, or null
+};
+
+template <typename T, int K, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY)
+    k_vjp_persistent(const MemberDev<T> *__restrict__ mem, int nmem, long long n_ghost, long long n_tile,
+                     long long n_flux, long long n_cell, long long n_gather, VjpArgs<T> va, unsigned *bar,
+                     unsigned *status, unsigned inject) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int ME = (K + 1) / 2;
+  constexpr int NT = TX * TY, WPB = NT / 32;
+  __shared__ long long sbeg[MEMBER_CACHE];
+  auto lookup = [&](long long it, int phase) {
+    return nmem <= MEMBER_CACHE ? find_member_cached(sbeg, nmem, it) : find_member(mem, nmem, it, phase);
+  };
+  const bool stamper = va.stamp && blockIdx.x == 0 && threadIdx.x == 0;
+  if (stamper) va.stamp[0] = va.stamp[1] = va.stamp[2] = global_ns();
+  // ghost ring and edge points of member m at this stage
+  auto gext_of = [&](const MemberDev<T> &m) -> const T * {
+    return va.tape ? va.tape + m.tape_off + (long long)va.tape_stage * (m.tape_ge + m.tape_ee) : m.gext;
+  };
+  auto ep_of = [&](const MemberDev<T> &m) -> const T * {
+    return va.tape ? va.tape + m.tape_off + (long long)va.tape_stage * (m.tape_ge + m.tape_ee) + m.tape_ge : m.ep;
+  };
+  if (!va.have_fwd) {
+    // forward recompute: ghost rows (as the forward stage's first phase), then tiles
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (long long it = (long long)blockIdx.x * WPB + warp; it < n_ghost; it += (long long)gridDim.x * WPB) {
+      int lo = 0, hi = va.ngrp - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (va.ggrp[mid].b_item <= it)
+          lo = mid;
+        else
+          hi = mid - 1;
+      }
+      const GhostGroup &G = va.ggrp[lo];
+      const long long local = it - G.b_item;
+      const int r = (int)(local / G.nchunk), c = (int)(local - (long long)r * G.nchunk);
+      const int k1 = min(G.nmem, (c + 1) * GHOST_GROUP_CHUNK);
+      for (int k = c * GHOST_GROUP_CHUNK; k < k1; ++k) {
+        const MemberDev<T> &m = mem[va.gmem[G.first + k]];
+        ghost_row<T, false>(r, lane, va.qs + m.off, m.gext, m.grow, m.gcol, m.gval, m.gdst, m.gsym, m.trow, m.tcol,
+                            m.tval, m.N, m.ne);
+      }
+    }
+    if (!grid_sync(bar, status, inject)) return;
+    if (stamper) va.stamp[1] = global_ns();
+    stage_member_begins(sbeg, mem, nmem, 1);
+    for (long long it = blockIdx.x; it < n_tile; it += gridDim.x) {
+      const MemberDev<T> &m = mem[lookup(it, 1)];
+      const int local = int(it - m.b_tile);
+      const int p = local / (m.tiles_x * m.tiles_y);
+      const int rem = local - p * m.tiles_x * m.tiles_y;
+      const int ty = rem / m.tiles_x, tx = rem - ty * m.tiles_x;
+      recon_tpp_tile<T, K>(smem_raw, p, tx * TX, ty * TY, TX, TY, va.qs + m.off, m.gext, va.w1, m.Xg, m.t1w, m.src8,
+                           m.ep, m.sb, m.N, m.ne, va.omega, va.fc);
+    }
+    if (!grid_sync(bar, status, inject)) return;
+    if (stamper) va.stamp[2] = global_ns();
+  }
+  // edge quadrature and LMARS adjoints, one thread per edge
+  stage_member_begins(sbeg, mem, nmem, 2);
+  for (long long it = (long long)blockIdx.x * NT + threadIdx.x; it < n_flux; it += (long long)gridDim.x * NT) {
+    const MemberDev<T> &m = mem[lookup(it, 2)];
+    flux_adj_item<T, ME>(it - m.b_flux, ep_of(m), m.mx, va.gw, m.bedge, m.bconv, va.lamL + m.off, m.lep, m.N,
+                         m.inv_dx);
+  }
+  if (!grid_sync(bar, status, inject)) return;
+  if (stamper) va.stamp[3] = global_ns();
+  // reconstruction and source adjoints, one block per tile
+  stage_member_begins(sbeg, mem, nmem, 1);
+  for (long long it = blockIdx.x; it < n_tile; it += gridDim.x) {
+    const MemberDev<T> &m = mem[lookup(it, 1)];
+    const int local = int(it - m.b_tile);
+    const int p = local / (m.tiles_x * m.tiles_y);
+    const int rem = local - p * m.tiles_x * m.tiles_y;
+    const int ty = rem / m.tiles_x, tx = rem - ty * m.tiles_x;
+    recon_tpp_adj_tile<T, K>(smem_raw, p, tx * TX, ty * TY, TX, TY, va.qs + m.off, gext_of(m), va.w1, m.Xg, m.t1w,
+                             m.lep, va.lamL + m.off, m.grad, m.N, m.ne, va.omega, va.fc);
+  }
+  if (!grid_sync(bar, status, inject)) return;
+  if (stamper) va.stamp[4] = global_ns();
+  // gather of the stencil gradients, one thread per extended cell
+  stage_member_begins(sbeg, mem, nmem, 4);
+  for (long long it = (long long)blockIdx.x * NT + threadIdx.x; it < n_gather; it += (long long)gridDim.x * NT) {
+    const MemberDev<T> &m = mem[lookup(it, 4)];
+    gather_adj_item<T, K>(it - m.b_gather, m.grad, m.ldir, m.lring, m.N);
+  }
+  if (!grid_sync(bar, status, inject)) return;
+  if (stamper) va.stamp[5] = global_ns();
+  // transposed ghost operator and the Runge-Kutta combination, one thread per cell
+  stage_member_begins(sbeg, mem, nmem, 3);
+  for (long long it = (long long)blockIdx.x * NT + threadIdx.x; it < n_cell; it += (long long)gridDim.x * NT) {
+    const MemberDev<T> &m = mem[lookup(it, 3)];
+    auto off = [&](const T *p) -> const T * { return p ? p + m.off : nullptr; };
+    ghost_adj_cell(it - m.b_cell, m.ldir, m.lring, m.gtp, m.gtr, m.gtv, m.gdst, off(va.x), off(va.y), off(va.z),
+                   va.out + m.off, va.a, va.b, va.d, va.c, m.N, m.ne);
+  }
+  if (va.stamp) {
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax(va.stamp + 6, global_ns());
+  }
+}
+
+// -------------------------------------------------------------------------------------
 // host side
 // -------------------------------------------------------------------------------------
 template <typename T>
-static int build_members(hope_ctx *ctx, int TX, int TY, std::vector<MemberDev<T>> &out, long long n[4]) {
+static int build_members(hope_ctx *ctx, int TX, int TY, std::vector<MemberDev<T>> &out, long long n[5]) {
   out.clear();
-  long long bg = 0, bt = 0, bf = 0, bc = 0;
+  long long bg = 0, bt = 0, bf = 0, bc = 0, bgat = 0, tape_acc = 0;
   for (auto &g : ctx->grids) {
     MemberDev<T> m{};
     m.N = g.N;
@@ -227,6 +402,19 @@ static int build_members(hope_ctx *ctx, int TX, int TY, std::vector<MemberDev<T>
     m.fy = (T *)g.fy;
     m.tiles_x = (g.N + TX - 1) / TX;
     m.tiles_y = (g.N + TY - 1) / TY;
+    m.lep = (T *)g.lep;
+    m.grad = (T *)g.grad;
+    m.lring = (T *)g.lring;
+    m.ldir = (T *)g.ldir;
+    m.gtp = g.gtp;
+    m.gtr = g.gtr;
+    m.gtv = (const T *)g.gtv;
+    m.tape_ge = 3LL * 6 * g.ne * g.ne;
+    m.tape_ee = 4LL * 3 * ctx->me * 6 * g.N * g.N;
+    m.tape_off = 2LL * (long long)ctx->total + tape_acc;
+    tape_acc += 3 * (m.tape_ge + m.tape_ee);
+    m.b_gather = bgat;
+    bgat += 6LL * g.ne * g.ne;
     m.b_ghost = bg;
     m.b_tile = bt;
     m.b_flux = bf;
@@ -241,6 +429,7 @@ static int build_members(hope_ctx *ctx, int TX, int TY, std::vector<MemberDev<T>
   n[1] = bt;
   n[2] = bf;
   n[3] = bc;
+  n[4] = bgat;
   return HOPE_OK;
 }
 
@@ -344,6 +533,127 @@ int stage_persistent(hope_ctx *ctx, const void *qs, const void *q0, void *out, i
   return stage_persistent_t<float>(ctx, qs, q0, out, mode, a, b, c, q0l, qsl, outl, st);
 }
 
+template <typename T, int K, int TX, int TY>
+static int launch_vjp_shape(hope_ctx *ctx, EnsembleState &es, const VjpArgs<T> &va, cudaStream_t st) {
+  auto kern = k_vjp_persistent<T, K, TX, TY>;
+  constexpr size_t fwd = recon_smem_bytes<T, K, TX, TY>();
+  constexpr size_t adj = recon_adj_tile_smem_bytes<T, K>(TX, TY, TX * TY);
+  const size_t smem = fwd > adj ? fwd : adj;
+  if (es.vgrid[es.shape] == 0) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      set_error("persistent stage VJP: shared-memory attribute failed");
+      return HOPE_ECUDA;
+    }
+    int per_sm = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, smem);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (per_sm < 1) {
+      set_error("persistent stage VJP: no resident block fits");
+      return HOPE_EUNSUPPORTED;
+    }
+    es.vgrid[es.shape] = per_sm * sms;
+  }
+  const MemberDev<T> *mem = (const MemberDev<T> *)es.members[es.shape];
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(es.vgrid[es.shape]);
+  cfg.blockDim = dim3(TX * TY);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const long long *n = es.items[es.shape];
+  const unsigned inject = es.inject_timeout ? 1u : 0u;
+  es.inject_timeout = 0;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, mem, (int)ctx->grids.size(), n[0], n[1], n[2], n[3], n[4], va,
+                                     es.barrier, ctx->status, inject);
+  if (e != cudaSuccess) {
+    set_error(std::string("persistent stage VJP launch: ") + cudaGetErrorString(e));
+    return HOPE_ECUDA;
+  }
+  return HOPE_OK;
+}
+
+template <typename T, int K>
+static int launch_vjp_any(hope_ctx *ctx, EnsembleState &es, const VjpArgs<T> &va, cudaStream_t st) {
+  switch (es.shape) {
+    case 0: return launch_vjp_shape<T, K, 16, 8>(ctx, es, va, st);
+    case 1: return launch_vjp_shape<T, K, 16, 4>(ctx, es, va, st);
+    default: return launch_vjp_shape<T, K, 32, 4>(ctx, es, va, st);
+  }
+}
+
+// The member tables again, now with the adjoint scratch pointers (the scratch is
+// allocated on the first VJP call); same device arrays, so captured graphs stay valid.
+template <typename T>
+static int ensemble_adjoint_members_t(hope_ctx *ctx) {
+  EnsembleState &es = *ctx->ens;
+  for (int s = 0; s < kNumShapes; ++s) {
+    std::vector<MemberDev<T>> mv;
+    long long n[5];
+    build_members<T>(ctx, kShapes[s].TX, kShapes[s].TY, mv, n);
+    if (cudaMemcpy(es.members[s], mv.data(), sizeof(MemberDev<T>) * mv.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+      set_error("persistent stage VJP: member table upload failed");
+      return HOPE_ECUDA;
+    }
+  }
+  es.adj_ready = 1;
+  return HOPE_OK;
+}
+
+template <typename T>
+static int vjp_persistent_t(hope_ctx *ctx, const void *qs, const void *lamL, void *out, const void *x, const void *y,
+                            const void *z, double a, double b, double d, double c, int have_fwd, const void *tape,
+                            int tape_stage, cudaStream_t st) {
+  EnsembleState &es = *ctx->ens;
+  if (!es.adj_ready) {
+    int rc = ensemble_adjoint_members_t<T>(ctx);
+    if (rc) return rc;
+  }
+  VjpArgs<T> va;
+  va.qs = (const T *)qs;
+  va.lamL = (const T *)lamL;
+  va.x = (const T *)x;
+  va.y = (const T *)y;
+  va.z = (const T *)z;
+  va.out = (T *)out;
+  va.a = (T)a;
+  va.b = (T)b;
+  va.d = (T)d;
+  va.c = (T)c;
+  va.have_fwd = have_fwd;
+  va.tape = (const T *)tape;
+  va.tape_stage = tape_stage;
+  va.omega = (T)ctx->omega;
+  for (int t = 0; t < 18; ++t) va.fc.c[t] = (T)ctx->fcoef[t];
+  va.gw = (const T *)ctx->gw;
+  va.w1 = (const T *)ctx->w1;
+  va.ggrp = (const GhostGroup *)es.ggrp;
+  va.gmem = es.gmem;
+  va.ngrp = es.ngrp;
+  va.stamp = ctx->profiling ? es.vstamps : nullptr;
+  if (va.stamp && cudaMemsetAsync(va.stamp + 6, 0, sizeof(unsigned long long), st) != cudaSuccess) return HOPE_ECUDA;
+  switch (ctx->k) {
+    case 3: return launch_vjp_any<T, 3>(ctx, es, va, st);
+    case 5: return launch_vjp_any<T, 5>(ctx, es, va, st);
+    case 7: return launch_vjp_any<T, 7>(ctx, es, va, st);
+    case 9: return launch_vjp_any<T, 9>(ctx, es, va, st);
+    case 11: return launch_vjp_any<T, 11>(ctx, es, va, st);
+  }
+  return HOPE_EINVAL;
+}
+
+int vjp_persistent(hope_ctx *ctx, const void *qs, const void *lamL, void *out, const void *x, const void *y,
+                   const void *z, double a, double b, double d, double c, int have_fwd, const void *tape,
+                   int tape_stage, cudaStream_t st) {
+  if (ctx->prec == HOPE_FP64)
+    return vjp_persistent_t<double>(ctx, qs, lamL, out, x, y, z, a, b, d, c, have_fwd, tape, tape_stage, st);
+  return vjp_persistent_t<float>(ctx, qs, lamL, out, x, y, z, a, b, d, c, have_fwd, tape, tape_stage, st);
+}
+
 template <typename T>
 static int ensemble_init_t(hope_ctx *ctx) {
   EnsembleState *es = new EnsembleState();
@@ -392,6 +702,8 @@ static int ensemble_init_t(hope_ctx *ctx) {
   }
   if (cudaMalloc(&es->barrier, 2 * sizeof(unsigned)) != cudaSuccess) return HOPE_ENOMEM;
   if (cudaMalloc(&es->stamps, 5 * PROF_STAGES * sizeof(unsigned long long)) != cudaSuccess) return HOPE_ENOMEM;
+  if (cudaMalloc(&es->vstamps, 7 * sizeof(unsigned long long)) != cudaSuccess) return HOPE_ENOMEM;
+  cudaMemset(es->vstamps, 0, 7 * sizeof(unsigned long long));
   cudaMemset(es->stamps, 0, 5 * PROF_STAGES * sizeof(unsigned long long));
   cudaMemset(es->barrier, 0, 2 * sizeof(unsigned));
   return HOPE_OK;
@@ -407,6 +719,7 @@ void ensemble_free(hope_ctx *ctx) {
     if (ctx->ens->members[s]) cudaFree(ctx->ens->members[s]);
   if (ctx->ens->barrier) cudaFree(ctx->ens->barrier);
   if (ctx->ens->stamps) cudaFree(ctx->ens->stamps);
+  if (ctx->ens->vstamps) cudaFree(ctx->ens->vstamps);
   if (ctx->ens->ggrp) cudaFree(ctx->ens->ggrp);
   if (ctx->ens->gmem) cudaFree(ctx->ens->gmem);
   delete ctx->ens;

@@ -8,13 +8,19 @@ namespace hope {
 
 struct EnsembleState {
   void *members[3] = {nullptr, nullptr, nullptr};  // MemberDev<T>[n] per tile shape
-  long long items[3][4] = {};                       // ghost rows, tiles, edges, cells
+  long long items[3][5] = {};                       // ghost rows, tiles, edges, cells, extended cells
   int grid[3] = {0, 0, 0};                          // resident blocks per shape
+  int vgrid[3] = {0, 0, 0};                         // resident blocks of the VJP launch per shape
+  int adj_ready = 0;  // member tables carry the adjoint scratch pointers
   int shape = 0;
   int tuned = 0;
   int inject_timeout = 0;  // the next launch's barriers expect one block more (test hook)
   unsigned *barrier = nullptr;  // [count, generation]
   unsigned long long *stamps = nullptr;  // profiling: per stage [start, 3 phase ends, end] (ns)
+  // profiling: the last VJP launch's [start, forward ghost end, forward tiles end, flux end,
+  // reconstruction end, gather end, end] (ns; the forward entries equal the start when the
+  // stage's forward came from a tape)
+  unsigned long long *vstamps = nullptr;
   void *ggrp = nullptr;  // GhostGroup[ngrp]: ghost-fill work grouped by shared operator
   int *gmem = nullptr;   // member indices of the groups
   int ngrp = 0;
@@ -26,6 +32,12 @@ void ensemble_reset_barrier(hope_ctx *ctx);
 int stage_persistent(hope_ctx *ctx, const void *qs, const void *q0, void *out, int mode, double a, double b,
                      double c, const void *q0l, const void *qsl, void *outl, cudaStream_t st);
 int ensemble_autotune(hope_ctx *ctx, const void *qs, void *out, int reps, float *ms_out, cudaStream_t st);
+// One stage VJP of every member in one persistent launch: out = a x + b y + d z + c L^T lamL
+// at qs (x, y, z may be null).  have_fwd: the ghost rings and edge points at qs are in the
+// members' buffers, or in `tape` (a step tape, stage slot tape_stage) when tape is not null.
+int vjp_persistent(hope_ctx *ctx, const void *qs, const void *lamL, void *out, const void *x, const void *y,
+                   const void *z, double a, double b, double d, double c, int have_fwd, const void *tape,
+                   int tape_stage, cudaStream_t st);
 void ensemble_shape(const hope_ctx *ctx, int *tx, int *ty, int *grid);
 
 }  // namespace hope

@@ -61,6 +61,10 @@ struct Grid {
   // [4][me][6][N][N], and psi_B's cell average as an affine map of the depth stencil,
   // weights [2][k*k][6][N][N] and constants [2][6][N][N]
   void *tsep = nullptr, *ttw = nullptr, *ttb = nullptr;
+  // WENO2D over a surface: the surface's extended averages [6][ne][ne] (added to the mass
+  // variable before the nonlinear reconstruction) and its TPP values at the cell points
+  // [me*me][6][N][N] (subtracted after it)
+  void *tsext = nullptr, *tscp = nullptr;
   CubeEdge edges[12];
   // transposed ghost operator (adjoint): CSR over interior cells
   int *gtp = nullptr;    // [6*N*N + 1]
@@ -109,6 +113,9 @@ struct hope_ctx {
   void *sig = nullptr;    // [npoc][2] sigma+, sigma-
   void *bform = nullptr;  // [l][l*l + l] Winv and its row sums per sub-stencil offset
   void *bcoef = nullptr;  // [l][l][l][l] indicator mode weights
+  // dimension-by-dimension WENO-Z (HOPE_WENO1D): 1-D split linear weights gamma+-
+  // [me+2][2][l], sigma+- [me+2][2], indicator eigenpairs per sub-stencil [l][l*l + l]
+  void *w1gpm = nullptr, *w1sig = nullptr, *w1bf = nullptr;
   // buffers
   void *state = nullptr;  // context-owned state
   void *q1 = nullptr, *q2 = nullptr, *lbuf = nullptr;

@@ -665,7 +665,8 @@ namespace hope {
 // and constants tb[2][6][N][N].  The gradient of phi_t = (P_depth + P_s)/sqrtG uses the
 // derivative weights of the TPP polynomials and the closed-form gradient of sqrtG.
 int build_topography_tables(const hope_ctx *ctx, int N, const double *phis_avg_host, std::vector<double> &sep,
-                            std::vector<double> &tw, std::vector<double> &tb) {
+                            std::vector<double> &tw, std::vector<double> &tb, std::vector<double> *sext,
+                            std::vector<double> *scp) {
   const int K = ctx->k, H = ctx->H, ME = ctx->me, KK = K * K, ne = N + 2 * H;
   const size_t pn = (size_t)6 * N * N;
   std::vector<double> nodes(ME), weights(ME);
@@ -697,6 +698,8 @@ int build_topography_tables(const hope_ctx *ctx, int N, const double *phis_avg_h
   sep.assign((size_t)4 * ME * pn, 0.0);
   tw.assign((size_t)2 * KK * pn, 0.0);
   tb.assign(2 * pn, 0.0);
+  if (sext) *sext = ext;
+  if (scp) scp->assign((size_t)ME * ME * pn, 0.0);
   // every cell writes only its own entries, so the panel rows run in parallel
 #pragma omp parallel for schedule(dynamic, 4)
   for (int pj = 0; pj < 6 * N; ++pj) {
@@ -734,6 +737,7 @@ int build_topography_tables(const hope_ctx *ctx, int N, const double *phis_avg_h
             const double *vx = &wv[(size_t)(2 + gg) * K], *vy = &wv[(size_t)(2 + h) * K];
             const double *dxw = &wd[(size_t)gg * K], *dyw = &wd[(size_t)h * K];
             const double Ps = tpp(vx, vy);
+            if (scp) (*scp)[((size_t)h * ME + gg) * pn + cell] = Ps;
             const double fs = Ps / sG;  // phi_s at the point
             const double dsx = (tpp(dxw, vy) / dx - fs * gx) / sG, dsy = (tpp(vx, dyw) / dx - fs * gy) / sG;
             // quadrature weight times sqrtG phi_s G^ij (true metric) of eq. 2.14
@@ -836,6 +840,46 @@ int setup_weno_tables(hope_ctx *ctx, const std::vector<double> &nodes) {
           bcoef[(((size_t)sy * l + k) * l + sx) * l + kp] = c;
         }
   int rc;
+  if (ctx->scheme == HOPE_WENO1D) {
+    // 1-D tables of the dimension-by-dimension comparator: split 1-D linear weights per
+    // position, and per sub-stencil the Jiang-Shu indicator form S - B0 (derivative orders
+    // 1..l-1) as eigenpairs, its constant mode's eigenvalue set to 0 and negatives clamped
+    std::vector<double> w1gpm((size_t)(me + 2) * 2 * l), w1sig((size_t)(me + 2) * 2);
+    for (int t = 0; t < me + 2; ++t) {
+      double sp = 0.0, sm = 0.0;
+      for (int sb = 0; sb < l; ++sb) {
+        const double gm = g1[(size_t)t * l + sb];
+        const double gpl = 0.5 * (3.0 * fabs(gm) + gm), gmi = 0.5 * (3.0 * fabs(gm) - gm);
+        w1gpm[((size_t)t * 2 + 0) * l + sb] = gpl;
+        w1gpm[((size_t)t * 2 + 1) * l + sb] = gmi;
+        sp += gpl;
+        sm += gmi;
+      }
+      w1sig[(size_t)t * 2] = sp;
+      w1sig[(size_t)t * 2 + 1] = sm;
+    }
+    std::vector<double> w1bf((size_t)l * (l * l + l));
+    for (int sb = 0; sb < l; ++sb) {
+      double Sm[HOPE_MAXME * HOPE_MAXME], B0[HOPE_MAXME * HOPE_MAXME], I[HOPE_MAXME * HOPE_MAXME];
+      weno_beta_forms_1d(l, sb - H, Sm, B0);
+      double mx = 0.0;
+      for (int a = 0; a < l * l; ++a) {
+        Sm[a] -= B0[a];
+        I[a] = (a % (l + 1)) == 0 ? 1.0 : 0.0;
+        mx = std::max(mx, fabs(Sm[a]));
+      }
+      double *Wv = &w1bf[(size_t)sb * (l * l + l)];
+      if (weno_beta_diag(l, Sm, I, Wv, Wv + l * l)) {
+        set_error("1-D WENO smoothness forms: eigen-decomposition failed");
+        return HOPE_EINVAL;
+      }
+      for (int k = 0; k < l; ++k)
+        if (Wv[l * l + k] < 1e-12 * mx) Wv[l * l + k] = 0.0;
+    }
+    if ((rc = upload_t(ctx, &ctx->w1gpm, w1gpm))) return rc;
+    if ((rc = upload_t(ctx, &ctx->w1sig, w1sig))) return rc;
+    if ((rc = upload_t(ctx, &ctx->w1bf, w1bf))) return rc;
+  }
   if ((rc = upload_t(ctx, &ctx->wsub, wsub))) return rc;
   if ((rc = upload_t(ctx, &ctx->gpm, gpm))) return rc;
   if ((rc = upload_t(ctx, &ctx->sig, sig))) return rc;

@@ -33,6 +33,10 @@ int build_cube_edges(const hope_ctx *ctx, int N, const std::vector<double> &node
                      std::vector<double> &conv);
 int setup_weno_tables(hope_ctx *ctx, const std::vector<double> &nodes);
 // Static tables of a bottom surface from the cell averages of sqrtG phi_s (FP64).
+// Optional outputs for the WENO2D reconstruction of sqrtG phi_t: the surface's extended
+// averages sext [6][ne][ne] (interior and ghost ring) and its TPP values at the cell points
+// scp [me*me][6][N][N] (y node major).
 int build_topography_tables(const hope_ctx *ctx, int N, const double *phis_avg_host, std::vector<double> &sep,
-                            std::vector<double> &tw, std::vector<double> &tb);
+                            std::vector<double> &tw, std::vector<double> &tb, std::vector<double> *sext = nullptr,
+                            std::vector<double> *scp = nullptr);
 }  // namespace hope

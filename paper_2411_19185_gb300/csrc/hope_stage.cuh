@@ -11,6 +11,7 @@
 #include "hope_kernels.cuh"
 #include "hope_setup_math.cuh"
 #include "hope_weno.cuh"
+#include "hope_weno1d.cuh"
 
 namespace hope {
 
@@ -87,8 +88,14 @@ int launch_recon_weno(hope_ctx *ctx, Grid &g, const T *qs, cudaStream_t st) {
     kern<<<grid, threads, smem, st>>>(qs, (const T *)g.gext, (const T *)ctx->wsub, (const T *)ctx->gpm,
                                       (const T *)ctx->sig, (const T *)ctx->bform, (const T *)ctx->bcoef,
                                       (const T *)g.Xg, (const T *)g.t1w, (T *)g.ep, (T *)g.sb, N, g.ne, TX, TY,
-                                      (T)ctx->omega, fcoef<T>(ctx), (T)ctx->eps);
+                                      (T)ctx->omega, fcoef<T>(ctx), (T)ctx->eps, (const T *)g.tsext,
+                                      (const T *)g.tsep, (const T *)g.tscp);
   };
+  if (g.tsext) {
+    // over a surface: FP64 takes the runtime-tile form (any shape), FP32 the 16 x 8 form
+    args(k_recon_weno<T, K, sizeof(T) == 8, true>);
+    return HOPE_OK;
+  }
   if constexpr (sizeof(T) == 8) {
     if (TX != REC_TX || TY != REC_TY) {
       args(k_recon_weno<T, K, true>);
@@ -97,6 +104,23 @@ int launch_recon_weno(hope_ctx *ctx, Grid &g, const T *qs, cudaStream_t st) {
   }
   args(k_recon_weno<T, K, false>);
   return HOPE_OK;
+  }
+}
+
+template <typename T, int K>
+int launch_recon_weno1d(hope_ctx *ctx, Grid &g, const T *qs, cudaStream_t st) {
+  if constexpr (K != 5) {
+    (void)ctx; (void)g; (void)qs; (void)st;
+    set_error("WENO1D is fifth order only");
+    return HOPE_EUNSUPPORTED;
+  } else {
+    const int N = g.N;
+    dim3 grid((N + REC_TX - 1) / REC_TX, (N + REC_TY - 1) / REC_TY, 6);
+    k_recon_weno1d<T, K><<<grid, REC_TX * REC_TY, sizeof(T) * Weno1dShape<T, K>::smem_elems(), st>>>(
+        qs, (const T *)g.gext, (const T *)ctx->wsub, (const T *)ctx->w1gpm, (const T *)ctx->w1sig,
+        (const T *)ctx->w1bf, (const T *)g.Xg, (const T *)g.t1w, (T *)g.ep, (T *)g.sb, N, g.ne, (T)ctx->omega,
+        fcoef<T>(ctx), (T)ctx->eps);
+    return HOPE_OK;
   }
 }
 
@@ -110,6 +134,9 @@ int weno_set_smem_attr() {
   if (K <= HOPE_WENO_ADJ_MAXK && smem_adj <= 227 * 1024) {
     cudaError_t e2 = cudaFuncSetAttribute(k_recon_weno_adj<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem_adj);
+    if (e2 == cudaSuccess)
+      e2 = cudaFuncSetAttribute(k_recon_weno_adj<T, K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_adj);
     if (e2 != cudaSuccess) {
       set_error(std::string("WENO adjoint shared memory attribute: ") + cudaGetErrorString(e2));
       return HOPE_ECUDA;
@@ -120,10 +147,18 @@ int weno_set_smem_attr() {
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   (void)smem;
   cudaError_t e = cudaFuncSetAttribute(k_recon_weno<T, K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if constexpr (K == 5) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_recon_weno1d<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(sizeof(T) * Weno1dShape<T, K>::smem_elems()));
+  }
   if constexpr (sizeof(T) == 8) {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_recon_weno<T, K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   }
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_recon_weno<T, K, sizeof(T) == 8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin);
   if (e != cudaSuccess) {
     set_error(std::string("WENO shared memory attribute: ") + cudaGetErrorString(e));
     return HOPE_ECUDA;
@@ -146,10 +181,11 @@ int launch_recon_weno_adj(hope_ctx *ctx, Grid &g, const T *qs, const T *lamL, cu
     set_error("WENO adjoint: order too high for the per-cell shared-memory staging");
     return HOPE_EUNSUPPORTED;
   }
-  k_recon_weno_adj<T, K><<<grid, REC_TX * REC_TY, smem, st>>>(
+  auto kern = g.tsext ? k_recon_weno_adj<T, K, true> : k_recon_weno_adj<T, K, false>;
+  kern<<<grid, REC_TX * REC_TY, smem, st>>>(
       qs, (const T *)g.gext, (const T *)ctx->wsub, (const T *)ctx->gpm, (const T *)ctx->sig, (const T *)ctx->bform,
       (const T *)ctx->bcoef, (const T *)g.Xg, (const T *)g.t1w, (const T *)g.lep, lamL, (T *)g.grad, N, g.ne,
-      (T)ctx->omega, fcoef<T>(ctx), (T)ctx->eps);
+      (T)ctx->omega, fcoef<T>(ctx), (T)ctx->eps, (const T *)g.tsext, (const T *)g.tscp);
   return HOPE_OK;
   }
 }
@@ -188,6 +224,9 @@ inline int stage_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *q0, T *out, 
   // reconstruction + sources
   if (ctx->scheme == HOPE_TPP) {
     launch_recon_tpp<T, K>(ctx, g, qs, st);
+  } else if (ctx->scheme == HOPE_WENO1D) {
+    int rc = launch_recon_weno1d<T, K>(ctx, g, qs, st);
+    if (rc) return rc;
   } else {
     int rc = launch_recon_weno<T, K>(ctx, g, qs, st);
     if (rc) return rc;
@@ -266,6 +305,10 @@ struct VjpComb {
   const void *x = nullptr, *y = nullptr, *z = nullptr;
   double a = 0, b = 0, d = 0, c = 1;
   int have_fwd = 0;  // the grids' ghost rings and edge points already hold the forward at qs
+  // ensembles: with have_fwd, the ghost rings and edge points are read from this step tape's
+  // stage slot instead (no copies); ignored by the per-grid path
+  const void *tape = nullptr;
+  int tape_stage = 0;
 };
 
 template <typename T, int K>
@@ -290,9 +333,10 @@ inline int stage_vjp_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *lamL, co
   const T inv_dx = (T)(2.0 * N / HOPE_PI);
   {
     long long items = 12LL * N * (N - 1) + 12LL * N;
-    k_flux_adj<T, ME><<<(int)((items + 255) / 256), 256, 0, st>>>((const T *)g.ep, (const T *)g.mx,
-                                                                   (const T *)ctx->gw, g.bedge, (const T *)g.bconv,
-                                                                   lamL, (T *)g.lep, N, inv_dx);
+    auto kern = g.tsep ? k_flux_adj<T, ME, true> : k_flux_adj<T, ME, false>;
+    kern<<<(int)((items + 255) / 256), 256, 0, st>>>((const T *)g.ep, (const T *)g.mx, (const T *)ctx->gw, g.bedge,
+                                                      (const T *)g.bconv, lamL, (T *)g.lep, N, inv_dx,
+                                                      (const T *)g.tsep);
   }
   if (ctx->scheme == HOPE_TPP) {
     k_recon_tpp_adj<T, K><<<grid, REC_TX * REC_TY, recon_adj_smem_bytes<T, K>(), st>>>(
@@ -301,6 +345,11 @@ inline int stage_vjp_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *lamL, co
   } else {
     int rc = launch_recon_weno_adj<T, K>(ctx, g, qs, lamL, st);
     if (rc) return rc;
+  }
+  if (g.tsep) {
+    // psi_B's stencil map, transposed, into the mass variable's stencil gradient
+    const long long cells = 6LL * N * N;
+    k_topo_src_adj<T, K><<<(int)((cells + 255) / 256), 256, 0, st>>>(lamL, (const T *)g.ttw, (T *)g.grad, N);
   }
   {
     long long total = 6LL * ne * ne;

@@ -50,12 +50,17 @@ constexpr int WENO_MAX_THREADS = 256;
 // default 16 x 8 tile with 128 threads as constants (the FP32 kernel is bound by its
 // instruction count, and constant strides save the address arithmetic); RT = true takes
 // the shape at run time (FP64 tiles chosen for balance).
-template <typename T, int K, bool RT = false>
+// TOPO (bottom topography, eqs. 2.13-2.14, reading c26): the mass variable reconstructed is
+// sqrtG phi_t = q0 + sqrtG phi_s (the surface's extended averages sext [6][ne][ne] added at
+// the tile load), and the surface's own TPP values at the points (sep at the edge points,
+// scp [me*me][6][N][N] at the cell points) are subtracted from it, leaving the depth.
+template <typename T, int K, bool RT = false, bool TOPO = false>
 __global__ void __launch_bounds__(RT ? WENO_MAX_THREADS : REC_TX * REC_TY)
     k_recon_weno(const T *__restrict__ q, const T *__restrict__ gext, const T *__restrict__ wsub_g,
                  const T *__restrict__ gpm_g, const T *__restrict__ sig_g, const T *__restrict__ bform_g,
                  const T *__restrict__ bcoef_g, const T *__restrict__ Xg, const T *__restrict__ t1w, T *__restrict__ ep, T *__restrict__ sb,
-                 int N, int ne, int TXr, int TYr, T omega, FCoef<T> fc, T eps) {
+                 int N, int ne, int TXr, int TYr, T omega, FCoef<T> fc, T eps, const T *__restrict__ sext = nullptr,
+                 const T *__restrict__ sep = nullptr, const T *__restrict__ scp = nullptr) {
   using W = WenoShape<T, K>;
   constexpr int L = W::L, S = W::S, ME = W::ME, NPOS = W::NPOS, NPOC = W::NPOC, H = (K - 1) / 2;
   const int TX = RT ? TXr : REC_TX, TY = RT ? TYr : REC_TY;
@@ -90,6 +95,9 @@ __global__ void __launch_bounds__(RT ? WENO_MAX_THREADS : REC_TX * REC_TY)
         val = q[v * pn + ((size_t)p * N + jj) * N + ii];
       else if (ii >= -H && ii < N + H && jj >= -H && jj < N + H)
         val = gext[v * pe + ((size_t)p * ne + (jj + H)) * ne + (ii + H)];
+      if constexpr (TOPO) {
+        if (v == 0) val += sext[((size_t)p * ne + (jj + H)) * ne + (ii + H)];
+      }
       raw[(v * RH + r) * RW + c] = val;
     }
   }
@@ -198,7 +206,13 @@ __global__ void __launch_bounds__(RT ? WENO_MAX_THREADS : REC_TX * REC_TY)
             Dp = fma(gp[ii], f[ii], Dp);
             Dm = fma(gp[S + ii], f[ii], Dm);
           }
-          const T val = sig[2 * pt] * Ap[jj] / Dp - sig[2 * pt + 1] * Am[jj] / Dm;
+          T val = sig[2 * pt] * Ap[jj] / Dp - sig[2 * pt + 1] * Am[jj] / Dm;
+          if constexpr (TOPO) {
+            if (v == 0)  // the depth: sqrtG phi_t minus the surface's TPP value at the point
+              val -= t < 2 ? sep[((size_t)t * ME + jj) * pn + cell]
+                           : (jj < 2 ? sep[((size_t)(2 + jj) * ME + g) * pn + cell]
+                                     : scp[((size_t)(jj - 2) * ME + g) * pn + cell]);
+          }
           if (t < 2) {
             ep[((size_t)(t * 3 + v) * ME + jj) * pn + cell] = val;
           } else if (jj < 2) {
@@ -302,13 +316,17 @@ __device__ __forceinline__ void weno_indicators(const T *Qv, const T *bform, con
   }
 }
 
-template <typename T, int K>
+// TOPO: over a surface the forward reconstructed sqrtG phi_t (sext added to the mass
+// variable's tile) and subtracted the surface's TPP values at the points; the recomputed
+// cell-point depths do the same (scp), the derivatives are those at the shifted tile.
+template <typename T, int K, bool TOPO = false>
 __global__ void __launch_bounds__(REC_TX *REC_TY)
     k_recon_weno_adj(const T *__restrict__ q, const T *__restrict__ gext, const T *__restrict__ wsub_g,
                      const T *__restrict__ gpm_g, const T *__restrict__ sig_g, const T *__restrict__ bform_g,
                      const T *__restrict__ bcoef_g, const T *__restrict__ Xg, const T *__restrict__ t1w,
                      const T *__restrict__ lep, const T *__restrict__ lamL, T *__restrict__ grad, int N, int ne,
-                     T omega, FCoef<T> fc, T eps) {
+                     T omega, FCoef<T> fc, T eps, const T *__restrict__ sext = nullptr,
+                     const T *__restrict__ scp = nullptr) {
   using W = WenoShape<T, K>;
   using SH = Shape<K>;
   constexpr int L = W::L, S = W::S, ME = W::ME, NPOS = W::NPOS, NPOC = W::NPOC, NT = W::NT, RW = SH::RW;
@@ -330,6 +348,15 @@ __global__ void __launch_bounds__(REC_TX *REC_TY)
   for (int t = threadIdx.x; t < L * (L * L + L); t += blockDim.x) bform[t] = bform_g[t];
   for (int t = threadIdx.x; t < S * S; t += blockDim.x) bcoef[t] = bcoef_g[t];
   load_tile<T, K>(raw, q, gext, p, i0, j0, N, ne);
+  if constexpr (TOPO) {
+    __syncthreads();
+    constexpr int H = (K - 1) / 2;
+    for (int idx = threadIdx.x; idx < SH::RH * SH::RW; idx += blockDim.x) {
+      const int r = idx / SH::RW, c = idx - r * SH::RW;
+      const int ii = i0 + c - H, jj = j0 + r - H;
+      if (ii >= -H && ii < N + H && jj >= -H && jj < N + H) raw[idx] += sext[((size_t)p * ne + (jj + H)) * ne + (ii + H)];
+    }
+  }
   __syncthreads();
   const int tid = threadIdx.x;
   const int tx = tid % REC_TX, ty = tid / REC_TX;
@@ -399,7 +426,11 @@ __global__ void __launch_bounds__(REC_TX *REC_TY)
           Dp = fma(gp[ii], f[ii], Dp);
           Dm = fma(gp[S + ii], f[ii], Dm);
         }
-        cq[(v * ME * ME + h * ME + g) * NT + tid] = sig[2 * pt] * Ap[h] / Dp - sig[2 * pt + 1] * Am[h] / Dm;
+        T val = sig[2 * pt] * Ap[h] / Dp - sig[2 * pt + 1] * Am[h] / Dm;
+        if constexpr (TOPO) {
+          if (v == 0) val -= scp[((size_t)h * ME + g) * pn + cell];
+        }
+        cq[(v * ME * ME + h * ME + g) * NT + tid] = val;
       }
     }
   }

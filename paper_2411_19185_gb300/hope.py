@@ -236,6 +236,14 @@ class Sphere:
         v = list(buf[:n.value])
         return [v[i:i + 4] for i in range(0, len(v), 4)]
 
+    def vjp_phase_times(self):
+        """Phases (ms) of the last persistent stage VJP of an ensemble, with profiling on:
+        forward ghost, forward reconstruction, flux adjoint, reconstruction adjoint,
+        gather, transposed ghost operator."""
+        t = (ctypes.c_float * 6)()
+        L.check(L.load().hope_vjp_phase_times(self._h, t))
+        return list(t)
+
     def autotune(self, reps=5):
         """Re-time the tile shapes -- of the persistent stage (ensembles) or of the TPP
         reconstruction (one sphere) -- and keep the fastest; returns (per-candidate ms,
@@ -277,6 +285,14 @@ def measure_fma_peak(precision):
     r = ctypes.c_double()
     L.check(L.load().hope_measure_fma_peak(precision, ctypes.byref(r)))
     return r.value
+
+
+def measure_fma_peak_clock(precision, reps=8):
+    """(flops/s, SM MHz during the measured launch, flops per SM per clock cycle)."""
+    r, mhz, fpc = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    L.check(L.load().hope_measure_fma_peak_clock(precision, reps, ctypes.byref(r), ctypes.byref(mhz),
+                                                 ctypes.byref(fpc)))
+    return r.value, mhz.value, fpc.value
 
 
 class _Rollout(torch.autograd.Function):

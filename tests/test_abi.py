@@ -40,6 +40,7 @@ def test_invalid_arguments_rejected_without_device(lib):
     assert lib.hope_init_grid(32, 4, 0, ctypes.byref(p), ctypes.byref(h)) == _lib.HOPE_OK - 1  # even order
     assert lib.hope_init_grid(2, 5, 0, ctypes.byref(p), ctypes.byref(h)) == -1  # N < order
     assert lib.hope_init_grid(32, 5, 7, ctypes.byref(p), ctypes.byref(h)) == -1  # bad scheme
+    assert lib.hope_init_grid(32, 7, _lib.HOPE_WENO1D, ctypes.byref(p), ctypes.byref(h)) == -6  # comparator: order 5
     p.precision = 9
     assert lib.hope_init_grid(32, 5, 0, ctypes.byref(p), ctypes.byref(h)) == -1
     assert not h.value

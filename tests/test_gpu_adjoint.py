@@ -119,6 +119,27 @@ def test_weno_tendency_vjp_matches_central_differences(hp, k, N):
     assert abs(adj - fd) <= 1e-4 * abs(fd), (adj, fd)
 
 
+@pytest.mark.parametrize("k,N", [(3, 10), (5, 11)])
+def test_weno_tendency_vjp_matches_central_differences_on_a_rough_state(hp, k, N):
+    """Where no two smoothness indicators of a cell are close, tau (eq. 3.24) is smooth
+    under the perturbation and central differences bound the WENO adjoint to 1e-6, as for
+    TPP: on a rough state (Rossby-Haurwitz times 1 + 0.3 xi, xi ~ U[-1, 1] per cell) the
+    indicators of a cell differ by O(beta) while a step of h = 1e-6 |q| moves them by
+    O(1e-6 beta), so the difference quotient crosses no kink (on the CPU the same check of
+    the PyTorch reference's autograd gradient against the oracle agrees to 2e-9)."""
+    s = hp.Sphere(N, k, scheme=hp.HOPE_WENO2D)
+    o = O.Oracle(N, 3)
+    q = torch.from_numpy(np.ascontiguousarray(
+        perturb_h(o.rossby_haurwitz(), noise_field((6, N, N), 51), amp=0.3))).cuda()
+    d = torch.from_numpy(fd_direction(q.shape, 52)).cuda() * q.abs().mean(dim=(1, 2, 3), keepdim=True)
+    lam = torch.from_numpy(fd_direction(q.shape, 53)).cuda()
+    h = 1e-6
+    fd = torch.sum(lam * directional(lambda x: s.tendency(x.contiguous()), q, d, h)).item()
+    adj = torch.sum(s.tendency_vjp(q, lam) * d).item()
+    assert abs(adj - fd) <= 1e-6 * abs(fd), (adj, fd)
+    assert s.status() == 0
+
+
 # ------------------------------------------------------------------ autograd reference
 @pytest.mark.parametrize("k,N,scheme", [(3, 8, "tpp"), (5, 10, "tpp"), (3, 8, "weno"), (5, 9, "weno")])
 def test_tendency_vjp_matches_torch_autograd_reference(hp, k, N, scheme):

@@ -32,6 +32,22 @@ def sample_cells(N, n, seed):
     return np.unique(np.concatenate([np.array(fixed), rng.choice(6 * N * N, size=n, replace=False)]))
 
 
+def front_cells(q, n, seed):
+    """Up to n seeded cells on a discontinuity of q[0] (a cell whose value differs from an
+    in-panel neighbour's by more than 1%): where a dam break's tendency is not round-off."""
+    a = q[0]
+    jump = np.zeros(a.shape, bool)
+    dx = np.abs(np.diff(a, axis=2)) > 0.01 * np.abs(a[:, :, 1:])
+    dy = np.abs(np.diff(a, axis=1)) > 0.01 * np.abs(a[:, 1:, :])
+    jump[:, :, 1:] |= dx
+    jump[:, :, :-1] |= dx
+    jump[:, 1:, :] |= dy
+    jump[:, :-1, :] |= dy
+    idx = np.flatnonzero(jump.ravel())
+    rng = np.random.default_rng(seed)
+    return rng.choice(idx, size=min(n, idx.size), replace=False)
+
+
 def rel_l2_cols(got, ref):
     return [float(np.linalg.norm(got[v] - ref[v]) / np.linalg.norm(ref[v])) for v in range(3)]
 
@@ -43,15 +59,18 @@ def rh_noise(o, seed):
 @pytest.mark.parametrize("state", ["dam", "rh_noise"])
 def test_c90_weno9_fp64_tendency_at_sampled_cells(hp, state):
     """Precision form's FP64 side at full size: C90, WENO9 (the benchmark's context and its
-    balanced tile deal), on the 2:1 dam break with Omega = 0 and on the 1%-noise
-    Rossby-Haurwitz state; the full-size device tendency at 235 cells against the oracle's."""
+    balanced tile deal), on the 2:1 dam break with Omega = 0 (cells on its front included:
+    elsewhere the fluid is at rest and the tendency is round-off) and on the 1%-noise
+    Rossby-Haurwitz state; the full-size device tendency at ~300 cells against the oracle's."""
     N, k = 90, 9
     om = 0.0 if state == "dam" else O.OMEGA
     s = hp.Sphere(N, k, hp.HOPE_WENO2D, hp.HOPE_FP64, omega=om, weno_eps=1e-40)
     o = O.Oracle(N, k, scheme=O.WENO, omega=om)
     q = o.dam_break(h_in=10.0, h_out=5.0) if state == "dam" else rh_noise(o, 3)
     d = s.tendency(torch.from_numpy(q).cuda()).cpu().numpy().reshape(3, -1)
-    cells = sample_cells(N, 200, 0)
+    cells = sample_cells(N, 150, 0)
+    if state == "dam":  # the fluid at rest has round-off tendencies: sample the front too
+        cells = np.unique(np.concatenate([cells, front_cells(q, 150, 1)]))
     ref = o.tendency_cells(q, cells)
     err = rel_l2_cols(d[:, cells], ref)
     assert max(err) < 1e-12, err

@@ -296,7 +296,7 @@ def test_recon_tile_shape_leaves_results_bitwise_equal(hp, prec, k, N):
     ref_t = s.tendency(q).clone()
     ref_s = q.clone()
     s.step(ref_s, 600.0, 2)
-    for tx, ty in [(16, 8), (7, 9), (N - 1, 3), (32, 16), (9, 32), (N + 3, 2)]:
+    for tx, ty in [(16, 8), (7, 9), (N - 1, 3), (32, 16), (9, 32), (N + 3, 2), (8, 8), (32, 4)]:
         if tx * ty > 512:
             continue
         s.set_recon_tile(tx, ty)
