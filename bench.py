@@ -71,12 +71,31 @@ def weno_recon_flops_per_launch(N, K):
     return 6 * N * N * per_cell
 
 
+def weno1d_recon_flops_per_launch(N, K):
+    """Algorithmic FLOPs of one dimension-by-dimension WENO-Z reconstruction + sources
+    launch (section 5.5's comparator, FMA = 2, reciprocal = 1): per cell and variable, the
+    indicators and factors of K stencil rows and NPOS row-value columns (L sub-stencils x L
+    eigen-modes of 3 L + 3 flops, tau, f), and K NPOS + n_poc line values (L sub-stencil
+    values and split sums of 2 L + 8 flops each, 7 for the combination); 28 flops of sources
+    per cell point."""
+    L = (K + 1) // 2
+    me, npos, npoc = L, L + 2, 4 * L + L * L
+    ind = L * L * (3 * L + 3) + 2 + 4 * L
+    val = L * (2 * L + 8) + 7
+    per_cell = 3 * ((K + npos) * ind + (K * npos + npoc) * val) + 28 * me * me
+    return 6 * N * N * per_cell
+
+
 def stage_flops(N, K, ghost_nnz, weno=False):
     """Algorithmic FLOPs of one RK stage on one sphere: ghost fill (10 per nonzero of G),
-    reconstruction + sources, LMARS + quadrature at the 12 N^2 me edge points, tendency +
-    stage combination (30 per cell)."""
+    reconstruction + sources (TPP; weno=True: genuine-2D WENO; weno="1d": the
+    dimension-by-dimension comparator), LMARS + quadrature at the 12 N^2 me edge points,
+    tendency + stage combination (30 per cell)."""
     me = (K + 1) // 2
-    rec = weno_recon_flops_per_launch(N, K) if weno else recon_flops_per_launch(N, K)
+    if weno == "1d":
+        rec = weno1d_recon_flops_per_launch(N, K)
+    else:
+        rec = weno_recon_flops_per_launch(N, K) if weno else recon_flops_per_launch(N, K)
     return 10 * ghost_nnz + rec + 12 * N * N * me * LMARS_FLOPS + 6 * N * N * 30
 
 
@@ -107,6 +126,75 @@ def step_roofline(flops_per_stage, state_bytes, g_bytes, stage_s, alu_peak, hbm_
         out[name] = {"bytes_per_stage": b, "bound": "alu" if t_alu >= t_hbm else "hbm",
                      "roofline_ms": 1e3 * max(t_alu, t_hbm), "frac": max(t_alu, t_hbm) / stage_s}
     return out
+
+
+# panel frames (n, e1, e2) of the state layout: panel p maps (X, Y) to (n + X e1 + Y e2)/delta
+PANEL_FRAMES = (((1, 0, 0), (0, 1, 0), (0, 0, 1)), ((0, 1, 0), (-1, 0, 0), (0, 0, 1)),
+                ((-1, 0, 0), (0, -1, 0), (0, 0, 1)), ((0, -1, 0), (1, 0, 0), (0, 0, 1)),
+                ((0, 0, 1), (0, 1, 0), (-1, 0, 0)), ((0, 0, -1), (0, 1, 0), (1, 0, 0)))
+
+
+def cell_geometry(N):
+    """Cell-centre longitude and latitude, and the cell average of the unit-sphere sqrtG
+    (eq. 2.8 over r^2, 6-point Gauss rule per direction), each of shape (6, N, N)."""
+    dx = np.pi / (2 * N)
+    c = -np.pi / 4 + (np.arange(N) + 0.5) * dx
+    X, Y = np.meshgrid(np.tan(c), np.tan(c), indexing="xy")  # [j][i]
+    d = np.sqrt(1 + X * X + Y * Y)
+    lon, lat = np.empty((6, N, N)), np.empty((6, N, N))
+    for p, (n, e1, e2) in enumerate(PANEL_FRAMES):
+        P = [(n[a] + X * e1[a] + Y * e2[a]) / d for a in range(3)]
+        lon[p], lat[p] = np.arctan2(P[1], P[0]), np.arcsin(np.clip(P[2], -1, 1))
+    g, w = np.polynomial.legendre.leggauss(6)
+    xs = c[:, None] + 0.5 * dx * g[None, :]  # [cell][node]
+    T = np.tan(xs)
+    sq = (1 + T[None, :, None, :] ** 2) * (1 + T[:, None, :, None] ** 2)  # [j][i][gy][gx]
+    sq = sq / (1 + T[None, :, None, :] ** 2 + T[:, None, :, None] ** 2) ** 1.5
+    sg = np.einsum("jiyx,y,x->ji", sq, w / 2, w / 2)
+    return lon, lat, np.broadcast_to(sg, (6, N, N)).copy()
+
+
+def front_anisotropy(h, lon, lat, lon0, lat0, dcell, jump, dmax):
+    """Azimuthal spread of a field about a centre (section 5.5's isotropy comparison):
+    cells are binned by great-circle distance d (bins of half a cell up to dmax), the
+    azimuthal mean profile hbar(d) is interpolated linearly between bin centres, and
+      spread     = RMS over cells of (h - hbar(d)) / jump,
+      axis_diag  = RMS over bins of the difference between the mean residuals h - hbar(d) of
+                   the grid-axis sectors (azimuth within 10 degrees of 0, 90, 180, 270) and of
+                   the diagonal sectors (45, 135, 225, 315), over jump.
+    An isotropic field gives ~0 for both; a grid imprint shows in axis_diag."""
+    h, lon, lat = (np.ravel(a) for a in (h, lon, lat))
+    cd = np.sin(lat0) * np.sin(lat) + np.cos(lat0) * np.cos(lat) * np.cos(lon - lon0)
+    dist = np.arccos(np.clip(cd, -1.0, 1.0))
+    az = np.arctan2(np.sin(lon - lon0) * np.cos(lat),
+                    np.cos(lat0) * np.sin(lat) - np.sin(lat0) * np.cos(lat) * np.cos(lon - lon0))
+    sel = dist < dmax
+    h, dist, az = h[sel], dist[sel], az[sel]
+    bw = 0.5 * dcell
+    nb = int(np.ceil(dmax / bw))
+    b = np.minimum((dist / bw).astype(int), nb - 1)
+    cnt = np.bincount(b, minlength=nb)
+    ok = cnt >= 8
+    mean = np.bincount(b, weights=h, minlength=nb)[ok] / cnt[ok]
+    centre = np.bincount(b, weights=dist, minlength=nb)[ok] / cnt[ok]
+    hbar = np.interp(dist, centre, mean)
+    spread = float(np.sqrt(np.mean((h - hbar) ** 2)) / jump)
+    sector = np.mod(np.degrees(az), 90.0)
+    axis = (sector < 10.0) | (sector > 80.0)
+    diag = np.abs(sector - 45.0) < 10.0
+
+    r = h - hbar  # residual about the interpolated mean profile (removes each bin's own slope)
+
+    def prof(m):
+        c = np.bincount(b[m], minlength=nb)
+        s = np.bincount(b[m], weights=r[m], minlength=nb)
+        return c, s
+    ca, sa = prof(axis)
+    cg, sg = prof(diag)
+    both = (ca >= 4) & (cg >= 4)
+    diff = sa[both] / ca[both] - sg[both] / cg[both]
+    axis_diag = float(np.sqrt(np.mean(diff ** 2)) / jump) if both.any() else float("nan")
+    return {"spread": spread, "axis_diag": axis_diag, "bins": int(ok.sum())}
 
 
 def cpu_model():
@@ -275,13 +363,17 @@ def measure_forms(hp, stream, fp64_peak):
     with torch.cuda.stream(stream):
         s.step(q, DT)
         rec = []
+        ksum = np.zeros(4)
         for _ in range(20):
             s.step(q, DT)
-            rec.extend(st[1] for st in s.kernel_times())
+            kt = s.kernel_times()
+            rec.extend(st[1] for st in kt)
+            ksum += np.sum(np.array(kt), axis=0)
     s.set_profiling(False)
     fl = recon_flops_per_launch(N_CELLS, ORDER)
     out["tpp11_c90_fp32"] = {"value": cells * 3 / (ms * 1e-3), "ms_per_step": ms,
                              "recon_ms": float(np.mean(rec)),
+                             "stage_kernel_ms": dict(zip(("ghost", "recon", "flux", "update"), (ksum / 60).tolist())),
                              "recon_frac_of_fp32_peak": fl / (np.mean(rec) * 1e-3) / fp32_peak,
                              "days": day * DT / 86400.0,
                              "rel_l2_h_vs_fp64": _rel(q32[0], q64[0]),
@@ -305,12 +397,15 @@ def measure_forms(hp, stream, fp64_peak):
         warm = qw.clone()
         with torch.cuda.stream(stream):
             sw.step(warm, 300.0, 1)
-        ms_run = _run(sw, qw, 300.0, nd, stream)
-        runs[name] = (qw, ms_run / nd, (sw.mass(qw) - m0) / m0, sw.status())
+        ms_run = _run(sw, qw, 300.0, day, stream)
+        h_day1 = qw[0].double().clone()
+        ms_run += _run(sw, qw, 300.0, nd - day, stream)
+        runs[name] = (qw, ms_run / nd, (sw.mass(qw) - m0) / m0, sw.status(), h_day1)
         del sw
+    d1 = {name: runs[name][4] for name in runs}
     h64, h64b, h32 = runs["fp64"][0][0], runs["fp64_eps12"][0][0], runs["fp32"][0][0]
     for name in ("fp64", "fp32"):
-        qw, msr, drift, st = runs[name]
+        qw, msr, drift, st, _ = runs[name]
         out["weno9_c90_dam_" + name] = {"value": cells * 3 / (msr * 1e-3), "ms_per_step": msr,
                                         "days": nd * 300.0 / 86400.0, "mass_drift": drift, "status": st,
                                         "roofline": roofline(stage_flops(N_CELLS, 9, nnz[name], weno=True),
@@ -318,7 +413,12 @@ def measure_forms(hp, stream, fp64_peak):
                                                              fp64_peak if name == "fp64" else fp32_peak)}
     out["weno9_c90_dam_fp32"].update({"rel_l2_h_vs_fp64": _rel(h32, h64),
                                       "rel_l2_h_vs_fp64_same_eps": _rel(h32, h64b),
-                                      "rel_l2_h_fp64_eps_1e-12_vs_1e-40": _rel(h64b, h64)})
+                                      "rel_l2_h_fp64_eps_1e-12_vs_1e-40": _rel(h64b, h64),
+                                      # day 1: the configured epsilon pair (1e-12 in FP32, 1e-40 in
+                                      # FP64) and the same-epsilon (arithmetic only) figure
+                                      "day1_rel_l2_h_vs_fp64_eps_1e-12_vs_1e-40": _rel(d1["fp32"], d1["fp64"]),
+                                      "day1_rel_l2_h_vs_fp64_same_eps": _rel(d1["fp32"], d1["fp64_eps12"]),
+                                      "day1_bound": 1e-5})
     del runs, h64, h64b, h32
     # differentiation form: C180 WENO5, geostrophic + 16 bumps of 50 m, 50 steps of 150 s
     # with recompute from checkpoints every 10 steps; loss 0.5 |h_T - h_target|^2
@@ -347,11 +447,20 @@ def measure_forms(hp, stream, fp64_peak):
         grads[name] = x.grad.double()
         c180 = 6 * 180 * 180 * 3 * nsteps
         fl = stage_flops(180, 5, s.ghost_nnz()[0], weno=True)
+        pk = fp64_peak if P == hp.HOPE_FP64 else fp32_peak
+        # forward + adjoint: the forward run, the backward's recompute of every step from
+        # its checkpoint, and the reverse stages, an adjoint stage counted as twice the
+        # forward stage's algorithmic FLOPs (the transposed linear maps cost the forward's
+        # multiply-adds, the nonlinear weights' derivatives one more pass of that size)
+        fa_flops = fl * 3 * nsteps * (1 + 1 + 2)
         out[name] = {"forward": c180 / (fwd * 1e-3), "forward_plus_adjoint": c180 / ((fwd + bwd) * 1e-3),
                      "steps": nsteps, "checkpoint_every": every, "fwd_ms": fwd, "adjoint_ms": bwd,
                      "adjoint_over_forward": bwd / fwd, "status": s.status(),
-                     "roofline_forward": roofline(fl, 3 * nsteps / (fwd * 1e-3),
-                                                  fp64_peak if P == hp.HOPE_FP64 else fp32_peak)}
+                     "roofline_forward": roofline(fl, 3 * nsteps / (fwd * 1e-3), pk),
+                     "roofline_forward_plus_adjoint": {
+                         "bound": "alu", "flops": fa_flops, "achieved_tflops": fa_flops / ((fwd + bwd) * 1e-3) / 1e12,
+                         "peak_tflops": pk / 1e12, "frac": fa_flops / ((fwd + bwd) * 1e-3) / pk,
+                         "convention": "forward run + recompute + reverse stages at 2x the forward stage FLOPs"}}
         del s
     out["adjoint_c180_weno5_fp32"]["rel_l2_grad_vs_fp64"] = _rel(grads["adjoint_c180_weno5_fp32"],
                                                                  grads["adjoint_c180_weno5_fp64"])
@@ -390,6 +499,17 @@ def measure_forms(hp, stream, fp64_peak):
                                    "roofline": roofline(sum(stage_flops(n, 7, 0) for n in members) +
                                                         10 * ens.ghost_nnz()[0], 3e3 / ms, fp32_peak)}
     del ens, q, qT, x, warm, target
+    # section 5.5: genuine-2D WENO-Z against the dimension-by-dimension comparator on the
+    # C90 dam break (isotropy of the front), each with its throughput and roofline fraction
+    try:
+        out["dam_anisotropy_c90_weno5"] = anisotropy_form(hp, stream, fp64_peak)
+    except Exception as exc:  # noqa: BLE001
+        out["dam_anisotropy_c90_weno5"] = {"error": repr(exc)}
+    # section 5.4: the perturbed jet as a second workload
+    try:
+        out["jet_c90_fp64"] = jet_form(hp, stream, fp64_peak)
+    except Exception as exc:  # noqa: BLE001
+        out["jet_c90_fp64"] = {"error": repr(exc)}
     # bottom topography: section 5.2's mountain flow against the flat step (the form is
     # reported, not the headline; a failure here is recorded instead of ending the run)
     try:
@@ -440,15 +560,16 @@ def run_reference(args, world, rank):
     print(json.dumps(line))
 
 
-def ensemble_members(hp, precision):
-    """The batching-form ensemble: 32 x C48, 24 x C96, 8 x C192, TPP7, Rossby-Haurwitz
-    wave 4 with seeded 1 % h noise per member."""
+def ensemble_members(hp, precision, members=None):
+    """The batching-form ensemble: 32 x C48, 24 x C96, 8 x C192 (or `members`), TPP7,
+    Rossby-Haurwitz wave 4 with seeded 1 % h noise per member."""
     import torch
     from synth import noise_field
-    members = [48] * 32 + [96] * 24 + [192] * 8
+    if members is None:
+        members = [48] * 32 + [96] * 24 + [192] * 8
     ens = hp.Sphere(members, 7, hp.HOPE_TPP, precision)
     q = ens.empty()
-    for N in (48, 96, 192):
+    for N in sorted(set(members)):
         base = hp.Sphere(N, 7, hp.HOPE_TPP, precision).rossby_haurwitz()
         for m, Nm in enumerate(members):
             if Nm == N:
@@ -489,6 +610,74 @@ def mountain_form(hp, steps):
     return out
 
 
+def anisotropy_form(hp, stream, fp64_peak, days=2.0, N=90):
+    """Section 5.5's comparison: the cylinder dam break (10 m inside a 20-degree cap at
+    (0, 0), 5 m outside, at rest, Omega = 0; the 2:1 ratio of eq. 5.19) at C90, fifth order,
+    FP64, SSP-RK3 dt = 300 s, with the genuine-2D WENO-Z, the dimension-by-dimension
+    comparator and the unlimited TPP5 as a linear reference.  After each simulated day the
+    azimuthal spread of h about the dam centre and the grid-axis / diagonal difference of
+    its residual profile (front_anisotropy) are recorded, with each run's throughput and
+    roofline fraction."""
+    import torch
+    dt = 300.0
+    nday = int(round(86400.0 / dt))
+    lon, lat, sg = cell_geometry(N)
+    dcell = np.pi / (2 * N)
+    out = {"N": N, "order": 5, "dt_s": dt, "days": days, "h_in_m": 10.0, "h_out_m": 5.0,
+           "cap_deg": 20.0, "fp64_peak_tflops": fp64_peak / 1e12}
+    for name, scheme, wflag in (("weno2d", hp.HOPE_WENO2D, True), ("weno1d", hp.HOPE_WENO1D, "1d"),
+                                ("tpp5", hp.HOPE_TPP, False)):
+        s = hp.Sphere(N, 5, scheme, hp.HOPE_FP64, omega=0.0)
+        q0 = s.dam_break(h_in=10.0, h_out=5.0)
+        q = q0.clone()
+        m0 = s.mass(q)
+        with torch.cuda.stream(stream):
+            s.step(q, dt, 2)  # captures this buffer's step graph (FP64: no low word to reset)
+        torch.cuda.synchronize()
+        q.copy_(q0)
+        res, ms_tot = {}, 0.0
+        for d in range(int(round(days))):
+            ms_tot += _run(s, q, dt, nday, stream)
+            h = (q[0].double().cpu().numpy() / sg) / s.gravity
+            res["day%d" % (d + 1)] = front_anisotropy(h, lon, lat, 0.0, 0.0, dcell, 5.0, np.radians(60.0))
+        msr = ms_tot / (nday * int(round(days)))
+        fl = stage_flops(N, 5, s.ghost_nnz()[0], weno=wflag)
+        res.update({"value": 6 * N * N * 3 / (msr * 1e-3), "ms_per_step": msr,
+                    "mass_drift": (s.mass(q) - m0) / m0, "status": s.status(),
+                    "roofline": roofline(fl, 3e3 / msr, fp64_peak)})
+        out[name] = res
+        del s, q, q0
+    return out
+
+
+def jet_form(hp, stream, fp64_peak, hours=24.0, N=90):
+    """Section 5.4's perturbed jet (eqs. 5.16-5.18) as a second workload at C90, FP64, with
+    the headline's TPP11 and with WENO5, SSP-RK3 dt = 150 s (the jet's 80 m/s plus the
+    gravity-wave speed put 300 s near the stability limit at this resolution); throughput,
+    roofline fraction and mass drift over `hours` simulated hours."""
+    import torch
+    dt = 150.0
+    n = int(round(hours * 3600.0 / dt))
+    out = {"N": N, "dt_s": dt, "hours": hours, "steps": n}
+    for name, scheme, k, wflag in (("tpp11", hp.HOPE_TPP, 11, False), ("weno5", hp.HOPE_WENO2D, 5, True)):
+        s = hp.Sphere(N, k, scheme, hp.HOPE_FP64)
+        q0 = s.galewsky()
+        q = q0.clone()
+        m0 = s.mass(q)
+        with torch.cuda.stream(stream):
+            s.step(q, dt, 2)
+        torch.cuda.synchronize()
+        q.copy_(q0)
+        ms = _run(s, q, dt, n, stream) / n
+        fl = stage_flops(N, k, s.ghost_nnz()[0], weno=wflag)
+        out[name] = {"value": 6 * N * N * 3 / (ms * 1e-3), "ms_per_step": ms,
+                     "mass_drift": (s.mass(q) - m0) / m0, "status": s.status(),
+                     "finite": bool(torch.isfinite(q).all().item()),
+                     "roofline": roofline(fl, 3e3 / ms, fp64_peak)}
+        del s, q, q0
+    return out
+
+
 def run_case(args):
     """Short single-form runs for profiling (`--case`): not the benchmark line."""
     import torch
@@ -510,6 +699,45 @@ def run_case(args):
         return
     if args.case == "mountain_c90_tpp11_fp64":
         print(json.dumps({"case": args.case, **mountain_form(hp, args.steps)}))
+        return
+    if args.case == "weno1d_c90":
+        # the comparator's stage at C90 (dam break, FP64), a few graph-replayed steps
+        s = hp.Sphere(90, 5, hp.HOPE_WENO1D, hp.HOPE_FP64, omega=0.0)
+        q = s.dam_break(h_in=10.0, h_out=5.0)
+        s.step(q, 300.0, args.steps)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.case, "steps": args.steps, "status": s.status()}))
+        return
+    if args.case in ("ensemble64_adjoint", "ensemble16_adjoint"):
+        # the batching form's reverse sweep: a taped rollout of args.steps steps and its
+        # backward (persistent forward and VJP launches); ensemble16: 8 x C96 + 8 x C48, a
+        # case small enough for a full profiler capture
+        small = [96] * 8 + [48] * 8 if args.case == "ensemble16_adjoint" else None
+        members, ens, q = ensemble_members(hp, hp.HOPE_FP32, small)
+        x = q.clone().requires_grad_(True)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        qT = ens.rollout(x, 45.0, args.steps, checkpoint_every=args.steps)
+        e[1].record()
+        (qT * qT).sum().backward()
+        e[2].record()
+        torch.cuda.synchronize()
+        # phases of one taped reverse stage (profiling stamps at the VJP launch's barriers)
+        tape = torch.empty(ens.tape_bytes(), dtype=torch.uint8, device="cuda")
+        qr = q.clone()
+        ens.step_record(qr, 45.0, tape)
+        ens.set_profiling(True)
+        ens.step_vjp_tape(q, tape, qr, 45.0)
+        ph = ens.vjp_phase_times()
+        ens.set_profiling(False)
+        print(json.dumps({"case": args.case, "steps": args.steps, "fwd_ms": e[0].elapsed_time(e[1]),
+                          "adjoint_ms": e[1].elapsed_time(e[2]), "status": ens.status(),
+                          "last_reverse_stage_phase_ms": dict(zip(("fwd_ghost", "fwd_recon", "flux_adj",
+                                                                   "recon_adj", "gather", "ghost_adj"), ph))}))
+        return
+    if args.case == "dam_anisotropy_c90":
+        peak = hp.measure_fma_peak(hp.HOPE_FP64)
+        print(json.dumps({"case": args.case, **anisotropy_form(hp, torch.cuda.current_stream(), peak)}))
         return
     from synth import bump_centres
     P = hp.HOPE_FP32 if args.case.endswith("fp32") else hp.HOPE_FP64
@@ -542,7 +770,8 @@ def main():
     ap.add_argument("--cpu-stages", type=int, default=150)
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--case", choices=["ensemble64", "adjoint_c180_fp64", "adjoint_c180_fp32",
-                                       "mountain_c90_tpp11_fp64"],
+                                       "mountain_c90_tpp11_fp64", "dam_anisotropy_c90", "weno1d_c90",
+                                       "ensemble64_adjoint", "ensemble16_adjoint"],
                     help="run one form briefly for profiling instead of the benchmark")
     args = ap.parse_args()
     if args.case:
@@ -560,7 +789,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_2411_19185_gb300 as hp
 
-    fp64_peak = hp.measure_fma_peak(hp.HOPE_FP64)
+    fp64_peak, peak_mhz, peak_fpc = hp.measure_fma_peak_clock(hp.HOPE_FP64, 8)
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
     s = hp.Sphere(N_CELLS, ORDER, hp.HOPE_TPP, hp.HOPE_FP64, coriolis_tilt=ALPHA)
     q = s.geostrophic(ALPHA)
     q_analytic = q.clone()
@@ -587,8 +817,8 @@ def main():
             flush.zero_()
             ev0[k].record(stream)
             s.step(q, DT)
-            s.mass(q)  # FP64 mass diagnostic, read back to the host
             ev1[k].record(stream)
+            s.mass(q)  # FP64 mass diagnostic, read back to the host (outside the timed events)
             kt = s.kernel_times()
             recon_ms.extend(st[1] for st in kt)
             kernel_sum += np.sum(np.array(kt), axis=0)
@@ -639,7 +869,8 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"kernel": "k_recon_tpp<double,11>", "bound": "alu", "achieved": achieved / 1e12,
                      "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                     "peak_source": "FP64 FMA microbenchmark measured in this run (hope_measure_fma_peak)",
+                     "peak_source": "FP64 FMA microbenchmark measured in this run (hope_measure_fma_peak_clock)",
+                     "peak_sm_mhz": peak_mhz, "peak_flops_per_sm_clock": peak_fpc,
                      "flops_per_launch": flops, "avg_launch_ms": recon_avg_ms,
                      "traffic": RECON_TRAFFIC_BYTES},
         "stage_kernel_ms": {"ghost": kernel_sum[0] / (3 * args.steps), "recon": kernel_sum[1] / (3 * args.steps),
@@ -654,6 +885,12 @@ def main():
         "device_status": status,
         "forms": forms,
     }
+    # the same fraction with the peak taken at the clock sampled during the timed region:
+    # the microbenchmark's flops per SM per cycle x SMs x median SM MHz of the run
+    if clocks and clocks.get("sm_mhz"):
+        peak_run = peak_fpc * nsm * clocks["sm_mhz"] * 1e6
+        line["roofline"]["peak_at_run_clock"] = peak_run / 1e12
+        line["roofline"]["frac_at_run_clock"] = achieved / peak_run
     g_nnz = s.ghost_nnz()[0]
     hbm_bps, hbm_src = measured_hbm_bps()
     line["step_roofline"] = step_roofline(stage_flops(N_CELLS, ORDER, g_nnz), 72 * cells, 12 * g_nnz,
