@@ -92,11 +92,30 @@ def test_batching_form_full_size_sample(hp):
     assert ens.status() == 0
 
 
-def test_autotune_reports_shapes(hp):
-    ens = hp.Sphere([16, 24], 7, precision=hp.HOPE_FP32)
+CANDIDATES = [(16, 8), (8, 16), (32, 4), (16, 4), (12, 10), (24, 5), (8, 8), (16, 16), (32, 8), (16, 12),
+              (24, 10), (12, 20)]
+
+
+def test_autotune_reports_shapes_and_keeps_the_results(hp):
+    """The persistent stage's autotuner times every candidate (tile shape x block size) and
+    keeps the fastest; a tile shape only regroups cells, so the steps after tuning equal a
+    fresh context's (default shape) bitwise, and step graphs captured before the retune are
+    dropped rather than replayed with the old shape."""
+    members = [16, 24, 13]
+    ens = hp.Sphere(members, 7, precision=hp.HOPE_FP32)
+    ref = hp.Sphere(members, 7, precision=hp.HOPE_FP32)
+    q0 = torch.cat([torch.from_numpy(s).reshape(-1) for s in member_states(members, 2, 7)]).to("cuda", torch.float32)
+    qa = q0.clone()
+    ens.step(qa, 450.0, 1)  # captures a graph with the initial shape
     ms, shape, grid = ens.autotune(reps=3)
-    assert len(ms) == 3 and all(t > 0 for t in ms)
-    assert shape in [(16, 8), (16, 4), (32, 4)] and grid >= 152
+    assert len(ms) >= 8 and all(t > 0 for t in ms), ms
+    assert shape in CANDIDATES and grid >= 152
+    qc = q0.clone()  # a new buffer: the FP32 low word of qa's earlier step does not carry over
+    qb = q0.clone()
+    ens.step(qc, 450.0, 2)
+    ref.step(qb, 450.0, 2)
+    assert torch.equal(qc, qb)
+    assert ens.status() == 0
 
 
 def test_grid_barrier_timeout_is_reported_and_recoverable(hp):
