@@ -296,16 +296,23 @@ int hope_status(hope_t ctx, unsigned *device_status);
 
 /*
  * Ensembles (hope_init_ensemble, TPP): each stage is one persistent cooperative launch over
- * all members' work lists.  hope_autotune times the compiled tile shapes (TX x TY cells per
- * work item: 16x8, 16x4, 32x4) for reps stages on the context's scratch buffers and keeps
- * the fastest; it runs once at hope_init_ensemble.  ms_out (3 floats, may be NULL) gets the
- * per-shape stage times, tx/ty/grid the chosen shape and resident grid size.  For a single
- * TPP sphere it times the reconstruction tile candidates 16 x 8, the model's shape and
- * 12 x 12 (-1 for a repeated candidate), keeps the fastest (as hope_set_recon_tile) and
- * returns the tile count in grid; it runs at hope_init_grid for FP32.  Returns
- * HOPE_EUNSUPPORTED for WENO2D contexts.
+ * all members' work lists.  hope_autotune times the candidate shapes of that launch -- a
+ * tile of TX x TY cells per reconstruction work item (a run-time argument) on blocks of 128
+ * or 256 threads: 16x8, 8x16, 32x4, 16x4, 12x10, 24x5, 8x8 on 128 threads, 16x16, 32x8,
+ * 16x12, 24x10, 12x20 on 256, less those whose tile does not fit the shared memory -- for
+ * reps stages on the context's scratch buffers and keeps the fastest; it runs once at
+ * hope_init_ensemble and drops captured step graphs when called again.  ms_out (may be
+ * NULL; HOPE_AUTOTUNE_MAX floats) gets one stage time per candidate, -1 after the last
+ * (hope_autotune_candidates gives their number); tx/ty/grid the chosen shape and resident
+ * grid size.  For a single TPP sphere it times the reconstruction tile candidates 16 x 8, the
+ * model's shape and 12 x 12 (3 entries, -1 for a repeated candidate), keeps the fastest (as
+ * hope_set_recon_tile) and returns the tile count in grid; it runs at hope_init_grid for
+ * FP32.  Returns HOPE_EUNSUPPORTED for WENO2D contexts.
  */
+#define HOPE_AUTOTUNE_MAX 16
 int hope_autotune(hope_t ctx, int reps, float *ms_out, int *tx, int *ty, int *grid);
+/* Number of autotuner candidates of the context (0 for contexts without a tuner). */
+int hope_autotune_candidates(hope_t ctx);
 
 /*
  * Tile shape of the per-kernel TPP reconstruction (single spheres; Section 4 describes the

@@ -14,6 +14,7 @@ HOPE_TPP, HOPE_WENO2D, HOPE_WENO1D = 0, 1, 2
 HOPE_FP64, HOPE_FP32 = 0, 1
 HOPE_SSPRK3, HOPE_WSRK3 = 0, 1
 HOPE_STATUS_NONPHYS_PHI, HOPE_STATUS_NAN, HOPE_STATUS_TIMEOUT = 1, 2, 4
+HOPE_AUTOTUNE_MAX = 16
 
 EXPORTED = [
     "hope_default_params", "hope_init_grid", "hope_init_ensemble", "hope_destroy", "hope_state_elems",
@@ -24,7 +25,7 @@ EXPORTED = [
     "hope_total_mass_noalloc", "hope_autotune", "hope_inject_fault", "hope_set_recon_tile", "hope_recon_tile",
     "hope_tape_bytes", "hope_step_record", "hope_step_vjp_tape", "hope_step_ssprk3_vjp",
     "hope_ghost_selfcheck", "hope_set_topography", "hope_topography_tables", "hope_measure_fma_peak_clock",
-    "hope_vjp_phase_times",
+    "hope_vjp_phase_times", "hope_autotune_candidates",
 ]
 
 
@@ -80,6 +81,7 @@ def load():
         "hope_measure_fma_peak": (i, [i, P(d)]),
         "hope_measure_fma_peak_clock": (i, [i, i, P(d), P(d), P(d)]),
         "hope_vjp_phase_times": (i, [vp, P(ctypes.c_float)]),
+        "hope_autotune_candidates": (i, [vp]),
         "hope_set_profiling": (i, [vp, i]),
         "hope_total_mass_noalloc": (i, [vp, i, i, P(d), vp]),
         "hope_autotune": (i, [vp, i, P(ctypes.c_float), P(i), P(i), P(i)]),

@@ -7,9 +7,12 @@
 //                  edge point of every cell (each point has exactly one writer)
 //   k_recon_*_adj  per cell: adjoint of the cell-point sources (eqs. 2.2, 2.3, 3.6),
 //                  then of the reconstruction (TPP: transposed sum factorisation), giving
-//                  the gradient with respect to the k x k stencil values
-//   k_gather_adj   per extended cell: sum of the stencil gradients of every cell whose
-//                  stencil covers it (deterministic, no atomics)
+//                  the gradient with respect to the k x k stencil values; TPP tiles add
+//                  them up on the tile's extended region in shared memory (fixed order)
+//                  and write that region per tile
+//   k_gather_*     per extended cell: sum of the contributions of every cell (WENO: the
+//                  per-cell stencil gradients) or tile (TPP: the tiles' extended regions)
+//                  whose stencils cover it (deterministic, no atomics)
 //   k_ghost_adj    interior cells += G^T lam_ring (transposed ghost operator, eq. 7.12),
 //                  fused with the Runge-Kutta combination of adjoint states
 #pragma once
@@ -252,20 +255,23 @@ __device__ __forceinline__ void source_vjp(const T q[3], T X, T Y, T os, T tw, T
 
 // ---------------------------------------------------------------------------------
 // TPP reconstruction + sources adjoint: per cell, the gradient with respect to its
-// K x K stencil, grad[v][b*K + a][cell] (a: x offset + H, b: y offset + H).
+// K x K stencil, summed over the tile's cells onto the tile's extended region
+// ((TY + K - 1) x (TX + K - 1) cells, the region its stencils cover), which is written to
+// slot tile_id of the tile buffer tbuf ([tile][3][TY+K-1][TX+K-1], valid part only).
 // One tile of at most TX x TY cells of panel p with its first cell at (i0, j0), called by
 // all threads of a block of at least TX*TY threads (the valid cells of a tile cut by the
 // panel's edge are packed onto the first threads); ends with a barrier so the shared
 // memory can be reused.  Shared memory: the forward tile's (raw tile, x-pass, weights)
-// plus the adjoint at the cell points, [3][me^2][blockDim.x].
+// plus the adjoint at the cell points [3][me^2][NT], one stencil row's gradient per cell
+// [3][K][NT] and the extended region [3][TY+K-1][TX+K-1] (NT = blockDim.x).
 // ---------------------------------------------------------------------------------
 template <typename T, int K>
 __device__ __forceinline__ void recon_tpp_adj_tile(unsigned char *smem_raw, int p, int i0, int j0, const int TX,
-                                                   const int TY, const T *__restrict__ q, const T *__restrict__ gext,
+                                                   const int TY, const long long tile_id, const T *__restrict__ q, const T *__restrict__ gext,
                                                    const T *__restrict__ w1g, const T *__restrict__ Xg,
                                                    const T *__restrict__ t1w, const T *__restrict__ lep,
-                                                   const T *__restrict__ lamL, T *__restrict__ grad, int N, int ne,
-                                                   T omega, const FCoef<T> &fc) {
+                                                   const T *__restrict__ lamL, T *__restrict__ tbuf, int N, int ne,
+                                                   T omega, const FCoef<T> &fc, const T *__restrict__ ttw = nullptr) {
   constexpr int H = (K - 1) / 2, ME = (K + 1) / 2, NPOS = ME + 2;
   const int RW = TX + 2 * H, RH = TY + 2 * H, NT = blockDim.x;
   const int vx = min(TX, N - i0), vy = min(TY, N - j0);
@@ -274,6 +280,14 @@ __device__ __forceinline__ void recon_tpp_adj_tile(unsigned char *smem_raw, int 
   T *xs = raw + 3 * RH * RW;                  // [3][NPOS][RH][TX]
   T *w1 = xs + 3 * NPOS * RH * TX;            // [NPOS][K]
   T *lcq = w1 + NPOS * K;                     // [3][ME*ME][NT] adjoint at cell points
+  // phase 2's scratch: one stencil row's gradient per cell [3][K][TX*TY] and the tile's
+  // gradient on its extended region [3][RH][RW]; it reuses the tile and x-pass region, which
+  // nothing reads after phase 1, when that is large enough (every shape the library uses),
+  // else it follows lcq
+  const int ncap = TX * TY;
+  const bool alias = 3 * K * ncap + 3 * RH * RW <= 3 * RH * RW + 3 * NPOS * RH * TX;
+  T *gs = alias ? raw : lcq + 3 * ME * ME * NT;
+  T *acc = gs + 3 * K * ncap;
   for (int t = threadIdx.x; t < NPOS * K; t += blockDim.x) w1[t] = w1g[t];
   {
     const size_t pn = (size_t)6 * N * N, pe = (size_t)6 * ne * ne;
@@ -306,11 +320,13 @@ __device__ __forceinline__ void recon_tpp_adj_tile(unsigned char *smem_raw, int 
   }
   __syncthreads();
   const int tid = threadIdx.x;
-  if (tid < vx * vy) {
-    const int ty = tid / vx, tx = tid - ty * vx;
-    const int i = i0 + tx, j = j0 + ty;
-    const size_t pn = (size_t)6 * N * N;
-    const size_t cell = ((size_t)p * N + j) * N + i;
+  const int nc = vx * vy;
+  const size_t pn = (size_t)6 * N * N;
+  const bool own = tid < nc;
+  const int ty = own ? tid / vx : 0, tx = own ? tid - ty * vx : 0;
+  const int i = i0 + tx, j = j0 + ty;
+  const size_t cell = ((size_t)p * N + j) * N + i;
+  if (own) {
     const T fc0 = fc.c[3 * p], fc1 = fc.c[3 * p + 1], fc2 = fc.c[3 * p + 2];
     const T lS1 = lamL[pn + cell], lS2 = lamL[2 * pn + cell];
     // phase 1: adjoint at the cell points (recomputed values, source VJP)
@@ -341,10 +357,17 @@ __device__ __forceinline__ void recon_tpp_adj_tile(unsigned char *smem_raw, int 
         for (int v = 0; v < 3; ++v) lcq[(v * ME * ME + h * ME + g) * NT + tid] = lq[v];
       }
     }
-    // phase 2: per stencil row b, gt[v][t] = sum over points at x-position t of
-    // w1[ty(pt)][b] lam(pt), then grad[v][b][a] = sum_t w1[t][a] gt[v][t]
+  }
+  __syncthreads();  // the tile and x-pass are dead from here on (phase 2's scratch may alias them)
+  for (int t = threadIdx.x; t < 3 * RH * RW; t += blockDim.x) acc[t] = T(0);
+  // phase 2: per stencil row b, gt[v][t] = sum over points at x-position t of
+  // w1[ty(pt)][b] lam(pt), then the row's gradient g[v][a] = sum_t w1[t][a] gt[v][t]
+  // (plus psi_B's transposed stencil map for the mass variable over a surface); the rows
+  // are added onto the tile's extended region: location (ty + b, tx + a) gains the
+  // gradient of cell (tx, ty), summed over a in order, then over b in order
 #pragma unroll 1
-    for (int b = 0; b < K; ++b) {
+  for (int b = 0; b < K; ++b) {
+    if (own) {
       T gacc[3][K];
 #pragma unroll
       for (int v = 0; v < 3; ++v)
@@ -383,34 +406,77 @@ __device__ __forceinline__ void recon_tpp_adj_tile(unsigned char *smem_raw, int 
           for (int v = 0; v < 3; ++v) gacc[v][a] = fma(w, gt[v], gacc[v][a]);
         }
       }
+      if (ttw) {  // psi_B (eq. 2.14): its weights on the mass variable's stencil, transposed
+        const T l1 = lamL[pn + cell], l2 = lamL[2 * pn + cell];
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+          const size_t c = (size_t)b * K + a;
+          gacc[0][a] += ttw[c * pn + cell] * l1 + ttw[((size_t)K * K + c) * pn + cell] * l2;
+        }
+      }
 #pragma unroll
       for (int v = 0; v < 3; ++v)
 #pragma unroll
-        for (int a = 0; a < K; ++a) grad[((size_t)v * K * K + b * K + a) * pn + cell] = gacc[v][a];
+        for (int a = 0; a < K; ++a) gs[(v * K + a) * ncap + tid] = gacc[v][a];
     }
+    __syncthreads();
+    // extended rows b .. b + vy - 1: each location sums its K cells of this row
+    for (int idx = threadIdx.x; idx < 3 * vy * vw; idx += blockDim.x) {
+      const int v = idx / (vy * vw);
+      const int rem = idx - v * vy * vw;
+      const int rr = rem / vw, c = rem - rr * vw;
+      T s = T(0);
+#pragma unroll
+      for (int a = 0; a < K; ++a) {
+        const int cx = c - a;
+        if (cx >= 0 && cx < vx) s += gs[(v * K + a) * ncap + rr * vx + cx];
+      }
+      acc[(v * RH + rr + b) * RW + c] += s;
+    }
+    __syncthreads();
+  }
+  // the tile's extended region [3][RH][RW] (valid part) to its slot of the tile buffer
+  T *tb = tbuf + (size_t)3 * RH * RW * tile_id;
+  for (int idx = threadIdx.x; idx < 3 * vh * vw; idx += blockDim.x) {
+    const int v = idx / (vh * vw);
+    const int rem = idx - v * vh * vw;
+    const int r = rem / vw, c = rem - r * vw;
+    tb[(v * RH + r) * RW + c] = acc[(v * RH + r) * RW + c];
   }
   __syncthreads();
 }
 
-// Shared memory of one reconstruction-adjoint tile of TX x TY cells with NT threads.
+// Shared memory of one reconstruction-adjoint tile of TX x TY cells with NT threads: the
+// forward tile's, the cell-point adjoints, and phase 2's scratch unless it fits the tile and
+// x-pass region it reuses.
 template <typename T, int K>
 __host__ __device__ constexpr size_t recon_adj_tile_smem_bytes(int TX, int TY, int NT) {
-  return recon_tile_smem_bytes<T, K>(TX, TY) + sizeof(T) * 3 * ((K + 1) / 2) * ((K + 1) / 2) * NT;
+  return recon_tile_smem_bytes<T, K>(TX, TY) + sizeof(T) * 3 * ((K + 1) / 2) * ((K + 1) / 2) * NT +
+         (3 * K * TX * TY <= 3 * ((K + 1) / 2 + 2) * (TY + K - 1) * TX
+              ? 0
+              : sizeof(T) * (3 * K * TX * TY + 3 * (TY + K - 1) * (TX + K - 1)));
+}
+
+// Elements of a member's tile buffer for TX x TY tiles.
+__host__ __device__ constexpr long long tile_buf_elems(int N, int K, int TX, int TY) {
+  return 6LL * ((N + TX - 1) / TX) * ((N + TY - 1) / TY) * 3 * (TY + K - 1) * (TX + K - 1);
 }
 
 template <typename T, int K>
 __global__ void __launch_bounds__(REC_TX *REC_TY)
     k_recon_tpp_adj(const T *__restrict__ q, const T *__restrict__ gext, const T *__restrict__ w1g,
                     const T *__restrict__ Xg, const T *__restrict__ t1w, const T *__restrict__ lep,
-                    const T *__restrict__ lamL, T *__restrict__ grad, int N, int ne, T omega, FCoef<T> fc) {
+                    const T *__restrict__ lamL, T *__restrict__ tbuf, int N, int ne, T omega, FCoef<T> fc,
+                    const T *__restrict__ ttw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  recon_tpp_adj_tile<T, K>(smem_raw, blockIdx.z, blockIdx.x * REC_TX, blockIdx.y * REC_TY, REC_TX, REC_TY, q, gext,
-                           w1g, Xg, t1w, lep, lamL, grad, N, ne, omega, fc);
+  const long long tile = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  recon_tpp_adj_tile<T, K>(smem_raw, blockIdx.z, blockIdx.x * REC_TX, blockIdx.y * REC_TY, REC_TX, REC_TY, tile, q,
+                           gext, w1g, Xg, t1w, lep, lamL, tbuf, N, ne, omega, fc, ttw);
 }
 
 template <typename T, int K>
 __host__ __device__ constexpr size_t recon_adj_smem_bytes() {
-  return recon_smem_bytes<T, K>() + sizeof(T) * 3 * Shape<K>::ME * Shape<K>::ME * REC_TX * REC_TY;
+  return recon_adj_tile_smem_bytes<T, K>(REC_TX, REC_TY, REC_TX * REC_TY);
 }
 
 // ---------------------------------------------------------------------------------
@@ -450,6 +516,53 @@ __device__ __forceinline__ void gather_adj_item(long long idx, const T *__restri
 #pragma unroll
     for (int v = 0; v < 3; ++v) lam_ring[v * pe + idx] = s[v];
   }
+}
+
+// Gather from a tile buffer (TPP): lam at every extended cell (xi, yj) of panel p is the sum,
+// over the tiles whose extended regions cover it (ascending tile row, then column), of
+// their contributions; TX x TY tiles, the last ones of a panel cut at its edge.
+template <typename T, int K>
+__device__ __forceinline__ void gather_tiles_item(long long idx, const T *__restrict__ tbuf, int TX, int TY,
+                                                  T *__restrict__ lam_direct, T *__restrict__ lam_ring, int N) {
+  constexpr int H = (K - 1) / 2;
+  const int ne = N + 2 * H, RW = TX + 2 * H, RH = TY + 2 * H;
+  const int ntx = (N + TX - 1) / TX, nty = (N + TY - 1) / TY;
+  const int ii = (int)(idx % ne);
+  const long long pj = idx / ne;
+  const int jj = (int)(pj % ne), p = (int)(pj / ne);
+  const int xi = ii - H, yj = jj - H;
+  const size_t pn = (size_t)6 * N * N, pe = (size_t)6 * ne * ne;
+  T s[3] = {0, 0, 0};
+  const int ty_hi = min(nty - 1, (yj + H) / TY), tx_hi = min(ntx - 1, (xi + H) / TX);
+  for (int ty = max(0, ty_hi - (2 * H + TY - 1) / TY - 1); ty <= ty_hi; ++ty) {
+    const int y0 = ty * TY - H, vy = min(TY, N - ty * TY);
+    if (yj < y0 || yj >= y0 + vy + 2 * H) continue;
+    for (int tx = max(0, tx_hi - (2 * H + TX - 1) / TX - 1); tx <= tx_hi; ++tx) {
+      const int x0 = tx * TX - H, vx = min(TX, N - tx * TX);
+      if (xi < x0 || xi >= x0 + vx + 2 * H) continue;
+      const T *tb = tbuf + (size_t)3 * RH * RW * (((size_t)p * nty + ty) * ntx + tx);
+#pragma unroll
+      for (int v = 0; v < 3; ++v) s[v] += tb[(v * RH + (yj - y0)) * RW + (xi - x0)];
+    }
+  }
+  if (xi >= 0 && xi < N && yj >= 0 && yj < N) {
+    const size_t cell = ((size_t)p * N + yj) * N + xi;
+#pragma unroll
+    for (int v = 0; v < 3; ++v) lam_direct[v * pn + cell] = s[v];
+  } else {
+#pragma unroll
+    for (int v = 0; v < 3; ++v) lam_ring[v * pe + idx] = s[v];
+  }
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(256)
+    k_gather_tiles(const T *__restrict__ tbuf, int TX, int TY, T *__restrict__ lam_direct, T *__restrict__ lam_ring,
+                   int N) {
+  const long long ne = N + K - 1;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 6LL * ne * ne) return;
+  gather_tiles_item<T, K>(idx, tbuf, TX, TY, lam_direct, lam_ring, N);
 }
 
 template <typename T, int K>

@@ -169,8 +169,14 @@ static int ensure_adjoint_scratch(hope_ctx *ctx) {
   for (auto &g : ctx->grids) {
     if (g.lep) continue;
     const size_t N = g.N, ne = g.ne, es = ctx->esize, me = ctx->me, K = ctx->k;
+    // TPP: one extended region per reconstruction tile, for the largest tile buffer of the
+    // per-kernel tiles and of the persistent launch's candidate shapes; WENO2D: the per-cell
+    // stencil gradients
+    size_t tiles = (size_t)tile_buf_elems(g.N, ctx->k, REC_TX, REC_TY);
+    if (ctx->ens) tiles = std::max(tiles, ensemble_tile_buf_elems(ctx, g.N));
+    const bool tpp = ctx->scheme == HOPE_TPP;
     if (cudaMalloc(&g.lep, es * 4 * 3 * me * 6 * N * N) != cudaSuccess ||
-        cudaMalloc(&g.grad, es * 3 * K * K * 6 * N * N) != cudaSuccess ||
+        (tpp ? cudaMalloc(&g.tbuf, es * tiles) : cudaMalloc(&g.grad, es * 3 * K * K * 6 * N * N)) != cudaSuccess ||
         cudaMalloc(&g.lring, es * 3 * 6 * ne * ne) != cudaSuccess ||
         cudaMalloc(&g.ldir, es * 3 * 6 * N * N) != cudaSuccess) {
       set_error("adjoint scratch allocation failed");
@@ -434,7 +440,7 @@ static void free_grid(Grid &g) {
     for (void *p : tables)
       if (p) cudaFree(p);
   }
-  void *scratch[] = {g.gext, g.ep, g.fx, g.fy, g.sb, g.lep, g.grad, g.lring, g.ldir, g.tsep, g.ttw, g.ttb,
+  void *scratch[] = {g.gext, g.ep, g.fx, g.fy, g.sb, g.lep, g.grad, g.tbuf, g.lring, g.ldir, g.tsep, g.ttw, g.ttb,
                      g.tsext, g.tscp};
   for (void *p : scratch)
     if (p) cudaFree(p);
@@ -1319,6 +1325,8 @@ int hope_autotune(hope_t ctx, int reps, float *ms_out, int *tx, int *ty, int *gr
     if (grid) *grid = 6 * ((g.N + g.rtx - 1) / g.rtx) * ((g.N + g.rty - 1) / g.rty);
     return HOPE_OK;
   }
+  HOPE_CUDA_TRY(cudaDeviceSynchronize());  // queued stages may still use the member table
+  drop_graphs(ctx);  // captured stages bake in the tile shape and block size
   int rc = ensemble_autotune(ctx, ctx->q1, ctx->lbuf, reps, ms_out, nullptr);
   if (rc) return rc;
   HOPE_CUDA_TRY(cudaDeviceSynchronize());
@@ -1328,6 +1336,11 @@ int hope_autotune(hope_t ctx, int reps, float *ms_out, int *tx, int *ty, int *gr
   if (ty) *ty = b;
   if (grid) *grid = c;
   return HOPE_OK;
+}
+
+int hope_autotune_candidates(hope_t ctx) {
+  if (!ctx) return 0;
+  return ctx->ens ? ensemble_num_shapes(ctx) : (ctx->scheme == HOPE_TPP ? 3 : 0);
 }
 
 int hope_inject_fault(hope_t ctx, int what) {

@@ -5,9 +5,12 @@
 // + stage combination) become work lists over all members, walked by a cooperative grid
 // of resident blocks and separated by grid-wide barriers.  Every barrier wait is bounded:
 // a block that waits longer than the limit sets HOPE_STATUS_TIMEOUT and the launch
-// returns instead of hanging.  The tile shape (TX x TY cells per work item) is chosen by
-// timing the compiled candidates (hope_autotune).
+// returns instead of hanging.  The tile shape (TX x TY cells per work item, a run-time
+// argument) and the block size (128 or 256 threads, compiled) are chosen by timing a list
+// of candidates (hope_autotune).
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include <string>
 #include <vector>
@@ -38,7 +41,7 @@ struct MemberDev {
   // stencil gradients, ring and interior adjoints, the transposed ghost operator, the
   // first item of the gather phase (6 ne^2 per member), and the member's block in a step
   // tape (element offset; ghost-ring and edge-point elements of one stage)
-  T *lep, *grad, *lring, *ldir;
+  T *lep, *tbuf, *lring, *ldir;
   const int *gtp, *gtr;
   const T *gtv;
   long long b_gather;
@@ -71,6 +74,7 @@ struct StageArgs {
   const GhostGroup *ggrp;     // ghost-fill groups
   const int *gmem;            // member indices of the groups
   int ngrp;
+  int tx, ty;                 // reconstruction tile (cells)
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -164,14 +168,15 @@ __device__ __forceinline__ int find_member(const MemberDev<T> *mem, int nmem, lo
   return lo;
 }
 
-template <typename T, int K, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 1024 / (TX * TY) : 1)
+template <typename T, int K, int NT>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 1024 / NT : 1)
     k_stage_persistent(const MemberDev<T> *__restrict__ mem, int nmem, long long n_ghost, long long n_tile,
                        long long n_flux, long long n_cell, StageArgs<T> sa, unsigned *bar, unsigned *status,
                        unsigned inject) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int ME = (K + 1) / 2;
-  constexpr int NT = TX * TY, WPB = NT / 32;
+  constexpr int WPB = NT / 32;
+  const int TX = sa.tx, TY = sa.ty;
   __shared__ long long sbeg[MEMBER_CACHE];
   auto lookup = [&](long long it, int phase) {
     return nmem <= MEMBER_CACHE ? find_member_cached(sbeg, nmem, it) : find_member(mem, nmem, it, phase);
@@ -264,16 +269,20 @@ struct VjpArgs {
   const int *gmem;
   int ngrp;
   unsigned long long *stamp;  // profiling: 7 phase stamps, or null
+  int tx, ty;                 // reconstruction tile (cells)
 };
 
-template <typename T, int K, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY)
+// FP32: registers capped for five resident 128-thread blocks (the phases are latency-bound;
+// the shared memory of a 16 x 8 tile allows five), FP64 uncapped (it would spill)
+template <typename T, int K, int NT>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 640 / NT : 1)
     k_vjp_persistent(const MemberDev<T> *__restrict__ mem, int nmem, long long n_ghost, long long n_tile,
                      long long n_flux, long long n_cell, long long n_gather, VjpArgs<T> va, unsigned *bar,
                      unsigned *status, unsigned inject) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int ME = (K + 1) / 2;
-  constexpr int NT = TX * TY, WPB = NT / 32;
+  constexpr int WPB = NT / 32;
+  const int TX = va.tx, TY = va.ty;
   __shared__ long long sbeg[MEMBER_CACHE];
   auto lookup = [&](long long it, int phase) {
     return nmem <= MEMBER_CACHE ? find_member_cached(sbeg, nmem, it) : find_member(mem, nmem, it, phase);
@@ -341,16 +350,16 @@ __global__ void __launch_bounds__(TX *TY)
     const int p = local / (m.tiles_x * m.tiles_y);
     const int rem = local - p * m.tiles_x * m.tiles_y;
     const int ty = rem / m.tiles_x, tx = rem - ty * m.tiles_x;
-    recon_tpp_adj_tile<T, K>(smem_raw, p, tx * TX, ty * TY, TX, TY, va.qs + m.off, gext_of(m), va.w1, m.Xg, m.t1w,
-                             m.lep, va.lamL + m.off, m.grad, m.N, m.ne, va.omega, va.fc);
+    recon_tpp_adj_tile<T, K>(smem_raw, p, tx * TX, ty * TY, TX, TY, local, va.qs + m.off, gext_of(m), va.w1, m.Xg,
+                             m.t1w, m.lep, va.lamL + m.off, m.tbuf, m.N, m.ne, va.omega, va.fc);
   }
   if (!grid_sync(bar, status, inject)) return;
   if (stamper) va.stamp[4] = global_ns();
-  // gather of the stencil gradients, one thread per extended cell
+  // gather of the tiles' extended regions, one thread per extended cell
   stage_member_begins(sbeg, mem, nmem, 4);
   for (long long it = (long long)blockIdx.x * NT + threadIdx.x; it < n_gather; it += (long long)gridDim.x * NT) {
     const MemberDev<T> &m = mem[lookup(it, 4)];
-    gather_adj_item<T, K>(it - m.b_gather, m.grad, m.ldir, m.lring, m.N);
+    gather_tiles_item<T, K>(it - m.b_gather, m.tbuf, TX, TY, m.ldir, m.lring, m.N);
   }
   if (!grid_sync(bar, status, inject)) return;
   if (stamper) va.stamp[5] = global_ns();
@@ -403,7 +412,7 @@ static int build_members(hope_ctx *ctx, int TX, int TY, std::vector<MemberDev<T>
     m.tiles_x = (g.N + TX - 1) / TX;
     m.tiles_y = (g.N + TY - 1) / TY;
     m.lep = (T *)g.lep;
-    m.grad = (T *)g.grad;
+    m.tbuf = (T *)g.tbuf;
     m.lring = (T *)g.lring;
     m.ldir = (T *)g.ldir;
     m.gtp = g.gtp;
@@ -433,34 +442,55 @@ static int build_members(hope_ctx *ctx, int TX, int TY, std::vector<MemberDev<T>
   return HOPE_OK;
 }
 
-struct PersistentShape {
-  int TX, TY;
-};
-static const PersistentShape kShapes[] = {{16, 8}, {16, 4}, {32, 4}};
-static const int kNumShapes = 3;
+// Candidate shapes: tiles of 32 to 256 cells on 128- and 256-thread blocks.
+static const EnsembleShape kCandidates[] = {
+    {16, 8, 128}, {8, 16, 128}, {32, 4, 128}, {16, 4, 128}, {12, 10, 128}, {24, 5, 128}, {8, 8, 128},
+    {16, 16, 256}, {32, 8, 256}, {16, 12, 256}, {24, 10, 256}, {12, 20, 256}};
 
-template <typename T, int K, int TX, int TY>
-static int launch_shape(hope_ctx *ctx, EnsembleState &es, const StageArgs<T> &sa, cudaStream_t st) {
-  auto kern = k_stage_persistent<T, K, TX, TY>;
-  const size_t smem = recon_smem_bytes<T, K, TX, TY>();
-  if (es.grid[es.shape] == 0) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-      set_error("persistent stage: shared-memory attribute failed");
+template <typename T, int K>
+static size_t stage_smem(const EnsembleShape &c) {
+  return recon_tile_smem_bytes<T, K>(c.tx, c.ty);
+}
+
+template <typename T, int K>
+static size_t vjp_smem(const EnsembleShape &c) {
+  const size_t f = recon_tile_smem_bytes<T, K>(c.tx, c.ty), a = recon_adj_tile_smem_bytes<T, K>(c.tx, c.ty, c.nt);
+  return f > a ? f : a;
+}
+
+// Cooperative launch of a persistent kernel with every block resident; *grid caches the
+// resident grid of this (kernel, shape).
+template <typename Kern, typename... Args>
+static int launch_coop(hope_ctx *ctx, Kern kern, int nt, size_t smem, int *grid, const char *what, cudaStream_t st,
+                       Args... args) {
+  if (*grid == 0) {
+    // opt in to the largest dynamic size the kernel can have (the block's limit less its
+    // static shared memory), so every candidate's tile fits
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) {
+      set_error(std::string(what) + ": kernel attributes unavailable");
+      return HOPE_ECUDA;
+    }
+    const int dyn_max = optin - (int)fa.sharedSizeBytes;
+    if ((long long)smem > dyn_max ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max) != cudaSuccess) {
+      set_error(std::string(what) + ": shared-memory attribute failed");
       return HOPE_ECUDA;
     }
     int per_sm = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     if (per_sm < 1) {
-      set_error("persistent stage: no resident block fits");
+      set_error(std::string(what) + ": no resident block fits");
       return HOPE_EUNSUPPORTED;
     }
-    es.grid[es.shape] = per_sm * sms;
+    *grid = per_sm * sms;
   }
-  const MemberDev<T> *mem = (const MemberDev<T> *)es.members[es.shape];
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(es.grid[es.shape]);
-  cfg.blockDim = dim3(TX * TY);
+  cfg.gridDim = dim3(*grid);
+  cfg.blockDim = dim3(nt);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -468,13 +498,9 @@ static int launch_shape(hope_ctx *ctx, EnsembleState &es, const StageArgs<T> &sa
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const long long *n = es.items[es.shape];
-  const unsigned inject = es.inject_timeout ? 1u : 0u;
-  es.inject_timeout = 0;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, mem, (int)ctx->grids.size(), n[0], n[1], n[2], n[3], sa,
-                                     es.barrier, ctx->status, inject);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args...);
   if (e != cudaSuccess) {
-    set_error(std::string("persistent stage launch: ") + cudaGetErrorString(e));
+    set_error(std::string(what) + " launch: " + cudaGetErrorString(e));
     return HOPE_ECUDA;
   }
   return HOPE_OK;
@@ -482,11 +508,18 @@ static int launch_shape(hope_ctx *ctx, EnsembleState &es, const StageArgs<T> &sa
 
 template <typename T, int K>
 static int launch_any(hope_ctx *ctx, EnsembleState &es, const StageArgs<T> &sa, cudaStream_t st) {
-  switch (es.shape) {
-    case 0: return launch_shape<T, K, 16, 8>(ctx, es, sa, st);
-    case 1: return launch_shape<T, K, 16, 4>(ctx, es, sa, st);
-    default: return launch_shape<T, K, 32, 4>(ctx, es, sa, st);
-  }
+  const EnsembleShape &c = es.cand[es.shape];
+  const MemberDev<T> *mem = (const MemberDev<T> *)es.members;
+  const long long *n = es.items;
+  const unsigned inject = es.inject_timeout ? 1u : 0u;
+  es.inject_timeout = 0;
+  const int nmem = (int)ctx->grids.size();
+  const size_t smem = stage_smem<T, K>(c);
+  if (c.nt == 256)
+    return launch_coop(ctx, k_stage_persistent<T, K, 256>, 256, smem, &es.grid[es.shape], "persistent stage", st, mem,
+                       nmem, n[0], n[1], n[2], n[3], sa, es.barrier, ctx->status, inject);
+  return launch_coop(ctx, k_stage_persistent<T, K, 128>, 128, smem, &es.grid[es.shape], "persistent stage", st, mem,
+                     nmem, n[0], n[1], n[2], n[3], sa, es.barrier, ctx->status, inject);
 }
 
 template <typename T>
@@ -515,6 +548,8 @@ static int stage_persistent_t(hope_ctx *ctx, const void *qs, const void *q0, voi
   sa.ggrp = (const GhostGroup *)es.ggrp;
   sa.gmem = es.gmem;
   sa.ngrp = es.ngrp;
+  sa.tx = es.cand[es.shape].tx;
+  sa.ty = es.cand[es.shape].ty;
   if (sa.stamp && cudaMemsetAsync(sa.stamp + 4, 0, sizeof(unsigned long long), st) != cudaSuccess) return HOPE_ECUDA;
   switch (ctx->k) {
     case 3: return launch_any<T, 3>(ctx, es, sa, st);
@@ -533,75 +568,44 @@ int stage_persistent(hope_ctx *ctx, const void *qs, const void *q0, void *out, i
   return stage_persistent_t<float>(ctx, qs, q0, out, mode, a, b, c, q0l, qsl, outl, st);
 }
 
-template <typename T, int K, int TX, int TY>
-static int launch_vjp_shape(hope_ctx *ctx, EnsembleState &es, const VjpArgs<T> &va, cudaStream_t st) {
-  auto kern = k_vjp_persistent<T, K, TX, TY>;
-  constexpr size_t fwd = recon_smem_bytes<T, K, TX, TY>();
-  constexpr size_t adj = recon_adj_tile_smem_bytes<T, K>(TX, TY, TX * TY);
-  const size_t smem = fwd > adj ? fwd : adj;
-  if (es.vgrid[es.shape] == 0) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-      set_error("persistent stage VJP: shared-memory attribute failed");
-      return HOPE_ECUDA;
-    }
-    int per_sm = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, smem);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-    if (per_sm < 1) {
-      set_error("persistent stage VJP: no resident block fits");
-      return HOPE_EUNSUPPORTED;
-    }
-    es.vgrid[es.shape] = per_sm * sms;
-  }
-  const MemberDev<T> *mem = (const MemberDev<T> *)es.members[es.shape];
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(es.vgrid[es.shape]);
-  cfg.blockDim = dim3(TX * TY);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  const long long *n = es.items[es.shape];
-  const unsigned inject = es.inject_timeout ? 1u : 0u;
-  es.inject_timeout = 0;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, mem, (int)ctx->grids.size(), n[0], n[1], n[2], n[3], n[4], va,
-                                     es.barrier, ctx->status, inject);
-  if (e != cudaSuccess) {
-    set_error(std::string("persistent stage VJP launch: ") + cudaGetErrorString(e));
-    return HOPE_ECUDA;
-  }
-  return HOPE_OK;
-}
-
 template <typename T, int K>
 static int launch_vjp_any(hope_ctx *ctx, EnsembleState &es, const VjpArgs<T> &va, cudaStream_t st) {
-  switch (es.shape) {
-    case 0: return launch_vjp_shape<T, K, 16, 8>(ctx, es, va, st);
-    case 1: return launch_vjp_shape<T, K, 16, 4>(ctx, es, va, st);
-    default: return launch_vjp_shape<T, K, 32, 4>(ctx, es, va, st);
-  }
+  const EnsembleShape &c = es.cand[es.shape];
+  const MemberDev<T> *mem = (const MemberDev<T> *)es.members;
+  const long long *n = es.items;
+  const unsigned inject = es.inject_timeout ? 1u : 0u;
+  es.inject_timeout = 0;
+  const int nmem = (int)ctx->grids.size();
+  const size_t smem = vjp_smem<T, K>(c);
+  if (c.nt == 256)
+    return launch_coop(ctx, k_vjp_persistent<T, K, 256>, 256, smem, &es.vgrid[es.shape], "persistent stage VJP", st,
+                       mem, nmem, n[0], n[1], n[2], n[3], n[4], va, es.barrier, ctx->status, inject);
+  return launch_coop(ctx, k_vjp_persistent<T, K, 128>, 128, smem, &es.vgrid[es.shape], "persistent stage VJP", st,
+                     mem, nmem, n[0], n[1], n[2], n[3], n[4], va, es.barrier, ctx->status, inject);
 }
 
-// The member tables again, now with the adjoint scratch pointers (the scratch is
-// allocated on the first VJP call); same device arrays, so captured graphs stay valid.
+// The member table of the current shape (with the adjoint scratch pointers once they
+// exist), uploaded into the context's one device array: captured graphs keep pointing at it,
+// but a change of shape makes them stale (the caller drops them).
 template <typename T>
-static int ensemble_adjoint_members_t(hope_ctx *ctx) {
+static int upload_members_t(hope_ctx *ctx) {
   EnsembleState &es = *ctx->ens;
-  for (int s = 0; s < kNumShapes; ++s) {
-    std::vector<MemberDev<T>> mv;
-    long long n[5];
-    build_members<T>(ctx, kShapes[s].TX, kShapes[s].TY, mv, n);
-    if (cudaMemcpy(es.members[s], mv.data(), sizeof(MemberDev<T>) * mv.size(), cudaMemcpyHostToDevice) !=
-        cudaSuccess) {
-      set_error("persistent stage VJP: member table upload failed");
-      return HOPE_ECUDA;
-    }
+  const EnsembleShape &c = es.cand[es.shape];
+  std::vector<MemberDev<T>> mv;
+  const long long ghost_items = es.items[0];
+  build_members<T>(ctx, c.tx, c.ty, mv, es.items);
+  if (es.ngrp) es.items[0] = ghost_items;  // ghost work is itemised by operator groups
+  if (!es.members && cudaMalloc(&es.members, sizeof(MemberDev<T>) * mv.size()) != cudaSuccess) return HOPE_ENOMEM;
+  if (cudaMemcpy(es.members, mv.data(), sizeof(MemberDev<T>) * mv.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    set_error("persistent stage: member table upload failed");
+    return HOPE_ECUDA;
   }
-  es.adj_ready = 1;
+  es.adj_ready = ctx->grids[0].lep != nullptr;
   return HOPE_OK;
+}
+
+static int upload_members(hope_ctx *ctx) {
+  return ctx->prec == HOPE_FP64 ? upload_members_t<double>(ctx) : upload_members_t<float>(ctx);
 }
 
 template <typename T>
@@ -610,7 +614,7 @@ static int vjp_persistent_t(hope_ctx *ctx, const void *qs, const void *lamL, voi
                             int tape_stage, cudaStream_t st) {
   EnsembleState &es = *ctx->ens;
   if (!es.adj_ready) {
-    int rc = ensemble_adjoint_members_t<T>(ctx);
+    int rc = upload_members_t<T>(ctx);
     if (rc) return rc;
   }
   VjpArgs<T> va;
@@ -635,6 +639,8 @@ static int vjp_persistent_t(hope_ctx *ctx, const void *qs, const void *lamL, voi
   va.gmem = es.gmem;
   va.ngrp = es.ngrp;
   va.stamp = ctx->profiling ? es.vstamps : nullptr;
+  va.tx = es.cand[es.shape].tx;
+  va.ty = es.cand[es.shape].ty;
   if (va.stamp && cudaMemsetAsync(va.stamp + 6, 0, sizeof(unsigned long long), st) != cudaSuccess) return HOPE_ECUDA;
   switch (ctx->k) {
     case 3: return launch_vjp_any<T, 3>(ctx, es, va, st);
@@ -658,12 +664,26 @@ template <typename T>
 static int ensemble_init_t(hope_ctx *ctx) {
   EnsembleState *es = new EnsembleState();
   ctx->ens = es;
-  for (int s = 0; s < kNumShapes; ++s) {
-    std::vector<MemberDev<T>> mv;
-    build_members<T>(ctx, kShapes[s].TX, kShapes[s].TY, mv, es->items[s]);
-    if (cudaMalloc(&es->members[s], sizeof(MemberDev<T>) * mv.size()) != cudaSuccess) return HOPE_ENOMEM;
-    cudaMemcpy(es->members[s], mv.data(), sizeof(MemberDev<T>) * mv.size(), cudaMemcpyHostToDevice);
+  for (const EnsembleShape &c : kCandidates) {
+    // a candidate whose tile needs more shared memory than a block may have is left out
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    size_t need = 0;
+    switch (ctx->k) {
+      case 3: need = vjp_smem<T, 3>(c); break;
+      case 5: need = vjp_smem<T, 5>(c); break;
+      case 7: need = vjp_smem<T, 7>(c); break;
+      case 9: need = vjp_smem<T, 9>(c); break;
+      default: need = vjp_smem<T, 11>(c); break;
+    }
+    const size_t static_smem = sizeof(long long) * MEMBER_CACHE + 64;  // the kernels' own shared arrays
+    if (need + static_smem <= (size_t)optin && es->ncand < ENS_MAX_SHAPES) es->cand[es->ncand++] = c;
   }
+  if (es->ncand == 0) {
+    set_error("persistent stage: no tile shape fits the shared memory");
+    return HOPE_EUNSUPPORTED;
+  }
+  es->shape = 0;
   {
     // ghost-fill groups: members that share an operator (the same table pointers)
     std::vector<const int *> tables;
@@ -692,7 +712,7 @@ static int ensemble_init_t(hope_ctx *ctx) {
       b += (long long)G.rows * G.nchunk;
       groups.push_back(G);
     }
-    for (int s = 0; s < kNumShapes; ++s) es->items[s][0] = b;
+    es->items[0] = b;
     es->ngrp = (int)groups.size();
     if (cudaMalloc(&es->ggrp, sizeof(GhostGroup) * groups.size()) != cudaSuccess ||
         cudaMalloc(&es->gmem, sizeof(int) * gm.size()) != cudaSuccess)
@@ -706,7 +726,7 @@ static int ensemble_init_t(hope_ctx *ctx) {
   cudaMemset(es->vstamps, 0, 7 * sizeof(unsigned long long));
   cudaMemset(es->stamps, 0, 5 * PROF_STAGES * sizeof(unsigned long long));
   cudaMemset(es->barrier, 0, 2 * sizeof(unsigned));
-  return HOPE_OK;
+  return upload_members_t<T>(ctx);
 }
 
 int ensemble_init(hope_ctx *ctx) {
@@ -715,8 +735,7 @@ int ensemble_init(hope_ctx *ctx) {
 
 void ensemble_free(hope_ctx *ctx) {
   if (!ctx->ens) return;
-  for (int s = 0; s < kNumShapes; ++s)
-    if (ctx->ens->members[s]) cudaFree(ctx->ens->members[s]);
+  if (ctx->ens->members) cudaFree(ctx->ens->members);
   if (ctx->ens->barrier) cudaFree(ctx->ens->barrier);
   if (ctx->ens->stamps) cudaFree(ctx->ens->stamps);
   if (ctx->ens->vstamps) cudaFree(ctx->ens->vstamps);
@@ -731,7 +750,8 @@ void ensemble_reset_barrier(hope_ctx *ctx) {
 }
 
 // Time `reps` tendency stages of every candidate shape on the scratch buffers and keep
-// the fastest.  ms_out (may be null) receives the per-shape times.
+// the fastest.  ms_out (may be null, ENS_MAX_SHAPES floats) receives the per-shape times
+// (-1 for a shape that failed to launch and past the candidates).
 int ensemble_autotune(hope_ctx *ctx, const void *qs, void *out, int reps, float *ms_out, cudaStream_t st) {
   EnsembleState &es = *ctx->ens;
   cudaEvent_t e0, e1;
@@ -739,13 +759,13 @@ int ensemble_autotune(hope_ctx *ctx, const void *qs, void *out, int reps, float 
   cudaEventCreate(&e1);
   float best = 1e30f;
   int best_s = 0;
-  for (int s = 0; s < kNumShapes; ++s) {
+  if (ms_out)
+    for (int s = 0; s < ENS_MAX_SHAPES; ++s) ms_out[s] = -1.0f;
+  int rc = HOPE_OK;
+  for (int s = 0; s < es.ncand; ++s) {
     es.shape = s;
-    int rc = stage_persistent(ctx, qs, nullptr, out, 0, 0, 0, 0, nullptr, nullptr, nullptr, st);
-    if (rc) {
-      if (ms_out) ms_out[s] = -1.0f;
-      continue;
-    }
+    if ((rc = upload_members(ctx))) break;
+    if (stage_persistent(ctx, qs, nullptr, out, 0, 0, 0, 0, nullptr, nullptr, nullptr, st)) continue;
     cudaEventRecord(e0, st);
     for (int r = 0; r < reps; ++r) stage_persistent(ctx, qs, nullptr, out, 0, 0, 0, 0, nullptr, nullptr, nullptr, st);
     cudaEventRecord(e1, st);
@@ -763,14 +783,25 @@ int ensemble_autotune(hope_ctx *ctx, const void *qs, void *out, int reps, float 
   cudaEventDestroy(e1);
   es.shape = best_s;
   es.tuned = 1;
+  if (rc == HOPE_OK) rc = upload_members(ctx);
+  if (rc) return rc;
   return cudaGetLastError() == cudaSuccess ? HOPE_OK : HOPE_ECUDA;
 }
 
 void ensemble_shape(const hope_ctx *ctx, int *tx, int *ty, int *grid) {
   const EnsembleState &es = *ctx->ens;
-  *tx = kShapes[es.shape].TX;
-  *ty = kShapes[es.shape].TY;
+  *tx = es.cand[es.shape].tx;
+  *ty = es.cand[es.shape].ty;
   *grid = es.grid[es.shape];
+}
+
+int ensemble_num_shapes(const hope_ctx *ctx) { return ctx->ens ? ctx->ens->ncand : 0; }
+
+size_t ensemble_tile_buf_elems(const hope_ctx *ctx, int N) {
+  size_t m = 0;
+  for (int s = 0; ctx->ens && s < ctx->ens->ncand; ++s)
+    m = std::max(m, (size_t)tile_buf_elems(N, ctx->k, ctx->ens->cand[s].tx, ctx->ens->cand[s].ty));
+  return m;
 }
 
 }  // namespace hope

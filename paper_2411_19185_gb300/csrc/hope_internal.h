@@ -72,7 +72,8 @@ struct Grid {
   void *gtv = nullptr;   // [nnz][5]
   // adjoint scratch (allocated on the first VJP call)
   void *lep = nullptr;    // like ep
-  void *grad = nullptr;   // [3][k*k][6][N][N]
+  void *grad = nullptr;   // [3][k*k][6][N][N] (WENO2D; TPP adds the gradients up per tile)
+  void *tbuf = nullptr;   // TPP: per reconstruction tile, its gradient on its extended region
   void *lring = nullptr;  // like gext
   void *ldir = nullptr;   // [3][6][N][N]
 };

@@ -338,23 +338,25 @@ inline int stage_vjp_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *lamL, co
                                                       (const T *)g.bconv, lamL, (T *)g.lep, N, inv_dx,
                                                       (const T *)g.tsep);
   }
+  const long long ext_cells = 6LL * ne * ne;
   if (ctx->scheme == HOPE_TPP) {
+    // per tile, the gradients added up on the tile's extended region (psi_B's transposed
+    // stencil map included over a surface), then gathered per extended cell
     k_recon_tpp_adj<T, K><<<grid, REC_TX * REC_TY, recon_adj_smem_bytes<T, K>(), st>>>(
         qs, (const T *)g.gext, (const T *)ctx->w1, (const T *)g.Xg, (const T *)g.t1w, (const T *)g.lep, lamL,
-        (T *)g.grad, N, ne, (T)ctx->omega, fcoef<T>(ctx));
+        (T *)g.tbuf, N, ne, (T)ctx->omega, fcoef<T>(ctx), (const T *)g.ttw);
+    k_gather_tiles<T, K><<<(int)((ext_cells + 255) / 256), 256, 0, st>>>((const T *)g.tbuf, REC_TX, REC_TY,
+                                                                        (T *)g.ldir, (T *)g.lring, N);
   } else {
     int rc = launch_recon_weno_adj<T, K>(ctx, g, qs, lamL, st);
     if (rc) return rc;
-  }
-  if (g.tsep) {
-    // psi_B's stencil map, transposed, into the mass variable's stencil gradient
-    const long long cells = 6LL * N * N;
-    k_topo_src_adj<T, K><<<(int)((cells + 255) / 256), 256, 0, st>>>(lamL, (const T *)g.ttw, (T *)g.grad, N);
-  }
-  {
-    long long total = 6LL * ne * ne;
-    k_gather_adj<T, K><<<(int)((total + 255) / 256), 256, 0, st>>>((const T *)g.grad, (T *)g.ldir, (T *)g.lring,
-                                                                    N);
+    if (g.tsep) {
+      // psi_B's stencil map, transposed, into the mass variable's stencil gradient
+      const long long cells = 6LL * N * N;
+      k_topo_src_adj<T, K><<<(int)((cells + 255) / 256), 256, 0, st>>>(lamL, (const T *)g.ttw, (T *)g.grad, N);
+    }
+    k_gather_adj<T, K><<<(int)((ext_cells + 255) / 256), 256, 0, st>>>((const T *)g.grad, (T *)g.ldir,
+                                                                      (T *)g.lring, N);
   }
   {
     long long cells = 6LL * N * N;

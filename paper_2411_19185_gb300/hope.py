@@ -247,11 +247,13 @@ class Sphere:
     def autotune(self, reps=5):
         """Re-time the tile shapes -- of the persistent stage (ensembles) or of the TPP
         reconstruction (one sphere) -- and keep the fastest; returns (per-candidate ms,
-        (tx, ty), resident grid or tile count)."""
-        ms = (ctypes.c_float * 3)()
+        (tx, ty), resident grid or tile count).  The times list has one entry per candidate
+        (three for one sphere; the candidate list of the persistent stage for an ensemble)."""
+        ms = (ctypes.c_float * L.HOPE_AUTOTUNE_MAX)()
         tx, ty, grid = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         L.check(L.load().hope_autotune(self._h, reps, ms, ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(grid)))
-        return list(ms), (tx.value, ty.value), grid.value
+        n = 3 if len(self.members) == 1 else L.load().hope_autotune_candidates(self._h)
+        return list(ms)[:n], (tx.value, ty.value), grid.value
 
     def recon_tile(self):
         """(tx, ty): cells per block of the per-kernel TPP reconstruction."""
