@@ -40,14 +40,30 @@ L2_FLUSH_BYTES = 512 << 20
 RECON_TRAFFIC_BYTES = 20398336  # 20.390144 MB read + 8 KB written
 
 
-def recon_flops_per_launch(N, K):
-    """Algorithmic FLOPs of one TPP reconstruction + sources launch (one stage):
-    sum-factorised x-pass over N x (N + 2H) cells at me + 2 positions and y-pass at the
-    n_poc = 4 me + me^2 points (K FMAs each, 3 variables), plus 28 flops of metric and
-    Coriolis sources per cell point (eqs. 2.2, 2.3, with the point polynomials tabulated)."""
+def recon_flops_per_launch_unfolded(N, K):
+    """FLOPs of one TPP reconstruction + sources launch with every point value a K-term
+    dot product: sum-factorised x-pass over N x (N + 2H) cells at me + 2 positions and
+    y-pass at the n_poc = 4 me + me^2 points (K FMAs each, 3 variables), plus 28 flops of
+    metric and Coriolis sources per cell point (eqs. 2.2, 2.3, point polynomials tabulated)."""
     me, H = (K + 1) // 2, (K - 1) // 2
     npoc = 4 * me + me * me
     per_panel = 3 * 2 * K * ((me + 2) * N * (N + 2 * H) + npoc * N * N) + 28 * me * me * N * N
+    return 6 * per_panel
+
+
+def recon_flops_per_launch(N, K):
+    """Algorithmic FLOPs of one TPP reconstruction + sources launch (one stage), the count
+    the kernel evaluates: the same sum-factorised passes with the positions taken in
+    mirror pairs (the weights at -xi are the weights at +xi reversed): per line, K - 1 flops
+    to fold it into sums and differences, 2K per pair (E: H + 1 terms, O: H terms, E +- O),
+    K for the middle node of odd me; plus 28 flops of sources per cell point."""
+    me, H = (K + 1) // 2, (K - 1) // 2
+    gp, odd = me // 2, me % 2
+    line_x = (K - 1) + (1 + gp) * 2 * K + odd * K            # the me + 2 x positions
+    edge_col = (K - 1) + gp * 2 * K + odd * K                # west/east columns: me nodes
+    node_col = (K - 1) + (1 + gp) * 2 * K + odd * K          # node columns: 2 edges + me nodes
+    per_panel = 3 * (line_x * N * (N + 2 * H) + (2 * edge_col + me * node_col) * N * N) \
+        + 28 * me * me * N * N
     return 6 * per_panel
 
 
@@ -885,6 +901,7 @@ def main():
                      "peak_source": "FP64 FMA microbenchmark measured in this run (hope_measure_fma_peak_clock)",
                      "peak_sm_mhz": peak_mhz, "peak_flops_per_sm_clock": peak_fpc,
                      "flops_per_launch": flops, "avg_launch_ms": recon_avg_ms,
+                     "flops_per_launch_unfolded": recon_flops_per_launch_unfolded(N_CELLS, ORDER),
                      "traffic": RECON_TRAFFIC_BYTES},
         "stage_kernel_ms": {"ghost": kernel_sum[0] / (3 * args.steps), "recon": kernel_sum[1] / (3 * args.steps),
                             "flux": kernel_sum[2] / (3 * args.steps), "update": kernel_sum[3] / (3 * args.steps)},

@@ -106,7 +106,7 @@ struct hope_ctx {
   size_t total = 0;  // elements of one (ensemble) state
   std::vector<hope::Grid> grids;
   // order-dependent tables (element type = precision)
-  void *w1 = nullptr;   // [me+2][k] 1-D TPP weights at xi = -1/2, +1/2, g_0..g_{me-1}
+  void *w1 = nullptr;   // [me+2][k] 1-D TPP weights at xi = -1/2, +1/2, g_0..g_{me-1}, then [1+(me+1)/2][k] mirror pairs
   void *gw = nullptr;   // [me] Gauss weights
   // WENO tables
   void *wsub = nullptr;   // [me+2][l][l]  1-D sub-stencil weights at the same positions

@@ -266,6 +266,42 @@ __host__ __device__ constexpr size_t recon_tile_smem_bytes(int TX, int TY) {
 // Largest thread count of a TPP reconstruction block (one thread per cell of the tile).
 constexpr int REC_MAX_THREADS = 512;
 
+// Mirror pairs of evaluation positions (t = 0: xi = -1/2, 1: +1/2, 2 + g: Gauss node g,
+// ascending): pair 0 is the two edges, pair 1 + g (g < me/2) the nodes g and me-1-g, and
+// for odd me the last pair is the middle node alone.  Their weights follow the point
+// weights in the w1 table (see k_setup_order).
+template <int K>
+struct MirrorPairs {
+  static constexpr int H = (K - 1) / 2, ME = (K + 1) / 2, NPOS = ME + 2;
+  static constexpr int NPAIR = 1 + (ME + 1) / 2;
+  static constexpr bool ODD = ME & 1;
+  __host__ __device__ static constexpr int minus(int pi) { return pi == 0 ? 0 : 1 + pi; }
+  __host__ __device__ static constexpr int plus(int pi) { return pi == 0 ? 1 : 2 + ME - pi; }
+};
+
+// Fold a line of K values in place: x[b] = x[b] + x[K-1-b], x[K-1-b] = x[b] - x[K-1-b].
+template <typename T, int K>
+__device__ __forceinline__ void mirror_fold(T *x) {
+#pragma unroll
+  for (int b = 0; b < (K - 1) / 2; ++b) {
+    const T s = x[b] + x[K - 1 - b], d = x[b] - x[K - 1 - b];
+    x[b] = s;
+    x[K - 1 - b] = d;
+  }
+}
+
+// Even and odd parts of one pair's value on a folded line: p(+xi) = E + O, p(-xi) = E - O.
+template <typename T, int K>
+__device__ __forceinline__ void mirror_eval(const T *w, const T *x, T &E, T &O) {
+  constexpr int H = (K - 1) / 2;
+  E = w[H] * x[H];
+  O = w[H + 1] * x[H + 1];
+#pragma unroll
+  for (int b = 0; b < H; ++b) E = fma(w[b], x[b], E);
+#pragma unroll
+  for (int b = H + 2; b < K; ++b) O = fma(w[b], x[b], O);
+}
+
 // One tile of at most TX x TY cells of panel p with its first cell at (i0, j0); called by
 // all threads of a block of at least TX*TY threads; ends with a barrier so the shared
 // memory can be reused for the next tile.  Tiles cut by the panel's edge only load,
@@ -282,10 +318,12 @@ __device__ __forceinline__ void recon_tpp_tile(unsigned char *smem_raw, int p, i
   const int RW = TX + 2 * H, RH = TY + 2 * H;
   const int vx = min(TX, N - i0), vy = min(TY, N - j0);
   const int vw = vx + 2 * H, vh = vy + 2 * H;
+  using MP = MirrorPairs<K>;
+  constexpr int NPAIR = MP::NPAIR;
   T *raw = reinterpret_cast<T *>(smem_raw);  // [3][RH][RW]
   T *xs = raw + 3 * RH * RW;                  // [3][NPOS][RH][TX]
-  T *w1 = xs + 3 * NPOS * RH * TX;            // [NPOS][K]
-  for (int t = threadIdx.x; t < NPOS * K; t += blockDim.x) w1[t] = w1g[t];
+  T *w1 = xs + 3 * NPOS * RH * TX;            // mirror-pair weights [NPAIR][K]
+  for (int t = threadIdx.x; t < NPAIR * K; t += blockDim.x) w1[t] = w1g[NPOS * K + t];
   {
     // extended tile of the 3 variables: interior cells from q, ring cells from gext
     const size_t pn = (size_t)6 * N * N, pe = (size_t)6 * ne * ne;
@@ -303,7 +341,8 @@ __device__ __forceinline__ void recon_tpp_tile(unsigned char *smem_raw, int p, i
     }
   }
   __syncthreads();
-  // x-pass: every row of the extended tile, every valid tile column, NPOS positions
+  // x-pass: every row of the extended tile, every valid tile column, the NPOS positions
+  // as mirror pairs of the folded row
   for (int idx = threadIdx.x; idx < 3 * vh * vx; idx += blockDim.x) {
     const int v = idx / (vh * vx);
     const int rem = idx - v * vh * vx;
@@ -312,12 +351,14 @@ __device__ __forceinline__ void recon_tpp_tile(unsigned char *smem_raw, int p, i
     T a[K];
 #pragma unroll
     for (int b = 0; b < K; ++b) a[b] = row[b];
+    mirror_fold<T, K>(a);
+    T *o = xs + ((size_t)v * NPOS * RH + r) * TX + c;
 #pragma unroll
-    for (int t = 0; t < NPOS; ++t) {
-      T s = 0;
-#pragma unroll
-      for (int b = 0; b < K; ++b) s = fma(w1[t * K + b], a[b], s);
-      xs[((v * NPOS + t) * RH + r) * TX + c] = s;
+    for (int pi = 0; pi < NPAIR; ++pi) {
+      T E, O;
+      mirror_eval<T, K>(w1 + pi * K, a, E, O);
+      o[MP::plus(pi) * RH * TX] = E + O;
+      if (MP::minus(pi) != MP::plus(pi)) o[MP::minus(pi) * RH * TX] = E - O;
     }
   }
   __syncthreads();
@@ -328,68 +369,73 @@ __device__ __forceinline__ void recon_tpp_tile(unsigned char *smem_raw, int p, i
     const size_t cell = ((size_t)p * N + j) * N + i;
     const T fc0 = fc.c[3 * p], fc1 = fc.c[3 * p + 1], fc2 = fc.c[3 * p + 2];
     T s1 = 0, s2 = 0;
+    // metric (eq. 2.2) and Coriolis (eq. 2.3) sources at the cell point (g, h)
+    auto source = [&](int g, int h, T X, const T qv[3]) {
+      const T Y = Xg[j * ME + h];
+      const size_t pt = (((size_t)j * N + i) * ME + h) * ME + g;
+      const T os = omega * (fc0 + fc1 * X + fc2 * Y);  // Omega sin(latitude) delta, eq. 2.5
+      const T rq = rcp(qv[0]);
+      if constexpr (sizeof(T) == 8) {
+        // FP64: the FP64 pipe is the bound, so the eight weighted polynomials are loaded
+        const T *c8 = src8 + pt * 8;
+        s1 += fma(c8[0], qv[1], c8[1] * qv[2]) * qv[1] * rq + os * fma(c8[4], qv[1], c8[5] * qv[2]);
+        s2 += fma(c8[2], qv[1], c8[3] * qv[2]) * qv[2] * rq + os * fma(c8[6], qv[1], c8[7] * qv[2]);
+      } else {
+        // FP32: arithmetic is cheap next to load latency, so the polynomials are evaluated
+        const T XY = X * Y, X2 = X * X, Y2 = Y * Y;
+        const T a1 = (-XY * Y * qv[1] + Y * (T(1) + Y2) * qv[2]) * qv[1] * rq +
+                     os * (-XY * qv[1] + (T(1) + Y2) * qv[2]);
+        const T a2 = (X * (T(1) + X2) * qv[1] - X2 * Y * qv[2]) * qv[2] * rq +
+                     os * (-(T(1) + X2) * qv[1] + XY * qv[2]);
+        const T tw = t1w[pt];
+        s1 = fma(tw, a1, s1);
+        s2 = fma(tw, a2, s2);
+      }
+    };
 #pragma unroll 1
     for (int t = 0; t < NPOS; ++t) {
       T col[3][K];
 #pragma unroll
-      for (int v = 0; v < 3; ++v)
+      for (int v = 0; v < 3; ++v) {
 #pragma unroll
         for (int b = 0; b < K; ++b) col[v][b] = xs[((v * NPOS + t) * RH + ty + b) * TX + tx];
+        mirror_fold<T, K>(col[v]);
+      }
       if (t < 2) {
         // west (t = 0) / east (t = 1) edge points at the Gauss nodes in y
 #pragma unroll
-        for (int r = 0; r < ME; ++r)
+        for (int pi = 1; pi < NPAIR; ++pi)
 #pragma unroll
           for (int v = 0; v < 3; ++v) {
-            T s = 0;
-#pragma unroll
-            for (int b = 0; b < K; ++b) s = fma(w1[(2 + r) * K + b], col[v][b], s);
-            ep[((size_t)(t * 3 + v) * ME + r) * pn + cell] = s;
+            T E, O;
+            mirror_eval<T, K>(w1 + pi * K, col[v], E, O);
+            ep[((size_t)(t * 3 + v) * ME + (ME - pi)) * pn + cell] = E + O;
+            if (MP::minus(pi) != MP::plus(pi)) ep[((size_t)(t * 3 + v) * ME + (pi - 1)) * pn + cell] = E - O;
           }
       } else {
         const int g = t - 2;
         // south / north edge points at x-node g
 #pragma unroll
-        for (int side = 0; side < 2; ++side)
-#pragma unroll
-          for (int v = 0; v < 3; ++v) {
-            T s = 0;
-#pragma unroll
-            for (int b = 0; b < K; ++b) s = fma(w1[side * K + b], col[v][b], s);
-            ep[((size_t)((2 + side) * 3 + v) * ME + g) * pn + cell] = s;
-          }
-        // cell points (g, h): metric (eq. 2.2) and Coriolis (eq. 2.3) sources
+        for (int v = 0; v < 3; ++v) {
+          T E, O;
+          mirror_eval<T, K>(w1, col[v], E, O);
+          ep[((size_t)(2 * 3 + v) * ME + g) * pn + cell] = E - O;
+          ep[((size_t)(3 * 3 + v) * ME + g) * pn + cell] = E + O;
+        }
+        // cell points (g, h) in mirror pairs of h
         const T X = Xg[i * ME + g];
 #pragma unroll 1
-        for (int h = 0; h < ME; ++h) {
-          T qv[3];
+        for (int pi = 1; pi < NPAIR; ++pi) {
+          T qp[3], qm[3];
 #pragma unroll
           for (int v = 0; v < 3; ++v) {
-            T s = 0;
-#pragma unroll
-            for (int b = 0; b < K; ++b) s = fma(w1[(2 + h) * K + b], col[v][b], s);
-            qv[v] = s;
+            T E, O;
+            mirror_eval<T, K>(w1 + pi * K, col[v], E, O);
+            qp[v] = E + O;
+            qm[v] = E - O;
           }
-          const T Y = Xg[j * ME + h];
-          const size_t pt = (((size_t)j * N + i) * ME + h) * ME + g;
-          const T os = omega * (fc0 + fc1 * X + fc2 * Y);  // Omega sin(latitude) delta, eq. 2.5
-          const T rq = rcp(qv[0]);
-          if constexpr (sizeof(T) == 8) {
-            // FP64: the FP64 pipe is the bound, so the eight weighted polynomials are loaded
-            const T *c8 = src8 + pt * 8;
-            s1 += fma(c8[0], qv[1], c8[1] * qv[2]) * qv[1] * rq + os * fma(c8[4], qv[1], c8[5] * qv[2]);
-            s2 += fma(c8[2], qv[1], c8[3] * qv[2]) * qv[2] * rq + os * fma(c8[6], qv[1], c8[7] * qv[2]);
-          } else {
-            // FP32: arithmetic is cheap next to load latency, so the polynomials are evaluated
-            const T XY = X * Y, X2 = X * X, Y2 = Y * Y;
-            const T a1 = (-XY * Y * qv[1] + Y * (T(1) + Y2) * qv[2]) * qv[1] * rq +
-                         os * (-XY * qv[1] + (T(1) + Y2) * qv[2]);
-            const T a2 = (X * (T(1) + X2) * qv[1] - X2 * Y * qv[2]) * qv[2] * rq +
-                         os * (-(T(1) + X2) * qv[1] + XY * qv[2]);
-            const T tw = t1w[pt];
-            s1 = fma(tw, a1, s1);
-            s2 = fma(tw, a2, s2);
-          }
+          source(g, ME - pi, X, qp);
+          if (!(MP::ODD && pi == NPAIR - 1)) source(g, pi - 1, X, qm);
         }
       }
     }

@@ -18,6 +18,13 @@ namespace hope {
 // -------------------------------------------------------------------------------
 // Device setup kernels (FP64), writing tables in the context precision T.
 // -------------------------------------------------------------------------------
+// w1 holds [me+2][K] point weights, then [npair][K] mirror-pair weights: a cell's weights
+// at -xi are its weights at +xi in reverse tap order (the stencil is symmetric about the
+// cell), so with the line folded into sums s_b = v_b + v_{K-1-b} and differences
+// d_b = v_b - v_{K-1-b} (b < H), E = c v_H + sum e_b s_b and O = sum o_b d_b give
+// p(+xi) = E + O and p(-xi) = E - O; e_b, o_b are the even and odd halves of the +xi
+// weights (stored at taps b and K-1-b, the centre weight c at tap H).  Pairs: the edges
+// -1/2, +1/2; the Gauss nodes g and me-1-g; for odd me the middle node alone (o = 0).
 template <typename T>
 __global__ void k_setup_order(int K, int me, T *w1, T *gw, double *nodes_out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -28,6 +35,18 @@ __global__ void k_setup_order(int K, int me, T *w1, T *gw, double *nodes_out) {
     double xi = t == 0 ? -0.5 : (t == 1 ? 0.5 : x[t - 2]);
     cell_avg_weights(K, -H, xi, r);
     for (int b = 0; b < K; ++b) w1[t * K + b] = (T)r[b];
+  }
+  const int npair = 1 + (me + 1) / 2;
+  T *eo = w1 + (me + 2) * K;
+  for (int pi = 0; pi < npair; ++pi) {
+    const bool self = (me & 1) && pi == npair - 1;
+    const double xi = pi == 0 ? 0.5 : x[me - pi];  // the +xi member of the pair
+    cell_avg_weights(K, -H, xi, r);
+    for (int b = 0; b < H; ++b) {
+      eo[pi * K + b] = (T)(0.5 * (r[b] + r[K - 1 - b]));
+      eo[pi * K + K - 1 - b] = self ? T(0) : (T)(0.5 * (r[b] - r[K - 1 - b]));
+    }
+    eo[pi * K + H] = (T)r[H];
   }
   for (int g = 0; g < me; ++g) {
     gw[g] = (T)w[g];
@@ -102,7 +121,7 @@ int setup_order_tables(hope_ctx *ctx, std::vector<double> &nodes, std::vector<do
   const int K = ctx->k, me = ctx->me;
   double *d_nw = nullptr;
   if (cudaMalloc(&d_nw, sizeof(double) * 2 * me) != cudaSuccess) return HOPE_ENOMEM;
-  if (cudaMalloc(&ctx->w1, ctx->esize * (me + 2) * K) != cudaSuccess) return HOPE_ENOMEM;
+  if (cudaMalloc(&ctx->w1, ctx->esize * (me + 2 + 1 + (me + 1) / 2) * K) != cudaSuccess) return HOPE_ENOMEM;
   if (cudaMalloc(&ctx->gw, ctx->esize * me) != cudaSuccess) return HOPE_ENOMEM;
   if (ctx->prec == HOPE_FP64)
     k_setup_order<double><<<1, 1>>>(K, me, (double *)ctx->w1, (double *)ctx->gw, d_nw);
