@@ -574,31 +574,14 @@ __global__ void __launch_bounds__(256)
   gather_adj_item<T, K>(idx, grad, lam_direct, lam_ring, N);
 }
 
-// ---------------------------------------------------------------------------------
-// Transposed ghost operator + Runge-Kutta adjoint combination, per interior cell:
-//   Lt = lam_direct + sum_rows G^T lam_ring
-//   out = a*x + b*y + d*z + c*Lt   (x, y, z may be null)
-// gtp/gtr/gtv: G^T in CSR over interior cells (row index = ghost row, weights as G).
-// ---------------------------------------------------------------------------------
+// Transposed ghost operator and Runge-Kutta combination: out = c (lam_direct + G^T lam_ring)
+// + a x + b y + d z per interior cell (x, y, z may be null).  G^T is a CSR over the cells
+// (gtp), each entry holding the ring position of its ghost row (gtr) and the row's 5
+// weights (gtv); only the band of cells along the panel edges has entries.
 template <typename T>
-__device__ __forceinline__ void ghost_adj_cell(long long cid, const T *__restrict__ lam_direct,
-                                               const T *__restrict__ lam_ring, const int *__restrict__ gtp,
-                                               const int *__restrict__ gtr, const T *__restrict__ gtv,
-                                               const int *__restrict__ gdst, const T *x, const T *y, const T *z,
-                                               T *out, T a, T b, T d, T c, int N, int ne) {
-  const long long ncell = 6LL * N * N;
-  const size_t pe = (size_t)6 * ne * ne;
-  T s0 = lam_direct[cid], s1 = lam_direct[ncell + cid], s2 = lam_direct[2 * ncell + cid];
-  for (int t = gtp[cid]; t < gtp[cid + 1]; ++t) {
-    const int r = gtr[t];
-    const int dpos = gdst[r];
-    const T *w = gtv + (size_t)t * 5;
-    const T g0 = lam_ring[dpos], g1 = lam_ring[pe + dpos], g2 = lam_ring[2 * pe + dpos];
-    s0 += w[0] * g0;
-    s1 += w[1] * g1 + w[3] * g2;
-    s2 += w[2] * g1 + w[4] * g2;
-  }
-  T r3[3] = {s0, s1, s2};
+__device__ __forceinline__ void ghost_adj_finish(long long cid, T s0, T s1, T s2, const T *x, const T *y,
+                                                 const T *z, T *out, T a, T b, T d, T c, long long ncell) {
+  const T r3[3] = {s0, s1, s2};
 #pragma unroll
   for (int v = 0; v < 3; ++v) {
     const long long k = v * ncell + cid;
@@ -610,14 +593,91 @@ __device__ __forceinline__ void ghost_adj_cell(long long cid, const T *__restric
   }
 }
 
+// A cell that no ghost row reads: the combination alone (band cells are left to
+// ghost_adj_band).
+template <typename T>
+__device__ __forceinline__ void ghost_adj_interior(long long cid, const T *__restrict__ lam_direct,
+                                                   const int *__restrict__ gtp, const T *x, const T *y, const T *z,
+                                                   T *out, T a, T b, T d, T c, int N) {
+  if (gtp[cid + 1] > gtp[cid]) return;
+  const long long ncell = 6LL * N * N;
+  ghost_adj_finish(cid, lam_direct[cid], lam_direct[ncell + cid], lam_direct[2 * ncell + cid], x, y, z, out, a, b,
+                   d, c, ncell);
+}
+
+// A band cell, by GADJ_LANES consecutive lanes of one warp (lane `sub` of the group):
+// lane sub adds entries sub, sub + GADJ_LANES, ... in order (GADJ_UNROLL entries' loads in
+// flight), the group sums its lanes by a fixed butterfly and lane 0, which started from the
+// direct part, writes the cell.  `valid` false: the lane only joins the butterfly (every
+// lane of the warp must reach the shuffles).
+constexpr int GADJ_LANES = 8;
+constexpr int GADJ_UNROLL = 4;
+template <typename T>
+__device__ __forceinline__ void ghost_adj_band(bool valid, long long band, int sub, const int *__restrict__ gband,
+                                               const T *__restrict__ lam_direct, const T *__restrict__ lam_ring,
+                                               const int *__restrict__ gtp, const int *__restrict__ gtr,
+                                               const T *__restrict__ gtv, const T *x, const T *y, const T *z, T *out,
+                                               T a, T b, T d, T c, int N, int ne) {
+  const long long ncell = 6LL * N * N;
+  const size_t pe = (size_t)6 * ne * ne;
+  long long cid = 0;
+  T s0 = 0, s1 = 0, s2 = 0;
+  if (valid) {
+    cid = gband[band];
+    if (sub == 0) {
+      s0 = lam_direct[cid];
+      s1 = lam_direct[ncell + cid];
+      s2 = lam_direct[2 * ncell + cid];
+    }
+    const int e0 = gtp[cid], e1 = gtp[cid + 1];
+    constexpr int U = GADJ_UNROLL;
+    for (int t0 = e0 + sub; t0 < e1; t0 += GADJ_LANES * U) {
+      T g[U][3], w[U][5];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int t = t0 + GADJ_LANES * u;
+        const bool ok = t < e1;
+        const int dpos = ok ? gtr[t] : 0;
+        g[u][0] = ok ? lam_ring[dpos] : T(0);
+        g[u][1] = ok ? lam_ring[pe + dpos] : T(0);
+        g[u][2] = ok ? lam_ring[2 * pe + dpos] : T(0);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) w[u][k] = ok ? gtv[(size_t)t * 5 + k] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        s0 += w[u][0] * g[u][0];
+        s1 += w[u][1] * g[u][1] + w[u][3] * g[u][2];
+        s2 += w[u][2] * g[u][1] + w[u][4] * g[u][2];
+      }
+    }
+  }
+#pragma unroll
+  for (int o = GADJ_LANES / 2; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o, GADJ_LANES);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o, GADJ_LANES);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o, GADJ_LANES);
+  }
+  if (valid && sub == 0) ghost_adj_finish(cid, s0, s1, s2, x, y, z, out, a, b, d, c, ncell);
+}
+
+// Threads [0, nlanes) (nlanes: GADJ_LANES per band cell, rounded up to whole warps) take
+// the band cells, the following ones a cell each.
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_ghost_adj(const T *__restrict__ lam_direct, const T *__restrict__ lam_ring, const int *__restrict__ gtp,
-                const int *__restrict__ gtr, const T *__restrict__ gtv, const int *__restrict__ gdst,
-                const T *x, const T *y, const T *z, T *out, T a, T b, T d, T c, int N, int ne) {
-  const long long cid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+                const int *__restrict__ gtr, const T *__restrict__ gtv, const int *__restrict__ gband, long long nband,
+                long long nlanes, const T *x, const T *y, const T *z, T *out, T a, T b, T d, T c, int N, int ne) {
+  const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (it < nlanes) {
+    const long long band = it / GADJ_LANES;
+    ghost_adj_band(band < nband, band, (int)(it % GADJ_LANES), gband, lam_direct, lam_ring, gtp, gtr, gtv, x, y, z,
+                   out, a, b, d, c, N, ne);
+    return;
+  }
+  const long long cid = it - nlanes;
   if (cid >= 6LL * N * N) return;
-  ghost_adj_cell(cid, lam_direct, lam_ring, gtp, gtr, gtv, gdst, x, y, z, out, a, b, d, c, N, ne);
+  ghost_adj_interior(cid, lam_direct, gtp, x, y, z, out, a, b, d, c, N);
 }
 
 }  // namespace hope

@@ -436,7 +436,7 @@ const char *hope_last_error_message(void) { return g_err.c_str(); }
 static void free_grid(Grid &g) {
   if (g.owns_tables) {
     void *tables[] = {g.Xg, g.t1w, g.mx, g.src8, g.gval, g.grow, g.gcol, g.gdst, g.gsym, g.bedge, g.bconv, g.gtp, g.gtr, g.gtv,
-                      g.trow, g.tcol, g.tval};
+                      g.trow, g.tcol, g.tval, g.gband};
     for (void *p : tables)
       if (p) cudaFree(p);
   }
@@ -588,7 +588,7 @@ static int init_impl(int n_members, const int *Ns, int order, int scheme, const 
       g.trow = src.trow; g.tcol = src.tcol; g.tval = src.tval; g.tnnz = src.tnnz;
       g.rows = src.rows; g.nnz = src.nnz;
       g.bedge = src.bedge; g.bconv = src.bconv;
-      g.gtp = src.gtp; g.gtr = src.gtr; g.gtv = src.gtv;
+      g.gtp = src.gtp; g.gtr = src.gtr; g.gtv = src.gtv; g.gband = src.gband; g.nband = src.nband;
       for (int e = 0; e < 12; ++e) g.edges[e] = src.edges[e];
       g.owns_tables = false;
       ctx->grids.push_back(g);
@@ -626,7 +626,9 @@ static int init_impl(int n_members, const int *Ns, int order, int scheme, const 
         TRY(upload(&gr.gval, vals, ctx->esize));
       }
       {
-        // transposed ghost operator for the adjoint: CSR over interior cells
+        // transposed ghost operator for the adjoint: CSR over interior cells, each entry
+        // holding the ring position its ghost row writes; and the list of the cells that
+        // have entries (the band along the panel edges)
         const int ncell = 6 * gr.N * gr.N;
         std::vector<int> tp(ncell + 1, 0), tr(cols.size());
         std::vector<double> tv(vals.size());
@@ -636,11 +638,17 @@ static int init_impl(int n_members, const int *Ns, int order, int scheme, const 
         for (int r = 0; r + 1 < (int)rowptr.size(); ++r)
           for (int t = rowptr[r]; t < rowptr[r + 1]; ++t) {
             int o = fill[cols[t]]++;
-            tr[o] = r;
+            tr[o] = dst[r];
             for (int u = 0; u < 5; ++u) tv[(size_t)5 * o + u] = vals[(size_t)5 * t + u];
           }
+        std::vector<int> band;
+        for (int c = 0; c < ncell; ++c)
+          if (tp[c + 1] > tp[c]) band.push_back(c);
+        gr.nband = (long long)band.size();
+        if (band.empty()) band.push_back(0);
         TRY(upload_int(&gr.gtp, tp));
         TRY(upload_int(&gr.gtr, tr));
+        TRY(upload_int(&gr.gband, band));
         TRY(upload(&gr.gtv, tv, ctx->esize));
       }
       std::vector<double> conv;

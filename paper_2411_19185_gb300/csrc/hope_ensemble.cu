@@ -42,9 +42,10 @@ struct MemberDev {
   // first item of the gather phase (6 ne^2 per member), and the member's block in a step
   // tape (element offset; ghost-ring and edge-point elements of one stage)
   T *lep, *tbuf, *lring, *ldir;
-  const int *gtp, *gtr;
+  const int *gtp, *gtr, *gband;
   const T *gtv;
-  long long b_gather;
+  long long nband;
+  long long b_gather, b_band;  // first item of the gather phase and of the band lanes
   long long tape_off, tape_ge, tape_ee;
 };
 
@@ -128,7 +129,12 @@ constexpr int MEMBER_CACHE = 128;
 
 template <typename T>
 __device__ __forceinline__ long long phase_begin(const MemberDev<T> &m, int phase) {
-  return phase == 0 ? m.b_ghost : phase == 1 ? m.b_tile : phase == 2 ? m.b_flux : phase == 3 ? m.b_cell : m.b_gather;
+  return phase == 0 ? m.b_ghost
+         : phase == 1 ? m.b_tile
+         : phase == 2 ? m.b_flux
+         : phase == 3 ? m.b_cell
+         : phase == 4 ? m.b_gather
+                      : m.b_band;
 }
 
 // Called by every thread of the block between two block-wide barriers.
@@ -277,7 +283,8 @@ struct VjpArgs {
 template <typename T, int K, int NT>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 640 / NT : 1)
     k_vjp_persistent(const MemberDev<T> *__restrict__ mem, int nmem, long long n_ghost, long long n_tile,
-                     long long n_flux, long long n_cell, long long n_gather, VjpArgs<T> va, unsigned *bar,
+                     long long n_flux, long long n_cell, long long n_gather, long long n_band, VjpArgs<T> va,
+                     unsigned *bar,
                      unsigned *status, unsigned inject) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int ME = (K + 1) / 2;
@@ -363,13 +370,26 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 640 / NT : 1)
   }
   if (!grid_sync(bar, status, inject)) return;
   if (stamper) va.stamp[5] = global_ns();
-  // transposed ghost operator and the Runge-Kutta combination, one thread per cell
+  // transposed ghost operator and the Runge-Kutta combination: a thread per cell that no
+  // ghost row reads, then GADJ_LANES lanes per band cell (the lane items padded to whole
+  // warps: every lane of a warp reaches the group's shuffles; a member's lanes start at a
+  // multiple of GADJ_LANES, so no group straddles two members or two warps)
   stage_member_begins(sbeg, mem, nmem, 3);
   for (long long it = (long long)blockIdx.x * NT + threadIdx.x; it < n_cell; it += (long long)gridDim.x * NT) {
     const MemberDev<T> &m = mem[lookup(it, 3)];
     auto off = [&](const T *p) -> const T * { return p ? p + m.off : nullptr; };
-    ghost_adj_cell(it - m.b_cell, m.ldir, m.lring, m.gtp, m.gtr, m.gtv, m.gdst, off(va.x), off(va.y), off(va.z),
-                   va.out + m.off, va.a, va.b, va.d, va.c, m.N, m.ne);
+    ghost_adj_interior(it - m.b_cell, m.ldir, m.gtp, off(va.x), off(va.y), off(va.z), va.out + m.off, va.a, va.b,
+                       va.d, va.c, m.N);
+  }
+  stage_member_begins(sbeg, mem, nmem, 5);
+  const long long n_band_pad = (n_band + 31) / 32 * 32;
+  for (long long it = (long long)blockIdx.x * NT + threadIdx.x; it < n_band_pad; it += (long long)gridDim.x * NT) {
+    const bool valid = it < n_band;
+    const MemberDev<T> &m = mem[lookup(valid ? it : n_band - 1, 5)];
+    const long long local = (valid ? it : n_band - 1) - m.b_band;
+    auto off = [&](const T *p) -> const T * { return p ? p + m.off : nullptr; };
+    ghost_adj_band(valid, local / GADJ_LANES, (int)(local % GADJ_LANES), m.gband, m.ldir, m.lring, m.gtp, m.gtr,
+                   m.gtv, off(va.x), off(va.y), off(va.z), va.out + m.off, va.a, va.b, va.d, va.c, m.N, m.ne);
   }
   if (va.stamp) {
     __syncthreads();
@@ -381,9 +401,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 640 / NT : 1)
 // host side
 // -------------------------------------------------------------------------------------
 template <typename T>
-static int build_members(hope_ctx *ctx, int TX, int TY, std::vector<MemberDev<T>> &out, long long n[5]) {
+static int build_members(hope_ctx *ctx, int TX, int TY, std::vector<MemberDev<T>> &out, long long n[6]) {
   out.clear();
-  long long bg = 0, bt = 0, bf = 0, bc = 0, bgat = 0, tape_acc = 0;
+  long long bg = 0, bt = 0, bf = 0, bc = 0, bgat = 0, bband = 0, tape_acc = 0;
   for (auto &g : ctx->grids) {
     MemberDev<T> m{};
     m.N = g.N;
@@ -418,6 +438,10 @@ static int build_members(hope_ctx *ctx, int TX, int TY, std::vector<MemberDev<T>
     m.gtp = g.gtp;
     m.gtr = g.gtr;
     m.gtv = (const T *)g.gtv;
+    m.gband = g.gband;
+    m.nband = g.nband;
+    m.b_band = bband;
+    bband += g.nband * GADJ_LANES;
     m.tape_ge = 3LL * 6 * g.ne * g.ne;
     m.tape_ee = 4LL * 3 * ctx->me * 6 * g.N * g.N;
     m.tape_off = 2LL * (long long)ctx->total + tape_acc;
@@ -439,6 +463,7 @@ static int build_members(hope_ctx *ctx, int TX, int TY, std::vector<MemberDev<T>
   n[2] = bf;
   n[3] = bc;
   n[4] = bgat;
+  n[5] = bband;
   return HOPE_OK;
 }
 
@@ -579,9 +604,9 @@ static int launch_vjp_any(hope_ctx *ctx, EnsembleState &es, const VjpArgs<T> &va
   const size_t smem = vjp_smem<T, K>(c);
   if (c.nt == 256)
     return launch_coop(ctx, k_vjp_persistent<T, K, 256>, 256, smem, &es.vgrid[es.shape], "persistent stage VJP", st,
-                       mem, nmem, n[0], n[1], n[2], n[3], n[4], va, es.barrier, ctx->status, inject);
+                       mem, nmem, n[0], n[1], n[2], n[3], n[4], n[5], va, es.barrier, ctx->status, inject);
   return launch_coop(ctx, k_vjp_persistent<T, K, 128>, 128, smem, &es.vgrid[es.shape], "persistent stage VJP", st,
-                     mem, nmem, n[0], n[1], n[2], n[3], n[4], va, es.barrier, ctx->status, inject);
+                     mem, nmem, n[0], n[1], n[2], n[3], n[4], n[5], va, es.barrier, ctx->status, inject);
 }
 
 // The member table of the current shape (with the adjoint scratch pointers once they

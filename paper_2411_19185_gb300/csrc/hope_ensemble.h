@@ -15,7 +15,7 @@ struct EnsembleShape {
 
 struct EnsembleState {
   void *members = nullptr;   // MemberDev<T>[n] for the current shape
-  long long items[5] = {};   // ghost items, tiles, edges, cells, extended cells (current shape)
+  long long items[6] = {};   // ghost items, tiles, edges, cells, extended cells, band lanes (current shape)
   EnsembleShape cand[ENS_MAX_SHAPES] = {};
   int ncand = 0;
   int grid[ENS_MAX_SHAPES] = {};   // resident blocks of the forward launch per candidate

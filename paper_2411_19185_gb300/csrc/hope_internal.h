@@ -68,7 +68,9 @@ struct Grid {
   CubeEdge edges[12];
   // transposed ghost operator (adjoint): CSR over interior cells
   int *gtp = nullptr;    // [6*N*N + 1]
-  int *gtr = nullptr;    // [nnz] ghost row
+  int *gtr = nullptr;    // [nnz] ring position of the entry's ghost row (its gdst)
+  int *gband = nullptr;  // [nband] cells that some ghost row reads (ascending)
+  long long nband = 0;
   void *gtv = nullptr;   // [nnz][5]
   // adjoint scratch (allocated on the first VJP call)
   void *lep = nullptr;    // like ep

@@ -359,10 +359,10 @@ inline int stage_vjp_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *lamL, co
                                                                       (T *)g.lring, N);
   }
   {
-    long long cells = 6LL * N * N;
-    k_ghost_adj<T><<<(int)((cells + 255) / 256), 256, 0, st>>>((const T *)g.ldir, (const T *)g.lring, g.gtp, g.gtr,
-                                                               (const T *)g.gtv, g.gdst, x, y, z, out, (T)cb.a,
-                                                               (T)cb.b, (T)cb.d, (T)cb.c, N, ne);
+    const long long cells = 6LL * N * N, nlanes = (g.nband * GADJ_LANES + 31) / 32 * 32;
+    k_ghost_adj<T><<<(int)((nlanes + cells + 255) / 256), 256, 0, st>>>(
+        (const T *)g.ldir, (const T *)g.lring, g.gtp, g.gtr, (const T *)g.gtv, g.gband, g.nband, nlanes, x, y, z, out,
+        (T)cb.a, (T)cb.b, (T)cb.d, (T)cb.c, N, ne);
   }
   HOPE_CUDA_TRY(cudaGetLastError());
   return HOPE_OK;
