@@ -67,7 +67,10 @@ def recon_flops_per_launch(N, K):
     return 6 * per_panel
 
 
-LMARS_FLOPS = 53  # per edge point: LMARS of eqs. 3.30-3.38 (sqrt, division = 1) + quadrature
+# per edge point: LMARS of eqs. 3.30-3.38 as evaluated (phi 2, the shared reciprocal 2,
+# velocities 6, square roots 2, c 2, m* 4, phi* 5, m 1, upwind flux m q_up 3, pressure 5)
+# + quadrature 6; a square root or division counts 1
+LMARS_FLOPS = 38
 
 
 def weno_recon_flops_per_launch(N, K):

@@ -359,12 +359,77 @@ __device__ __forceinline__ void recon_tpp_adj_tile(unsigned char *smem_raw, int 
     }
   }
   __syncthreads();  // the tile and x-pass are dead from here on (phase 2's scratch may alias them)
+  T *tb = tbuf + (size_t)3 * RH * RW * tile_id;
+  if (!ttw) {
+    // phase 2, the transposes of the two passes: the transposed y-pass adds each cell's
+    // point adjoints into the adjoints of its x-pass values (lxs, over the dead x-pass
+    // region), stencil row by stencil row -- in row b the cells of a tile column add into
+    // distinct x-pass rows ty + b, so no two threads update one value; then each location
+    // of the extended region gathers its transposed x-pass terms (positions in order,
+    // taps in order) and is written to the tile buffer
+    T *lxs = xs;  // [3][NPOS][RH][TX]
+    for (int t = threadIdx.x; t < 3 * NPOS * RH * TX; t += blockDim.x) lxs[t] = T(0);
+    __syncthreads();
+#pragma unroll 1
+    for (int b = 0; b < K; ++b) {
+      if (own) {
+#pragma unroll 1
+        for (int t = 0; t < NPOS; ++t) {
+          T gt[3] = {0, 0, 0};
+          if (t < 2) {
+#pragma unroll
+            for (int r = 0; r < ME; ++r) {
+              const T w = w1[(2 + r) * K + b];
+#pragma unroll
+              for (int v = 0; v < 3; ++v) gt[v] = fma(w, lep[((size_t)(t * 3 + v) * ME + r) * pn + cell], gt[v]);
+            }
+          } else {
+            const int g = t - 2;
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+              const T w = w1[side * K + b];
+#pragma unroll
+              for (int v = 0; v < 3; ++v)
+                gt[v] = fma(w, lep[((size_t)((2 + side) * 3 + v) * ME + g) * pn + cell], gt[v]);
+            }
+#pragma unroll
+            for (int h = 0; h < ME; ++h) {
+              const T w = w1[(2 + h) * K + b];
+#pragma unroll
+              for (int v = 0; v < 3; ++v) gt[v] = fma(w, lcq[(v * ME * ME + h * ME + g) * NT + tid], gt[v]);
+            }
+          }
+#pragma unroll
+          for (int v = 0; v < 3; ++v) lxs[((v * NPOS + t) * RH + ty + b) * TX + tx] += gt[v];
+        }
+      }
+      __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < 3 * vh * vw; idx += blockDim.x) {
+      const int v = idx / (vh * vw);
+      const int rem = idx - v * vh * vw;
+      const int r = rem / vw, c = rem - r * vw;
+      T sacc = T(0);
+#pragma unroll
+      for (int t = 0; t < NPOS; ++t) {
+        const T *lrow = lxs + ((v * NPOS + t) * RH + r) * TX;
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+          const int cx = c - a;
+          if (cx >= 0 && cx < vx) sacc = fma(w1[t * K + a], lrow[cx], sacc);
+        }
+      }
+      tb[(v * RH + r) * RW + c] = sacc;
+    }
+    __syncthreads();
+    return;
+  }
   for (int t = threadIdx.x; t < 3 * RH * RW; t += blockDim.x) acc[t] = T(0);
-  // phase 2: per stencil row b, gt[v][t] = sum over points at x-position t of
-  // w1[ty(pt)][b] lam(pt), then the row's gradient g[v][a] = sum_t w1[t][a] gt[v][t]
-  // (plus psi_B's transposed stencil map for the mass variable over a surface); the rows
-  // are added onto the tile's extended region: location (ty + b, tx + a) gains the
-  // gradient of cell (tx, ty), summed over a in order, then over b in order
+  // phase 2 over a surface (psi_B's transposed stencil map is not separable): per stencil
+  // row b, gt[v][t] = sum over points at x-position t of w1[ty(pt)][b] lam(pt), then the
+  // row's gradient g[v][a] = sum_t w1[t][a] gt[v][t] plus psi_B's terms for the mass
+  // variable; the rows are added onto the tile's extended region: location (ty + b,
+  // tx + a) gains the gradient of cell (tx, ty), summed over a in order, then over b in order
 #pragma unroll 1
   for (int b = 0; b < K; ++b) {
     if (own) {
@@ -436,7 +501,6 @@ __device__ __forceinline__ void recon_tpp_adj_tile(unsigned char *smem_raw, int 
     __syncthreads();
   }
   // the tile's extended region [3][RH][RW] (valid part) to its slot of the tile buffer
-  T *tb = tbuf + (size_t)3 * RH * RW * tile_id;
   for (int idx = threadIdx.x; idx < 3 * vh * vw; idx += blockDim.x) {
     const int v = idx / (vh * vw);
     const int rem = idx - v * vh * vw;

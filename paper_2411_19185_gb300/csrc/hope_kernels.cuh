@@ -481,9 +481,11 @@ __device__ __forceinline__ void lmars(const T qL[3], const T qR[3], const T *m5,
   const T ms = T(0.5) * (uL + uR) - (sR - sL);
   const T ph = T(0.5) * (phL + phR - c * (uR - uL));
   const T m = ms * s11;
-  const T am = fabs(m);
+  // 1/2 [m (qL + qR) - |m| (qR - qL)] is the upwind state times m: qL for m >= 0, else qR
+  // (a select instead of the cancelling terms)
+  const bool up = m >= T(0);
 #pragma unroll
-  for (int v = 0; v < 3; ++v) F[v] = T(0.5) * (m * (qL[v] + qR[v]) - am * (qR[v] - qL[v]));
+  for (int v = 0; v < 3; ++v) F[v] = m * (up ? qL[v] : qR[v]);
   const T p2 = ph * ph;
   F[1] += (dir ? pc : pn) * p2;
   F[2] += (dir ? pn : pc) * p2;
@@ -509,9 +511,11 @@ __device__ __forceinline__ void lmars_topo(const T qL[3], const T qR[3], T sL, T
   const T ms = T(0.5) * (uL + uR) - (cR - cL) - (fsR - fsL) * rcp(c + c);
   const T ph = T(0.5) * ((phL + fsL) + (phR + fsR) - c * (uR - uL));
   const T m = ms * s11;
-  const T am = fabs(m);
+  // 1/2 [m (qL + qR) - |m| (qR - qL)] is the upwind state times m: qL for m >= 0, else qR
+  // (a select instead of the cancelling terms)
+  const bool up = m >= T(0);
 #pragma unroll
-  for (int v = 0; v < 3; ++v) F[v] = T(0.5) * (m * (qL[v] + qR[v]) - am * (qR[v] - qL[v]));
+  for (int v = 0; v < 3; ++v) F[v] = m * (up ? qL[v] : qR[v]);
   const T p2 = ph * ph;
   F[1] += (dir ? pc : pn) * p2;
   F[2] += (dir ? pn : pc) * p2;
