@@ -26,9 +26,9 @@ namespace hope {
 // surface enters the interface velocity through -(phi_s,R - phi_s,L)/(2c), whose derivative
 // with respect to c joins the adjoint of c, and the interface value through constants.
 template <typename T, bool TOPO = false>
-__device__ __forceinline__ void lmars_vjp(const T qL[3], const T qR[3], const T *m5, int dir, const T lF[3],
-                                          T lqL[3], T lqR[3], T zL = T(0), T zR = T(0)) {
-  const T isg = m5[0], s11 = m5[1], is11 = m5[2], pn = m5[3], pc = m5[4];
+__device__ __forceinline__ void lmars_vjp(const T qL[3], const T qR[3], const T *m5, size_t mstr, int dir,
+                                          const T lF[3], T lqL[3], T lqR[3], T zL = T(0), T zR = T(0)) {
+  const T isg = m5[0], s11 = m5[mstr], is11 = m5[2 * mstr], pn = m5[3 * mstr], pc = m5[4 * mstr];
   const T qnL = dir ? qL[2] : qL[1], qnR = dir ? qR[2] : qR[1];
   const T phL = qL[0] * isg, phR = qR[0] * isg;
   const T rLR = rcp(qL[0] * qR[0]);
@@ -85,30 +85,32 @@ __device__ __forceinline__ void lmars_vjp(const T qL[3], const T qR[3], const T 
 // One edge item (interior x-edges, interior y-edges, then the 12 cube edges x N cells).
 // TOPO: over a surface, sep[4][me][6][N][N] = sqrtG phi_s at the edge points.
 template <typename T, int ME, bool TOPO = false>
-__device__ __forceinline__ void flux_adj_item(long long idx, const T *__restrict__ ep, const T *__restrict__ mx,
+__device__ __forceinline__ void flux_adj_item(int idx, const T *__restrict__ ep, const T *__restrict__ mx,
                                               const T *__restrict__ gwg, const int *__restrict__ bedge,
                                               const T *__restrict__ bconv, const T *__restrict__ lamL,
                                               T *__restrict__ lep, int N, T inv_dx,
                                               const T *__restrict__ sep = nullptr) {
-  const long long nx = 6LL * N * (N - 1), ny = nx;
+  // 32-bit item arithmetic: 12 N (N + 1) < 2^31 for N <= 8192
+  const int nx = 6 * N * (N - 1), ny = nx;
   const size_t pn = (size_t)6 * N * N;
+  const size_t mstr = metric_plane(N, ME);
   T gw[ME];
 #pragma unroll
   for (int g = 0; g < ME; ++g) gw[g] = gwg[g];
   if (idx < nx + ny) {
     const int dir = idx < nx ? 0 : 1;
-    long long r = dir ? idx - nx : idx;
+    const unsigned r = (unsigned)(dir ? idx - nx : idx);
     int p, a, e;
     if (dir == 0) {
-      e = 1 + (int)(r % (N - 1));
-      long long t = r / (N - 1);
-      a = (int)(t % N);
-      p = (int)(t / N);
+      const unsigned t = r / (unsigned)(N - 1);
+      e = 1 + (int)(r - t * (unsigned)(N - 1));
+      p = (int)(t / (unsigned)N);
+      a = (int)(t - (unsigned)p * N);
     } else {
-      a = (int)(r % N);
-      long long t = r / N;
-      e = 1 + (int)(t % (N - 1));
-      p = (int)(t / (N - 1));
+      const unsigned t = r / (unsigned)N;
+      a = (int)(r - t * (unsigned)N);
+      p = (int)(t / (unsigned)(N - 1));
+      e = 1 + (int)(t - (unsigned)p * (N - 1));
     }
     size_t cl, cr;
     if (dir == 0) {
@@ -131,11 +133,12 @@ __device__ __forceinline__ void flux_adj_item(long long idx, const T *__restrict
         qR[v] = ep[((size_t)(sr * 3 + v) * ME + g) * pn + cr];
         lF[v] = gw[g] * lFbar[v];
       }
+      const T *m5 = mx + (dir ? metric_y(N, ME, e, a, g) : metric_x(N, e, a, g));
       if constexpr (TOPO)
-        lmars_vjp<T, true>(qL, qR, mx + (((size_t)e * N + a) * ME + g) * 5, dir, lF, lqL, lqR,
-                           sep[((size_t)sl * ME + g) * pn + cl], sep[((size_t)sr * ME + g) * pn + cr]);
+        lmars_vjp<T, true>(qL, qR, m5, mstr, dir, lF, lqL, lqR, sep[((size_t)sl * ME + g) * pn + cl],
+                           sep[((size_t)sr * ME + g) * pn + cr]);
       else
-        lmars_vjp(qL, qR, mx + (((size_t)e * N + a) * ME + g) * 5, dir, lF, lqL, lqR);
+        lmars_vjp(qL, qR, m5, mstr, dir, lF, lqL, lqR);
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
         lep[((size_t)(sl * 3 + v) * ME + g) * pn + cl] = lqL[v];
@@ -144,8 +147,8 @@ __device__ __forceinline__ void flux_adj_item(long long idx, const T *__restrict
     }
     return;
   }
-  long long r = idx - nx - ny;
-  const int ce = (int)(r / N), t = (int)(r % N);
+  const int r = idx - nx - ny;
+  const int ce = r / N, t = r - ce * N;
   const int A = bedge[ce * 5 + 0], sA = bedge[ce * 5 + 1], B = bedge[ce * 5 + 2], sB = bedge[ce * 5 + 3],
             flip = bedge[ce * 5 + 4];
   const int tB = flip ? N - 1 - t : t;
@@ -183,7 +186,7 @@ __device__ __forceinline__ void flux_adj_item(long long idx, const T *__restrict
     lF[0] = gw[g] * (lFA[0] + sg * lFB[0]);
     lF[1] = gw[g] * lFA[1] + gw[gB] * sg * (cv[5] * lFB[1] + cv[7] * lFB[2]);
     lF[2] = gw[g] * lFA[2] + gw[gB] * sg * (cv[6] * lFB[1] + cv[8] * lFB[2]);
-    const T *m5 = mx + (((size_t)eA * N + t) * ME + g) * 5;
+    const T *m5 = mx + metric_y(N, ME, eA, t, g);
     T lin[3], lo[3];
     T zin = T(0), zo = T(0);
     if constexpr (TOPO) {
@@ -191,11 +194,11 @@ __device__ __forceinline__ void flux_adj_item(long long idx, const T *__restrict
       zo = cv[0] * sep[((size_t)sB * ME + gB) * pn + cB];
     }
     if (sA & 1) {
-      lmars_vjp<T, TOPO>(qin, qo, m5, dirA, lF, l1, l2, zin, zo);
+      lmars_vjp<T, TOPO>(qin, qo, m5, mstr, dirA, lF, l1, l2, zin, zo);
 #pragma unroll
       for (int v = 0; v < 3; ++v) { lin[v] = l1[v]; lo[v] = l2[v]; }
     } else {
-      lmars_vjp<T, TOPO>(qo, qin, m5, dirA, lF, l1, l2, zo, zin);
+      lmars_vjp<T, TOPO>(qo, qin, m5, mstr, dirA, lF, l1, l2, zo, zin);
 #pragma unroll
       for (int v = 0; v < 3; ++v) { lo[v] = l1[v]; lin[v] = l2[v]; }
     }
@@ -218,7 +221,7 @@ __global__ void __launch_bounds__(256)
                T *__restrict__ lep, int N, T inv_dx, const T *__restrict__ sep = nullptr) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= 12LL * N * (N - 1) + 12LL * N) return;
-  flux_adj_item<T, ME, TOPO>(idx, ep, mx, gwg, bedge, bconv, lamL, lep, N, inv_dx, sep);
+  flux_adj_item<T, ME, TOPO>((int)idx, ep, mx, gwg, bedge, bconv, lamL, lep, N, inv_dx, sep);
 }
 
 // ---------------------------------------------------------------------------------

@@ -473,6 +473,19 @@ static int alloc(void **p, size_t bytes) {
   return HOPE_OK;
 }
 
+// Ghost-operator weights from [entry][5] to five planes [5][entry], so that a warp's load
+// of one weight over 32 consecutive entries reads one contiguous run.
+extern "C++" {
+template <typename V>
+std::vector<V> weight_planes(const std::vector<V> &v) {
+  const size_t n = v.size() / 5;
+  std::vector<V> t(v.size());
+  for (size_t e = 0; e < n; ++e)
+    for (int k = 0; k < 5; ++k) t[k * n + e] = v[e * 5 + k];
+  return t;
+}
+}
+
 static int upload(void **dst, const std::vector<double> &v, int esize) {
   size_t bytes = (size_t)esize * (v.empty() ? 1 : v.size());
   int rc = alloc(dst, bytes);
@@ -585,7 +598,7 @@ static int init_impl(int n_members, const int *Ns, int order, int scheme, const 
       g.Xg = src.Xg; g.t1w = src.t1w; g.mx = src.mx; g.src8 = src.src8;
       g.gval = src.gval; g.grow = src.grow; g.gcol = src.gcol; g.gdst = src.gdst; g.gsym = src.gsym;
       g.ghost_symmetric = src.ghost_symmetric;
-      g.trow = src.trow; g.tcol = src.tcol; g.tval = src.tval; g.tnnz = src.tnnz;
+      g.trow = src.trow; g.tcol = src.tcol; g.tval = src.tval; g.tnnz = src.tnnz; g.gstride = src.gstride;
       g.rows = src.rows; g.nnz = src.nnz;
       g.bedge = src.bedge; g.bconv = src.bconv;
       g.gtp = src.gtp; g.gtr = src.gtr; g.gtv = src.gtv; g.gband = src.gband; g.nband = src.nband;
@@ -611,6 +624,8 @@ static int init_impl(int n_members, const int *Ns, int order, int scheme, const 
       if (ctx->prec == HOPE_FP64) {
         TRY(upload_int(&gr.grow, split.head_ptr));
         TRY(upload_int(&gr.gcol, split.head_col));
+        // FP64 contexts keep [entry][5] (GHOST_PLANES)
+        gr.gstride = (long long)split.head_col.size();
         TRY(upload(&gr.gval, split.head_val, ctx->esize));
         TRY(upload_int(&gr.trow, split.tail_ptr));
         TRY(upload_int(&gr.tcol, split.tail_col));
@@ -623,7 +638,9 @@ static int init_impl(int n_members, const int *Ns, int order, int scheme, const 
         for (size_t e = 0; e < cols.size(); ++e) tagged[e] = cols[e] | (sym.ccode[e] << 28);
         TRY(upload_int(&gr.grow, rowptr));
         TRY(upload_int(&gr.gcol, tagged));
-        TRY(upload(&gr.gval, vals, ctx->esize));
+        // FP32 contexts store five weight planes (GHOST_PLANES)
+        gr.gstride = (long long)cols.size();
+        TRY(upload(&gr.gval, weight_planes(vals), ctx->esize));
       }
       {
         // transposed ghost operator for the adjoint: CSR over interior cells, each entry
@@ -1015,7 +1032,7 @@ int hope_launches_per_stage(hope_t ctx, int *launches) {
   if (!ctx || !launches) return HOPE_EINVAL;
   *launches = ctx->ens ? 1 : 4 * (int)ctx->grids.size();
   if (!ctx->ens)
-    for (auto &g : ctx->grids) *launches += g.tsep ? 1 : 0;
+    for (auto &g : ctx->grids) *launches += (g.tsep && ctx->scheme != HOPE_TPP) ? 1 : 0;  // TPP: psi_B in recon
   return HOPE_OK;
 }
 

@@ -30,6 +30,7 @@ struct MemberDev {
   const T *gval;
   const int *trow, *tcol;
   const float *tval;
+  size_t gs;  // plane stride of gval (FP32 contexts)
   T *gext;
   const T *Xg, *t1w, *src8, *mx, *bconv;
   const int *bedge;
@@ -50,15 +51,112 @@ struct MemberDev {
 };
 
 // Ghost-fill work of the members that share one ghost operator (equal N): one item per
-// (operator row, chunk of up to GHOST_GROUP_CHUNK members), chunks fastest, so the warps
-// that apply one row to the members of a group run back to back on one SM and find the
-// row's weights in L1 instead of streaming them once per member.  The rows use their own
+// (operator row, chunk of up to GHOST_GROUP_CHUNK members), chunks fastest; one warp
+// applies the row to the whole chunk (ghost_row_members), and the chunks of a row run back
+// to back on one SM, where they find the row's weights in L1.  The rows use their own
 // weights (no cube-symmetry transforms: this reuse already keeps the weights on chip).
-constexpr int GHOST_GROUP_CHUNK = 8;
+constexpr int GHOST_GROUP_CHUNK = 4;
 struct GhostGroup {
   long long b_item;  // first item
   int rows, nchunk, first, nmem;  // operator rows; member chunks; members gmem[first ...]
 };
+
+// One ghost row applied at once to the MB members of a chunk (unused slots repeat the
+// first member and are not stored): each lane loads an entry's column and five weights
+// once and applies them to every member, so the weights stay in registers instead of being
+// read again per member.  Every member's sums take the entries in ghost_row's order (lane
+// l: entries b + l, b + l + 32, ...), then the same reduce-scatter, so each member's ring
+// equals ghost_row's bit for bit.  q[m]: member m's state; ring[m]: its ghost ring.
+template <typename T, int MB>
+__device__ __forceinline__ void ghost_row_members(int row, int lane, const T *const (&q)[MB], T *const (&ring)[MB],
+                                                  int nm, const int *__restrict__ grow,
+                                                  const int *__restrict__ gcol, const T *__restrict__ gval,
+                                                  const int *__restrict__ gdst, const int *__restrict__ trow,
+                                                  const int *__restrict__ tcol, const float *__restrict__ tval,
+                                                  int N, int ne, size_t gs) {
+  const size_t pn = (size_t)6 * N * N, pe = (size_t)6 * ne * ne;
+  T s[MB][3];
+#pragma unroll
+  for (int m = 0; m < MB; ++m) s[m][0] = s[m][1] = s[m][2] = T(0);
+  const int b = grow[row], e = grow[row + 1];
+  for (int t = b + lane; t < e; t += 32) {
+    const int cc = gcol[t] & 0x0FFFFFFF;
+    T w[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) w[k] = gval[GHOST_PLANES<T> ? k * gs + t : 5 * (size_t)t + k];
+#pragma unroll
+    for (int m = 0; m < MB; ++m) {
+      const T a0 = q[m][cc], a1 = q[m][pn + cc], a2 = q[m][2 * pn + cc];
+      s[m][0] = fma(w[0], a0, s[m][0]);
+      s[m][1] = fma(w[1], a1, fma(w[2], a2, s[m][1]));
+      s[m][2] = fma(w[3], a1, fma(w[4], a2, s[m][2]));
+    }
+  }
+  if constexpr (sizeof(T) == 8) {
+    if (trow) {
+      // FP64 contexts: the FP32 tail of negligible weights, as ghost_row evaluates it
+      float f[MB][3];
+#pragma unroll
+      for (int m = 0; m < MB; ++m) f[m][0] = f[m][1] = f[m][2] = 0.f;
+      const int tb = trow[row], te = trow[row + 1];
+      for (int t = tb + lane; t < te; t += 32) {
+        const int cc = tcol[t] & 0x0FFFFFFF;
+        float w[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) w[k] = tval[5 * (size_t)t + k];
+#pragma unroll
+        for (int m = 0; m < MB; ++m) {
+          const float a0 = f64_to_f32_trunc(q[m][cc]), a1 = f64_to_f32_trunc(q[m][pn + cc]),
+                      a2 = f64_to_f32_trunc(q[m][2 * pn + cc]);
+          f[m][0] = fmaf(w[0], a0, f[m][0]);
+          f[m][1] = fmaf(w[1], a1, fmaf(w[2], a2, f[m][1]));
+          f[m][2] = fmaf(w[3], a1, fmaf(w[4], a2, f[m][2]));
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < MB; ++m) {
+        s[m][0] += (T)f[m][0];
+        s[m][1] += (T)f[m][1];
+        s[m][2] += (T)f[m][2];
+      }
+    }
+  }
+  const int dst = gdst[row];
+#pragma unroll
+  for (int m = 0; m < MB; ++m)
+    if (m < nm) ghost_reduce_store(lane, s[m][0], s[m][1], s[m][2], ring[m], pe, dst);
+}
+
+// Ghost-fill item `it` (a row of a group's operator and a chunk of its members), for every
+// thread of a warp.
+template <typename T>
+__device__ __forceinline__ void ghost_item(long long it, int lane, const GhostGroup *__restrict__ ggrp, int ngrp,
+                                           const int *__restrict__ gmem, const MemberDev<T> *__restrict__ mem,
+                                           const T *__restrict__ qs) {
+  int lo = 0, hi = ngrp - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (ggrp[mid].b_item <= it)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const GhostGroup &G = ggrp[lo];
+  const long long local = it - G.b_item;
+  const int r = (int)(local / G.nchunk), c = (int)(local - (long long)r * G.nchunk);
+  const int k0 = c * GHOST_GROUP_CHUNK, nm = min(G.nmem - k0, GHOST_GROUP_CHUNK);
+  const T *q[GHOST_GROUP_CHUNK];
+  T *ring[GHOST_GROUP_CHUNK];
+#pragma unroll
+  for (int k = 0; k < GHOST_GROUP_CHUNK; ++k) {
+    const MemberDev<T> &m = mem[gmem[G.first + k0 + (k < nm ? k : 0)]];
+    q[k] = qs + m.off;
+    ring[k] = m.gext;
+  }
+  const MemberDev<T> &m0 = mem[gmem[G.first + k0]];
+  ghost_row_members<T, GHOST_GROUP_CHUNK>(r, lane, q, ring, nm, m0.grow, m0.gcol, m0.gval, m0.gdst, m0.trow, m0.tcol,
+                                          m0.tval, m0.N, m0.ne, m0.gs);
+}
 
 template <typename T>
 struct StageArgs {
@@ -174,11 +272,13 @@ __device__ __forceinline__ int find_member(const MemberDev<T> *mem, int nmem, lo
   return lo;
 }
 
+// FP32: 128-thread blocks are capped at 64 registers (8 resident blocks), 256-thread
+// blocks at 80 (3 resident blocks); the autotuner times both kinds.  FP64 is uncapped.
 template <typename T, int K, int NT>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 1024 / NT : 1)
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT == 128 ? 8 : 3) : 1)
     k_stage_persistent(const MemberDev<T> *__restrict__ mem, int nmem, long long n_ghost, long long n_tile,
                        long long n_flux, long long n_cell, StageArgs<T> sa, unsigned *bar, unsigned *status,
-                       unsigned inject) {
+                       unsigned inject, const __grid_constant__ PairW<T, K> pw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int ME = (K + 1) / 2;
   constexpr int WPB = NT / 32;
@@ -192,25 +292,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 1024 / NT : 1)
   // phase 1: ghost rows, one warp per (row, member chunk) item
   {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (long long it = (long long)blockIdx.x * WPB + warp; it < n_ghost; it += (long long)gridDim.x * WPB) {
-      int lo = 0, hi = sa.ngrp - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (sa.ggrp[mid].b_item <= it)
-          lo = mid;
-        else
-          hi = mid - 1;
-      }
-      const GhostGroup &G = sa.ggrp[lo];
-      const long long local = it - G.b_item;
-      const int r = (int)(local / G.nchunk), c = (int)(local - (long long)r * G.nchunk);
-      const int k1 = min(G.nmem, (c + 1) * GHOST_GROUP_CHUNK);
-      for (int k = c * GHOST_GROUP_CHUNK; k < k1; ++k) {
-        const MemberDev<T> &m = mem[sa.gmem[G.first + k]];
-        ghost_row<T, false>(r, lane, sa.qs + m.off, m.gext, m.grow, m.gcol, m.gval, m.gdst, m.gsym, m.trow, m.tcol, m.tval, m.N,
-                  m.ne);
-      }
-    }
+    for (long long it = (long long)blockIdx.x * WPB + warp; it < n_ghost; it += (long long)gridDim.x * WPB)
+      ghost_item(it, lane, sa.ggrp, sa.ngrp, sa.gmem, mem, sa.qs);
   }
   if (!grid_sync(bar, status, inject)) return;
   if (stamper) sa.stamp[1] = global_ns();
@@ -222,7 +305,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 1024 / NT : 1)
     const int p = local / (m.tiles_x * m.tiles_y);
     const int rem = local - p * m.tiles_x * m.tiles_y;
     const int ty = rem / m.tiles_x, tx = rem - ty * m.tiles_x;
-    recon_tpp_tile<T, K>(smem_raw, p, tx * TX, ty * TY, TX, TY, sa.qs + m.off, m.gext, sa.w1, m.Xg, m.t1w, m.src8, m.ep,
+    recon_tpp_tile<T, K>(smem_raw, p, tx * TX, ty * TY, TX, TY, sa.qs + m.off, m.gext, pw.w, m.Xg, m.t1w, m.src8, m.ep,
                                  m.sb, m.N, m.ne, sa.omega, sa.fc);
   }
   if (!grid_sync(bar, status, inject)) return;
@@ -231,7 +314,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 1024 / NT : 1)
   stage_member_begins(sbeg, mem, nmem, 2);
   for (long long it = (long long)blockIdx.x * NT + threadIdx.x; it < n_flux; it += (long long)gridDim.x * NT) {
     const MemberDev<T> &m = mem[lookup(it, 2)];
-    flux_item<T, ME>(it - m.b_flux, m.ep, m.mx, sa.gw, m.bedge, m.bconv, m.fx, m.fy, m.N, status);
+    flux_item<T, ME>((int)(it - m.b_flux), m.ep, m.mx, sa.gw, m.bedge, m.bconv, m.fx, m.fy, m.N, status);
   }
   if (!grid_sync(bar, status, inject)) return;
   if (stamper) sa.stamp[3] = global_ns();
@@ -240,7 +323,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 1024 / NT : 1)
   for (long long it = (long long)blockIdx.x * NT + threadIdx.x; it < n_cell; it += (long long)gridDim.x * NT) {
     const MemberDev<T> &m = mem[lookup(it, 3)];
     auto off = [&](const T *p) -> const T * { return p ? p + m.off : nullptr; };
-    update_cell(it - m.b_cell, m.fx, m.fy, m.sb, off(sa.q0), sa.qs + m.off, sa.out + m.off, m.N,
+    update_cell((int)(it - m.b_cell), m.fx, m.fy, m.sb, off(sa.q0), sa.qs + m.off, sa.out + m.off, m.N,
                 m.inv_dx, sa.mode, sa.a, sa.b, sa.c, sa.alo, sa.blo, sa.clo, off(sa.q0l), off(sa.qsl),
                 sa.outl ? sa.outl + m.off : nullptr, status);
   }
@@ -284,8 +367,8 @@ template <typename T, int K, int NT>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 640 / NT : 1)
     k_vjp_persistent(const MemberDev<T> *__restrict__ mem, int nmem, long long n_ghost, long long n_tile,
                      long long n_flux, long long n_cell, long long n_gather, long long n_band, VjpArgs<T> va,
-                     unsigned *bar,
-                     unsigned *status, unsigned inject) {
+                     unsigned *bar, unsigned *status, unsigned inject,
+                     const __grid_constant__ PairW<T, K> pw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int ME = (K + 1) / 2;
   constexpr int WPB = NT / 32;
@@ -306,25 +389,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 640 / NT : 1)
   if (!va.have_fwd) {
     // forward recompute: ghost rows (as the forward stage's first phase), then tiles
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (long long it = (long long)blockIdx.x * WPB + warp; it < n_ghost; it += (long long)gridDim.x * WPB) {
-      int lo = 0, hi = va.ngrp - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (va.ggrp[mid].b_item <= it)
-          lo = mid;
-        else
-          hi = mid - 1;
-      }
-      const GhostGroup &G = va.ggrp[lo];
-      const long long local = it - G.b_item;
-      const int r = (int)(local / G.nchunk), c = (int)(local - (long long)r * G.nchunk);
-      const int k1 = min(G.nmem, (c + 1) * GHOST_GROUP_CHUNK);
-      for (int k = c * GHOST_GROUP_CHUNK; k < k1; ++k) {
-        const MemberDev<T> &m = mem[va.gmem[G.first + k]];
-        ghost_row<T, false>(r, lane, va.qs + m.off, m.gext, m.grow, m.gcol, m.gval, m.gdst, m.gsym, m.trow, m.tcol,
-                            m.tval, m.N, m.ne);
-      }
-    }
+    for (long long it = (long long)blockIdx.x * WPB + warp; it < n_ghost; it += (long long)gridDim.x * WPB)
+      ghost_item(it, lane, va.ggrp, va.ngrp, va.gmem, mem, va.qs);
     if (!grid_sync(bar, status, inject)) return;
     if (stamper) va.stamp[1] = global_ns();
     stage_member_begins(sbeg, mem, nmem, 1);
@@ -334,7 +400,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 640 / NT : 1)
       const int p = local / (m.tiles_x * m.tiles_y);
       const int rem = local - p * m.tiles_x * m.tiles_y;
       const int ty = rem / m.tiles_x, tx = rem - ty * m.tiles_x;
-      recon_tpp_tile<T, K>(smem_raw, p, tx * TX, ty * TY, TX, TY, va.qs + m.off, m.gext, va.w1, m.Xg, m.t1w, m.src8,
+      recon_tpp_tile<T, K>(smem_raw, p, tx * TX, ty * TY, TX, TY, va.qs + m.off, m.gext, pw.w, m.Xg, m.t1w, m.src8,
                            m.ep, m.sb, m.N, m.ne, va.omega, va.fc);
     }
     if (!grid_sync(bar, status, inject)) return;
@@ -344,7 +410,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 640 / NT : 1)
   stage_member_begins(sbeg, mem, nmem, 2);
   for (long long it = (long long)blockIdx.x * NT + threadIdx.x; it < n_flux; it += (long long)gridDim.x * NT) {
     const MemberDev<T> &m = mem[lookup(it, 2)];
-    flux_adj_item<T, ME>(it - m.b_flux, ep_of(m), m.mx, va.gw, m.bedge, m.bconv, va.lamL + m.off, m.lep, m.N,
+    flux_adj_item<T, ME>((int)(it - m.b_flux), ep_of(m), m.mx, va.gw, m.bedge, m.bconv, va.lamL + m.off, m.lep, m.N,
                          m.inv_dx);
   }
   if (!grid_sync(bar, status, inject)) return;
@@ -418,6 +484,7 @@ static int build_members(hope_ctx *ctx, int TX, int TY, std::vector<MemberDev<T>
     m.trow = g.trow;
     m.tcol = g.tcol;
     m.tval = g.tval;
+    m.gs = (size_t)g.gstride;
     m.gext = (T *)g.gext;
     m.Xg = (const T *)g.Xg;
     m.t1w = (const T *)g.t1w;
@@ -540,11 +607,12 @@ static int launch_any(hope_ctx *ctx, EnsembleState &es, const StageArgs<T> &sa, 
   es.inject_timeout = 0;
   const int nmem = (int)ctx->grids.size();
   const size_t smem = stage_smem<T, K>(c);
+  const PairW<T, K> pw = pair_weights<T, K>(ctx->w1_host.data());
   if (c.nt == 256)
     return launch_coop(ctx, k_stage_persistent<T, K, 256>, 256, smem, &es.grid[es.shape], "persistent stage", st, mem,
-                       nmem, n[0], n[1], n[2], n[3], sa, es.barrier, ctx->status, inject);
+                       nmem, n[0], n[1], n[2], n[3], sa, es.barrier, ctx->status, inject, pw);
   return launch_coop(ctx, k_stage_persistent<T, K, 128>, 128, smem, &es.grid[es.shape], "persistent stage", st, mem,
-                     nmem, n[0], n[1], n[2], n[3], sa, es.barrier, ctx->status, inject);
+                     nmem, n[0], n[1], n[2], n[3], sa, es.barrier, ctx->status, inject, pw);
 }
 
 template <typename T>
@@ -602,11 +670,12 @@ static int launch_vjp_any(hope_ctx *ctx, EnsembleState &es, const VjpArgs<T> &va
   es.inject_timeout = 0;
   const int nmem = (int)ctx->grids.size();
   const size_t smem = vjp_smem<T, K>(c);
+  const PairW<T, K> pw = pair_weights<T, K>(ctx->w1_host.data());
   if (c.nt == 256)
     return launch_coop(ctx, k_vjp_persistent<T, K, 256>, 256, smem, &es.vgrid[es.shape], "persistent stage VJP", st,
-                       mem, nmem, n[0], n[1], n[2], n[3], n[4], n[5], va, es.barrier, ctx->status, inject);
+                       mem, nmem, n[0], n[1], n[2], n[3], n[4], n[5], va, es.barrier, ctx->status, inject, pw);
   return launch_coop(ctx, k_vjp_persistent<T, K, 128>, 128, smem, &es.vgrid[es.shape], "persistent stage VJP", st,
-                     mem, nmem, n[0], n[1], n[2], n[3], n[4], n[5], va, es.barrier, ctx->status, inject);
+                     mem, nmem, n[0], n[1], n[2], n[3], n[4], n[5], va, es.barrier, ctx->status, inject, pw);
 }
 
 // The member table of the current shape (with the adjoint scratch pointers once they

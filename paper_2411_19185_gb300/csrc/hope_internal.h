@@ -34,9 +34,12 @@ struct Grid {
   // tables (element type = context precision)
   void *Xg = nullptr;    // [N][me]  tan of the cell Gauss-node coordinates
   void *t1w = nullptr;   // [N][N][me][me]  2/delta^2 * W_gh at the cell points
-  void *mx = nullptr;    // [N+1][N][me][5] x-edge metric terms (transposed use for y-edges)
+  void *mx = nullptr;    // edge-point metric terms: [2 orders][5][me][...] (metric_x / metric_y)
   void *src8 = nullptr;  // [N][N][me][me][8] source polynomials times the cell-point weight
-  void *gval = nullptr;  // [nnz][5] ghost operator weights (mass, C00, C01, C10, C11)
+  // ghost operator weights (mass, C00, C01, C10, C11): [5][gstride] planes in FP32 contexts,
+  // [gstride][5] in FP64 contexts (GHOST_PLANES)
+  void *gval = nullptr;
+  long long gstride = 0;  // entries of grow/gcol/gval
   int *grow = nullptr;   // [rows+1]
   int *gcol = nullptr;   // [nnz]  source cell p*N*N + j*N + i
   int *gdst = nullptr;   // [rows] destination p*ne*ne + jj*ne + ii
@@ -47,7 +50,7 @@ struct Grid {
   long long rows = 0, nnz = 0;
   // FP64 contexts: grow/gcol/gval hold the FP64 head of each row, these the FP32 tail
   int *trow = nullptr, *tcol = nullptr;
-  float *tval = nullptr;
+  float *tval = nullptr;  // [tnnz][5]
   long long tnnz = 0;
   int *bedge = nullptr;  // [12][5] CubeEdge
   void *bconv = nullptr; // [12][N][me][9] ratio_BA, C_BA[4], C_AB[4]
@@ -110,6 +113,7 @@ struct hope_ctx {
   // order-dependent tables (element type = precision)
   void *w1 = nullptr;   // [me+2][k] 1-D TPP weights at xi = -1/2, +1/2, g_0..g_{me-1}, then [1+(me+1)/2][k] mirror pairs
   void *gw = nullptr;   // [me] Gauss weights
+  std::vector<unsigned char> w1_host;  // host copy of w1 (context precision), for by-value kernel arguments
   // WENO tables
   void *wsub = nullptr;   // [me+2][l][l]  1-D sub-stencil weights at the same positions
   void *gpm = nullptr;    // [npoc][2][s] normalised gamma+/sigma+, gamma-/sigma-

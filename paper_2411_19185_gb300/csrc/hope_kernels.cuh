@@ -13,6 +13,8 @@
 //   k_update     flux difference + sources (eq. 3.1) fused with the RK stage combination
 #pragma once
 #include <cuda_runtime.h>
+
+#include <cstring>
 #include <stdint.h>
 
 #include "../../include/hope.h"
@@ -109,13 +111,42 @@ __device__ __forceinline__ void sym_apply(int code, float &x, float &y) {
 // symmetry transforms (the weights stay in L2); otherwise the row's own weights (every
 // row holds the same values in its own order) and no transforms.
 constexpr int GHOST_UNROLL = 4;
+
+// Layout of the ghost-operator weights: FP32 contexts store five planes [5][entries]
+// (a warp's load of one weight over 32 consecutive entries reads one contiguous run, which
+// relieves the L1 of the FP32 kernels); FP64 contexts keep [entries][5] for the head and
+// the FP32 tail (their kernels wait on the FP64 pipe, and one base address per entry
+// measured faster there).
+template <typename T>
+constexpr bool GHOST_PLANES = sizeof(T) == 4;
+
+// End of a ghost row: a reduce-scatter of the lanes' partial sums s0, s1, s2.  The
+// half-warps exchange the variables they do not keep (lanes 0-15 keep s0, s1; lanes 16-31
+// keep s2 and a zero), the 8-lane groups likewise, and each group sums its variable: lanes
+// 0, 8, 16 end with the row's s0, s1, s2 (6 additions a lane instead of 15 for three
+// butterflies) and store them at ring position dst of the three variables.
+template <typename T>
+__device__ __forceinline__ void ghost_reduce_store(int lane, T s0, T s1, T s2, T *__restrict__ gext, size_t pe,
+                                                   int dst) {
+  const bool hi16 = lane & 16, hi8 = lane & 8;
+  T ka = hi16 ? s2 : s0, kb = hi16 ? T(0) : s1;
+  const T xa = hi16 ? s0 : s2, xb = hi16 ? s1 : T(0);
+  ka += __shfl_xor_sync(0xffffffffu, xa, 16);
+  kb += __shfl_xor_sync(0xffffffffu, xb, 16);
+  T v = hi8 ? kb : ka;
+  v += __shfl_xor_sync(0xffffffffu, hi8 ? ka : kb, 8);
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((lane & 7) == 0 && lane < 24) gext[(size_t)(lane >> 3) * pe + dst] = v;
+}
+
 template <typename T, bool SYM = true>
 __device__ __forceinline__ void ghost_row(int row, int lane, const T *__restrict__ q, T *__restrict__ gext,
                                           const int *__restrict__ grow, const int *__restrict__ gcol,
                                           const T *__restrict__ gval, const int *__restrict__ gdst,
                                           const int *__restrict__ gsym, const int *__restrict__ trow,
                                           const int *__restrict__ tcol, const float *__restrict__ tval, int N,
-                                          int ne) {
+                                          int ne, size_t gs) {
   size_t pn = (size_t)6 * N * N, pe = (size_t)6 * ne * ne;
   const int info = SYM ? gsym[row] : row;
   const int wrow = info & 0x0FFFFFFF, ocode = info >> 28;
@@ -135,13 +166,14 @@ __device__ __forceinline__ void ghost_row(int row, int lane, const T *__restrict
     for (int u = 0; u < U; ++u) {
       const bool ok = c[u] >= 0;
       const int cc = ok ? (c[u] & 0x0FFFFFFF) : 0;
-      const T *wp = gval + (size_t)(wb + (ok ? t0 + 32 * u - b : 0)) * 5;
+      const size_t we = (size_t)(wb + (ok ? t0 + 32 * u - b : 0));
+      const T *wp = gval + (GHOST_PLANES<T> ? we : 5 * we);
       a[u][0] = q[cc];
       a[u][1] = q[pn + cc];
       a[u][2] = q[2 * pn + cc];
       if (SYM) sym_apply(ok ? c[u] >> 28 : 0, a[u][1], a[u][2]);
 #pragma unroll
-      for (int k = 0; k < 5; ++k) w[u][k] = ok ? wp[k] : T(0);
+      for (int k = 0; k < 5; ++k) w[u][k] = ok ? wp[GHOST_PLANES<T> ? k * gs : k] : T(0);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -185,21 +217,9 @@ __device__ __forceinline__ void ghost_row(int row, int lane, const T *__restrict
     }
   }
   // the row's output transform is a signed permutation (exact), so it is applied to each
-  // lane's partial sums; then a reduce-scatter: the half-warps exchange the variables they
-  // do not keep (lanes 0-15 keep s0, s1; lanes 16-31 keep s2 and a zero), the 8-lane
-  // groups likewise, and each group sums its variable: lanes 0, 8, 16 end with the row's
-  // s0, s1, s2 (6 additions a lane instead of 15 for three butterflies)
+  // lane's partial sums
   if (SYM) sym_apply(ocode, s1, s2);
-  const bool hi16 = lane & 16, hi8 = lane & 8;
-  T ka = hi16 ? s2 : s0, kb = hi16 ? T(0) : s1;
-  const T xa = hi16 ? s0 : s2, xb = hi16 ? s1 : T(0);
-  ka += __shfl_xor_sync(0xffffffffu, xa, 16);
-  kb += __shfl_xor_sync(0xffffffffu, xb, 16);
-  T v = hi8 ? kb : ka;
-  v += __shfl_xor_sync(0xffffffffu, hi8 ? ka : kb, 8);
-#pragma unroll
-  for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((lane & 7) == 0 && lane < 24) gext[(size_t)(lane >> 3) * pe + gdst[row]] = v;
+  ghost_reduce_store(lane, s0, s1, s2, gext, pe, gdst[row]);
 }
 
 template <typename T>
@@ -208,11 +228,11 @@ __global__ void __launch_bounds__(256, 4) k_ghost(const T *__restrict__ q, T *__
                                                const T *__restrict__ gval, const int *__restrict__ gdst,
                                                const int *__restrict__ gsym, const int *__restrict__ trow,
                                                const int *__restrict__ tcol, const float *__restrict__ tval,
-                                               int rows, int N, int ne) {
+                                               int rows, int N, int ne, size_t gs) {
   // grid of resident blocks; warps stride over the rows so every SM gets an equal share
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows; row += nwarps)
-    ghost_row(row, threadIdx.x & 31, q, gext, grow, gcol, gval, gdst, gsym, trow, tcol, tval, N, ne);
+    ghost_row(row, threadIdx.x & 31, q, gext, grow, gcol, gval, gdst, gsym, trow, tcol, tval, N, ne, gs);
 }
 
 // ---------------------------------------------------------------------------------
@@ -305,18 +325,38 @@ __device__ __forceinline__ void mirror_eval(const T *w, const T *x, T &E, T &O) 
   for (int b = H + 2; b < K; ++b) O = fma(w[b], x[b], O);
 }
 
+// Mirror-pair weights of order K passed by value: a kernel parameter lives in the constant
+// bank, so the reconstruction's multiply-adds take the weights as constant operands instead
+// of loading each one from shared memory (the weights depend on k alone).
+template <typename T, int K>
+struct PairW {
+  T w[MirrorPairs<K>::NPAIR * K];
+};
+
+// The mirror-pair rows of a host copy of the 1-D weight table (point rows first).
+template <typename T, int K>
+inline PairW<T, K> pair_weights(const unsigned char *w1_host) {
+  PairW<T, K> pw;
+  memcpy(pw.w, w1_host + sizeof(T) * MirrorPairs<K>::NPOS * K, sizeof(pw.w));
+  return pw;
+}
+
 // One tile of at most TX x TY cells of panel p with its first cell at (i0, j0); called by
 // all threads of a block of at least TX*TY threads; ends with a barrier so the shared
 // memory can be reused for the next tile.  Tiles cut by the panel's edge only load,
 // sweep and evaluate their vx x vy valid cells, and the cell phase packs those cells onto
 // the first vx*vy threads so the idle warps of a ragged tile issue nothing.
-template <typename T, int K>
+// TOPO (bottom topography, single spheres): psi_B of eq. 2.14, an affine map of the cell's
+// k x k depth stencil (weights ttw[2][k*k][cells], constants ttb[2][cells]), is added to the
+// sources from the tile already in shared memory.
+template <typename T, int K, bool TOPO = false>
 __device__ __forceinline__ void recon_tpp_tile(unsigned char *smem_raw, int p, int i0, int j0, const int TX,
                                                const int TY, const T *__restrict__ q, const T *__restrict__ gext,
-                                               const T *__restrict__ w1g, const T *__restrict__ Xg,
+                                               const T *w1p, const T *__restrict__ Xg,
                                                const T *__restrict__ t1w, const T *__restrict__ src8,
                                                T *__restrict__ ep, T *__restrict__ sb, int N, int ne, T omega,
-                                               const FCoef<T> &fc) {
+                                               const FCoef<T> &fc, const T *__restrict__ ttw = nullptr,
+                                               const T *__restrict__ ttb = nullptr) {
   constexpr int H = (K - 1) / 2, ME = (K + 1) / 2, NPOS = ME + 2;
   const int RW = TX + 2 * H, RH = TY + 2 * H;
   const int vx = min(TX, N - i0), vy = min(TY, N - j0);
@@ -325,8 +365,14 @@ __device__ __forceinline__ void recon_tpp_tile(unsigned char *smem_raw, int p, i
   constexpr int NPAIR = MP::NPAIR;
   T *raw = reinterpret_cast<T *>(smem_raw);  // [3][RH][RW]
   T *xs = raw + 3 * RH * RW;                  // [3][NPOS][RH][TX]
-  T *w1 = xs + 3 * NPOS * RH * TX;            // mirror-pair weights [NPAIR][K]
-  for (int t = threadIdx.x; t < NPAIR * K; t += blockDim.x) w1[t] = w1g[NPOS * K + t];
+  // FP32 multiplies by the weights of the parameter space directly; FP64 (bound by its FP64
+  // pipe, where this measured faster) stages them in shared memory first
+  const T *w1 = w1p;
+  if constexpr (sizeof(T) == 8) {
+    T *w1s = xs + 3 * NPOS * RH * TX;  // [NPAIR][K]
+    for (int t = threadIdx.x; t < NPAIR * K; t += blockDim.x) w1s[t] = w1p[t];
+    w1 = w1s;
+  }
   {
     // extended tile of the 3 variables: interior cells from q, ring cells from gext
     const size_t pn = (size_t)6 * N * N, pe = (size_t)6 * ne * ne;
@@ -442,6 +488,23 @@ __device__ __forceinline__ void recon_tpp_tile(unsigned char *smem_raw, int p, i
         }
       }
     }
+    if constexpr (TOPO) {
+      // psi_B from the depth stencil in shared memory (rows ty.., columns tx.. of variable 0)
+      const T *st = raw + ty * RW + tx;
+      T b1 = ttb[cell], b2 = ttb[pn + cell];
+#pragma unroll 1
+      for (int b = 0; b < K; ++b) {
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+          const T v = st[b * RW + a];
+          const size_t c = (size_t)(b * K + a);
+          b1 = fma(ttw[c * pn + cell], v, b1);
+          b2 = fma(ttw[((size_t)K * K + c) * pn + cell], v, b2);
+        }
+      }
+      s1 += b1;
+      s2 += b2;
+    }
     sb[cell] = s1;
     sb[pn + cell] = s2;
   }
@@ -450,25 +513,39 @@ __device__ __forceinline__ void recon_tpp_tile(unsigned char *smem_raw, int p, i
 
 // One block per tile of TX x TY cells (blockIdx.x, blockIdx.y: tile column and row,
 // blockIdx.z: panel); TX*TY <= blockDim.x <= REC_MAX_THREADS.
-template <typename T, int K>
+template <typename T, int K, bool TOPO = false>
 __global__ void __launch_bounds__(REC_MAX_THREADS)
-    k_recon_tpp(const T *__restrict__ q, const T *__restrict__ gext, const T *__restrict__ w1g,
-                const T *__restrict__ Xg, const T *__restrict__ t1w, const T *__restrict__ src8,
-                T *__restrict__ ep, T *__restrict__ sb, int N, int ne, int TX, int TY, T omega, FCoef<T> fc) {
+    k_recon_tpp(const T *__restrict__ q, const T *__restrict__ gext, const T *__restrict__ Xg,
+                const T *__restrict__ t1w, const T *__restrict__ src8, T *__restrict__ ep, T *__restrict__ sb,
+                int N, int ne, int TX, int TY, T omega, FCoef<T> fc, const T *__restrict__ ttw,
+                const T *__restrict__ ttb, const __grid_constant__ PairW<T, K> pw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  recon_tpp_tile<T, K>(smem_raw, blockIdx.z, blockIdx.x * TX, blockIdx.y * TY, TX, TY, q, gext, w1g, Xg, t1w, src8,
-                       ep, sb, N, ne, omega, fc);
+  recon_tpp_tile<T, K, TOPO>(smem_raw, blockIdx.z, blockIdx.x * TX, blockIdx.y * TY, TX, TY, q, gext, pw.w, Xg, t1w,
+                             src8, ep, sb, N, ne, omega, fc, ttw, ttb);
 }
 
 // ---------------------------------------------------------------------------------
-// LMARS flux at one edge point (eqs. 3.31-3.38) from table metric terms:
-// m5 = {1/sqrtG, sqrt(G^nn), 1/sqrt(G^nn), sqrtG G^nn/2, sqrtG G^nc/2} (true metric).
-// dir 0: x-edge (normal momentum var 1), 1: y-edge (var 2).
+// Metric terms of the edge points (k_setup_grid): five planes {1/sqrtG, sqrt(G^nn),
+// 1/sqrt(G^nn), sqrtG G^nn/2, sqrtG G^nc/2} (true metric) of me x N x (N+1) values each,
+// stored twice: with the edge-line index e fastest (x-edges, whose consecutive items take
+// consecutive lines) and then with the position a along the line fastest (y-edges and
+// cube edges, whose consecutive items take consecutive positions), so that each of the
+// five loads of a warp reads one contiguous run.  The planes are metric_plane() apart.
+// ---------------------------------------------------------------------------------
+__host__ __device__ __forceinline__ size_t metric_plane(int N, int ME) { return (size_t)ME * N * (N + 1); }
+__device__ __forceinline__ size_t metric_x(int N, int e, int a, int g) { return ((size_t)g * N + a) * (N + 1) + e; }
+__device__ __forceinline__ size_t metric_y(int N, int ME, int e, int a, int g) {
+  return 5 * metric_plane(N, ME) + ((size_t)g * (N + 1) + e) * N + a;
+}
+
+// ---------------------------------------------------------------------------------
+// LMARS flux at one edge point (eqs. 3.31-3.38) from table metric terms m5[c * mstr],
+// c = 0..4 as listed above.  dir 0: x-edge (normal momentum var 1), 1: y-edge (var 2).
 // ---------------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ void lmars(const T qL[3], const T qR[3], const T *m5, int dir, T F[3],
+__device__ __forceinline__ void lmars(const T qL[3], const T qR[3], const T *m5, size_t mstr, int dir, T F[3],
                                       unsigned *status) {
-  const T isg = m5[0], s11 = m5[1], is11 = m5[2], pn = m5[3], pc = m5[4];
+  const T isg = m5[0], s11 = m5[mstr], is11 = m5[2 * mstr], pn = m5[3 * mstr], pc = m5[4 * mstr];
   const T phL = qL[0] * isg, phR = qR[0] * isg;
   if (!(phL > T(0)) || !(phR > T(0))) atomicOr(status, HOPE_STATUS_NONPHYS_PHI);
   // normal momentum component (selects, not a runtime index, keep the arrays in registers)
@@ -497,9 +574,9 @@ __device__ __forceinline__ void lmars(const T qL[3], const T qR[3], const T *m5,
 // (phi_t,R - phi_t,L)/(2c) = (cR - cL) + (phi_s,R - phi_s,L)/(2c).  With sL = sR = 0 the
 // result is lmars()'s exactly.
 template <typename T>
-__device__ __forceinline__ void lmars_topo(const T qL[3], const T qR[3], T sL, T sR, const T *m5, int dir, T F[3],
-                                           unsigned *status) {
-  const T isg = m5[0], s11 = m5[1], is11 = m5[2], pn = m5[3], pc = m5[4];
+__device__ __forceinline__ void lmars_topo(const T qL[3], const T qR[3], T sL, T sR, const T *m5, size_t mstr,
+                                           int dir, T F[3], unsigned *status) {
+  const T isg = m5[0], s11 = m5[mstr], is11 = m5[2 * mstr], pn = m5[3 * mstr], pc = m5[4 * mstr];
   const T phL = qL[0] * isg, phR = qR[0] * isg;
   if (!(phL > T(0)) || !(phR > T(0))) atomicOr(status, HOPE_STATUS_NONPHYS_PHI);
   const T fsL = sL * isg, fsR = sR * isg;
@@ -527,31 +604,33 @@ __device__ __forceinline__ void lmars_topo(const T qL[3], const T qR[3], T sL, T
 // (same side and node order as ep).
 // ---------------------------------------------------------------------------------
 template <typename T, int ME, bool TOPO = false>
-__device__ __forceinline__ void flux_item(long long idx, const T *__restrict__ ep, const T *__restrict__ mx,
+__device__ __forceinline__ void flux_item(int idx, const T *__restrict__ ep, const T *__restrict__ mx,
                                           const T *__restrict__ gwg, const int *__restrict__ bedge,
                                           const T *__restrict__ bconv, T *__restrict__ fx, T *__restrict__ fy,
                                           int N, unsigned *status, const T *__restrict__ sep = nullptr) {
-  const long long nx = 6LL * N * (N - 1), ny = nx;
+  // 32-bit item arithmetic: 12 N (N + 1) < 2^31 for N <= 8192
+  const int nx = 6 * N * (N - 1), ny = nx;
   const size_t pn = (size_t)6 * N * N;
   const size_t fe = (size_t)6 * N * (N + 1);
+  const size_t ms = metric_plane(N, ME);
   T gw[ME];
 #pragma unroll
   for (int g = 0; g < ME; ++g) gw[g] = gwg[g];
   if (idx < nx + ny) {
     const int dir = idx < nx ? 0 : 1;
-    long long r = dir ? idx - nx : idx;
+    const unsigned r = (unsigned)(dir ? idx - nx : idx);
     // x-edge: (p, j, e=1..N-1), e fastest; y-edge: (p, e=1..N-1, i), i fastest
     int p, a, e;  // a = row j (x) / column i (y)
     if (dir == 0) {
-      e = 1 + (int)(r % (N - 1));
-      long long t = r / (N - 1);
-      a = (int)(t % N);
-      p = (int)(t / N);
+      const unsigned t = r / (unsigned)(N - 1);
+      e = 1 + (int)(r - t * (unsigned)(N - 1));
+      p = (int)(t / (unsigned)N);
+      a = (int)(t - (unsigned)p * N);
     } else {
-      a = (int)(r % N);
-      long long t = r / N;
-      e = 1 + (int)(t % (N - 1));
-      p = (int)(t / (N - 1));
+      const unsigned t = r / (unsigned)N;
+      a = (int)(r - t * (unsigned)N);
+      p = (int)(t / (unsigned)(N - 1));
+      e = 1 + (int)(t - (unsigned)p * (N - 1));
     }
     size_t cl, cr;  // left / right (below / above) cells
     if (dir == 0) {
@@ -571,11 +650,12 @@ __device__ __forceinline__ void flux_item(long long idx, const T *__restrict__ e
         qL[v] = ep[((size_t)(sl * 3 + v) * ME + g) * pn + cl];
         qR[v] = ep[((size_t)(sr * 3 + v) * ME + g) * pn + cr];
       }
+      const T *m5 = mx + (dir ? metric_y(N, ME, e, a, g) : metric_x(N, e, a, g));
       if constexpr (TOPO)
-        lmars_topo(qL, qR, sep[((size_t)sl * ME + g) * pn + cl], sep[((size_t)sr * ME + g) * pn + cr],
-                   mx + (((size_t)e * N + a) * ME + g) * 5, dir, F, status);
+        lmars_topo(qL, qR, sep[((size_t)sl * ME + g) * pn + cl], sep[((size_t)sr * ME + g) * pn + cr], m5, ms, dir,
+                   F, status);
       else
-        lmars(qL, qR, mx + (((size_t)e * N + a) * ME + g) * 5, dir, F, status);
+        lmars(qL, qR, m5, ms, dir, F, status);
 #pragma unroll
       for (int v = 0; v < 3; ++v) acc[v].add(gw[g] * F[v]);
     }
@@ -589,8 +669,8 @@ __device__ __forceinline__ void flux_item(long long idx, const T *__restrict__ e
     return;
   }
   // panel-boundary edge: cube edge ce, cell t along it
-  long long r = idx - nx - ny;
-  const int ce = (int)(r / N), t = (int)(r % N);
+  const int r = idx - nx - ny;
+  const int ce = r / N, t = r - ce * N;
   const int A = bedge[ce * 5 + 0], sA = bedge[ce * 5 + 1], B = bedge[ce * 5 + 2], sB = bedge[ce * 5 + 3],
             flip = bedge[ce * 5 + 4];
   const int tB = flip ? N - 1 - t : t;
@@ -618,19 +698,19 @@ __device__ __forceinline__ void flux_item(long long idx, const T *__restrict__ e
     qo[0] = cv[0] * qb[0];
     qo[1] = cv[1] * qb[1] + cv[2] * qb[2];
     qo[2] = cv[3] * qb[1] + cv[4] * qb[2];
-    const T *m5 = mx + (((size_t)eA * N + t) * ME + g) * 5;
+    const T *m5 = mx + metric_y(N, ME, eA, t, g);
     if constexpr (TOPO) {
       const T sin_ = sep[((size_t)sA * ME + g) * pn + cA];
       const T so = cv[0] * sep[((size_t)sB * ME + gB) * pn + cB];
       if (sA & 1)
-        lmars_topo(qin, qo, sin_, so, m5, dirA, F, status);
+        lmars_topo(qin, qo, sin_, so, m5, ms, dirA, F, status);
       else
-        lmars_topo(qo, qin, so, sin_, m5, dirA, F, status);
+        lmars_topo(qo, qin, so, sin_, m5, ms, dirA, F, status);
     } else {
       if (sA & 1)
-        lmars(qin, qo, m5, dirA, F, status);
+        lmars(qin, qo, m5, ms, dirA, F, status);
       else
-        lmars(qo, qin, m5, dirA, F, status);
+        lmars(qo, qin, m5, ms, dirA, F, status);
     }
 #pragma unroll
     for (int v = 0; v < 3; ++v) accA[v].add(gw[g] * F[v]);
@@ -662,7 +742,7 @@ __global__ void __launch_bounds__(256)
   const long long n = 12LL * N * (N - 1) + 12LL * N;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
        idx += (long long)gridDim.x * blockDim.x)
-    flux_item<T, ME>(idx, ep, mx, gwg, bedge, bconv, fx, fy, N, status);
+    flux_item<T, ME>((int)idx, ep, mx, gwg, bedge, bconv, fx, fy, N, status);
 }
 
 template <typename T, int ME>
@@ -673,7 +753,7 @@ __global__ void __launch_bounds__(256)
   const long long n = 12LL * N * (N - 1) + 12LL * N;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
        idx += (long long)gridDim.x * blockDim.x)
-    flux_item<T, ME, true>(idx, ep, mx, gwg, bedge, bconv, fx, fy, N, status, sep);
+    flux_item<T, ME, true>((int)idx, ep, mx, gwg, bedge, bconv, fx, fy, N, status, sep);
 }
 
 // ---------------------------------------------------------------------------------
@@ -753,14 +833,15 @@ __device__ __forceinline__ T combine(T a, T q0, T b, T qs, T c, T L, T alo, T bl
 }
 
 template <typename T>
-__device__ __forceinline__ void update_cell(long long cid, const T *__restrict__ fx, const T *__restrict__ fy,
+__device__ __forceinline__ void update_cell(int cid, const T *__restrict__ fx, const T *__restrict__ fy,
                                             const T *__restrict__ sb, const T *q0, const T *qs, T *out, int N,
                                             T inv_dx, int mode, T a, T b, T c, T alo, T blo, T clo, const T *q0l,
                                             const T *qsl, T *outl, unsigned *status) {
-  const long long ncell = 6LL * N * N;
-  const int i = (int)(cid % N);
-  const long long pj = cid / N;  // p*N + j
-  const int j = (int)(pj % N), p = (int)(pj / N);
+  // 32-bit cell arithmetic: 3 * 6 N^2 < 2^31 for N <= 8192
+  const int ncell = 6 * N * N;
+  const int pj = (int)((unsigned)cid / (unsigned)N);  // p*N + j
+  const int i = cid - pj * N;
+  const int p = (int)((unsigned)pj / (unsigned)N), j = pj - p * N;
   const size_t fe = (size_t)6 * N * (N + 1);
   bool bad = false;
 #pragma unroll
@@ -776,7 +857,7 @@ __device__ __forceinline__ void update_cell(long long cid, const T *__restrict__
     if (mode == 0) {
       r = L;
     } else {
-      const long long idx = v * ncell + cid;
+      const int idx = v * ncell + cid;
       r = combine(a, q0[idx], b, qs[idx], c, L, alo, blo, clo, q0l, qsl, outl, idx);
     }
     bad |= !isfinite(r);
@@ -790,8 +871,8 @@ __global__ void __launch_bounds__(256)
     k_update(const T *__restrict__ fx, const T *__restrict__ fy, const T *__restrict__ sb,
              const T *q0, const T *qs, T *out, int N, T inv_dx, int mode, T a, T b, T c, T alo, T blo,
              T clo, const T *q0l, const T *qsl, T *outl, unsigned *status) {
-  long long cid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (cid >= 6LL * N * N) return;
+  const int cid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cid >= 6 * N * N) return;
   update_cell(cid, fx, fy, sb, q0, qs, out, N, inv_dx, mode, a, b, c, alo, blo, clo, q0l, qsl, outl, status);
 }
 

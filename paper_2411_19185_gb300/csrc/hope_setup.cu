@@ -101,12 +101,16 @@ __global__ void k_setup_grid(int N, int me, double radius, const double *__restr
       double sg = (1.0 + X * X) * (1.0 + Y * Y) / (d2 * d);
       double g11 = d2 / (1.0 + X * X);  // unit-sphere G^11 (eq. 2.6)
       double s11 = sqrt(g11) / radius;
-      T *o = mx + r * 5;
-      o[0] = (T)(1.0 / sg);
-      o[1] = (T)s11;
-      o[2] = (T)(1.0 / s11);
-      o[3] = (T)(0.5 * (1.0 + Y * Y) / (d * r2));  // sqrtG G^11 / 2 (true metric)
-      o[4] = (T)(0.5 * X * Y / (d * r2));          // sqrtG G^12 / 2
+      const T v[5] = {(T)(1.0 / sg), (T)s11, (T)(1.0 / s11),
+                      (T)(0.5 * (1.0 + Y * Y) / (d * r2)),  // sqrtG G^11 / 2 (true metric)
+                      (T)(0.5 * X * Y / (d * r2))};         // sqrtG G^12 / 2
+      // five planes, stored with e fastest and again with the position j fastest
+      const size_t plane = (size_t)me * N * (N + 1);
+      const size_t ox = ((size_t)g * N + j) * (N + 1) + e, oy = 5 * plane + ((size_t)g * (N + 1) + e) * N + j;
+      for (int c = 0; c < 5; ++c) {
+        mx[c * plane + ox] = v[c];
+        mx[c * plane + oy] = v[c];
+      }
     }
   }
 }
@@ -128,7 +132,9 @@ int setup_order_tables(hope_ctx *ctx, std::vector<double> &nodes, std::vector<do
   else
     k_setup_order<float><<<1, 1>>>(K, me, (float *)ctx->w1, (float *)ctx->gw, d_nw);
   std::vector<double> nw(2 * me);
-  if (cudaMemcpy(nw.data(), d_nw, sizeof(double) * 2 * me, cudaMemcpyDeviceToHost) != cudaSuccess) {
+  ctx->w1_host.resize((size_t)ctx->esize * (me + 2 + 1 + (me + 1) / 2) * K);
+  if (cudaMemcpy(nw.data(), d_nw, sizeof(double) * 2 * me, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(ctx->w1_host.data(), ctx->w1, ctx->w1_host.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
     cudaFree(d_nw);
     return HOPE_ECUDA;
   }
@@ -149,7 +155,7 @@ int setup_grid_tables(hope_ctx *ctx, Grid &gr, const std::vector<double> &nodes,
   size_t es = ctx->esize;
   if (cudaMalloc(&gr.Xg, es * N * me) != cudaSuccess) return HOPE_ENOMEM;
   if (cudaMalloc(&gr.t1w, es * (size_t)N * N * me * me) != cudaSuccess) return HOPE_ENOMEM;
-  if (cudaMalloc(&gr.mx, es * (size_t)(N + 1) * N * me * 5) != cudaSuccess) return HOPE_ENOMEM;
+  if (cudaMalloc(&gr.mx, es * (size_t)(N + 1) * N * me * 10) != cudaSuccess) return HOPE_ENOMEM;
   // the tabulated source polynomials serve only the FP64 TPP reconstruction
   if (ctx->prec == HOPE_FP64 && ctx->scheme == HOPE_TPP &&
       cudaMalloc(&gr.src8, es * (size_t)N * N * me * me * 8) != cudaSuccess)

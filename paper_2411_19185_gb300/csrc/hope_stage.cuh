@@ -199,9 +199,11 @@ inline void launch_recon_tpp(hope_ctx *ctx, Grid &g, const T *qs, cudaStream_t s
   const int N = g.N, TX = g.rtx, TY = g.rty;
   dim3 grid((N + TX - 1) / TX, (N + TY - 1) / TY, 6);
   const int threads = (TX * TY + 31) / 32 * 32;
-  k_recon_tpp<T, K><<<grid, threads, recon_tile_smem_bytes<T, K>(TX, TY), st>>>(
-      qs, (const T *)g.gext, (const T *)ctx->w1, (const T *)g.Xg, (const T *)g.t1w, (const T *)g.src8, (T *)g.ep,
-      (T *)g.sb, N, g.ne, TX, TY, (T)ctx->omega, fcoef<T>(ctx));
+  // over a surface psi_B (eq. 2.14) is added in the tile's epilogue
+  auto kern = g.tsep ? k_recon_tpp<T, K, true> : k_recon_tpp<T, K, false>;
+  kern<<<grid, threads, recon_tile_smem_bytes<T, K>(TX, TY), st>>>(
+      qs, (const T *)g.gext, (const T *)g.Xg, (const T *)g.t1w, (const T *)g.src8, (T *)g.ep, (T *)g.sb, N, g.ne,
+      TX, TY, (T)ctx->omega, fcoef<T>(ctx), (const T *)g.ttw, (const T *)g.ttb, pair_weights<T, K>(ctx->w1_host.data()));
 }
 
 template <typename T, int K>
@@ -218,7 +220,7 @@ inline int stage_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *q0, T *out, 
   if (g.rows > 0) {
     if (!g.ghost_grid) g.ghost_grid = resident_blocks(k_ghost<T>, ctx, g.rows * 32);
     k_ghost<T><<<g.ghost_grid, 256, 0, st>>>(qs, (T *)g.gext, g.grow, g.gcol, (const T *)g.gval, g.gdst, g.gsym,
-                                       g.trow, g.tcol, g.tval, (int)g.rows, N, ne);
+                                       g.trow, g.tcol, g.tval, (int)g.rows, N, ne, (size_t)g.gstride);
   }
   mark(1);
   // reconstruction + sources
@@ -231,8 +233,8 @@ inline int stage_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *q0, T *out, 
     int rc = launch_recon_weno<T, K>(ctx, g, qs, st);
     if (rc) return rc;
   }
-  // bottom topography: psi_B (eq. 2.14) added to the sources
-  if (g.tsep) {
+  // bottom topography: psi_B (eq. 2.14) added to the sources (TPP: in the reconstruction)
+  if (g.tsep && ctx->scheme != HOPE_TPP) {
     const long long cells = 6LL * N * N;
     k_topo_src<T, K><<<(int)((cells + 255) / 256), 256, 0, st>>>(qs, (const T *)g.gext, (const T *)g.ttw,
                                                                  (const T *)g.ttb, (T *)g.sb, N, ne);
@@ -292,7 +294,8 @@ inline int set_smem_attr() {
   int optin = 0, dev = 0;
   HOPE_CUDA_TRY(cudaGetDevice(&dev));
   HOPE_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  HOPE_CUDA_TRY(cudaFuncSetAttribute(k_recon_tpp<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  HOPE_CUDA_TRY(cudaFuncSetAttribute(k_recon_tpp<T, K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  HOPE_CUDA_TRY(cudaFuncSetAttribute(k_recon_tpp<T, K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   HOPE_CUDA_TRY(cudaFuncSetAttribute(k_recon_tpp_adj<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)recon_adj_smem_bytes<T, K>()));
   return weno_set_smem_attr<T, K>();
@@ -319,7 +322,7 @@ inline int stage_vjp_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *lamL, co
   if (g.rows > 0 && !cb.have_fwd) {
     if (!g.ghost_grid) g.ghost_grid = resident_blocks(k_ghost<T>, ctx, g.rows * 32);
     k_ghost<T><<<g.ghost_grid, 256, 0, st>>>(qs, (T *)g.gext, g.grow, g.gcol, (const T *)g.gval, g.gdst, g.gsym, g.trow, g.tcol,
-                                       g.tval, (int)g.rows, N, ne);
+                                       g.tval, (int)g.rows, N, ne, (size_t)g.gstride);
   }
   dim3 grid((N + REC_TX - 1) / REC_TX, (N + REC_TY - 1) / REC_TY, 6);
   if (cb.have_fwd) {

@@ -76,7 +76,8 @@ def test_tendency_over_mountain_fp64(hp, k, N, scheme):
     ref = o.tendency(q)
     assert max(rel_l2(d, ref)) < 1e-11, rel_l2(d, ref)
     assert s.status() == 0
-    assert s.launches_per_stage() == 5
+    # TPP adds psi_B in the reconstruction's epilogue; WENO2D runs a separate source kernel
+    assert s.launches_per_stage() == (4 if scheme == "tpp" else 5)
 
 
 def test_steps_over_mountain_fp64(hp):
