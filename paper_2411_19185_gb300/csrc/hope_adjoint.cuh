@@ -294,10 +294,8 @@ __device__ __forceinline__ void recon_tpp_adj_tile(unsigned char *smem_raw, int 
   for (int t = threadIdx.x; t < NPOS * K; t += blockDim.x) w1[t] = w1g[t];
   {
     const size_t pn = (size_t)6 * N * N, pe = (size_t)6 * ne * ne;
-    for (int idx = threadIdx.x; idx < 3 * vh * vw; idx += blockDim.x) {
-      const int v = idx / (vh * vw);
-      const int rem = idx - v * vh * vw;
-      const int r = rem / vw, c = rem - r * vw;
+    for (BoxWalk bw(vh, vw); bw.v < 3; bw.next()) {
+      const int v = bw.v, r = bw.r, c = bw.c;
       const int i = i0 + c - H, j = j0 + r - H;
       T val = T(0);
       if (i >= 0 && i < N && j >= 0 && j < N)
@@ -308,10 +306,8 @@ __device__ __forceinline__ void recon_tpp_adj_tile(unsigned char *smem_raw, int 
     }
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < 3 * vh * vx; idx += blockDim.x) {
-    const int v = idx / (vh * vx);
-    const int rem = idx - v * vh * vx;
-    const int r = rem / vx, c = rem - r * vx;
+  for (BoxWalk bw(vh, vx); bw.v < 3; bw.next()) {
+    const int v = bw.v, r = bw.r, c = bw.c;
     const T *row = raw + (v * RH + r) * RW + c;
 #pragma unroll
     for (int t = 0; t < NPOS; ++t) {
@@ -408,10 +404,8 @@ __device__ __forceinline__ void recon_tpp_adj_tile(unsigned char *smem_raw, int 
       }
       __syncthreads();
     }
-    for (int idx = threadIdx.x; idx < 3 * vh * vw; idx += blockDim.x) {
-      const int v = idx / (vh * vw);
-      const int rem = idx - v * vh * vw;
-      const int r = rem / vw, c = rem - r * vw;
+    for (BoxWalk bw(vh, vw); bw.v < 3; bw.next()) {
+      const int v = bw.v, r = bw.r, c = bw.c;
       T sacc = T(0);
 #pragma unroll
       for (int t = 0; t < NPOS; ++t) {
@@ -504,10 +498,8 @@ __device__ __forceinline__ void recon_tpp_adj_tile(unsigned char *smem_raw, int 
     __syncthreads();
   }
   // the tile's extended region [3][RH][RW] (valid part) to its slot of the tile buffer
-  for (int idx = threadIdx.x; idx < 3 * vh * vw; idx += blockDim.x) {
-    const int v = idx / (vh * vw);
-    const int rem = idx - v * vh * vw;
-    const int r = rem / vw, c = rem - r * vw;
+  for (BoxWalk bw(vh, vw); bw.v < 3; bw.next()) {
+    const int v = bw.v, r = bw.r, c = bw.c;
     tb[(v * RH + r) * RW + c] = acc[(v * RH + r) * RW + c];
   }
   __syncthreads();

@@ -314,7 +314,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT == 128 ? 8 : 3) : 1)
   stage_member_begins(sbeg, mem, nmem, 2);
   for (long long it = (long long)blockIdx.x * NT + threadIdx.x; it < n_flux; it += (long long)gridDim.x * NT) {
     const MemberDev<T> &m = mem[lookup(it, 2)];
-    flux_item<T, ME>((int)(it - m.b_flux), m.ep, m.mx, sa.gw, m.bedge, m.bconv, m.fx, m.fy, m.N, status);
+    flux_item<T, ME, false, sizeof(T) == 4>((int)(it - m.b_flux), m.ep, m.mx, sa.gw, m.bedge, m.bconv, m.fx, m.fy,
+                                            m.N, status);
   }
   if (!grid_sync(bar, status, inject)) return;
   if (stamper) sa.stamp[3] = global_ns();

@@ -87,6 +87,35 @@ __device__ __forceinline__ float f64_to_f32_trunc(double x) {
   return __uint_as_float(sign | ((unsigned)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
 }
 
+// (v, r, c) of the items threadIdx.x, threadIdx.x + blockDim.x, ... of a 3 x h x w box (c
+// fastest), advanced by carries: the block stride is split once into (sv, sr, sc), and each
+// component carries at most one into the next, so no item costs an integer division.
+struct BoxWalk {
+  int v, r, c, sv, sr, sc, h, w;
+  __device__ __forceinline__ BoxWalk(int h_, int w_) : h(h_), w(w_) {
+    const int hw = h * w, s = (int)threadIdx.x, d = (int)blockDim.x;
+    v = s / hw;
+    r = (s - v * hw) / w;
+    c = s - v * hw - r * w;
+    sv = d / hw;
+    sr = (d - sv * hw) / w;
+    sc = d - sv * hw - sr * w;
+  }
+  __device__ __forceinline__ void next() {
+    c += sc;
+    r += sr;
+    v += sv;
+    if (c >= w) {
+      c -= w;
+      ++r;
+    }
+    if (r >= h) {
+      r -= h;
+      ++v;
+    }
+  }
+};
+
 // Cube symmetry of the ghost operator (eq. 7.12 with the mean-at-tie reading): row r is
 // the image of a panel-0 row under a rotation of the cube, so it reuses that row's weights
 // (gsym[r] low bits) with its own columns.  Momentum components go through 2x2 signed
@@ -376,10 +405,8 @@ __device__ __forceinline__ void recon_tpp_tile(unsigned char *smem_raw, int p, i
   {
     // extended tile of the 3 variables: interior cells from q, ring cells from gext
     const size_t pn = (size_t)6 * N * N, pe = (size_t)6 * ne * ne;
-    for (int idx = threadIdx.x; idx < 3 * vh * vw; idx += blockDim.x) {
-      const int v = idx / (vh * vw);
-      const int rem = idx - v * vh * vw;
-      const int r = rem / vw, c = rem - r * vw;
+    for (BoxWalk bw(vh, vw); bw.v < 3; bw.next()) {
+      const int v = bw.v, r = bw.r, c = bw.c;
       const int i = i0 + c - H, j = j0 + r - H;
       T val = T(0);
       if (i >= 0 && i < N && j >= 0 && j < N)
@@ -392,10 +419,8 @@ __device__ __forceinline__ void recon_tpp_tile(unsigned char *smem_raw, int p, i
   __syncthreads();
   // x-pass: every row of the extended tile, every valid tile column, the NPOS positions
   // as mirror pairs of the folded row
-  for (int idx = threadIdx.x; idx < 3 * vh * vx; idx += blockDim.x) {
-    const int v = idx / (vh * vx);
-    const int rem = idx - v * vh * vx;
-    const int r = rem / vx, c = rem - r * vx;
+  for (BoxWalk bw(vh, vx); bw.v < 3; bw.next()) {
+    const int v = bw.v, r = bw.r, c = bw.c;
     const T *row = raw + (v * RH + r) * RW + c;
     T a[K];
 #pragma unroll
@@ -603,7 +628,96 @@ __device__ __forceinline__ void lmars_topo(const T qL[3], const T qR[3], T sL, T
 // TOPO: bottom topography, with sep[4][me][6][N][N] = sqrtG phi_s at the edge points
 // (same side and node order as ep).
 // ---------------------------------------------------------------------------------
-template <typename T, int ME, bool TOPO = false>
+// Panel-boundary edge item r (cube edge r / N, cell r % N along it): the flux in panel A's
+// frame and its conversion to panel B's (eqs. 3.26-3.29, reading c10).
+template <typename T, int ME, bool TOPO>
+__device__ __forceinline__ void flux_cube_item(int r, const T *__restrict__ ep, const T *__restrict__ mx,
+                                            const T *__restrict__ gwg, const int *__restrict__ bedge,
+                                            const T *__restrict__ bconv, T *__restrict__ fx, T *__restrict__ fy,
+                                            int N, unsigned *status, const T *__restrict__ sep) {
+  const size_t pn = (size_t)6 * N * N;
+  const size_t fe = (size_t)6 * N * (N + 1);
+  const size_t ms = metric_plane(N, ME);
+  T gw[ME];
+#pragma unroll
+  for (int g = 0; g < ME; ++g) gw[g] = gwg[g];
+  const int ce = r / N, t = r - ce * N;
+  const int A = bedge[ce * 5 + 0], sA = bedge[ce * 5 + 1], B = bedge[ce * 5 + 2], sB = bedge[ce * 5 + 3],
+            flip = bedge[ce * 5 + 4];
+  const int tB = flip ? N - 1 - t : t;
+  auto side_cell = [N](int P, int side, int tt) -> size_t {
+    int ci = side == 0 ? 0 : (side == 1 ? N - 1 : tt);
+    int cj = side == 2 ? 0 : (side == 3 ? N - 1 : tt);
+    return ((size_t)P * N + cj) * N + ci;
+  };
+  const size_t cA = side_cell(A, sA, t), cB = side_cell(B, sB, tB);
+  const int dirA = sA >> 1, dirB = sB >> 1;
+  const T sgA = (sA & 1) ? T(1) : T(-1), sgB = (sB & 1) ? T(1) : T(-1);
+  const T sg = -sgA * sgB;
+  const int eA = (sA & 1) ? N : 0;
+  Acc<T> accA[3], accB[3];
+#pragma unroll
+  for (int g = 0; g < ME; ++g) {
+    const int gB = flip ? ME - 1 - g : g;
+    const T *cv = bconv + (((size_t)ce * N + t) * ME + g) * 9;
+    T qin[3], qb[3], qo[3], F[3];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      qin[v] = ep[((size_t)(sA * 3 + v) * ME + g) * pn + cA];
+      qb[v] = ep[((size_t)(sB * 3 + v) * ME + gB) * pn + cB];
+    }
+    qo[0] = cv[0] * qb[0];
+    qo[1] = cv[1] * qb[1] + cv[2] * qb[2];
+    qo[2] = cv[3] * qb[1] + cv[4] * qb[2];
+    const T *m5 = mx + metric_y(N, ME, eA, t, g);
+    if constexpr (TOPO) {
+      const T sin_ = sep[((size_t)sA * ME + g) * pn + cA];
+      const T so = cv[0] * sep[((size_t)sB * ME + gB) * pn + cB];
+      if (sA & 1)
+        lmars_topo(qin, qo, sin_, so, m5, ms, dirA, F, status);
+      else
+        lmars_topo(qo, qin, so, sin_, m5, ms, dirA, F, status);
+    } else {
+      if (sA & 1)
+        lmars(qin, qo, m5, ms, dirA, F, status);
+      else
+        lmars(qo, qin, m5, ms, dirA, F, status);
+    }
+#pragma unroll
+    for (int v = 0; v < 3; ++v) accA[v].add(gw[g] * F[v]);
+    accB[1].add(gw[gB] * sg * (cv[5] * F[1] + cv[6] * F[2]));
+    accB[2].add(gw[gB] * sg * (cv[7] * F[1] + cv[8] * F[2]));
+  }
+  const T fA0 = accA[0].value();
+  const T outA[3] = {fA0, accA[1].value(), accA[2].value()};
+  const T outB[3] = {sg * fA0, accB[1].value(), accB[2].value()};
+  const int eB = (sB & 1) ? N : 0;
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    if (dirA == 0)
+      fx[v * fe + ((size_t)A * N + t) * (N + 1) + eA] = outA[v];
+    else
+      fy[v * fe + ((size_t)A * (N + 1) + eA) * N + t] = outA[v];
+    if (dirB == 0)
+      fx[v * fe + ((size_t)B * N + tB) * (N + 1) + eB] = outB[v];
+    else
+      fy[v * fe + ((size_t)B * (N + 1) + eB) * N + tB] = outB[v];
+  }
+}
+
+// The same item out of line, for the FP32 persistent stage: inlined, its register demand
+// (both panels' sums and the conversions) sets the allocation of the whole edge loop, which
+// then spills under the persistent kernel's register cap.
+template <typename T, int ME, bool TOPO>
+__device__ __noinline__ void flux_cube_item_outline(int r, const T *__restrict__ ep, const T *__restrict__ mx,
+                                                    const T *__restrict__ gwg, const int *__restrict__ bedge,
+                                                    const T *__restrict__ bconv, T *__restrict__ fx,
+                                                    T *__restrict__ fy, int N, unsigned *status,
+                                                    const T *__restrict__ sep) {
+  flux_cube_item<T, ME, TOPO>(r, ep, mx, gwg, bedge, bconv, fx, fy, N, status, sep);
+}
+
+template <typename T, int ME, bool TOPO = false, bool OUTLINE = false>
 __device__ __forceinline__ void flux_item(int idx, const T *__restrict__ ep, const T *__restrict__ mx,
                                           const T *__restrict__ gwg, const int *__restrict__ bedge,
                                           const T *__restrict__ bconv, T *__restrict__ fx, T *__restrict__ fy,
@@ -669,69 +783,10 @@ __device__ __forceinline__ void flux_item(int idx, const T *__restrict__ ep, con
     return;
   }
   // panel-boundary edge: cube edge ce, cell t along it
-  const int r = idx - nx - ny;
-  const int ce = r / N, t = r - ce * N;
-  const int A = bedge[ce * 5 + 0], sA = bedge[ce * 5 + 1], B = bedge[ce * 5 + 2], sB = bedge[ce * 5 + 3],
-            flip = bedge[ce * 5 + 4];
-  const int tB = flip ? N - 1 - t : t;
-  auto side_cell = [N](int P, int side, int tt) -> size_t {
-    int ci = side == 0 ? 0 : (side == 1 ? N - 1 : tt);
-    int cj = side == 2 ? 0 : (side == 3 ? N - 1 : tt);
-    return ((size_t)P * N + cj) * N + ci;
-  };
-  const size_t cA = side_cell(A, sA, t), cB = side_cell(B, sB, tB);
-  const int dirA = sA >> 1, dirB = sB >> 1;
-  const T sgA = (sA & 1) ? T(1) : T(-1), sgB = (sB & 1) ? T(1) : T(-1);
-  const T sg = -sgA * sgB;
-  const int eA = (sA & 1) ? N : 0;
-  Acc<T> accA[3], accB[3];
-#pragma unroll
-  for (int g = 0; g < ME; ++g) {
-    const int gB = flip ? ME - 1 - g : g;
-    const T *cv = bconv + (((size_t)ce * N + t) * ME + g) * 9;
-    T qin[3], qb[3], qo[3], F[3];
-#pragma unroll
-    for (int v = 0; v < 3; ++v) {
-      qin[v] = ep[((size_t)(sA * 3 + v) * ME + g) * pn + cA];
-      qb[v] = ep[((size_t)(sB * 3 + v) * ME + gB) * pn + cB];
-    }
-    qo[0] = cv[0] * qb[0];
-    qo[1] = cv[1] * qb[1] + cv[2] * qb[2];
-    qo[2] = cv[3] * qb[1] + cv[4] * qb[2];
-    const T *m5 = mx + metric_y(N, ME, eA, t, g);
-    if constexpr (TOPO) {
-      const T sin_ = sep[((size_t)sA * ME + g) * pn + cA];
-      const T so = cv[0] * sep[((size_t)sB * ME + gB) * pn + cB];
-      if (sA & 1)
-        lmars_topo(qin, qo, sin_, so, m5, ms, dirA, F, status);
-      else
-        lmars_topo(qo, qin, so, sin_, m5, ms, dirA, F, status);
-    } else {
-      if (sA & 1)
-        lmars(qin, qo, m5, ms, dirA, F, status);
-      else
-        lmars(qo, qin, m5, ms, dirA, F, status);
-    }
-#pragma unroll
-    for (int v = 0; v < 3; ++v) accA[v].add(gw[g] * F[v]);
-    accB[1].add(gw[gB] * sg * (cv[5] * F[1] + cv[6] * F[2]));
-    accB[2].add(gw[gB] * sg * (cv[7] * F[1] + cv[8] * F[2]));
-  }
-  const T fA0 = accA[0].value();
-  const T outA[3] = {fA0, accA[1].value(), accA[2].value()};
-  const T outB[3] = {sg * fA0, accB[1].value(), accB[2].value()};
-  const int eB = (sB & 1) ? N : 0;
-#pragma unroll
-  for (int v = 0; v < 3; ++v) {
-    if (dirA == 0)
-      fx[v * fe + ((size_t)A * N + t) * (N + 1) + eA] = outA[v];
-    else
-      fy[v * fe + ((size_t)A * (N + 1) + eA) * N + t] = outA[v];
-    if (dirB == 0)
-      fx[v * fe + ((size_t)B * N + tB) * (N + 1) + eB] = outB[v];
-    else
-      fy[v * fe + ((size_t)B * (N + 1) + eB) * N + tB] = outB[v];
-  }
+  if constexpr (OUTLINE)
+    flux_cube_item_outline<T, ME, TOPO>(idx - nx - ny, ep, mx, gwg, bedge, bconv, fx, fy, N, status, sep);
+  else
+    flux_cube_item<T, ME, TOPO>(idx - nx - ny, ep, mx, gwg, bedge, bconv, fx, fy, N, status, sep);
 }
 
 template <typename T, int ME>
