@@ -37,7 +37,7 @@ L2_FLUSH_BYTES = 512 << 20
 
 # DRAM bytes per launch of the dominant kernel from the ncu capture summarised in
 # profiles/recon_tpp11_c90_fp64.md (None until captured for the current kernel).
-RECON_TRAFFIC_BYTES = 20395520  # 20.387328 MB read + 8.192 KB written (mirror-pair kernel)
+RECON_TRAFFIC_BYTES = 20399104  # 20.393728 MB read + 5.376 KB written (profiles/recon_tpp11_c90_fp64.md)
 
 
 def recon_flops_per_launch(N, K):
