@@ -168,7 +168,7 @@ struct StageArgs {
   int mode;
   T omega;
   FCoef<T> fc;
-  const T *gw, *w1;
+  const T *gw;
   unsigned long long *stamp;  // profiling: [start, 3 phase ends, end] or null
   const GhostGroup *ggrp;     // ghost-fill groups
   const int *gmem;            // member indices of the groups
@@ -637,7 +637,6 @@ static int stage_persistent_t(hope_ctx *ctx, const void *qs, const void *q0, voi
   sa.omega = (T)ctx->omega;
   for (int t = 0; t < 18; ++t) sa.fc.c[t] = (T)ctx->fcoef[t];
   sa.gw = (const T *)ctx->gw;
-  sa.w1 = (const T *)ctx->w1;
   sa.stamp = ctx->profiling && ctx->prof_stage >= 0 ? es.stamps + 5 * ctx->prof_stage : nullptr;
   sa.ggrp = (const GhostGroup *)es.ggrp;
   sa.gmem = es.gmem;
