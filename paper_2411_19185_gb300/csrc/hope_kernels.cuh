@@ -63,6 +63,13 @@ __device__ __forceinline__ float sqrt_pos<float>(float x) {
   return r;
 }
 
+// Programmatic dependent launch: the four per-grid stage kernels are launched with
+// programmatic stream serialization, so each can be scheduled while its predecessor in the
+// stream drains.  Each calls griddep_wait() before its first memory access; the wait returns
+// once the preceding grid has completed and its writes are visible (at once when the kernel
+// was launched without the attribute), so the kernels see exactly what a serial launch sees.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Coriolis coefficients per panel: sin(latitude about the rotation axis) * delta
 // = c0 + c1 X + c2 Y (eq. 2.5 for an untilted axis: Y, 1 or -1).
 template <typename T>
@@ -258,6 +265,7 @@ __global__ void __launch_bounds__(256, 4) k_ghost(const T *__restrict__ q, T *__
                                                const int *__restrict__ gsym, const int *__restrict__ trow,
                                                const int *__restrict__ tcol, const float *__restrict__ tval,
                                                int rows, int N, int ne, size_t gs) {
+  griddep_wait();
   // grid of resident blocks; warps stride over the rows so every SM gets an equal share
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows; row += nwarps)
@@ -545,6 +553,7 @@ __global__ void __launch_bounds__(REC_MAX_THREADS)
                 int N, int ne, int TX, int TY, T omega, FCoef<T> fc, const T *__restrict__ ttw,
                 const T *__restrict__ ttb, const __grid_constant__ PairW<T, K> pw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  griddep_wait();
   recon_tpp_tile<T, K, TOPO>(smem_raw, blockIdx.z, blockIdx.x * TX, blockIdx.y * TY, TX, TY, q, gext, pw.w, Xg, t1w,
                              src8, ep, sb, N, ne, omega, fc, ttw, ttb);
 }
@@ -794,6 +803,7 @@ __global__ void __launch_bounds__(256)
     k_flux(const T *__restrict__ ep, const T *__restrict__ mx, const T *__restrict__ gwg,
            const int *__restrict__ bedge, const T *__restrict__ bconv, T *__restrict__ fx,
            T *__restrict__ fy, int N, unsigned *status) {
+  griddep_wait();
   const long long n = 12LL * N * (N - 1) + 12LL * N;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
        idx += (long long)gridDim.x * blockDim.x)
@@ -928,6 +938,7 @@ __global__ void __launch_bounds__(256)
              T clo, const T *q0l, const T *qsl, T *outl, unsigned *status) {
   const int cid = blockIdx.x * blockDim.x + threadIdx.x;
   if (cid >= 6 * N * N) return;
+  griddep_wait();
   update_cell(cid, fx, fy, sb, q0, qs, out, N, inv_dx, mode, a, b, c, alo, blo, clo, q0l, qsl, outl, status);
 }
 

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <utility>
 
 #include "hope_adjoint.cuh"
 #include "hope_internal.h"
@@ -190,20 +191,39 @@ int launch_recon_weno_adj(hope_ctx *ctx, Grid &g, const T *qs, const T *lamL, cu
   }
 }
 
+// Launch of a stage kernel with programmatic stream serialization (the kernel calls
+// griddep_wait() before touching memory; see hope_kernels.cuh).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 // -------------------------------------------------------------------------------
 // One stage on one grid: out = L(qs) (mode 0) or a*q0 + b*qs + c*L(qs) (mode 1).
 // -------------------------------------------------------------------------------
 // TPP reconstruction + sources of one grid with the grid's tile shape.
 template <typename T, int K>
-inline void launch_recon_tpp(hope_ctx *ctx, Grid &g, const T *qs, cudaStream_t st) {
+inline cudaError_t launch_recon_tpp(hope_ctx *ctx, Grid &g, const T *qs, cudaStream_t st) {
   const int N = g.N, TX = g.rtx, TY = g.rty;
   dim3 grid((N + TX - 1) / TX, (N + TY - 1) / TY, 6);
   const int threads = (TX * TY + 31) / 32 * 32;
   // over a surface psi_B (eq. 2.14) is added in the tile's epilogue
   auto kern = g.tsep ? k_recon_tpp<T, K, true> : k_recon_tpp<T, K, false>;
-  kern<<<grid, threads, recon_tile_smem_bytes<T, K>(TX, TY), st>>>(
-      qs, (const T *)g.gext, (const T *)g.Xg, (const T *)g.t1w, (const T *)g.src8, (T *)g.ep, (T *)g.sb, N, g.ne,
-      TX, TY, (T)ctx->omega, fcoef<T>(ctx), (const T *)g.ttw, (const T *)g.ttb, pair_weights<T, K>(ctx->w1_host.data()));
+  return launch_pdl(kern, grid, dim3(threads), recon_tile_smem_bytes<T, K>(TX, TY), st, qs, (const T *)g.gext,
+                    (const T *)g.Xg, (const T *)g.t1w, (const T *)g.src8, (T *)g.ep, (T *)g.sb, N, g.ne, TX, TY,
+                    (T)ctx->omega, fcoef<T>(ctx), (const T *)g.ttw, (const T *)g.ttb,
+                    pair_weights<T, K>(ctx->w1_host.data()));
 }
 
 template <typename T, int K>
@@ -219,13 +239,14 @@ inline int stage_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *q0, T *out, 
   // ghost ring
   if (g.rows > 0) {
     if (!g.ghost_grid) g.ghost_grid = resident_blocks(k_ghost<T>, ctx, g.rows * 32);
-    k_ghost<T><<<g.ghost_grid, 256, 0, st>>>(qs, (T *)g.gext, g.grow, g.gcol, (const T *)g.gval, g.gdst, g.gsym,
-                                       g.trow, g.tcol, g.tval, (int)g.rows, N, ne, (size_t)g.gstride);
+    HOPE_CUDA_TRY(launch_pdl(k_ghost<T>, dim3(g.ghost_grid), dim3(256), 0, st, qs, (T *)g.gext, g.grow, g.gcol,
+                             (const T *)g.gval, g.gdst, g.gsym, g.trow, g.tcol, g.tval, (int)g.rows, N, ne,
+                             (size_t)g.gstride));
   }
   mark(1);
   // reconstruction + sources
   if (ctx->scheme == HOPE_TPP) {
-    launch_recon_tpp<T, K>(ctx, g, qs, st);
+    HOPE_CUDA_TRY((launch_recon_tpp<T, K>(ctx, g, qs, st)));
   } else if (ctx->scheme == HOPE_WENO1D) {
     int rc = launch_recon_weno1d<T, K>(ctx, g, qs, st);
     if (rc) return rc;
@@ -249,9 +270,9 @@ inline int stage_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *q0, T *out, 
           ctx->status, (const T *)g.tsep);
     } else {
       if (!g.flux_tpb) balanced_grid(k_flux<T, ME>, items, ctx->nsm, 256, &g.flux_grid, &g.flux_tpb);
-      k_flux<T, ME><<<g.flux_grid, g.flux_tpb, 0, st>>>((const T *)g.ep, (const T *)g.mx, (const T *)ctx->gw,
-                                                        g.bedge, (const T *)g.bconv, (T *)g.fx, (T *)g.fy, N,
-                                                        ctx->status);
+      HOPE_CUDA_TRY(launch_pdl(k_flux<T, ME>, dim3(g.flux_grid), dim3(g.flux_tpb), 0, st, (const T *)g.ep,
+                               (const T *)g.mx, (const T *)ctx->gw, g.bedge, (const T *)g.bconv, (T *)g.fx,
+                               (T *)g.fy, N, ctx->status));
     }
   }
   mark(3);
@@ -259,9 +280,9 @@ inline int stage_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *q0, T *out, 
   {
     long long cells = 6LL * N * N;
     int blocks = (int)((cells + 255) / 256);
-    k_update<T><<<blocks, 256, 0, st>>>((const T *)g.fx, (const T *)g.fy, (const T *)g.sb, q0, qs, out, N,
-                                        (T)(2.0 * N / HOPE_PI), mode, (T)a, (T)b, (T)c, coef_lo<T>(a),
-                                        coef_lo<T>(b), coef_lo<T>(c), q0l, qsl, outl, ctx->status);
+    HOPE_CUDA_TRY(launch_pdl(k_update<T>, dim3(blocks), dim3(256), 0, st, (const T *)g.fx, (const T *)g.fy,
+                             (const T *)g.sb, q0, qs, out, N, (T)(2.0 * N / HOPE_PI), mode, (T)a, (T)b, (T)c,
+                             coef_lo<T>(a), coef_lo<T>(b), coef_lo<T>(c), q0l, qsl, outl, ctx->status));
   }
   mark(4);
   HOPE_CUDA_TRY(cudaGetLastError());
@@ -328,7 +349,7 @@ inline int stage_vjp_grid(hope_ctx *ctx, Grid &g, const T *qs, const T *lamL, co
   if (cb.have_fwd) {
     // ghost ring and edge points restored from a step tape
   } else if (ctx->scheme == HOPE_TPP) {
-    launch_recon_tpp<T, K>(ctx, g, qs, st);
+    HOPE_CUDA_TRY((launch_recon_tpp<T, K>(ctx, g, qs, st)));
   } else {
     int rc = launch_recon_weno<T, K>(ctx, g, qs, st);
     if (rc) return rc;
