@@ -37,7 +37,12 @@ L2_FLUSH_BYTES = 512 << 20
 
 # DRAM bytes per launch of the dominant kernel from the ncu capture summarised in
 # profiles/recon_tpp11_c90_fp64.md (None until captured for the current kernel).
-RECON_TRAFFIC_BYTES = 20399104  # 20.393728 MB read + 5.376 KB written (profiles/recon_tpp11_c90_fp64.md)
+# DRAM bytes of one launch of the reconstruction from the last ncu capture
+# (profiles/recon_tpp11_c90_fp64.md: 20.393728 MB read + 5.376 KB written).  The kernel has
+# changed since (a griddepcontrol wait before its first access, memory accesses unchanged),
+# so the line's `traffic` is null and the figure travels as `traffic_last_capture`.
+RECON_TRAFFIC_BYTES = 20399104
+RECON_TRAFFIC_CURRENT = False
 
 
 def recon_flops_per_launch(N, K):
@@ -911,7 +916,8 @@ def main():
                      "peak_source": "FP64 FMA microbenchmark measured in this run (hope_measure_fma_peak_clock)",
                      "peak_sm_mhz": peak_mhz, "peak_flops_per_sm_clock": peak_fpc,
                      "flops_per_launch": flops, "avg_launch_ms": recon_avg_ms,
-                     "traffic": RECON_TRAFFIC_BYTES,
+                     "traffic": RECON_TRAFFIC_BYTES if RECON_TRAFFIC_CURRENT else None,
+                     "traffic_last_capture": RECON_TRAFFIC_BYTES,
                      # the same outputs as the kernel evaluates them (mirror pairs): fewer
                      # operations, so the measurement plan's count above reads above the
                      # FMA peak while the FP64 pipe itself is about 80 % busy
