@@ -142,12 +142,6 @@ __device__ __forceinline__ void sym_apply(int code, float &x, float &y) {
   y = __int_as_float(s2 ^ (int)((unsigned)((code >> 2) & 1) << 31));
 }
 
-// One ghost row: FP64/FP32 head sum in the context precision, plus (FP64 contexts) the
-// FP32 tail of negligible weights.  SYM: weights of the row's representative with the
-// symmetry transforms (the weights stay in L2); otherwise the row's own weights (every
-// row holds the same values in its own order) and no transforms.
-constexpr int GHOST_UNROLL = 4;
-
 // Layout of the ghost-operator weights: FP32 contexts store five planes [5][entries]
 // (a warp's load of one weight over 32 consecutive entries reads one contiguous run, which
 // relieves the L1 of the FP32 kernels); FP64 contexts keep [entries][5] for the head and
@@ -175,6 +169,12 @@ __device__ __forceinline__ void ghost_reduce_store(int lane, T s0, T s1, T s2, T
   for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if ((lane & 7) == 0 && lane < 24) gext[(size_t)(lane >> 3) * pe + dst] = v;
 }
+
+// One ghost row: FP64/FP32 head sum in the context precision, plus (FP64 contexts) the
+// FP32 tail of negligible weights.  SYM: weights of the row's representative with the
+// symmetry transforms (the weights stay in L2); otherwise the row's own weights (every
+// row holds the same values in its own order) and no transforms.
+constexpr int GHOST_UNROLL = 4;
 
 template <typename T, bool SYM = true>
 __device__ __forceinline__ void ghost_row(int row, int lane, const T *__restrict__ q, T *__restrict__ gext,
