@@ -66,7 +66,9 @@ struct GhostGroup {
 // once and applies them to every member, so the weights stay in registers instead of being
 // read again per member.  Every member's sums take the entries in ghost_row's order (lane
 // l: entries b + l, b + l + 32, ...), then the same reduce-scatter, so each member's ring
-// equals ghost_row's bit for bit.  q[m]: member m's state; ring[m]: its ghost ring.
+// equals ghost_row<T, false>'s bit for bit (ghost_row's padding lanes add zero products,
+// which can only change the sign of a zero sum).  q[m]: member m's state; ring[m]: its
+// ghost ring.
 template <typename T, int MB>
 __device__ __forceinline__ void ghost_row_members(int row, int lane, const T *const (&q)[MB], T *const (&ring)[MB],
                                                   int nm, const int *__restrict__ grow,
